@@ -1,0 +1,195 @@
+/*
+ * cdsdp.h — C ABI of the GB300 chordally decomposed ADMM solver for sparse SDPs
+ * (Zheng, Fantuzzi, Papachristodoulou, Goulart, Wynn, "Chordal decomposition in
+ * operator-splitting methods for sparse semidefinite programs", arXiv 1707.05058).
+ *
+ * Problem (Section 1, Eqs. PrimalSDP / DualSDP):
+ *     min <C, X>  s.t.  <A_i, X> = b_i (i = 0..m-1),  X PSD
+ *     max b^T y   s.t.  Z + sum_i y_i A_i = C,        Z PSD
+ *
+ * Conventions for every function:
+ *   - Return value is a cdsdp_status: negative values are errors, non-negative
+ *     values are solve outcomes.  No function aborts, exits or traps.
+ *   - Matrices are given as 0-based lower-triangle triplets (row >= col); an
+ *     upper-triangle entry is an error (CDSDP_ERR_ARG).  Duplicate triplets are
+ *     summed.  Off-diagonal entries stand for both (row,col) and (col,row).
+ *   - Host arrays passed in are copied; the caller keeps ownership.
+ *   - "d_" arguments are device pointers on the current CUDA device; the
+ *     caller owns that memory.  The library itself never allocates device
+ *     memory: the caller provides the workspace (cdsdp_workspace_bytes).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef CDSDP_H
+#define CDSDP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cdsdp cdsdp; /* opaque; created by cdsdp_setup, released by cdsdp_free */
+
+typedef enum {
+    CDSDP_PRIMAL = 0, /* Algorithm 1: domain-space decomposition (Section 4.1) */
+    CDSDP_DUAL = 1,   /* Algorithm 2: range-space decomposition (Section 4.2)  */
+    CDSDP_HSDE = 2    /* Algorithm 3: homogeneous self-dual embedding (Section 5) */
+} cdsdp_form;
+
+typedef enum {
+    CDSDP_SOLVED = 0,
+    CDSDP_MAX_ITER = 1,
+    CDSDP_PRIMAL_INFEASIBLE = 2, /* HSDE only: certificate u_y / (b^T u_y)        */
+    CDSDP_DUAL_INFEASIBLE = 3,   /* HSDE only: certificate -u_x / (c^T u_x)       */
+    CDSDP_ERR_ARG = -1,          /* malformed argument                            */
+    CDSDP_ERR_RANK = -2,         /* A not full row rank: Cholesky pivot <= 0      */
+    CDSDP_ERR_CUDA = -3,         /* a CUDA runtime call failed                    */
+    CDSDP_ERR_NOMEM = -4,        /* host allocation failed / workspace too small  */
+    CDSDP_ERR_TIMEOUT = -5,      /* a bounded device wait gave up                 */
+    CDSDP_ERR_NUMERIC = -6,      /* NaN or Inf met in the iteration               */
+    CDSDP_ERR_STATE = -7,        /* call out of order (e.g. solve before bind)    */
+    CDSDP_ERR_UNSUPPORTED = -8   /* size beyond what this build handles           */
+} cdsdp_status;
+
+typedef enum {
+    CDSDP_FP32_PROJECTION = 0, /* eigensolve + rebuild in float32, clique state float32,
+                                  affine step, residuals and tau/kappa in float64 */
+    CDSDP_FP64 = 1             /* float64 everywhere */
+} cdsdp_precision;
+
+typedef struct {
+    double eps;            /* stopping tolerance eps_tol (Sections 4.1.4, 4.2.4, 5.2.3) */
+    int max_iter;          /* n_max                                                     */
+    double rho;            /* ADMM penalty (Algorithms 1, 2); unused by HSDE            */
+    int precision;         /* cdsdp_precision                                           */
+    int use_graph;         /* 1: whole solve is one CUDA graph with a device-side while
+                              loop; 0: one launch per phase, host polls every check_every */
+    int check_every;       /* host poll period when use_graph = 0                       */
+    int jacobi_max_sweeps; /* cap on Jacobi sweeps per projection                       */
+    int warm_start;        /* reserved, must be 0                                        */
+    int profile;           /* 1: run the use_graph = 0 path and bracket every projection
+                              launch with CUDA events on `stream` (see cdsdp_profile)      */
+} cdsdp_opts;
+
+typedef struct {
+    int n, m;
+    int p;                   /* number of maximal cliques                           */
+    int max_clique;          /* largest |C_k|                                        */
+    long long nnz_pattern;   /* lower-triangle entries of the extended pattern E*   */
+    long long n_d_lower;     /* sum_k |C_k|(|C_k|+1)/2                               */
+    long long nnz_A;         /* stored nonzeros of A after merging duplicates        */
+    long long n_fill;        /* fill edges added by the chordal extension            */
+    int chordal;             /* 1 if the aggregate pattern was already chordal       */
+    int diag_factor;         /* 1 if A D^-1 A^T is diagonal (e.g. MaxCut, Section 4.1.2) */
+    long long upload_bytes;  /* size of the one host-to-device copy cdsdp_bind makes   */
+} cdsdp_info_t;
+
+/* Fill `o` with defaults: eps 1e-4, max_iter 2000, rho 1, FP32 projection,
+ * graph on, check_every 50, 30 Jacobi sweeps, no profiling. */
+void cdsdp_default_opts(cdsdp_opts* o);
+
+/* Data preprocessing of Algorithms 1-3 (host only, no GPU call):
+ * aggregate sparsity pattern E* of C, every A_i and the optional extra
+ * edges P (Section 2.1, Eq. AggregateSparsity), chordal extension and maximal
+ * cliques (Section 6.1.1; maximum cardinality search when already chordal,
+ * minimum-degree elimination otherwise; cliques sorted lexicographically),
+ * the entry selectors H_k (Section 4), D = sum_k H_k^T H_k, and the cached
+ * inverses of A D^-1 A^T (Eq. ADMMprimalFatorization) and of
+ * I + A (I + D/2)^-1 A^T (Eq. HSDEFactorizationFinal), with
+ * zeta_hat (Proposition 2).
+ *   n, m        matrix order and number of constraints (n >= 1, m >= 1)
+ *   A_*         nnzA triplets (constraint, row, col, value)
+ *   b           m values
+ *   C_*         nnzC triplets
+ *   P_*         nnzP extra pattern edges (may be 0 / NULL)
+ *   out         receives the handle
+ * Errors: CDSDP_ERR_ARG (bad index, upper entry, non-finite value),
+ *         CDSDP_ERR_RANK (A D^-1 A^T not positive definite), CDSDP_ERR_NOMEM. */
+int cdsdp_setup(int n, int m,
+                long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
+                const double* b,
+                long long nnzC, const int* C_row, const int* C_col, const double* C_val,
+                long long nnzP, const int* P_row, const int* P_col,
+                cdsdp** out);
+
+int cdsdp_info(const cdsdp* h, cdsdp_info_t* info);
+
+/* Maximal cliques in canonical order: offsets[p+1], vertices[offsets[p]],
+ * each clique ascending (Section 2.1, natural ordering). */
+int cdsdp_cliques(const cdsdp* h, int* offsets, int* vertices);
+
+/* Extended pattern E*, lower triangle incl. diagonal, column-major order:
+ * rows[nnz_pattern], cols[nnz_pattern].  X and Z are returned in this order. */
+int cdsdp_pattern(const cdsdp* h, int* rows, int* cols);
+
+/* Device workspace the caller must provide for solves of up to max_iter
+ * iterations (history included). */
+int cdsdp_workspace_bytes(const cdsdp* h, int max_iter, size_t* bytes);
+
+/* Attach a caller-owned device workspace (>= cdsdp_workspace_bytes, 256-byte
+ * aligned) and upload the preprocessed problem into it with one host-to-device
+ * copy on `stream`.  The workspace must stay allocated until cdsdp_free or the
+ * next cdsdp_bind.  Errors: CDSDP_ERR_NOMEM (too small), CDSDP_ERR_ARG
+ * (misaligned), CDSDP_ERR_CUDA. */
+int cdsdp_bind(cdsdp* h, void* d_workspace, size_t bytes, int max_iter, void* stream);
+
+/* Run Algorithm 1, 2 or 3 on the bound workspace from zero initial guesses
+ * (HSDE: u = (0,..,0,1), v = (0,..,0,1)) until the stopping test of the form
+ * holds or max_iter iterations.  Blocks until the solve is done.
+ * Host outputs (each may be NULL):
+ *   X     [nnz_pattern] primal solution on E* (pattern order)
+ *   y     [m]           dual multipliers
+ *   Z     [nnz_pattern] dual slack on E*
+ *   hist  [iters x 8]   per-iteration residuals, row-major:
+ *         primal/dual: eps_c, eps_lambda, 0, 0, <C,X>, b^T y, 0, 0
+ *         HSDE tau>0:  eps_p, eps_d, eps_g, eps_c, <C,X>, b^T y, tau, kappa
+ *         HSDE tau=0:  ||A^T u_y + H^T v_z||, ||A u_x||, b^T u_y, c^T u_x, 0, 0, tau, kappa
+ *   iters number of iterations run
+ *   cert  HSDE certificate: [m] (primal infeasible) or [nnz_pattern] (dual
+ *         infeasible); must hold max(m, nnz_pattern) doubles
+ * Returns the outcome (CDSDP_SOLVED, CDSDP_MAX_ITER, CDSDP_*_INFEASIBLE) or
+ * an error (CDSDP_ERR_STATE if no workspace is bound, CDSDP_ERR_NUMERIC on
+ * NaN/Inf, CDSDP_ERR_CUDA). */
+int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream,
+                double* X, double* y, double* Z, double* hist, int* iters, double* cert);
+
+/* Kernel timings of the last solve run with opts.profile = 1:
+ *   proj_ms       summed duration of the projection launches (CUDA events on
+ *                 the solve's stream), over the iterations actually run
+ *   proj_launches number of projection launches summed
+ *   iter_ms       summed duration of whole iterations
+ * Errors: CDSDP_ERR_STATE when the last solve was not profiled. */
+int cdsdp_profile(const cdsdp* h, double* proj_ms, int* proj_launches, double* iter_ms);
+
+/* Copy the last solve's results again (same meaning as in cdsdp_solve). */
+int cdsdp_results(cdsdp* h, void* stream, double* X, double* y, double* Z, double* hist, double* cert);
+
+int cdsdp_free(cdsdp* h);
+
+const char* cdsdp_strerror(int status);
+
+/* Standalone batched PSD projection P(W) = V max(Lambda, 0) V^T
+ * (Section 4.1.2, Eq. XkUpdate) of p symmetric blocks, one warp per block
+ * (block size <= 32) or one thread block per block (33..128).
+ *   d_off[p+1]    offsets of each block's lower-packed storage (int32)
+ *   d_size[p]     block orders s_k (1..128)
+ *   d_W           lower-packed inputs, column-major within a block:
+ *                 entry (a, b), a >= b, at d_off[k] + b*(2 s_k - b + 1)/2 + (a - b)
+ *   d_X           lower-packed outputs, same layout (may alias d_W)
+ *   d_eig         optional [sum_k s_k] eigenvalues (block k at its vertex
+ *                 offset d_voff[k]); NULL to skip
+ *   d_V           optional [sum_k s_k^2] eigenvectors, column-major per block
+ *                 at d_vvoff[k]; NULL to skip
+ *   d_voff/d_vvoff offsets for d_eig / d_V (int32, p entries); NULL if unused
+ *   precision     CDSDP_FP32_PROJECTION: float data; CDSDP_FP64: double data
+ * Errors: CDSDP_ERR_ARG (p < 0, size out of range), CDSDP_ERR_CUDA. */
+int cdsdp_psd_project(int p, const int* d_off, const int* d_size, int max_size,
+                      const void* d_W, void* d_X, void* d_eig, const int* d_voff, void* d_V, const int* d_vvoff,
+                      int precision, int max_sweeps, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDSDP_H */

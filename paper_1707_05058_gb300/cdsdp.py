@@ -1,0 +1,233 @@
+"""ctypes binding of the C ABI in include/cdsdp.h (argument marshalling only).
+
+Every step of the solver runs inside libcdsdp.so: the host preprocessing in
+its C++ setup code and every iteration in its CUDA kernels.  This module only
+converts arrays, allocates the device workspace through PyTorch and passes
+pointers and the current CUDA stream.  Importing it fails loudly when the
+library has not been built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcdsdp.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libcdsdp.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+PRIMAL, DUAL, HSDE = 0, 1, 2
+FORMS = {"primal": PRIMAL, "dual": DUAL, "hsde": HSDE}
+FP32, FP64 = 0, 1
+SOLVED, MAX_ITER, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE = 0, 1, 2, 3
+
+_i32p = ctypes.POINTER(ctypes.c_int)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_ll = ctypes.c_longlong
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("max_iter", ctypes.c_int), ("rho", ctypes.c_double),
+                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("jacobi_max_sweeps", ctypes.c_int), ("warm_start", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int), ("max_clique", ctypes.c_int),
+                ("nnz_pattern", _ll), ("n_d_lower", _ll), ("nnz_A", _ll), ("n_fill", _ll),
+                ("chordal", ctypes.c_int), ("diag_factor", ctypes.c_int), ("upload_bytes", _ll)]
+
+
+_lib.cdsdp_default_opts.argtypes = [ctypes.POINTER(Opts)]
+_lib.cdsdp_default_opts.restype = None
+_lib.cdsdp_setup.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32p, _f64p, _f64p,
+                             _ll, _i32p, _i32p, _f64p, _ll, _i32p, _i32p, ctypes.POINTER(_vp)]
+_lib.cdsdp_info.argtypes = [_vp, ctypes.POINTER(Info)]
+_lib.cdsdp_cliques.argtypes = [_vp, _i32p, _i32p]
+_lib.cdsdp_pattern.argtypes = [_vp, _i32p, _i32p]
+_lib.cdsdp_workspace_bytes.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+_lib.cdsdp_bind.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.c_int, _vp]
+_lib.cdsdp_solve.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, _f64p, _f64p, _f64p, _f64p, _i32p, _f64p]
+_lib.cdsdp_results.argtypes = [_vp, _vp, _f64p, _f64p, _f64p, _f64p, _f64p]
+_lib.cdsdp_free.argtypes = [_vp]
+_lib.cdsdp_profile.argtypes = [_vp, _f64p, _i32p, _f64p]
+_lib.cdsdp_strerror.argtypes = [ctypes.c_int]
+_lib.cdsdp_strerror.restype = ctypes.c_char_p
+_lib.cdsdp_psd_project.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
+                                   ctypes.c_int, ctypes.c_int, _vp]
+
+EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", "cdsdp_pattern",
+            "cdsdp_workspace_bytes", "cdsdp_bind", "cdsdp_solve", "cdsdp_results", "cdsdp_free",
+            "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile"]
+
+
+class CdsdpError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+        self.status = status
+
+
+def strerror(status: int) -> str:
+    return _lib.cdsdp_strerror(int(status)).decode()
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _lib.cdsdp_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp32": FP32, "fp64": FP64}[v]
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct)) if a is not None and a.size else None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Problem:
+    """One SDP after the data preprocessing of Algorithms 1-3 (host only)."""
+
+    def __init__(self, prob):
+        (A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col) = prob.arrays()
+        self._keep = (A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col)
+        h = _vp()
+        st = _lib.cdsdp_setup(int(prob.n), int(prob.m), A_con.size, _ptr(A_con, ctypes.c_int), _ptr(A_row, ctypes.c_int),
+                              _ptr(A_col, ctypes.c_int), _ptr(A_val, ctypes.c_double), _ptr(b, ctypes.c_double),
+                              C_row.size, _ptr(C_row, ctypes.c_int), _ptr(C_col, ctypes.c_int),
+                              _ptr(C_val, ctypes.c_double), P_row.size, _ptr(P_row, ctypes.c_int),
+                              _ptr(P_col, ctypes.c_int), ctypes.byref(h))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_setup")
+        self._h = h
+        self.workspace = None
+        self.max_iter = 0
+        inf = Info()
+        _lib.cdsdp_info(self._h, ctypes.byref(inf))
+        self.info = {f: getattr(inf, f) for f, _ in Info._fields_}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.cdsdp_free(h)
+            self._h = None
+
+    def cliques(self):
+        p = self.info["p"]
+        off = np.zeros(p + 1, np.int32)
+        tot = int(self.info["n_d_lower"])  # upper bound on the vertex count
+        vert = np.zeros(max(tot, 1), np.int32)
+        _lib.cdsdp_cliques(self._h, _ptr(off, ctypes.c_int), _ptr(vert, ctypes.c_int))
+        return off, vert[:off[-1]]
+
+    def clique_list(self):
+        off, vert = self.cliques()
+        return [tuple(int(v) for v in vert[off[k]:off[k + 1]]) for k in range(len(off) - 1)]
+
+    def pattern(self):
+        nz = int(self.info["nnz_pattern"])
+        r = np.zeros(nz, np.int32)
+        c = np.zeros(nz, np.int32)
+        _lib.cdsdp_pattern(self._h, _ptr(r, ctypes.c_int), _ptr(c, ctypes.c_int))
+        return r, c
+
+    def workspace_bytes(self, max_iter):
+        n = ctypes.c_size_t()
+        st = _lib.cdsdp_workspace_bytes(self._h, int(max_iter), ctypes.byref(n))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_workspace_bytes")
+        return n.value
+
+    def bind(self, max_iter=2000, stream=None, device="cuda"):
+        """Allocate the device workspace with PyTorch and upload the problem."""
+        import torch
+        nbytes = self.workspace_bytes(max_iter)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        st = _lib.cdsdp_bind(self._h, ctypes.c_void_p(ws.data_ptr()), nbytes, int(max_iter), _stream_ptr(stream))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_bind")
+        self.workspace = ws
+        self.max_iter = max_iter
+        return self
+
+    def solve(self, form="primal", stream=None, outputs=True, **opts):
+        o = default_opts(**opts)
+        if self.workspace is None or o.max_iter > self.max_iter:
+            self.bind(max(o.max_iter, self.max_iter))
+        nz, m = int(self.info["nnz_pattern"]), int(self.info["m"])
+        X = np.zeros(nz) if outputs else None
+        y = np.zeros(m) if outputs else None
+        Z = np.zeros(nz) if outputs else None
+        hist = np.zeros((o.max_iter, 8)) if outputs else None
+        cert = np.zeros(max(nz, m)) if outputs else None
+        iters = ctypes.c_int(0)
+        st = _lib.cdsdp_solve(self._h, FORMS.get(form, form), ctypes.byref(o), _stream_ptr(stream),
+                              _ptr(X, ctypes.c_double), _ptr(y, ctypes.c_double), _ptr(Z, ctypes.c_double),
+                              _ptr(hist, ctypes.c_double), ctypes.byref(iters), _ptr(cert, ctypes.c_double))
+        if st < 0:
+            raise CdsdpError(st, "cdsdp_solve")
+        out = dict(status=st, iters=iters.value)
+        if outputs:
+            out.update(X=X, y=y, Z=Z, hist=hist[:iters.value])
+            if st == PRIMAL_INFEASIBLE:
+                out["cert"] = cert[:m]
+            elif st == DUAL_INFEASIBLE:
+                out["cert"] = cert[:nz]
+        return out
+
+    def profile(self):
+        """(projection ms summed, projection launches, iteration ms summed) of
+        the last solve run with profile=1."""
+        a, c = ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int()
+        st = _lib.cdsdp_profile(self._h, ctypes.byref(a), ctypes.byref(n), ctypes.byref(c))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_profile")
+        return a.value, n.value, c.value
+
+    def results(self, stream=None):
+        nz, m = int(self.info["nnz_pattern"]), int(self.info["m"])
+        X, y, Z = np.zeros(nz), np.zeros(m), np.zeros(nz)
+        st = _lib.cdsdp_results(self._h, _stream_ptr(stream), _ptr(X, ctypes.c_double), _ptr(y, ctypes.c_double),
+                                _ptr(Z, ctypes.c_double), None, None)
+        if st < 0:
+            raise CdsdpError(st, "cdsdp_results")
+        return X, y, Z
+
+
+def psd_project(W, offsets, sizes, eig_offsets=None, vec_offsets=None, want_eig=False, max_sweeps=30, stream=None):
+    """Batched PSD projection of lower-packed blocks (torch CUDA tensors).
+    W: float32 or float64 [n_packed]; offsets int32 [p+1]; sizes int32 [p].
+    Returns X (and eigenvalues, eigenvectors when want_eig)."""
+    import torch
+    p = int(sizes.numel())
+    X = torch.empty_like(W)
+    prec = FP64 if W.dtype == torch.float64 else FP32
+    eig = vec = None
+    if want_eig:
+        eig = torch.empty(int(eig_offsets[-1].item()) if eig_offsets is not None else 0, dtype=W.dtype, device=W.device)
+        vec = torch.empty(int(vec_offsets[-1].item()) if vec_offsets is not None else 0, dtype=W.dtype, device=W.device)
+    maxs = int(sizes.max().item()) if p else 1
+    st = _lib.cdsdp_psd_project(p, ctypes.c_void_p(offsets.data_ptr()), ctypes.c_void_p(sizes.data_ptr()), maxs,
+                                ctypes.c_void_p(W.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                ctypes.c_void_p(eig.data_ptr()) if eig is not None else None,
+                                ctypes.c_void_p(eig_offsets.data_ptr()) if eig is not None else None,
+                                ctypes.c_void_p(vec.data_ptr()) if vec is not None else None,
+                                ctypes.c_void_p(vec_offsets.data_ptr()) if vec is not None else None,
+                                prec, int(max_sweeps), _stream_ptr(stream))
+    if st != 0:
+        raise CdsdpError(st, "cdsdp_psd_project")
+    return (X, eig, vec) if want_eig else X

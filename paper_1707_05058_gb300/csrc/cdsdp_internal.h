@@ -1,0 +1,61 @@
+// Internal declarations shared by the host setup (setup.cpp) and the CUDA
+// solver (solver.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cdsdp.h"
+
+namespace cdsdp_impl {
+
+// Everything the data-preprocessing step of Algorithms 1-3 produces, on the host.
+struct HostProblem {
+    int n = 0, m = 0;
+    // extended pattern E*, lower entries (row >= col), column-major order
+    std::vector<int> prow, pcol, colptr;  // colptr[n+1] indexes prow/pcol
+    // maximal cliques, each ascending, list in lexicographic order
+    std::vector<int> cl_off, cl_vert;
+    int max_clique = 0;
+    // lower-packed clique storage: clique k owns [pk_off[k], pk_off[k+1]);
+    // entry (a, b), a >= b, of the |C_k| x |C_k| block sits at
+    // pk_off[k] + b*(2s - b + 1)/2 + (a - b)
+    std::vector<int> pk_off;
+    std::vector<int> gmap;            // packed position -> pattern entry (H_k)
+    std::vector<int> sc_ptr, sc_idx;  // pattern entry -> packed positions (H^T)
+    std::vector<double> c, D;         // per pattern entry
+    // A as CSR over (constraint, pattern entry), unweighted values
+    std::vector<int> a_ptr, a_col;
+    std::vector<double> a_val;
+    // A^T as CSR over (pattern entry, constraint)
+    std::vector<int> at_ptr, at_col;
+    std::vector<double> at_val;
+    std::vector<double> b;
+    long long nfill = 0;
+    bool chordal = false;
+    bool diag_factor = false;
+    // cached inverses (dense row-major m x m, or the diagonal when diag_factor)
+    std::vector<double> minv;         // (A W D^-1 A^T)^-1, Algorithms 1-2
+    std::vector<double> kinv;         // (I + A W P^-1 A^T)^-1, P = I + D/2, Algorithm 3
+    // HSDE constants (Proposition 2): zeta_hat = M^-1 zeta / (1 + zeta^T M^-1 zeta);
+    // its s/t parts equal +-H zhat_x / 2 and are formed on the fly.
+    std::vector<double> zhat_x, zhat_y;
+    double zeta_dot_zhat = 0.0;
+    std::vector<double> atb;          // A^T b per pattern entry
+    std::vector<double> a_zhat_x;     // A W zhat_x per constraint
+    double norm_b = 0.0, norm_c = 0.0;
+};
+
+// Build everything above.  Returns a cdsdp_status.
+int build_host_problem(int n, int m,
+                       long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
+                       const double* b,
+                       long long nnzC, const int* C_row, const int* C_col, const double* C_val,
+                       long long nnzP, const int* P_row, const int* P_col,
+                       HostProblem& hp);
+
+inline int packed_size(int s) { return s * (s + 1) / 2; }
+
+}  // namespace cdsdp_impl

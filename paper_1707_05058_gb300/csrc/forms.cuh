@@ -1,0 +1,281 @@
+// Kernels specific to Algorithm 2 (dual) and Algorithm 3 (HSDE) of
+// arXiv 1707.05058, and the result-assembly kernels.
+#pragma once
+
+#include "affine.cuh"
+
+namespace cdsdp_dev {
+
+// Algorithm 2, after the KKT solve: v_k = z_k + lambda_k/rho + H_k x (Eq. vkEqn),
+// lambda_k <- lambda_k + rho (z_k - v_k) (Eq. MultUpdateDualSDP), one warp per
+// clique; part[k][0..3] = |z_k - v_k|^2, |z_k|^2, |v_k|^2, |lambda_k|^2.
+template <typename T>
+__global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho) {
+    if (stopped(d)) return;
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const T* z = reinterpret_cast<const T*>(d.ck0);
+    T* v = reinterpret_cast<T*>(d.ck1);
+    T* lam = reinterpret_cast<T*>(d.ck2);
+    for (int k = w0; k < d.p; k += nw) {
+        const int off = d.pk_off[k], s = d.csize[k], npk = s * (s + 1) / 2;
+        double p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+        for (int f = lane; f < npk; f += 32) {
+            const int ent = d.gmap[off + f];
+            const double zz = z[off + f], ll = lam[off + f];
+            const T vn = T(zz + ll / rho + d.x[ent]);
+            const T ln = T(ll + rho * (zz - double(vn)));
+            v[off + f] = vn;
+            lam[off + f] = ln;
+            const double w = d.wgt[ent];
+            const double dv = zz - double(vn);
+            p0 += w * dv * dv;
+            p1 += w * zz * zz;
+            p2 += w * double(vn) * double(vn);
+            p3 += w * double(ln) * double(ln);
+        }
+        p0 = warp_sum(p0); p1 = warp_sum(p1); p2 = warp_sum(p2); p3 = warp_sum(p3);
+        if (lane == 0) {
+            double* pk = d.part + (size_t)k * PART_COLS;
+            pk[0] = p0; pk[1] = p1; pk[2] = p2; pk[3] = p3;
+        }
+    }
+}
+
+// Algorithm 2 stopping test (Eq. DualConsensusResidual, eps_lambda).
+__global__ void k_finish_dual(Dev d, double rho, double eps, int nbe, int nbr, int use_cond,
+                              cudaGraphConditionalHandle hnd) {
+    __shared__ double sh[32];
+    if (stopped(d)) { if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(hnd, 0u); return; }
+    double s[6];
+    for (int c = 0; c < 6; ++c) s[c] = (c == 4) ? 0.0 : sum_col(d.part, d.p, c, sh);
+    const double cx = sum_col(d.parte, nbe, 0, sh);
+    const double by = sum_col(d.partr, nbr, 0, sh);
+    if (threadIdx.x == 0) {
+        const int it = d.ctl[CTL_ITER] + 1;
+        const double ec = sqrt(s[0]) / fmax(fmax(sqrt(s[1]), sqrt(s[2])), 1e-300);
+        const double el = rho * sqrt(s[5]) / fmax(sqrt(s[3]), 1e-300);
+        double* h = d.hist + (size_t)(it - 1) * HIST_COLS;
+        h[0] = ec; h[1] = el; h[2] = 0; h[3] = 0; h[4] = -rho * cx; h[5] = by; h[6] = 0; h[7] = 0;
+        const bool bad = !isfinite(ec) || !isfinite(el);
+        finish_common(d, bad, it > 1 && fmax(ec, el) <= eps, it, use_cond, hnd);
+    }
+}
+
+// ---- Algorithm 3 ------------------------------------------------------------
+// Per iteration, with omega = u + v, omega_2 = tau + kappa, nu = omega_1 - omega_2 zeta
+// (Eqs. LinearSystem-MatrixInverseResult, Appendix B); h = r = w = 0 in v stay
+// exactly zero from the zero start, so only v_z and kappa are stored.
+
+// eta / P with eta = nu_11 + A^T nu_21 + H^T (nu_12 + nu_22)/2 (Eq. ThirBlkFlops_s1),
+// nu_11 = u_x - omega_2 c, nu_21 = u_y + omega_2 b, nu_12 = u_s + v_z, nu_22 = u_t.
+template <typename T>
+__global__ void __launch_bounds__(ETHREADS) k_hsde_eta(Dev d) {
+    if (stopped(d)) return;
+    const double w2 = d.scal[SC_TAU] + d.scal[SC_KAPPA];
+    const T* us = reinterpret_cast<const T*>(d.ck0);
+    const T* vz = reinterpret_cast<const T*>(d.ck1);
+    const T* ut = reinterpret_cast<const T*>(d.ck2);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.NE; e += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = d.sc_ptr[e]; j < d.sc_ptr[e + 1]; ++j) {
+            const int q = d.sc_idx[j];
+            acc += double(us[q]) + double(vz[q]) + double(ut[q]);
+        }
+        const double eta = d.x[e] - w2 * d.c[e] + d.atuy[e] + w2 * d.atb[e] + 0.5 * acc;
+        d.q[e] = eta * d.pinv[e];
+    }
+}
+
+// sigma_11 = P^-1 eta - P^-1 A^T (I + A P^-1 A^T)^-1 A P^-1 eta (Eq. MatrixInvFlops);
+// partial <c, sigma_11> in parte[block][2].
+__global__ void __launch_bounds__(ETHREADS) k_hsde_sigma11(Dev d) {
+    __shared__ double sh[32];
+    if (stopped(d)) return;
+    double cs[1] = {0.0};
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.NE; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = d.at_ptr[e]; q < d.at_ptr[e + 1]; ++q) s += d.at_val[q] * d.hh[d.at_col[q]];
+        const double v = d.q[e] - d.pinv[e] * s;
+        d.s11[e] = v;
+        cs[0] += d.wgt[e] * d.c[e] * v;
+    }
+    block_sum<1>(cs, sh);
+    if (threadIdx.x == 0) d.parte[blockIdx.x * PART_COLS + 2] = cs[0];
+}
+
+// sigma_21 = nu_21 - A sigma_11 (Eq. AppendixEqSigma2); partial <b, sigma_21>
+// in partr[block][2]; A sigma_11 kept for the primal residual.
+__global__ void __launch_bounds__(RTHREADS) k_hsde_sigma21(Dev d) {
+    __shared__ double sh[32];
+    if (stopped(d)) return;
+    const double w2 = d.scal[SC_TAU] + d.scal[SC_KAPPA];
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    double bs[1] = {0.0};
+    for (int i = w0; i < d.m; i += nw) {
+        double s = 0.0;
+        for (int q = d.a_ptr[i] + lane; q < d.a_ptr[i + 1]; q += 32) s += d.a_valw[q] * d.s11[d.a_col[q]];
+        s = warp_sum(s);
+        if (lane == 0) {
+            d.as11[i] = s;
+            const double v = d.y[i] + w2 * d.b[i] - s;
+            d.s21[i] = v;
+            bs[0] += d.b[i] * v;
+        }
+    }
+    block_sum<1>(bs, sh);
+    if (threadIdx.x == 0) d.partr[blockIdx.x * PART_COLS + 2] = bs[0];
+}
+
+// gamma = zeta^T sigma, u_hat_2 = omega_2 + zeta^T u_hat_1 = omega_2 + gamma (1 - zeta^T zeta_hat)
+// (Eqs. MatrixInverseResult, FirstBlockElimination); tau <- max(0, u_hat_tau - kappa),
+// kappa <- kappa - u_hat_tau + tau (Eqs. HsdeStep2-3 on the R_+ component).
+__global__ void k_hsde_gamma(Dev d, int nbe, int nbr) {
+    __shared__ double sh[32];
+    if (stopped(d)) return;
+    const double cs = sum_col(d.parte, nbe, 2, sh);
+    const double bs = sum_col(d.partr, nbr, 2, sh);
+    if (threadIdx.x == 0) {
+        const double tau = d.scal[SC_TAU], kappa = d.scal[SC_KAPPA];
+        const double w2 = tau + kappa;
+        const double gamma = cs - bs;
+        const double tauhat = w2 + gamma * (1.0 - d.zeta_dot_zhat);
+        const double tn = fmax(0.0, tauhat - kappa);
+        d.scal[SC_GAMMA] = gamma;
+        d.scal[SC_TAUHAT] = tauhat;
+        d.scal[SC_TAU] = tn;
+        d.scal[SC_KAPPA] = kappa - tauhat + tn;
+    }
+}
+
+// u_x <- sigma_11 - gamma zeta_hat_x; A^T u_y with u_y = sigma_21 - gamma zeta_hat_y;
+// partials: |A^T u_y + H^T v_z - tau c|^2 (parte col 0) and <c, u_x> (col 1).
+template <typename T>
+__global__ void __launch_bounds__(ETHREADS) k_hsde_entry_update(Dev d) {
+    __shared__ double sh[64];
+    if (stopped(d)) return;
+    const double gamma = d.scal[SC_GAMMA], tau = d.scal[SC_TAU];
+    const T* vz = reinterpret_cast<const T*>(d.ck1);
+    double p[2] = {0.0, 0.0};
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.NE; e += gridDim.x * blockDim.x) {
+        const double ux = d.s11[e] - gamma * d.zhx[e];
+        d.x[e] = ux;
+        double a = 0.0;
+        for (int q = d.at_ptr[e]; q < d.at_ptr[e + 1]; ++q) {
+            const int i = d.at_col[q];
+            a += d.at_val[q] * (d.s21[i] - gamma * d.zhy[i]);
+        }
+        d.atuy[e] = a;
+        double hv = 0.0;
+        for (int j = d.sc_ptr[e]; j < d.sc_ptr[e + 1]; ++j) hv += double(vz[d.sc_idx[j]]);
+        const double r = a + hv - tau * d.c[e];
+        p[0] += d.wgt[e] * r * r;
+        p[1] += d.wgt[e] * d.c[e] * ux;
+    }
+    block_sum<2>(p, sh);
+    if (threadIdx.x == 0) {
+        d.parte[blockIdx.x * PART_COLS + 0] = p[0];
+        d.parte[blockIdx.x * PART_COLS + 1] = p[1];
+    }
+}
+
+// u_y <- sigma_21 - gamma zeta_hat_y; A u_x = A sigma_11 - gamma A zeta_hat_x;
+// partials |A u_x - tau b|^2 (partr col 0) and <b, u_y> (col 1).
+__global__ void __launch_bounds__(RTHREADS) k_hsde_row_update(Dev d) {
+    __shared__ double sh[64];
+    if (stopped(d)) return;
+    const double gamma = d.scal[SC_GAMMA], tau = d.scal[SC_TAU];
+    double p[2] = {0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += gridDim.x * blockDim.x) {
+        const double uy = d.s21[i] - gamma * d.zhy[i];
+        d.y[i] = uy;
+        const double r = d.as11[i] - gamma * d.azhx[i] - tau * d.b[i];
+        p[0] += r * r;
+        p[1] += d.b[i] * uy;
+    }
+    block_sum<2>(p, sh);
+    if (threadIdx.x == 0) {
+        d.partr[blockIdx.x * PART_COLS + 0] = p[0];
+        d.partr[blockIdx.x * PART_COLS + 1] = p[1];
+    }
+}
+
+// Algorithm 3 stopping tests: Eqs. HSDEerror and HSDEconsensusResidual when
+// tau > 0; otherwise the infeasibility tests (each certificate on its own):
+// b^T u_y > 0 and |A^T u_y + H^T v_z| <= eps b^T u_y / |b|  -> primal infeasible,
+// c^T u_x < 0 and |A u_x| <= -eps c^T u_x / |c|             -> dual infeasible.
+__global__ void k_finish_hsde(Dev d, double eps, int nbe, int nbr, int use_cond, cudaGraphConditionalHandle hnd) {
+    __shared__ double sh[32];
+    if (stopped(d)) { if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(hnd, 0u); return; }
+    double s[6];
+    for (int c = 0; c < 6; ++c) s[c] = sum_col(d.part, d.p, c, sh);
+    const double rd2 = sum_col(d.parte, nbe, 0, sh);
+    const double cux = sum_col(d.parte, nbe, 1, sh);
+    const double rp2 = sum_col(d.partr, nbr, 0, sh);
+    const double buy = sum_col(d.partr, nbr, 1, sh);
+    if (threadIdx.x == 0) {
+        const int it = d.ctl[CTL_ITER] + 1;
+        const double tau = d.scal[SC_TAU], kappa = d.scal[SC_KAPPA];
+        double* h = d.hist + (size_t)(it - 1) * HIST_COLS;
+        h[6] = tau; h[7] = kappa;
+        bool bad = !isfinite(tau) || !isfinite(kappa);
+        bool stop = false;
+        if (tau > 0) {
+            const double pc = sqrt(s[0]) / fmax(fmax(sqrt(s[1]), sqrt(s[2])), 1e-300);
+            const double dc = sqrt(s[3]) / fmax(fmax(sqrt(s[4]), sqrt(s[5])), 1e-300);
+            const double ep = sqrt(rp2) / tau / (1.0 + d.norm_b);
+            const double ed = sqrt(rd2) / tau / (1.0 + d.norm_c);
+            const double cx = cux / tau, by = buy / tau;
+            const double eg = fabs(cx - by) / (1.0 + fabs(cx) + fabs(by));
+            const double ec = fmax(pc, dc);
+            h[0] = ep; h[1] = ed; h[2] = eg; h[3] = ec; h[4] = cx; h[5] = by;
+            bad = bad || !isfinite(ep) || !isfinite(ed) || !isfinite(eg) || !isfinite(ec);
+            if (!bad && fmax(fmax(ep, ed), fmax(eg, ec)) <= eps) { d.ctl[CTL_STATUS] = 0; stop = true; }
+        } else {
+            const double rp = sqrt(rd2), rdd = sqrt(rp2);
+            h[0] = rp; h[1] = rdd; h[2] = buy; h[3] = cux; h[4] = 0; h[5] = 0;
+            bad = bad || !isfinite(rp) || !isfinite(rdd);
+            if (!bad && buy > 0 && rp <= eps * buy / fmax(d.norm_b, 1e-300)) { d.ctl[CTL_STATUS] = 2; stop = true; }
+            else if (!bad && cux < 0 && rdd <= -eps * cux / fmax(d.norm_c, 1e-300)) { d.ctl[CTL_STATUS] = 3; stop = true; }
+        }
+        int done = 0;
+        if (bad) { d.ctl[CTL_STATUS] = -6; done = 1; }
+        else if (stop) done = 1;
+        else if (it >= d.max_iter) { d.ctl[CTL_STATUS] = 1; done = 1; }
+        d.ctl[CTL_ITER] = it;
+        if (done) d.ctl[CTL_DONE] = 1;
+        if (use_cond) cudaGraphSetConditional(hnd, done ? 0u : 1u);
+    }
+}
+
+// ---- set-up and result assembly --------------------------------------------
+
+__global__ void k_init(Dev d, int form) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        d.scal[SC_TAU] = (form == 2) ? 1.0 : 0.0;
+        d.scal[SC_KAPPA] = (form == 2) ? 1.0 : 0.0;
+        d.ctl[CTL_DONE] = 0;
+        d.ctl[CTL_ITER] = 0;
+        d.ctl[CTL_STATUS] = 1;
+    }
+}
+
+// out = scale * in (scale from a device scalar when sptr != nullptr: 1/ *sptr)
+__global__ void k_scale_out(int n, const double* __restrict__ in, double scale, const double* sptr,
+                            double* __restrict__ out) {
+    const double sc = sptr ? (*sptr > 0 ? scale / *sptr : scale) : scale;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = sc * in[i];
+}
+
+// dot product helper for certificates: out[0] = sum_i w_i a_i b_i (w may be null), one block
+__global__ void k_dot(int n, const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ w,
+                      double* out) {
+    __shared__ double sh[32];
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += (w ? w[i] : 1.0) * a[i] * b[i];
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) *out = v[0];
+}
+
+}  // namespace cdsdp_dev

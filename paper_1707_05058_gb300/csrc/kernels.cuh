@@ -1,0 +1,114 @@
+// Device kernels of the decomposed ADMM iteration (arXiv 1707.05058,
+// Algorithms 1-3).  Storage convention (differs from the paper's full vec(),
+// equivalently): every symmetric quantity is stored on the lower triangle of
+// the extended pattern E*, and inner products weight off-diagonal entries by 2.
+// A clique block is stored lower-packed, column-major:
+//   entry (a, b), a >= b, of block k at pk_off[k] + b*(2s - b + 1)/2 + (a - b).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cdsdp_dev {
+
+enum { CTL_DONE = 0, CTL_ITER = 1, CTL_STATUS = 2, CTL_NAN = 3, CTL_WORDS = 16 };
+// iteration scalars of Algorithm 3
+enum { SC_TAU = 0, SC_KAPPA = 1, SC_OMEGA2 = 2, SC_GAMMA = 3, SC_TAUHAT = 4, SC_WORDS = 32 };
+enum { HIST_COLS = 8, PART_COLS = 8 };
+
+// Device views of the workspace (all pointers into the caller's buffer).
+struct Dev {
+    int n, m, NE, p, nd;
+    int diag_factor;
+    // constants
+    const double* c;      // [NE]
+    const double* dinv;   // [NE]  1 / D
+    const double* pinv;   // [NE]  1 / (1 + D/2)
+    const double* wgt;    // [NE]  1 on the diagonal, 2 off it
+    const int* a_ptr;     // [m+1]
+    const int* a_col;     // [nnzA]
+    const double* a_valw; // [nnzA] w_e * A_ie  (A W)
+    const int* at_ptr;    // [NE+1]
+    const int* at_col;    // [nnzA]
+    const double* at_val; // [nnzA] A_ie     (A^T)
+    const double* b;      // [m]
+    const double* minv;   // [m*m] or [m]
+    const double* kinv;   // [m*m] or [m]
+    const int* gmap;      // [nd] packed position -> pattern entry
+    const int* pk_off;    // [p+1]
+    const int* csize;     // [p]
+    const int* sc_ptr;    // [NE+1]
+    const int* sc_idx;    // [nd]
+    const double* zhx;    // [NE] zeta_hat, x part
+    const double* zhy;    // [m]  zeta_hat, y part
+    const double* atb;    // [NE] A^T b
+    const double* azhx;   // [m]  A W zeta_hat_x
+    double zeta_dot_zhat, norm_b, norm_c;
+    // state
+    double* x;            // [NE]
+    double* t;            // [NE]
+    double* q;            // [NE]
+    double* s11;          // [NE]
+    double* atuy;         // [NE]
+    double* y;            // [m]
+    double* g;            // [m]
+    double* hh;           // [m]
+    double* s21;          // [m]
+    double* as11;         // [m]
+    void* ck0;            // [nd] clique vectors (float or double)
+    void* ck1;
+    void* ck2;
+    double* part;         // [p * PART_COLS] per-clique partial sums
+    double* parte;        // [NBLK_E * PART_COLS] per-block partials, pattern-entry kernels
+    double* partr;        // [NBLK_R * PART_COLS] per-block partials, constraint-row kernels
+    double* scal;         // [SC_WORDS]
+    int* ctl;             // [CTL_WORDS]
+    double* hist;         // [max_iter * HIST_COLS]
+    int max_iter;
+};
+
+constexpr int NBLK_E = 1216;  // 152 SMs x 8
+constexpr int NBLK_R = 1216;
+constexpr int ETHREADS = 256;
+constexpr int RTHREADS = 256;
+
+__device__ __forceinline__ bool stopped(const Dev& d) {
+    return *((volatile int*)d.ctl + CTL_DONE) != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block reduction of NV doubles per thread; result valid in
+// thread 0.  `sh` holds 32 * NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp * NV + k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = (lane < nw) ? sh[lane * NV + k] : 0.0;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    }
+    __syncthreads();
+}
+
+template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+
+}  // namespace cdsdp_dev

@@ -1,0 +1,396 @@
+// Host data preprocessing of Algorithms 1-3 (arXiv 1707.05058): aggregate
+// pattern (Section 2.1), chordal extension and maximal cliques (Section 6.1.1),
+// entry selectors H_k and D = sum_k H_k^T H_k (Section 4), the cached
+// inverses of A D^-1 A^T (Eq. ADMMprimalFatorization) and of
+// I + A (I + D/2)^-1 A^T (Eq. HSDEFactorizationFinal), and zeta_hat
+// (Proposition 2).  Runs once per problem, on the CPU; not on the hot path.
+//
+// Canonical rules (fixed so that results are reproducible bit for bit):
+//  * chordality: maximum cardinality search, ties to the smallest vertex; the
+//    reverse visiting order is tested as a perfect elimination order (PEO).
+//  * non-chordal patterns: exact minimum-degree elimination game, ties to the
+//    smallest vertex; eliminating v joins its remaining neighbours.
+//  * maximal cliques: K_v = {v} U later-neighbours(v) is kept unless some u
+//    with parent(u) = v has |later(u)| = |later(v)| + 1 (parent = first later
+//    neighbour); cliques sorted ascending, list sorted lexicographically.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <new>
+#include <set>
+#include <utility>
+
+#include "cdsdp_internal.h"
+
+namespace cdsdp_impl {
+namespace {
+
+// Dense Cholesky (lower, row-major, in place) followed by the explicit
+// inverse inv = L^-T L^-1.  Returns false on a non-positive pivot.
+bool spd_inverse(std::vector<double>& a, int m, std::vector<double>& inv) {
+    double maxdiag = 0.0;
+    for (int i = 0; i < m; ++i) maxdiag = std::max(maxdiag, std::fabs(a[(size_t)i * m + i]));
+    for (int j = 0; j < m; ++j) {
+        double d = a[(size_t)j * m + j];
+        for (int k = 0; k < j; ++k) d -= a[(size_t)j * m + k] * a[(size_t)j * m + k];
+        if (!(d > 1e-14 * maxdiag)) return false;
+        double ljj = std::sqrt(d);
+        a[(size_t)j * m + j] = ljj;
+        for (int i = j + 1; i < m; ++i) {
+            double s = a[(size_t)i * m + j];
+            const double* ri = &a[(size_t)i * m];
+            const double* rj = &a[(size_t)j * m];
+            for (int k = 0; k < j; ++k) s -= ri[k] * rj[k];
+            a[(size_t)i * m + j] = s / ljj;
+        }
+    }
+    // W = L^-1 (lower), by forward substitution column by column of I
+    std::vector<double> w((size_t)m * m, 0.0);
+    for (int j = 0; j < m; ++j) {
+        for (int i = j; i < m; ++i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int k = j; k < i; ++k) s -= a[(size_t)i * m + k] * w[(size_t)k * m + j];
+            w[(size_t)i * m + j] = s / a[(size_t)i * m + i];
+        }
+    }
+    // inv = W^T W
+    inv.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = 0.0;
+            for (int k = i; k < m; ++k) s += w[(size_t)k * m + i] * w[(size_t)k * m + j];
+            inv[(size_t)i * m + j] = s;
+            inv[(size_t)j * m + i] = s;
+        }
+    return true;
+}
+
+int entry_of(const HostProblem& hp, int i, int j) {  // i >= j
+    const int* beg = hp.prow.data() + hp.colptr[j];
+    const int* end = hp.prow.data() + hp.colptr[j + 1];
+    const int* it = std::lower_bound(beg, end, i);
+    if (it == end || *it != i) return -1;
+    return (int)(it - hp.prow.data());
+}
+
+}  // namespace
+
+int build_host_problem(int n, int m,
+                       long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
+                       const double* bvec,
+                       long long nnzC, const int* C_row, const int* C_col, const double* C_val,
+                       long long nnzP, const int* P_row, const int* P_col,
+                       HostProblem& hp) {
+    if (n < 1 || m < 1 || nnzA < 0 || nnzC < 0 || nnzP < 0) return CDSDP_ERR_ARG;
+    if (nnzA > 0 && (!A_con || !A_row || !A_col || !A_val)) return CDSDP_ERR_ARG;
+    if (nnzC > 0 && (!C_row || !C_col || !C_val)) return CDSDP_ERR_ARG;
+    if (nnzP > 0 && (!P_row || !P_col)) return CDSDP_ERR_ARG;
+    if (!bvec) return CDSDP_ERR_ARG;
+    if (nnzA > 2000000000LL || nnzC > 2000000000LL || nnzP > 2000000000LL) return CDSDP_ERR_UNSUPPORTED;
+    auto bad_pair = [n](int r, int c) { return r < 0 || c < 0 || r >= n || c >= n || r < c; };
+    for (long long k = 0; k < nnzA; ++k)
+        if (bad_pair(A_row[k], A_col[k]) || A_con[k] < 0 || A_con[k] >= m || !std::isfinite(A_val[k]))
+            return CDSDP_ERR_ARG;
+    for (long long k = 0; k < nnzC; ++k)
+        if (bad_pair(C_row[k], C_col[k]) || !std::isfinite(C_val[k])) return CDSDP_ERR_ARG;
+    for (long long k = 0; k < nnzP; ++k)
+        if (bad_pair(P_row[k], P_col[k])) return CDSDP_ERR_ARG;
+    for (int i = 0; i < m; ++i)
+        if (!std::isfinite(bvec[i])) return CDSDP_ERR_ARG;
+
+    hp = HostProblem();
+    hp.n = n;
+    hp.m = m;
+
+    // ---- aggregate pattern (off-diagonal adjacency, sorted, unique)
+    std::vector<std::vector<int>> adj(n);
+    auto add_edge = [&](int r, int c) {
+        if (r != c) { adj[r].push_back(c); adj[c].push_back(r); }
+    };
+    for (long long k = 0; k < nnzC; ++k) add_edge(C_row[k], C_col[k]);
+    for (long long k = 0; k < nnzA; ++k) add_edge(A_row[k], A_col[k]);
+    for (long long k = 0; k < nnzP; ++k) add_edge(P_row[k], P_col[k]);
+    long long nedges = 0;
+    for (auto& a : adj) {
+        std::sort(a.begin(), a.end());
+        a.erase(std::unique(a.begin(), a.end()), a.end());
+        nedges += (long long)a.size();
+    }
+    nedges /= 2;
+
+    // ---- maximum cardinality search with buckets (ties: smallest vertex)
+    std::vector<int> visit;
+    visit.reserve(n);
+    {
+        std::vector<int> weight(n, 0);
+        std::vector<char> done(n, 0);
+        std::vector<std::set<int>> bucket(n + 1);
+        for (int v = 0; v < n; ++v) bucket[0].insert(v);
+        int top = 0;
+        for (int step = 0; step < n; ++step) {
+            while (top > 0 && bucket[top].empty()) --top;
+            int v = *bucket[top].begin();
+            bucket[top].erase(bucket[top].begin());
+            done[v] = 1;
+            visit.push_back(v);
+            for (int u : adj[v]) {
+                if (done[u]) continue;
+                bucket[weight[u]].erase(u);
+                ++weight[u];
+                bucket[weight[u]].insert(u);
+                if (weight[u] > top) top = weight[u];
+            }
+        }
+    }
+    std::vector<int> elim(visit.rbegin(), visit.rend());
+    std::vector<int> pos(n);
+    for (int k = 0; k < n; ++k) pos[elim[k]] = k;
+    // later neighbours per vertex for this order
+    std::vector<std::vector<int>> later(n);
+    for (int v = 0; v < n; ++v)
+        for (int u : adj[v])
+            if (pos[u] > pos[v]) later[v].push_back(u);
+    // Tarjan-Yannakakis PEO test: later(v) \ {parent} must lie in adj(parent)
+    bool chordal = true;
+    for (int v = 0; v < n && chordal; ++v) {
+        if (later[v].empty()) continue;
+        int par = later[v][0];
+        for (int u : later[v]) if (pos[u] < pos[par]) par = u;
+        for (int u : later[v]) {
+            if (u == par) continue;
+            if (!std::binary_search(adj[par].begin(), adj[par].end(), u)) { chordal = false; break; }
+        }
+    }
+    hp.chordal = chordal;
+    if (!chordal) {
+        // exact minimum-degree elimination game (ties: smallest vertex)
+        std::vector<std::set<int>> g(n);
+        for (int v = 0; v < n; ++v) g[v].insert(adj[v].begin(), adj[v].end());
+        std::set<std::pair<int, int>> order;
+        for (int v = 0; v < n; ++v) order.insert({(int)g[v].size(), v});
+        for (int k = 0; k < n; ++k) {
+            int v = order.begin()->second;
+            order.erase(order.begin());
+            elim[k] = v;
+            pos[v] = k;
+            std::vector<int> nb(g[v].begin(), g[v].end());
+            later[v] = nb;
+            for (int u : nb) {
+                order.erase({(int)g[u].size(), u});
+                g[u].erase(v);
+            }
+            for (size_t a = 0; a < nb.size(); ++a)
+                for (size_t c2 = a + 1; c2 < nb.size(); ++c2) {
+                    int x = nb[a], y = nb[c2];
+                    if (g[x].insert(y).second) g[y].insert(x);
+                }
+            for (int u : nb) order.insert({(int)g[u].size(), u});
+            g[v].clear();
+        }
+    }
+    for (auto& l : later) std::sort(l.begin(), l.end());
+
+    // ---- maximal cliques (parent rule on the PEO)
+    std::vector<char> maximal(n, 1);
+    for (int u = 0; u < n; ++u) {
+        if (later[u].empty()) continue;
+        int par = later[u][0];
+        for (int x : later[u]) if (pos[x] < pos[par]) par = x;
+        if (later[u].size() == later[par].size() + 1) maximal[par] = 0;
+    }
+    std::vector<std::vector<int>> cliques;
+    for (int v = 0; v < n; ++v) {
+        if (!maximal[v]) continue;
+        std::vector<int> k = later[v];
+        k.push_back(v);
+        std::sort(k.begin(), k.end());
+        cliques.push_back(std::move(k));
+    }
+    std::sort(cliques.begin(), cliques.end());
+    hp.cl_off.assign(1, 0);
+    for (auto& k : cliques) {
+        hp.cl_vert.insert(hp.cl_vert.end(), k.begin(), k.end());
+        hp.cl_off.push_back((int)hp.cl_vert.size());
+        hp.max_clique = std::max(hp.max_clique, (int)k.size());
+    }
+
+    // ---- extended pattern, lower, column-major
+    {
+        std::vector<std::vector<int>> col(n);
+        long long off = 0;
+        for (int v = 0; v < n; ++v) {
+            col[v].push_back(v);
+            for (int u : later[v]) {
+                col[std::min(u, v)].push_back(std::max(u, v));
+                ++off;
+            }
+        }
+        hp.nfill = off - nedges;
+        hp.colptr.assign(n + 1, 0);
+        for (int j = 0; j < n; ++j) {
+            std::sort(col[j].begin(), col[j].end());
+            hp.colptr[j + 1] = hp.colptr[j] + (int)col[j].size();
+        }
+        hp.prow.reserve(hp.colptr[n]);
+        hp.pcol.reserve(hp.colptr[n]);
+        for (int j = 0; j < n; ++j)
+            for (int i : col[j]) { hp.prow.push_back(i); hp.pcol.push_back(j); }
+    }
+    const int NE = (int)hp.prow.size();
+
+    // ---- H_k (gather map), H^T (scatter map), D
+    const int p = (int)cliques.size();
+    hp.pk_off.assign(p + 1, 0);
+    for (int k = 0; k < p; ++k) hp.pk_off[k + 1] = hp.pk_off[k] + packed_size((int)cliques[k].size());
+    hp.gmap.resize(hp.pk_off[p]);
+    for (int k = 0; k < p; ++k) {
+        const auto& cl = cliques[k];
+        int s = (int)cl.size(), q = hp.pk_off[k];
+        for (int bb = 0; bb < s; ++bb)
+            for (int a = bb; a < s; ++a) {
+                int e = entry_of(hp, cl[a], cl[bb]);
+                if (e < 0) return CDSDP_ERR_ARG;  // cannot happen for a valid extension
+                hp.gmap[q++] = e;
+            }
+    }
+    hp.sc_ptr.assign(NE + 1, 0);
+    for (int e : hp.gmap) ++hp.sc_ptr[e + 1];
+    for (int e = 0; e < NE; ++e) hp.sc_ptr[e + 1] += hp.sc_ptr[e];
+    hp.sc_idx.resize(hp.gmap.size());
+    {
+        std::vector<int> fill(hp.sc_ptr.begin(), hp.sc_ptr.end() - 1);
+        for (int q = 0; q < (int)hp.gmap.size(); ++q) hp.sc_idx[fill[hp.gmap[q]]++] = q;
+    }
+    hp.D.resize(NE);
+    for (int e = 0; e < NE; ++e) hp.D[e] = (double)(hp.sc_ptr[e + 1] - hp.sc_ptr[e]);
+
+    // ---- c, A (CSR over entries, duplicates merged), A^T
+    hp.c.assign(NE, 0.0);
+    for (long long k = 0; k < nnzC; ++k) hp.c[entry_of(hp, C_row[k], C_col[k])] += C_val[k];
+    {
+        std::vector<std::pair<long long, double>> t;
+        t.reserve(nnzA);
+        for (long long k = 0; k < nnzA; ++k)
+            t.push_back({(long long)A_con[k] * NE + entry_of(hp, A_row[k], A_col[k]), A_val[k]});
+        std::sort(t.begin(), t.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+        hp.a_ptr.assign(m + 1, 0);
+        long long last = -1;
+        for (auto& kv : t) {
+            if (kv.first == last) { hp.a_val.back() += kv.second; continue; }
+            last = kv.first;
+            int con = (int)(kv.first / NE), e = (int)(kv.first % NE);
+            hp.a_col.push_back(e);
+            hp.a_val.push_back(kv.second);
+            ++hp.a_ptr[con + 1];
+        }
+        for (int i = 0; i < m; ++i) hp.a_ptr[i + 1] += hp.a_ptr[i];
+        hp.at_ptr.assign(NE + 1, 0);
+        for (int e : hp.a_col) ++hp.at_ptr[e + 1];
+        for (int e = 0; e < NE; ++e) hp.at_ptr[e + 1] += hp.at_ptr[e];
+        hp.at_col.resize(hp.a_col.size());
+        hp.at_val.resize(hp.a_col.size());
+        std::vector<int> fill(hp.at_ptr.begin(), hp.at_ptr.end() - 1);
+        for (int i = 0; i < m; ++i)
+            for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) {
+                int dst = fill[hp.a_col[q]]++;
+                hp.at_col[dst] = i;
+                hp.at_val[dst] = hp.a_val[q];
+            }
+    }
+    hp.b.assign(bvec, bvec + m);
+
+    // ---- cached inverses: S(d) = A W diag(d)^-1 A^T (+ I for HSDE)
+    auto wgt = [&](int e) { return hp.prow[e] == hp.pcol[e] ? 1.0 : 2.0; };
+    bool structurally_diag = true;
+    for (int e = 0; e < NE && structurally_diag; ++e)
+        if (hp.at_ptr[e + 1] - hp.at_ptr[e] > 1) structurally_diag = false;
+    if (!structurally_diag && m > 8192) return CDSDP_ERR_UNSUPPORTED;
+    auto build = [&](bool hsde, std::vector<double>& inv) -> int {
+        if (structurally_diag) {
+            inv.assign(m, hsde ? 1.0 : 0.0);
+            for (int e = 0; e < NE; ++e)
+                for (int q = hp.at_ptr[e]; q < hp.at_ptr[e + 1]; ++q) {
+                    double dd = hsde ? 1.0 + 0.5 * hp.D[e] : hp.D[e];
+                    inv[hp.at_col[q]] += wgt(e) * hp.at_val[q] * hp.at_val[q] / dd;
+                }
+            for (int i = 0; i < m; ++i) {
+                if (!(inv[i] > 0.0)) return CDSDP_ERR_RANK;
+                inv[i] = 1.0 / inv[i];
+            }
+            return CDSDP_SOLVED;
+        }
+        std::vector<double> S((size_t)m * m, 0.0);
+        for (int i = 0; hsde && i < m; ++i) S[(size_t)i * m + i] = 1.0;
+        for (int e = 0; e < NE; ++e) {
+            double f = wgt(e) / (hsde ? 1.0 + 0.5 * hp.D[e] : hp.D[e]);
+            for (int q1 = hp.at_ptr[e]; q1 < hp.at_ptr[e + 1]; ++q1) {
+                double v1 = f * hp.at_val[q1];
+                double* row = &S[(size_t)hp.at_col[q1] * m];
+                for (int q2 = hp.at_ptr[e]; q2 < hp.at_ptr[e + 1]; ++q2) row[hp.at_col[q2]] += v1 * hp.at_val[q2];
+            }
+        }
+        return spd_inverse(S, m, inv) ? CDSDP_SOLVED : CDSDP_ERR_RANK;
+    };
+    hp.diag_factor = structurally_diag;
+    int st = build(false, hp.minv);
+    if (st != CDSDP_SOLVED) return st;
+    st = build(true, hp.kinv);
+    if (st != CDSDP_SOLVED) return st;
+
+    // ---- HSDE: zeta_hat from one inner solve with nu = zeta = (c, 0, -b, 0)
+    {
+        auto kinv_apply = [&](const std::vector<double>& r, std::vector<double>& out) {
+            out.assign(m, 0.0);
+            if (hp.diag_factor) { for (int i = 0; i < m; ++i) out[i] = hp.kinv[i] * r[i]; return; }
+            for (int i = 0; i < m; ++i) {
+                double s = 0.0;
+                for (int j = 0; j < m; ++j) s += hp.kinv[(size_t)i * m + j] * r[j];
+                out[i] = s;
+            }
+        };
+        auto A_w = [&](const std::vector<double>& x, std::vector<double>& out) {  // A W x
+            out.assign(m, 0.0);
+            for (int i = 0; i < m; ++i) {
+                double s = 0.0;
+                for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) s += hp.a_val[q] * wgt(hp.a_col[q]) * x[hp.a_col[q]];
+                out[i] = s;
+            }
+        };
+        auto A_T = [&](const std::vector<double>& y, std::vector<double>& out) {
+            out.assign(NE, 0.0);
+            for (int e = 0; e < NE; ++e) {
+                double s = 0.0;
+                for (int q = hp.at_ptr[e]; q < hp.at_ptr[e + 1]; ++q) s += hp.at_val[q] * y[hp.at_col[q]];
+                out[e] = s;
+            }
+        };
+        A_T(hp.b, hp.atb);
+        std::vector<double> pe(NE), r, hh, athh, s11(NE), as11;
+        for (int e = 0; e < NE; ++e) pe[e] = (hp.c[e] - hp.atb[e]) / (1.0 + 0.5 * hp.D[e]);
+        A_w(pe, r);
+        kinv_apply(r, hh);
+        A_T(hh, athh);
+        for (int e = 0; e < NE; ++e) s11[e] = pe[e] - athh[e] / (1.0 + 0.5 * hp.D[e]);
+        A_w(s11, as11);
+        std::vector<double> s21(m);
+        for (int i = 0; i < m; ++i) s21[i] = -hp.b[i] - as11[i];
+        double zMz = 0.0;
+        for (int e = 0; e < NE; ++e) zMz += wgt(e) * hp.c[e] * s11[e];
+        for (int i = 0; i < m; ++i) zMz -= hp.b[i] * s21[i];
+        double denom = 1.0 + zMz;
+        hp.zhat_x.resize(NE);
+        hp.zhat_y.resize(m);
+        for (int e = 0; e < NE; ++e) hp.zhat_x[e] = s11[e] / denom;
+        for (int i = 0; i < m; ++i) hp.zhat_y[i] = s21[i] / denom;
+        hp.zeta_dot_zhat = zMz / denom;
+        A_w(hp.zhat_x, hp.a_zhat_x);
+        double nb = 0.0, nc = 0.0;
+        for (int i = 0; i < m; ++i) nb += hp.b[i] * hp.b[i];
+        for (int e = 0; e < NE; ++e) nc += wgt(e) * hp.c[e] * hp.c[e];
+        hp.norm_b = std::sqrt(nb);
+        hp.norm_c = std::sqrt(nc);
+    }
+    return CDSDP_SOLVED;
+}
+
+}  // namespace cdsdp_impl

@@ -1,0 +1,644 @@
+// C ABI (include/cdsdp.h) of the GB300 decomposed-ADMM solver: workspace
+// layout, upload, the per-iteration launch sequences of Algorithms 1-3
+// (arXiv 1707.05058), the CUDA-graph while loop, and result download.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cdsdp_internal.h"
+#include "forms.cuh"
+#include "jacobi.cuh"
+
+using namespace cdsdp_dev;
+using cdsdp_impl::HostProblem;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// Clique size classes handled by the warp-per-clique projection.
+constexpr int kClasses[] = {4, 8, 12, 16, 24, 32};
+constexpr int kNumClasses = 6;
+inline int class_of(int s) {
+    for (int c = 0; c < kNumClasses; ++c)
+        if (s <= kClasses[c]) return c;
+    return -1;
+}
+
+struct Layout {
+    // constants
+    size_t c, dinv, pinv, wgt, a_ptr, a_col, a_valw, at_ptr, at_col, at_val, b, minv, kinv, gmap, pk_off, csize,
+        sc_ptr, sc_idx, zhx, zhy, atb, azhx, blist;
+    size_t const_end;
+    // state
+    size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, part, parte, partr, scal, ctl, hist;
+    size_t total;
+};
+
+}  // namespace
+
+struct cdsdp {
+    HostProblem hp;
+    Layout L{};
+    std::vector<unsigned char> image;  // host copy of the constant section
+    int cls_off[kNumClasses + 1] = {0};
+    unsigned char* ws = nullptr;
+    size_t ws_bytes = 0;
+    int ws_max_iter = 0;
+    Dev dev{};
+    int GE = 1, GR = 1;  // grid sizes of the pattern-entry and constraint-row kernels
+    // cached graph of a whole solve
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int g_form = -1;
+    cdsdp_opts g_opts{};
+    // last solve
+    int last_form = -1, last_iters = 0, last_status = CDSDP_ERR_STATE;
+    std::string err;
+    // profiling: event pairs around projection launches and whole iterations
+    std::vector<cudaEvent_t> ev;
+    bool last_profiled = false;
+    double prof_proj_ms = 0.0, prof_iter_ms = 0.0;
+    int prof_launches = 0;
+};
+
+namespace {
+
+int fail_cuda(cdsdp* h, cudaError_t e, const char* what) {
+    if (h) h->err = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return CDSDP_ERR_CUDA;
+}
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return fail_cuda(h, _e, #call); \
+    } while (0)
+
+Layout make_layout(const HostProblem& hp, int max_iter) {
+    Layout L{};
+    size_t o = 0;
+    const size_t NE = hp.prow.size(), m = hp.m, nd = hp.gmap.size(), p = hp.cl_off.size() - 1;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1)); return r; };
+    const size_t nnzA = hp.a_col.size();
+    const size_t minv_n = hp.diag_factor ? m : m * m;
+    L.c = take(NE * 8); L.dinv = take(NE * 8); L.pinv = take(NE * 8); L.wgt = take(NE * 8);
+    L.a_ptr = take((m + 1) * 4); L.a_col = take(nnzA * 4); L.a_valw = take(nnzA * 8);
+    L.at_ptr = take((NE + 1) * 4); L.at_col = take(nnzA * 4); L.at_val = take(nnzA * 8);
+    L.b = take(m * 8); L.minv = take(minv_n * 8); L.kinv = take(minv_n * 8);
+    L.gmap = take(nd * 4); L.pk_off = take((p + 1) * 4); L.csize = take(p * 4);
+    L.sc_ptr = take((NE + 1) * 4); L.sc_idx = take(nd * 4);
+    L.zhx = take(NE * 8); L.zhy = take(m * 8); L.atb = take(NE * 8); L.azhx = take(m * 8);
+    L.blist = take(p * 4);
+    L.const_end = o;
+    L.x = take(NE * 8); L.t = take(NE * 8); L.q = take(NE * 8); L.s11 = take(NE * 8); L.atuy = take(NE * 8);
+    L.y = take(m * 8); L.g = take(m * 8); L.hh = take(m * 8); L.s21 = take(m * 8); L.as11 = take(m * 8);
+    L.ck0 = take(nd * 8); L.ck1 = take(nd * 8); L.ck2 = take(nd * 8);
+    L.part = take(p * PART_COLS * 8);
+    L.parte = take((size_t)NBLK_E * PART_COLS * 8);
+    L.partr = take((size_t)NBLK_R * PART_COLS * 8);
+    L.scal = take(SC_WORDS * 8);
+    L.ctl = take(CTL_WORDS * 4);
+    L.hist = take((size_t)std::max(max_iter, 1) * HIST_COLS * 8);
+    L.total = o;
+    return L;
+}
+
+template <typename V>
+void put(std::vector<unsigned char>& img, size_t off, const std::vector<V>& v) {
+    if (!v.empty()) std::memcpy(img.data() + off, v.data(), v.size() * sizeof(V));
+}
+
+void build_image(cdsdp* h) {
+    const HostProblem& hp = h->hp;
+    const Layout& L = h->L;
+    const int NE = (int)hp.prow.size(), p = (int)hp.cl_off.size() - 1;
+    h->image.assign(L.const_end, 0);
+    auto& img = h->image;
+    put(img, L.c, hp.c);
+    std::vector<double> dinv(NE), pinv(NE), wgt(NE), aw(hp.a_val.size());
+    for (int e = 0; e < NE; ++e) {
+        dinv[e] = 1.0 / hp.D[e];
+        pinv[e] = 1.0 / (1.0 + 0.5 * hp.D[e]);
+        wgt[e] = hp.prow[e] == hp.pcol[e] ? 1.0 : 2.0;
+    }
+    for (size_t q = 0; q < hp.a_val.size(); ++q) aw[q] = wgt[hp.a_col[q]] * hp.a_val[q];
+    put(img, L.dinv, dinv); put(img, L.pinv, pinv); put(img, L.wgt, wgt);
+    put(img, L.a_ptr, hp.a_ptr); put(img, L.a_col, hp.a_col); put(img, L.a_valw, aw);
+    put(img, L.at_ptr, hp.at_ptr); put(img, L.at_col, hp.at_col); put(img, L.at_val, hp.at_val);
+    put(img, L.b, hp.b); put(img, L.minv, hp.minv); put(img, L.kinv, hp.kinv);
+    put(img, L.gmap, hp.gmap); put(img, L.pk_off, hp.pk_off);
+    std::vector<int> cs(p);
+    for (int k = 0; k < p; ++k) cs[k] = hp.cl_off[k + 1] - hp.cl_off[k];
+    put(img, L.csize, cs);
+    put(img, L.sc_ptr, hp.sc_ptr); put(img, L.sc_idx, hp.sc_idx);
+    put(img, L.zhx, hp.zhat_x); put(img, L.zhy, hp.zhat_y); put(img, L.atb, hp.atb); put(img, L.azhx, hp.a_zhat_x);
+    // clique lists by size class
+    std::vector<int> blist;
+    for (int c = 0; c < kNumClasses; ++c) {
+        h->cls_off[c] = (int)blist.size();
+        for (int k = 0; k < p; ++k)
+            if (class_of(cs[k]) == c) blist.push_back(k);
+    }
+    h->cls_off[kNumClasses] = (int)blist.size();
+    put(img, L.blist, blist);
+}
+
+void make_dev(cdsdp* h) {
+    const HostProblem& hp = h->hp;
+    const Layout& L = h->L;
+    unsigned char* w = h->ws;
+    Dev& d = h->dev;
+    d.n = hp.n; d.m = hp.m; d.NE = (int)hp.prow.size(); d.p = (int)hp.cl_off.size() - 1; d.nd = (int)hp.gmap.size();
+    d.diag_factor = hp.diag_factor ? 1 : 0;
+    d.c = (const double*)(w + L.c); d.dinv = (const double*)(w + L.dinv); d.pinv = (const double*)(w + L.pinv);
+    d.wgt = (const double*)(w + L.wgt);
+    d.a_ptr = (const int*)(w + L.a_ptr); d.a_col = (const int*)(w + L.a_col); d.a_valw = (const double*)(w + L.a_valw);
+    d.at_ptr = (const int*)(w + L.at_ptr); d.at_col = (const int*)(w + L.at_col); d.at_val = (const double*)(w + L.at_val);
+    d.b = (const double*)(w + L.b); d.minv = (const double*)(w + L.minv); d.kinv = (const double*)(w + L.kinv);
+    d.gmap = (const int*)(w + L.gmap); d.pk_off = (const int*)(w + L.pk_off); d.csize = (const int*)(w + L.csize);
+    d.sc_ptr = (const int*)(w + L.sc_ptr); d.sc_idx = (const int*)(w + L.sc_idx);
+    d.zhx = (const double*)(w + L.zhx); d.zhy = (const double*)(w + L.zhy);
+    d.atb = (const double*)(w + L.atb); d.azhx = (const double*)(w + L.azhx);
+    d.zeta_dot_zhat = hp.zeta_dot_zhat; d.norm_b = hp.norm_b; d.norm_c = hp.norm_c;
+    d.x = (double*)(w + L.x); d.t = (double*)(w + L.t); d.q = (double*)(w + L.q); d.s11 = (double*)(w + L.s11);
+    d.atuy = (double*)(w + L.atuy);
+    d.y = (double*)(w + L.y); d.g = (double*)(w + L.g); d.hh = (double*)(w + L.hh); d.s21 = (double*)(w + L.s21);
+    d.as11 = (double*)(w + L.as11);
+    d.ck0 = w + L.ck0; d.ck1 = w + L.ck1; d.ck2 = w + L.ck2;
+    d.part = (double*)(w + L.part); d.parte = (double*)(w + L.parte); d.partr = (double*)(w + L.partr);
+    d.scal = (double*)(w + L.scal); d.ctl = (int*)(w + L.ctl); d.hist = (double*)(w + L.hist);
+    d.max_iter = h->ws_max_iter;
+    h->GE = std::max(1, std::min(NBLK_E, (d.NE + ETHREADS - 1) / ETHREADS));
+    h->GR = std::max(1, std::min(NBLK_R, (d.m + (RTHREADS / 32) - 1) / (RTHREADS / 32)));
+}
+
+// ---- projection dispatch ----------------------------------------------------
+
+template <typename T, int MAXS>
+cudaError_t launch_proj_class(cdsdp* h, int form, const int* list, int nlist, const cdsdp_opts& o, cudaStream_t st) {
+    if (nlist <= 0) return cudaSuccess;
+    const size_t smem = 4 * WarpTile<T, MAXS>::bytes;
+    const int grid = std::min((nlist + 3) / 4, 152 * 32);
+    const double tolrel = sizeof(T) == 4 ? 1.2e-7 : 2.3e-16;
+    static bool attr_set[3] = {false, false, false};
+    if (form == 0) {
+        if (!attr_set[0]) { cudaFuncSetAttribute(k_project_primal<T, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr_set[0] = true; }
+        k_project_primal<T, MAXS><<<grid, 128, smem, st>>>(h->dev, list, nlist, o.rho, tolrel, o.jacobi_max_sweeps);
+    } else if (form == 1) {
+        if (!attr_set[1]) { cudaFuncSetAttribute(k_project_dual<T, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr_set[1] = true; }
+        k_project_dual<T, MAXS><<<grid, 128, smem, st>>>(h->dev, list, nlist, o.rho, tolrel, o.jacobi_max_sweeps);
+    } else {
+        if (!attr_set[2]) { cudaFuncSetAttribute(k_project_hsde<T, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr_set[2] = true; }
+        k_project_hsde<T, MAXS><<<grid, 128, smem, st>>>(h->dev, list, nlist, tolrel, o.jacobi_max_sweeps);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, cudaStream_t st) {
+    const int* bl = (const int*)(h->ws + h->L.blist);
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < kNumClasses && e == cudaSuccess; ++c) {
+        const int* list = bl + h->cls_off[c];
+        const int nl = h->cls_off[c + 1] - h->cls_off[c];
+        switch (kClasses[c]) {
+            case 4: e = launch_proj_class<T, 4>(h, form, list, nl, o, st); break;
+            case 8: e = launch_proj_class<T, 8>(h, form, list, nl, o, st); break;
+            case 12: e = launch_proj_class<T, 12>(h, form, list, nl, o, st); break;
+            case 16: e = launch_proj_class<T, 16>(h, form, list, nl, o, st); break;
+            case 24: e = launch_proj_class<T, 24>(h, form, list, nl, o, st); break;
+            case 32: e = launch_proj_class<T, 32>(h, form, list, nl, o, st); break;
+        }
+    }
+    return e;
+}
+
+// ---- one ADMM iteration -----------------------------------------------------
+
+template <typename T>
+cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream_t st, int use_cond,
+                             cudaGraphConditionalHandle hnd, cudaEvent_t ev0, cudaEvent_t ev1) {
+    Dev& d = h->dev;
+    const int GE = h->GE, GR = h->GR, PG = std::max(1, std::min((d.p + 3) / 4, 152 * 32));
+    const double rho = o.rho;
+    cudaError_t e;
+    if (form == 0) {  // Algorithm 1
+        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0 / rho, 1.0, 1.0 / rho, d.dinv, d.t, 1);
+        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, d.g);
+        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0);
+        k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (ev0) cudaEventRecord(ev0, st);
+        if ((e = launch_projection<T>(h, 0, o, st)) != cudaSuccess) return e;
+        if (ev1) cudaEventRecord(ev1, st);
+        k_finish_primal<<<1, 256, 0, st>>>(d, rho, o.eps, GE, GR, use_cond, hnd);
+    } else if (form == 1) {  // Algorithm 2
+        if (ev0) cudaEventRecord(ev0, st);
+        if ((e = launch_projection<T>(h, 1, o, st)) != cudaSuccess) return e;
+        if (ev1) cudaEventRecord(ev1, st);
+        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0 / rho, d.dinv, d.t, 1);
+        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0 / rho, d.g);
+        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0);
+        k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x);
+        k_vlam_dual<T><<<PG, 128, 0, st>>>(d, rho);
+        k_finish_dual<<<1, 256, 0, st>>>(d, rho, o.eps, GE, GR, use_cond, hnd);
+    } else {  // Algorithm 3
+        k_hsde_eta<T><<<GE, ETHREADS, 0, st>>>(d);
+        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.q, 0.0, d.g);
+        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.kinv, d.g, d.hh, -1);
+        k_hsde_sigma11<<<GE, ETHREADS, 0, st>>>(d);
+        k_hsde_sigma21<<<GR, RTHREADS, 0, st>>>(d);
+        k_hsde_gamma<<<1, 256, 0, st>>>(d, GE, GR);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (ev0) cudaEventRecord(ev0, st);
+        if ((e = launch_projection<T>(h, 2, o, st)) != cudaSuccess) return e;
+        if (ev1) cudaEventRecord(ev1, st);
+        k_hsde_entry_update<T><<<GE, ETHREADS, 0, st>>>(d);
+        k_hsde_row_update<<<GR, RTHREADS, 0, st>>>(d);
+        k_finish_hsde<<<1, 256, 0, st>>>(d, o.eps, GE, GR, use_cond, hnd);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iteration_any(cdsdp* h, int form, const cdsdp_opts& o, cudaStream_t st, int use_cond,
+                                 cudaGraphConditionalHandle hnd, cudaEvent_t ev0 = nullptr,
+                                 cudaEvent_t ev1 = nullptr) {
+    return o.precision == CDSDP_FP64 ? launch_iteration<double>(h, form, o, st, use_cond, hnd, ev0, ev1)
+                                     : launch_iteration<float>(h, form, o, st, use_cond, hnd, ev0, ev1);
+}
+
+bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
+    return a.eps == b.eps && a.max_iter == b.max_iter && a.rho == b.rho && a.precision == b.precision &&
+           a.jacobi_max_sweeps == b.jacobi_max_sweeps;
+}
+
+void drop_graph(cdsdp* h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    h->g_form = -1;
+}
+
+// The whole solve as one graph: a while node whose body is one iteration;
+// the iteration's last kernel clears the condition when the solve is done.
+int build_graph(cdsdp* h, int form, const cdsdp_opts& o) {
+    drop_graph(h);
+    CK(cudaGraphCreate(&h->graph, 0));
+    cudaGraphConditionalHandle hnd;
+    CK(cudaGraphConditionalHandleCreate(&hnd, h->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hnd;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = launch_iteration_any(h, form, o, cs, 1, hnd);
+        e = cudaStreamEndCapture(cs, &body);
+        if (e2 != cudaSuccess) e = e2;
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) { drop_graph(h); return fail_cuda(h, e, "graph capture"); }
+    e = cudaGraphInstantiate(&h->gexec, h->graph, 0);
+    if (e != cudaSuccess) { drop_graph(h); return fail_cuda(h, e, "cudaGraphInstantiate"); }
+    h->g_form = form;
+    h->g_opts = o;
+    return CDSDP_SOLVED;
+}
+
+int check_opts(const cdsdp* h, const cdsdp_opts& o) {
+    if (!(o.eps >= 0) || o.max_iter < 1 || !(o.rho > 0) || o.jacobi_max_sweeps < 1 || o.check_every < 1) return CDSDP_ERR_ARG;
+    if (o.precision != CDSDP_FP32_PROJECTION && o.precision != CDSDP_FP64) return CDSDP_ERR_ARG;
+    if (o.max_iter > h->ws_max_iter) return CDSDP_ERR_ARG;
+    if (o.warm_start != 0) return CDSDP_ERR_ARG;
+    return CDSDP_SOLVED;
+}
+
+int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, double* hist, double* cert) {
+    Dev& d = h->dev;
+    const int form = h->last_form;
+    const int NE = d.NE, m = d.m;
+    const bool fp64 = h->g_opts.precision == CDSDP_FP64;
+    double* tmpE = d.t;  // scratch after the solve
+    double* tmpM = d.g;
+    const double* tau = d.scal + SC_TAU;
+    const double rho = h->g_opts.rho;
+    if (X) {
+        if (form == 0) k_scale_out<<<64, 256, 0, st>>>(NE, d.x, 1.0, nullptr, tmpE);
+        else if (form == 1) k_scale_out<<<64, 256, 0, st>>>(NE, d.x, -rho, nullptr, tmpE);
+        else k_scale_out<<<64, 256, 0, st>>>(NE, d.x, 1.0, tau, tmpE);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(X, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (y) {
+        if (form == 0) k_scale_out<<<8, 256, 0, st>>>(m, d.y, -rho, nullptr, tmpM);
+        else if (form == 1) k_scale_out<<<8, 256, 0, st>>>(m, d.y, 1.0, nullptr, tmpM);
+        else k_scale_out<<<8, 256, 0, st>>>(m, d.y, 1.0, tau, tmpM);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(y, tmpM, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (Z) {
+        const void* src = form == 0 ? d.ck1 : (form == 1 ? d.ck0 : d.ck1);  // lambda, z, v_z
+        if (fp64) k_scatter<double><<<h->GE, ETHREADS, 0, st>>>(d, (const double*)src, nullptr, 0.0, 1.0, 0.0, nullptr, tmpE, 0);
+        else k_scatter<float><<<h->GE, ETHREADS, 0, st>>>(d, (const float*)src, nullptr, 0.0, 1.0, 0.0, nullptr, tmpE, 0);
+        if (form == 2) k_scale_out<<<64, 256, 0, st>>>(NE, tmpE, 1.0, tau, tmpE);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(Z, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (hist && h->last_iters > 0) {
+        CK(cudaMemcpyAsync(hist, d.hist, (size_t)h->last_iters * HIST_COLS * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (cert && form == 2) {
+        if (h->last_status == CDSDP_PRIMAL_INFEASIBLE) {  // u_y / (b^T u_y)
+            double* dots = d.scal + 8;
+            k_dot<<<1, 256, 0, st>>>(m, d.y, d.b, nullptr, dots);
+            k_scale_out<<<8, 256, 0, st>>>(m, d.y, 1.0, dots, tmpM);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(cert, tmpM, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        } else if (h->last_status == CDSDP_DUAL_INFEASIBLE) {  // -u_x / (c^T u_x)
+            double* dots = d.scal + 8;
+            k_dot<<<1, 256, 0, st>>>(NE, d.x, d.c, d.wgt, dots);
+            k_scale_out<<<64, 256, 0, st>>>(NE, d.x, 1.0, dots, tmpE);
+            k_scale_out<<<64, 256, 0, st>>>(NE, tmpE, -1.0, nullptr, tmpE);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(cert, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+    }
+    return CDSDP_SOLVED;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+
+extern "C" {
+
+void cdsdp_default_opts(cdsdp_opts* o) {
+    if (!o) return;
+    o->eps = 1e-4;
+    o->max_iter = 2000;
+    o->rho = 1.0;
+    o->precision = CDSDP_FP32_PROJECTION;
+    o->use_graph = 1;
+    o->check_every = 50;
+    o->jacobi_max_sweeps = 30;
+    o->warm_start = 0;
+    o->profile = 0;
+}
+
+int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
+                const double* b, long long nnzC, const int* C_row, const int* C_col, const double* C_val,
+                long long nnzP, const int* P_row, const int* P_col, cdsdp** out) {
+    if (!out) return CDSDP_ERR_ARG;
+    *out = nullptr;
+    cdsdp* h = new (std::nothrow) cdsdp();
+    if (!h) return CDSDP_ERR_NOMEM;
+    int st;
+    try {
+        st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val,
+                                            nnzP, P_row, P_col, h->hp);
+    } catch (const std::bad_alloc&) {
+        st = CDSDP_ERR_NOMEM;
+    }
+    if (st != CDSDP_SOLVED) { delete h; return st; }
+    *out = h;
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_info(const cdsdp* h, cdsdp_info_t* info) {
+    if (!h || !info) return CDSDP_ERR_ARG;
+    const HostProblem& hp = h->hp;
+    info->n = hp.n;
+    info->m = hp.m;
+    info->p = (int)hp.cl_off.size() - 1;
+    info->max_clique = hp.max_clique;
+    info->nnz_pattern = (long long)hp.prow.size();
+    info->n_d_lower = (long long)hp.gmap.size();
+    info->nnz_A = (long long)hp.a_col.size();
+    info->n_fill = hp.nfill;
+    info->chordal = hp.chordal ? 1 : 0;
+    info->diag_factor = hp.diag_factor ? 1 : 0;
+    info->upload_bytes = (long long)make_layout(hp, 1).const_end;
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_cliques(const cdsdp* h, int* offsets, int* vertices) {
+    if (!h || !offsets || !vertices) return CDSDP_ERR_ARG;
+    std::copy(h->hp.cl_off.begin(), h->hp.cl_off.end(), offsets);
+    std::copy(h->hp.cl_vert.begin(), h->hp.cl_vert.end(), vertices);
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_pattern(const cdsdp* h, int* rows, int* cols) {
+    if (!h || !rows || !cols) return CDSDP_ERR_ARG;
+    std::copy(h->hp.prow.begin(), h->hp.prow.end(), rows);
+    std::copy(h->hp.pcol.begin(), h->hp.pcol.end(), cols);
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_workspace_bytes(const cdsdp* h, int max_iter, size_t* bytes) {
+    if (!h || !bytes || max_iter < 1) return CDSDP_ERR_ARG;
+    *bytes = make_layout(h->hp, max_iter).total;
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_bind(cdsdp* h, void* d_workspace, size_t bytes, int max_iter, void* stream) {
+    if (!h || !d_workspace || max_iter < 1) return CDSDP_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) return CDSDP_ERR_ARG;
+    if (h->hp.max_clique > 32) return CDSDP_ERR_UNSUPPORTED;
+    Layout L = make_layout(h->hp, max_iter);
+    if (bytes < L.total) return CDSDP_ERR_NOMEM;
+    drop_graph(h);
+    h->L = L;
+    h->ws = (unsigned char*)d_workspace;
+    h->ws_bytes = bytes;
+    h->ws_max_iter = max_iter;
+    try {
+        build_image(h);
+    } catch (const std::bad_alloc&) {
+        h->ws = nullptr;
+        return CDSDP_ERR_NOMEM;
+    }
+    make_dev(h);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(h->ws, h->image.data(), h->image.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double* X, double* y, double* Z,
+                double* hist, int* iters, double* cert) {
+    if (!h) return CDSDP_ERR_ARG;
+    if (!h->ws) return CDSDP_ERR_STATE;
+    if (form < 0 || form > 2) return CDSDP_ERR_ARG;
+    cdsdp_opts o;
+    if (opts) o = *opts; else cdsdp_default_opts(&o);
+    int rc = check_opts(h, o);
+    if (rc != CDSDP_SOLVED) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Dev& d = h->dev;
+    d.max_iter = o.max_iter;
+    // zero the state (clique vectors, iterates, partials, history)
+    CK(cudaMemsetAsync(h->ws + h->L.const_end, 0, h->L.total - h->L.const_end, st));
+    k_init<<<1, 32, 0, st>>>(d, form);
+    CK(cudaGetLastError());
+    h->last_profiled = false;
+    if (o.profile) {
+        // 4 events per iteration: iteration start, projection start/end, iteration end
+        const size_t need = (size_t)4 * o.max_iter;
+        while (h->ev.size() < need) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            h->ev.push_back(e);
+        }
+        int ctl[CTL_WORDS];
+        int launched = 0;
+        for (int it = 0; it < o.max_iter; ++it) {
+            CK(cudaEventRecord(h->ev[4 * it], st));
+            CK(launch_iteration_any(h, form, o, st, 0, cudaGraphConditionalHandle{}, h->ev[4 * it + 1], h->ev[4 * it + 2]));
+            CK(cudaEventRecord(h->ev[4 * it + 3], st));
+            ++launched;
+            if ((it + 1) % o.check_every == 0 || it + 1 == o.max_iter) {
+                CK(cudaMemcpyAsync(ctl, d.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (ctl[CTL_DONE]) break;
+            }
+        }
+        CK(cudaStreamSynchronize(st));
+        CK(cudaMemcpyAsync(ctl, d.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int ran = std::min(launched, ctl[CTL_ITER]);
+        h->prof_proj_ms = h->prof_iter_ms = 0.0;
+        for (int it = 0; it < ran; ++it) {
+            float a = 0.f, b = 0.f;
+            CK(cudaEventElapsedTime(&a, h->ev[4 * it + 1], h->ev[4 * it + 2]));
+            CK(cudaEventElapsedTime(&b, h->ev[4 * it], h->ev[4 * it + 3]));
+            h->prof_proj_ms += a;
+            h->prof_iter_ms += b;
+        }
+        h->prof_launches = ran;
+        h->last_profiled = true;
+    } else if (o.use_graph) {
+        if (!h->gexec || h->g_form != form || !same_opts(h->g_opts, o)) {
+            rc = build_graph(h, form, o);
+            if (rc != CDSDP_SOLVED) return rc;
+        }
+        CK(cudaGraphLaunch(h->gexec, st));
+    } else {
+        int ctl[CTL_WORDS];
+        for (int it = 0; it < o.max_iter; ++it) {
+            CK(launch_iteration_any(h, form, o, st, 0, cudaGraphConditionalHandle{}));
+            if ((it + 1) % o.check_every == 0 || it + 1 == o.max_iter) {
+                CK(cudaMemcpyAsync(ctl, d.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (ctl[CTL_DONE]) break;
+            }
+        }
+        h->g_opts = o;
+    }
+    int ctl[CTL_WORDS];
+    CK(cudaMemcpyAsync(ctl, d.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h->g_opts = o;
+    h->last_form = form;
+    h->last_iters = ctl[CTL_ITER];
+    h->last_status = ctl[CTL_STATUS];
+    if (iters) *iters = h->last_iters;
+    rc = copy_results(h, st, X, y, Z, hist, cert);
+    if (rc != CDSDP_SOLVED) return rc;
+    return h->last_status;
+}
+
+int cdsdp_results(cdsdp* h, void* stream, double* X, double* y, double* Z, double* hist, double* cert) {
+    if (!h) return CDSDP_ERR_ARG;
+    if (!h->ws || h->last_form < 0) return CDSDP_ERR_STATE;
+    return copy_results(h, (cudaStream_t)stream, X, y, Z, hist, cert);
+}
+
+int cdsdp_profile(const cdsdp* h, double* proj_ms, int* proj_launches, double* iter_ms) {
+    if (!h) return CDSDP_ERR_ARG;
+    if (!h->last_profiled) return CDSDP_ERR_STATE;
+    if (proj_ms) *proj_ms = h->prof_proj_ms;
+    if (proj_launches) *proj_launches = h->prof_launches;
+    if (iter_ms) *iter_ms = h->prof_iter_ms;
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_free(cdsdp* h) {
+    if (!h) return CDSDP_ERR_ARG;
+    drop_graph(h);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    delete h;
+    return CDSDP_SOLVED;
+}
+
+const char* cdsdp_strerror(int s) {
+    switch (s) {
+        case CDSDP_SOLVED: return "solved";
+        case CDSDP_MAX_ITER: return "maximum number of iterations reached";
+        case CDSDP_PRIMAL_INFEASIBLE: return "primal infeasible (certificate returned)";
+        case CDSDP_DUAL_INFEASIBLE: return "dual infeasible (certificate returned)";
+        case CDSDP_ERR_ARG: return "invalid argument";
+        case CDSDP_ERR_RANK: return "A is not full row rank (factorisation failed)";
+        case CDSDP_ERR_CUDA: return "CUDA runtime error";
+        case CDSDP_ERR_NOMEM: return "out of memory or workspace too small";
+        case CDSDP_ERR_TIMEOUT: return "bounded device wait timed out";
+        case CDSDP_ERR_NUMERIC: return "NaN or Inf in the iteration";
+        case CDSDP_ERR_STATE: return "call out of order";
+        case CDSDP_ERR_UNSUPPORTED: return "size not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+int cdsdp_psd_project(int p, const int* d_off, const int* d_size, int max_size, const void* d_W, void* d_X, void* d_eig,
+                      const int* d_voff, void* d_V, const int* d_vvoff, int precision, int max_sweeps, void* stream) {
+    cdsdp* h = nullptr;
+    if (p < 0 || max_size < 1 || max_size > 32 || max_sweeps < 1) return p == 0 ? CDSDP_SOLVED : CDSDP_ERR_ARG;
+    if (p == 0) return CDSDP_SOLVED;
+    if (!d_off || !d_size || !d_W || !d_X) return CDSDP_ERR_ARG;
+    if ((d_eig && !d_voff) || (d_V && !d_vvoff)) return CDSDP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = std::min((p + 3) / 4, 152 * 64);
+    const int c = class_of(max_size);
+#define PROJ_CASE(T, S)                                                                                             \
+    case S: {                                                                                                      \
+        const size_t smem = 4 * WarpTile<T, S>::bytes;                                                            \
+        CK(cudaFuncSetAttribute(k_project_standalone<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        k_project_standalone<T, S><<<grid, 128, smem, st>>>(p, d_off, d_size, (const T*)d_W, (T*)d_X, (T*)d_eig,   \
+                                                            d_voff, (T*)d_V, d_vvoff, sizeof(T) == 4 ? 1.2e-7 : 2.3e-16, \
+                                                            max_sweeps);                                          \
+        break;                                                                                                     \
+    }
+    if (precision == CDSDP_FP64) {
+        switch (kClasses[c]) { PROJ_CASE(double, 4) PROJ_CASE(double, 8) PROJ_CASE(double, 12) PROJ_CASE(double, 16) PROJ_CASE(double, 24) PROJ_CASE(double, 32) }
+    } else if (precision == CDSDP_FP32_PROJECTION) {
+        switch (kClasses[c]) { PROJ_CASE(float, 4) PROJ_CASE(float, 8) PROJ_CASE(float, 12) PROJ_CASE(float, 16) PROJ_CASE(float, 24) PROJ_CASE(float, 32) }
+    } else {
+        return CDSDP_ERR_ARG;
+    }
+#undef PROJ_CASE
+    CK(cudaGetLastError());
+    return CDSDP_SOLVED;
+}
+
+}  // extern "C"

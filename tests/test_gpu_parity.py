@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances.  The FP64 path runs the same algorithm as the oracle with another
+rounding order (lower-packed storage, a cached explicit inverse instead of
+Cholesky solves), so iterates agree to ~1e-12 and must agree to 1e-8 after
+hundreds of iterations (PSD projection and the affine step are
+nonexpansive, so differences do not grow).  The FP32 path projects in float32
+(unit roundoff 6e-8 on clique blocks of order <= 32): each projection is within
+~1e-5 ||W||_F of the exact one, and solutions at eps = 1e-4 must match the
+oracle's to the stopping accuracy: relative objective gap <= 1e-4 and
+primal/dual residuals <= 1e-4 (the workload's stated tolerance)."""
+import numpy as np
+import pytest
+
+from oracle import admm, psd
+from paper_1707_05058_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _pack(blocks):
+    """Lower-packed column-major storage of a list of symmetric blocks."""
+    out = []
+    for B in blocks:
+        s = B.shape[0]
+        for b in range(s):
+            out.extend(B[b:, b].tolist())
+    return np.array(out)
+
+
+def _unpack(vec, sizes):
+    res, o = [], 0
+    for s in sizes:
+        B = np.zeros((s, s))
+        for b in range(s):
+            B[b:, b] = vec[o:o + s - b]
+            B[b, b:] = vec[o:o + s - b]
+            o += s - b
+        res.append(B)
+    return res
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("sizes", [[1, 2, 3], [11] * 300, [15] * 5, [32] * 64,
+                                   list(range(1, 33)) * 3, [4, 8, 12, 16, 24, 32, 7, 5]])
+def test_psd_projection_kernel(lib, torch_cuda, prec, sizes):
+    torch = torch_cuda
+    rng = np.random.default_rng(len(sizes) + sum(sizes))
+    blocks = []
+    for s in sizes:
+        G = W._f32(rng.standard_normal((s, s)) * rng.uniform(0.1, 10))
+        blocks.append(W._f32(0.5 * (G + G.T)))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Wv = torch.tensor(_pack(blocks), dtype=dt, device="cuda")
+    off = torch.tensor(np.concatenate([[0], np.cumsum([s * (s + 1) // 2 for s in sizes])]), dtype=torch.int32, device="cuda")
+    sz = torch.tensor(sizes, dtype=torch.int32, device="cuda")
+    X = lib.psd_project(Wv, off, sz)
+    torch.cuda.synchronize()
+    got = _unpack(X.double().cpu().numpy(), sizes)
+    want = [psd.psd_project(B[None])[0] for B in blocks]
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    for B, g, w in zip(blocks, got, want):
+        assert np.linalg.norm(g - w) <= tol * max(np.linalg.norm(B), 1e-30) * B.shape[0]
+
+
+def test_psd_projection_eigenpairs(lib, torch_cuda):
+    torch = torch_cuda
+    sizes = [9] * 40 + [20] * 10
+    rng = np.random.default_rng(5)
+    blocks = [(lambda G: 0.5 * (G + G.T))(rng.standard_normal((s, s))) for s in sizes]
+    Wv = torch.tensor(_pack(blocks), dtype=torch.float64, device="cuda")
+    off = torch.tensor(np.concatenate([[0], np.cumsum([s * (s + 1) // 2 for s in sizes])]), dtype=torch.int32, device="cuda")
+    sz = torch.tensor(sizes, dtype=torch.int32, device="cuda")
+    eoff = torch.tensor(np.concatenate([[0], np.cumsum(sizes)]), dtype=torch.int32, device="cuda")
+    voff = torch.tensor(np.concatenate([[0], np.cumsum([s * s for s in sizes])]), dtype=torch.int32, device="cuda")
+    X, lam, V = lib.psd_project(Wv, off, sz, eoff, voff, want_eig=True)
+    lam = lam.cpu().numpy(); V = V.cpu().numpy()
+    for k, (B, s) in enumerate(zip(blocks, sizes)):
+        l = lam[eoff[k].item():eoff[k].item() + s]
+        Vk = V[voff[k].item():voff[k].item() + s * s].reshape(s, s, order="F")
+        np.testing.assert_allclose(np.sort(l), np.linalg.eigvalsh(B), atol=1e-12 * np.abs(B).max() * s)
+        np.testing.assert_allclose(Vk.T @ Vk, np.eye(s), atol=1e-12)
+        np.testing.assert_allclose((Vk * l) @ Vk.T, B, atol=1e-11 * np.abs(B).max() * s)
+
+
+def _oracle_lower(dp, v):
+    return dp.lower_values(v)
+
+
+def _solve_both(lib, prob, form, eps, max_iter, prec="fp64", **kw):
+    dp, ref = admm.solve(prob, form, eps=eps, max_iter=max_iter)
+    P = lib.Problem(prob).bind(max_iter=max_iter)
+    out = P.solve(form, eps=eps, max_iter=max_iter, precision=prec, **kw)
+    return dp, ref, P, out
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+@pytest.mark.parametrize("form", ["primal", "dual", "hsde"])
+def test_block_arrow_fp64_matches_oracle(lib, torch_cuda, form, use_graph):
+    """Small block-arrow workload (l=5, d=10, h=5, m=30): FP64 GPU vs oracle:
+    same iteration count, same residual history, same X, y, Z."""
+    prob = W.workload(0)
+    max_iter = 2000 if form != "hsde" else 1200
+    dp, ref, P, out = _solve_both(lib, prob, form, 1e-4, max_iter, use_graph=use_graph, check_every=7)
+    assert out["status"] == ref.status
+    assert abs(out["iters"] - ref.iters) <= 1
+    k = min(out["iters"], ref.iters, 50)
+    np.testing.assert_allclose(out["hist"][:k, :6], ref.hist[:k, :6], rtol=1e-8, atol=1e-10)
+    for name, a, b in (("X", out["X"], _oracle_lower(dp, ref.X)), ("Z", out["Z"], _oracle_lower(dp, ref.Z)),
+                       ("y", out["y"], ref.y)):
+        scale = max(1.0, np.abs(b).max())
+        assert np.abs(a - b).max() <= 1e-7 * scale, name
+
+
+@pytest.mark.parametrize("form", ["primal", "dual", "hsde"])
+def test_block_arrow_fp32_matches_oracle(lib, torch_cuda, form):
+    """FP32-projection form on the small block-arrow workload: solved at
+    eps=1e-4 with objective within 1e-4 of the FP64 oracle's."""
+    prob = W.workload(0)
+    dp, ref, P, out = _solve_both(lib, prob, form, 1e-4, 3000, prec="fp32")
+    assert out["status"] == 0 and ref.status == 0
+    obj_gpu = float(dp.c @ _full(dp, out["X"]))
+    obj_ref = float(dp.c @ ref.X)
+    assert abs(obj_gpu - obj_ref) <= 1e-4 * abs(obj_ref)
+    rp, rd, gap = _kkt(dp, out)
+    assert max(rp, rd) <= 5e-4
+
+
+def _full(dp, lower_vals):
+    x = np.zeros(dp.N)
+    for (i, j), v in zip(dp.lower, lower_vals):
+        x[dp.full_index[(i, j)]] = v
+        x[dp.full_index[(j, i)]] = v
+    return x
+
+
+def _kkt(dp, out):
+    X, Z = _full(dp, out["X"]), _full(dp, out["Z"])
+    y = out["y"]
+    rp = np.linalg.norm(dp.A @ X - dp.b) / (1 + np.linalg.norm(dp.b))
+    rd = np.linalg.norm(dp.A.T @ y + Z - dp.c) / (1 + np.linalg.norm(dp.c))
+    cx, by = dp.c @ X, dp.b @ y
+    return rp, rd, abs(cx - by) / (1 + abs(cx) + abs(by))
+
+
+CLOSED = [W.lambda_max_tridiagonal(8, 1.0, 0.5), W.lovasz_theta_cycle(5), W.maxcut_cycle(5),
+          W.maxcut_cycle(6), W.maxcut_cycle(31)]
+
+
+@pytest.mark.parametrize("form", ["primal", "dual", "hsde"])
+@pytest.mark.parametrize("prob", CLOSED, ids=lambda p: p.name)
+def test_closed_forms_on_gpu(lib, torch_cuda, prob, form):
+    dp = admm.decompose(prob)
+    P = lib.Problem(prob).bind(max_iter=20000)
+    out = P.solve(form, eps=1e-8, max_iter=20000, precision="fp64")
+    assert out["status"] == 0
+    obj = float(dp.c @ _full(dp, out["X"]))
+    assert abs(obj - prob.optimum) <= 1e-6 * max(1, abs(prob.optimum))
+
+
+def test_hsde_infeasibility_on_gpu(lib, torch_cuda):
+    P = lib.Problem(W.primal_infeasible()).bind(max_iter=5000)
+    out = P.solve("hsde", eps=1e-6, max_iter=5000, precision="fp64")
+    assert out["status"] == lib.PRIMAL_INFEASIBLE
+    np.testing.assert_allclose(out["cert"], [-1.0], atol=1e-5)
+    prob = W.dual_infeasible()
+    dp = admm.decompose(prob)
+    P = lib.Problem(prob).bind(max_iter=5000)
+    out = P.solve("hsde", eps=1e-6, max_iter=5000, precision="fp64")
+    assert out["status"] == lib.DUAL_INFEASIBLE
+    x = _full(dp, out["cert"])
+    assert abs(dp.c @ x + 1) < 1e-9 and np.linalg.norm(dp.A @ x) < 1e-5
+
+
+def test_banded_full_size_trajectory(lib, torch_cuda):
+    """Banded n=2000, w=10, m=500 (1990 cliques of size 11) at full size, in
+    the graph configuration the benchmark times: the first 15 FP64 iterates
+    equal the oracle's."""
+    prob = W.workload(1)
+    dp = admm.decompose(prob)
+    ref = admm.primal_admm(dp, eps=0.0, max_iter=15)
+    P = lib.Problem(prob).bind(max_iter=15)
+    out = P.solve("primal", eps=0.0, max_iter=15, precision="fp64")
+    assert out["iters"] == 15 and out["status"] == lib.MAX_ITER
+    np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-9, atol=1e-12)
+    Xr = _oracle_lower(dp, ref.X)
+    assert np.abs(out["X"] - Xr).max() <= 1e-9 * np.abs(Xr).max()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_banded_full_size_converges(lib, torch_cuda, prec):
+    """Banded workload solved to eps=1e-4: KKT residuals of the returned
+    (X, y, Z), computed here independently, are <= 1e-4 (primal/dual) and every
+    clique block of X is PSD (Grone, Theorem 1)."""
+    prob = W.workload(1)
+    dp = admm.decompose(prob)
+    P = lib.Problem(prob).bind(max_iter=2000)
+    out = P.solve("primal", eps=1e-4, max_iter=2000, precision=prec)
+    assert out["status"] == 0
+    rp, rd, gap = _kkt(dp, out)
+    assert rp <= 1e-4 and rd <= 1e-4
+    X = _full(dp, out["X"])
+    for ix, cl in zip(dp.clique_idx[::97], dp.cliques[::97]):
+        blk = X[ix].reshape(len(cl), len(cl), order="F")
+        assert np.linalg.eigvalsh(blk).min() >= -1e-5 * np.abs(blk).max()
+
+
+def test_repeat_solves_identical(lib, torch_cuda):
+    """Deterministic reductions: two solves give bit-identical results."""
+    P = lib.Problem(W.workload(0)).bind(max_iter=500)
+    a = P.solve("primal", eps=1e-5, max_iter=500)
+    b = P.solve("primal", eps=1e-5, max_iter=500)
+    assert a["iters"] == b["iters"]
+    np.testing.assert_array_equal(a["X"], b["X"])
+    np.testing.assert_array_equal(a["hist"], b["hist"])
