@@ -261,10 +261,12 @@ __global__ void k_init(Dev d, int form) {
     }
 }
 
-// out = scale * in (scale from a device scalar when sptr != nullptr: 1/ *sptr)
+// out = scale * in, or scale * in / *sptr: mode 1 divides only when *sptr > 0
+// (the tau of Algorithm 3), mode 2 always divides (certificate normalisation).
 __global__ void k_scale_out(int n, const double* __restrict__ in, double scale, const double* sptr,
-                            double* __restrict__ out) {
-    const double sc = sptr ? (*sptr > 0 ? scale / *sptr : scale) : scale;
+                            double* __restrict__ out, int mode = 1) {
+    double sc = scale;
+    if (sptr && (mode == 2 || *sptr > 0)) sc = scale / *sptr;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = sc * in[i];
 }
 

@@ -370,14 +370,13 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
         if (h->last_status == CDSDP_PRIMAL_INFEASIBLE) {  // u_y / (b^T u_y)
             double* dots = d.scal + 8;
             k_dot<<<1, 256, 0, st>>>(m, d.y, d.b, nullptr, dots);
-            k_scale_out<<<8, 256, 0, st>>>(m, d.y, 1.0, dots, tmpM);
+            k_scale_out<<<8, 256, 0, st>>>(m, d.y, 1.0, dots, tmpM, 2);
             CK(cudaGetLastError());
             CK(cudaMemcpyAsync(cert, tmpM, m * sizeof(double), cudaMemcpyDeviceToHost, st));
         } else if (h->last_status == CDSDP_DUAL_INFEASIBLE) {  // -u_x / (c^T u_x)
             double* dots = d.scal + 8;
             k_dot<<<1, 256, 0, st>>>(NE, d.x, d.c, d.wgt, dots);
-            k_scale_out<<<64, 256, 0, st>>>(NE, d.x, 1.0, dots, tmpE);
-            k_scale_out<<<64, 256, 0, st>>>(NE, tmpE, -1.0, nullptr, tmpE);
+            k_scale_out<<<64, 256, 0, st>>>(NE, d.x, -1.0, dots, tmpE, 2);
             CK(cudaGetLastError());
             CK(cudaMemcpyAsync(cert, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
         }
