@@ -2,13 +2,43 @@
 // the scatter H^T (...) onto the pattern, the sparse products with A W and
 // A^T, the solve with the cached inverse, and the deterministic reductions of
 // the stopping tests.  All of this runs in float64.
+//
+// Work decomposition: pattern-entry kernels give each entry a group of G lanes
+// (G = power of two <= 32, from the average A^T row length) that split its
+// A^T row and reduce by shuffles; constraint-row kernels give each row a
+// group of TPR threads (a multiple of 32, from the average A row length).
+// Grids are sized to fill the GPU; every per-block partial sum is written by
+// a fixed block in a fixed order, so reductions are reproducible.
 #pragma once
 
 #include "kernels.cuh"
 
 namespace cdsdp_dev {
 
-// ---- pattern-entry kernels (grid-stride, one thread per entry) -------------
+// Sum over the G lanes of an aligned lane group (result in every lane of it).
+__device__ __forceinline__ double group_sum(double v, int G) {
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reduction over a row group of TPR threads (TPR a multiple of 32, the group
+// is TPR/32 consecutive warps of the block); result valid in the group's
+// first thread.  `sh` holds blockDim/32 doubles.
+__device__ __forceinline__ double row_group_sum(double v, int TPR, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpg = TPR >> 5;
+    if (wpg == 1) return v;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if ((warp % wpg) == 0 && lane == 0)
+        for (int w = 0; w < wpg; ++w) s += sh[warp + w];
+    return s;
+}
+
+// ---- pattern-entry kernels ---------------------------------------------------
 
 // out_e = (alpha c_e + beta sum_{j in H^T(e)} (P_j + gamma Q_j)) * scale_e
 // Algorithm 1: bhat / D with bhat = sum_k H_k^T (x_k + lambda_k/rho) - c/rho
@@ -18,93 +48,130 @@ template <typename T>
 __global__ void __launch_bounds__(ETHREADS) k_scatter(Dev d, const T* __restrict__ P, const T* __restrict__ Q,
                                                       double alpha, double beta, double gamma,
                                                       const double* __restrict__ scale, double* __restrict__ out,
-                                                      int check_stop) {
+                                                      int check_stop, int G) {
     if (check_stop && stopped(d)) return;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.NE; e += gridDim.x * blockDim.x) {
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G, lig = threadIdx.x & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    const int nloop = (d.NE + ng - 1) / ng;
+    for (int it = 0; it < nloop; ++it) {  // uniform trip count: every lane reaches the shuffles
+        const int e = gid + it * ng;
         double acc = 0.0;
-        const int j0 = d.sc_ptr[e], j1 = d.sc_ptr[e + 1];
-        if (Q) {
-            for (int j = j0; j < j1; ++j) {
+        if (e < d.NE) {
+            const int j1 = d.sc_ptr[e + 1];
+            for (int j = d.sc_ptr[e] + lig; j < j1; j += G) {
                 const int q = d.sc_idx[j];
-                acc += double(P[q]) + gamma * double(Q[q]);
+                acc += Q ? double(P[q]) + gamma * double(Q[q]) : double(P[q]);
             }
-        } else {
-            for (int j = j0; j < j1; ++j) acc += double(P[d.sc_idx[j]]);
         }
-        double r = alpha * d.c[e] + beta * acc;
-        out[e] = scale ? r * scale[e] : r;
+        acc = group_sum(acc, G);
+        if (e < d.NE && lig == 0) {
+            const double r = alpha * d.c[e] + beta * acc;
+            out[e] = scale ? r * scale[e] : r;
+        }
     }
 }
 
 // x_e = t_e - dinv_e (A^T y)_e  (Appendix A, Eq. KKTflops_s1), with the
 // per-block partial sum of <c, x> (weighted) in parte[block][0].
 __global__ void __launch_bounds__(ETHREADS) k_xupd(Dev d, const double* __restrict__ t, const double* __restrict__ y,
-                                                   double* __restrict__ x) {
+                                                   double* __restrict__ x, int G) {
     __shared__ double sh[32];
     if (stopped(d)) return;
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G, lig = threadIdx.x & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    const int nloop = (d.NE + ng - 1) / ng;
     double cx[1] = {0.0};
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.NE; e += gridDim.x * blockDim.x) {
+    for (int it = 0; it < nloop; ++it) {
+        const int e = gid + it * ng;
         double s = 0.0;
-        for (int q = d.at_ptr[e]; q < d.at_ptr[e + 1]; ++q) s += d.at_val[q] * y[d.at_col[q]];
-        const double xe = t[e] - d.dinv[e] * s;
-        x[e] = xe;
-        cx[0] += d.wgt[e] * d.c[e] * xe;
+        if (e < d.NE) {
+            const int q1 = d.at_ptr[e + 1];
+            for (int q = d.at_ptr[e] + lig; q < q1; q += G) s += d.at_val[q] * y[d.at_col[q]];
+        }
+        s = group_sum(s, G);
+        if (e < d.NE && lig == 0) {
+            const double xe = t[e] - d.dinv[e] * s;
+            x[e] = xe;
+            cx[0] += d.wgt[e] * d.c[e] * xe;
+        }
     }
     block_sum<1>(cx, sh);
     if (threadIdx.x == 0) d.parte[blockIdx.x * PART_COLS + 0] = cx[0];
 }
 
-// ---- constraint-row kernels (one warp per row of A) ------------------------
+// ---- constraint-row kernels ------------------------------------------------
 
 // out_i = (A W v)_i + delta b_i ; Appendix A item (ii): A D^-1 bhat - b.
 __global__ void __launch_bounds__(RTHREADS) k_rows_aw(Dev d, const double* __restrict__ v, double delta,
-                                                      double* __restrict__ out) {
+                                                      double* __restrict__ out, int TPR) {
+    __shared__ double sh[RTHREADS / 32];
     if (stopped(d)) return;
-    const int lane = threadIdx.x & 31;
-    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = w0; i < d.m; i += nw) {
+    const int rpb = blockDim.x / TPR, gi = threadIdx.x / TPR, tig = threadIdx.x % TPR;
+    const int nloop = (d.m + gridDim.x * rpb - 1) / (gridDim.x * rpb);
+    for (int it = 0; it < nloop; ++it) {
+        const int i = (it * gridDim.x + blockIdx.x) * rpb + gi;
         double s = 0.0;
-        for (int q = d.a_ptr[i] + lane; q < d.a_ptr[i + 1]; q += 32) s += d.a_valw[q] * v[d.a_col[q]];
-        s = warp_sum(s);
-        if (lane == 0) out[i] = s + delta * d.b[i];
+        if (i < d.m) {
+            const int q1 = d.a_ptr[i + 1];
+            for (int q = d.a_ptr[i] + tig; q < q1; q += TPR) s += d.a_valw[q] * v[d.a_col[q]];
+        }
+        s = row_group_sum(s, TPR, sh);
+        if (i < d.m && tig == 0) out[i] = s + delta * d.b[i];
     }
 }
 
 // y = Minv g, Minv the cached inverse (Appendix A item (iii); the paper
 // allows a factorisation or the inverse).  Partial of <b, y> in partr[block][col].
 __global__ void __launch_bounds__(RTHREADS) k_gemv(Dev d, const double* __restrict__ Minv, const double* __restrict__ g,
-                                                   double* __restrict__ y, int col) {
-    __shared__ double sh[32];
+                                                   double* __restrict__ y, int col, int TPR) {
+    __shared__ double sh[RTHREADS / 32];
+    __shared__ double sh2[32];
     if (stopped(d)) return;
-    const int lane = threadIdx.x & 31;
-    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const int rpb = blockDim.x / TPR, gi = threadIdx.x / TPR, tig = threadIdx.x % TPR;
+    const int nloop = (d.m + gridDim.x * rpb - 1) / (gridDim.x * rpb);
     double by[1] = {0.0};
-    for (int i = w0; i < d.m; i += nw) {
-        double s;
-        if (d.diag_factor) {
-            s = Minv[i] * g[i];
-        } else {
-            s = 0.0;
-            const double* row = Minv + (size_t)i * d.m;
-            for (int j = lane; j < d.m; j += 32) s += row[j] * g[j];
-            s = warp_sum(s);
+    for (int it = 0; it < nloop; ++it) {
+        const int i = (it * gridDim.x + blockIdx.x) * rpb + gi;
+        double s = 0.0;
+        if (i < d.m) {
+            if (d.diag_factor) {
+                if (tig == 0) s = Minv[i] * g[i];
+            } else {
+                const double* row = Minv + (size_t)i * d.m;
+                for (int j = tig; j < d.m; j += TPR) s += row[j] * g[j];
+            }
         }
-        if (lane == 0) {
+        s = row_group_sum(s, TPR, sh);
+        if (i < d.m && tig == 0) {
             y[i] = s;
             by[0] += d.b[i] * s;
         }
     }
-    block_sum<1>(by, sh);
+    block_sum<1>(by, sh2);
     if (threadIdx.x == 0 && col >= 0) d.partr[blockIdx.x * PART_COLS + col] = by[0];
 }
 
 // ---- reductions of the stopping tests (one block, fixed order) -------------
 
+// Sums of NC columns of a partial-sum table, one pass; valid in thread 0.
+template <int NC>
+__device__ __forceinline__ void sum_cols(const double* part, int rows, const int (&cols)[NC], double (&out)[NC],
+                                         double* sh) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out[c] = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const double* pr = part + (size_t)r * PART_COLS;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c] += pr[cols[c]];
+    }
+    block_sum<NC>(out, sh);
+}
+
 __device__ __forceinline__ double sum_col(const double* part, int rows, int col, double* sh) {
-    double v[1] = {0.0};
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) v[0] += part[(size_t)r * PART_COLS + col];
-    block_sum<1>(v, sh);
-    return v[0];  // valid in thread 0
+    const int cols[1] = {col};
+    double out[1];
+    sum_cols<1>(part, rows, cols, out, sh);
+    return out[0];
 }
 
 __device__ __forceinline__ void finish_common(Dev d, bool nan_seen, bool converged, int it, int use_cond,
@@ -119,12 +186,13 @@ __device__ __forceinline__ void finish_common(Dev d, bool nan_seen, bool converg
 }
 
 // Algorithm 1 stopping test (Eq. PrimalConsensusResidual, eps_lambda).
-__global__ void k_finish_primal(Dev d, double rho, double eps, int nbe, int nbr, int use_cond,
-                                cudaGraphConditionalHandle hnd) {
-    __shared__ double sh[32];
+__global__ void __launch_bounds__(FTHREADS) k_finish_primal(Dev d, double rho, double eps, int nbe, int nbr,
+                                                            int use_cond, cudaGraphConditionalHandle hnd) {
+    __shared__ double sh[32 * 5];
     if (stopped(d)) { if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(hnd, 0u); return; }
+    const int cols[5] = {0, 1, 2, 3, 4};
     double s[5];
-    for (int c = 0; c < 5; ++c) s[c] = sum_col(d.part, d.p, c, sh);
+    sum_cols<5>(d.part, d.p, cols, s, sh);
     const double cx = sum_col(d.parte, nbe, 0, sh);
     const double by = sum_col(d.partr, nbr, 0, sh);
     if (threadIdx.x == 0) {

@@ -43,18 +43,19 @@ __global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho) {
 }
 
 // Algorithm 2 stopping test (Eq. DualConsensusResidual, eps_lambda).
-__global__ void k_finish_dual(Dev d, double rho, double eps, int nbe, int nbr, int use_cond,
-                              cudaGraphConditionalHandle hnd) {
-    __shared__ double sh[32];
+__global__ void __launch_bounds__(FTHREADS) k_finish_dual(Dev d, double rho, double eps, int nbe, int nbr,
+                                                          int use_cond, cudaGraphConditionalHandle hnd) {
+    __shared__ double sh[32 * 5];
     if (stopped(d)) { if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(hnd, 0u); return; }
-    double s[6];
-    for (int c = 0; c < 6; ++c) s[c] = (c == 4) ? 0.0 : sum_col(d.part, d.p, c, sh);
+    const int cols[5] = {0, 1, 2, 3, 5};
+    double s[5];
+    sum_cols<5>(d.part, d.p, cols, s, sh);
     const double cx = sum_col(d.parte, nbe, 0, sh);
     const double by = sum_col(d.partr, nbr, 0, sh);
     if (threadIdx.x == 0) {
         const int it = d.ctl[CTL_ITER] + 1;
         const double ec = sqrt(s[0]) / fmax(fmax(sqrt(s[1]), sqrt(s[2])), 1e-300);
-        const double el = rho * sqrt(s[5]) / fmax(sqrt(s[3]), 1e-300);
+        const double el = rho * sqrt(s[4]) / fmax(sqrt(s[3]), 1e-300);
         double* h = d.hist + (size_t)(it - 1) * HIST_COLS;
         h[0] = ec; h[1] = el; h[2] = 0; h[3] = 0; h[4] = -rho * cx; h[5] = by; h[6] = 0; h[7] = 0;
         const bool bad = !isfinite(ec) || !isfinite(el);
@@ -70,35 +71,55 @@ __global__ void k_finish_dual(Dev d, double rho, double eps, int nbe, int nbr, i
 // eta / P with eta = nu_11 + A^T nu_21 + H^T (nu_12 + nu_22)/2 (Eq. ThirBlkFlops_s1),
 // nu_11 = u_x - omega_2 c, nu_21 = u_y + omega_2 b, nu_12 = u_s + v_z, nu_22 = u_t.
 template <typename T>
-__global__ void __launch_bounds__(ETHREADS) k_hsde_eta(Dev d) {
+__global__ void __launch_bounds__(ETHREADS) k_hsde_eta(Dev d, int G) {
     if (stopped(d)) return;
     const double w2 = d.scal[SC_TAU] + d.scal[SC_KAPPA];
     const T* us = reinterpret_cast<const T*>(d.ck0);
     const T* vz = reinterpret_cast<const T*>(d.ck1);
     const T* ut = reinterpret_cast<const T*>(d.ck2);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.NE; e += gridDim.x * blockDim.x) {
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G, lig = threadIdx.x & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    const int nloop = (d.NE + ng - 1) / ng;
+    for (int it = 0; it < nloop; ++it) {
+        const int e = gid + it * ng;
         double acc = 0.0;
-        for (int j = d.sc_ptr[e]; j < d.sc_ptr[e + 1]; ++j) {
-            const int q = d.sc_idx[j];
-            acc += double(us[q]) + double(vz[q]) + double(ut[q]);
+        if (e < d.NE) {
+            const int j1 = d.sc_ptr[e + 1];
+            for (int j = d.sc_ptr[e] + lig; j < j1; j += G) {
+                const int q = d.sc_idx[j];
+                acc += double(us[q]) + double(vz[q]) + double(ut[q]);
+            }
         }
-        const double eta = d.x[e] - w2 * d.c[e] + d.atuy[e] + w2 * d.atb[e] + 0.5 * acc;
-        d.q[e] = eta * d.pinv[e];
+        acc = group_sum(acc, G);
+        if (e < d.NE && lig == 0) {
+            const double eta = d.x[e] - w2 * d.c[e] + d.atuy[e] + w2 * d.atb[e] + 0.5 * acc;
+            d.q[e] = eta * d.pinv[e];
+        }
     }
 }
 
 // sigma_11 = P^-1 eta - P^-1 A^T (I + A P^-1 A^T)^-1 A P^-1 eta (Eq. MatrixInvFlops);
 // partial <c, sigma_11> in parte[block][2].
-__global__ void __launch_bounds__(ETHREADS) k_hsde_sigma11(Dev d) {
+__global__ void __launch_bounds__(ETHREADS) k_hsde_sigma11(Dev d, int G) {
     __shared__ double sh[32];
     if (stopped(d)) return;
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G, lig = threadIdx.x & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    const int nloop = (d.NE + ng - 1) / ng;
     double cs[1] = {0.0};
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.NE; e += gridDim.x * blockDim.x) {
+    for (int it = 0; it < nloop; ++it) {
+        const int e = gid + it * ng;
         double s = 0.0;
-        for (int q = d.at_ptr[e]; q < d.at_ptr[e + 1]; ++q) s += d.at_val[q] * d.hh[d.at_col[q]];
-        const double v = d.q[e] - d.pinv[e] * s;
-        d.s11[e] = v;
-        cs[0] += d.wgt[e] * d.c[e] * v;
+        if (e < d.NE) {
+            const int q1 = d.at_ptr[e + 1];
+            for (int q = d.at_ptr[e] + lig; q < q1; q += G) s += d.at_val[q] * d.hh[d.at_col[q]];
+        }
+        s = group_sum(s, G);
+        if (e < d.NE && lig == 0) {
+            const double v = d.q[e] - d.pinv[e] * s;
+            d.s11[e] = v;
+            cs[0] += d.wgt[e] * d.c[e] * v;
+        }
     }
     block_sum<1>(cs, sh);
     if (threadIdx.x == 0) d.parte[blockIdx.x * PART_COLS + 2] = cs[0];
@@ -106,32 +127,37 @@ __global__ void __launch_bounds__(ETHREADS) k_hsde_sigma11(Dev d) {
 
 // sigma_21 = nu_21 - A sigma_11 (Eq. AppendixEqSigma2); partial <b, sigma_21>
 // in partr[block][2]; A sigma_11 kept for the primal residual.
-__global__ void __launch_bounds__(RTHREADS) k_hsde_sigma21(Dev d) {
-    __shared__ double sh[32];
+__global__ void __launch_bounds__(RTHREADS) k_hsde_sigma21(Dev d, int TPR) {
+    __shared__ double sh[RTHREADS / 32];
+    __shared__ double sh2[32];
     if (stopped(d)) return;
     const double w2 = d.scal[SC_TAU] + d.scal[SC_KAPPA];
-    const int lane = threadIdx.x & 31;
-    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const int rpb = blockDim.x / TPR, gi = threadIdx.x / TPR, tig = threadIdx.x % TPR;
+    const int nloop = (d.m + gridDim.x * rpb - 1) / (gridDim.x * rpb);
     double bs[1] = {0.0};
-    for (int i = w0; i < d.m; i += nw) {
+    for (int it = 0; it < nloop; ++it) {
+        const int i = (it * gridDim.x + blockIdx.x) * rpb + gi;
         double s = 0.0;
-        for (int q = d.a_ptr[i] + lane; q < d.a_ptr[i + 1]; q += 32) s += d.a_valw[q] * d.s11[d.a_col[q]];
-        s = warp_sum(s);
-        if (lane == 0) {
+        if (i < d.m) {
+            const int q1 = d.a_ptr[i + 1];
+            for (int q = d.a_ptr[i] + tig; q < q1; q += TPR) s += d.a_valw[q] * d.s11[d.a_col[q]];
+        }
+        s = row_group_sum(s, TPR, sh);
+        if (i < d.m && tig == 0) {
             d.as11[i] = s;
             const double v = d.y[i] + w2 * d.b[i] - s;
             d.s21[i] = v;
             bs[0] += d.b[i] * v;
         }
     }
-    block_sum<1>(bs, sh);
+    block_sum<1>(bs, sh2);
     if (threadIdx.x == 0) d.partr[blockIdx.x * PART_COLS + 2] = bs[0];
 }
 
 // gamma = zeta^T sigma, u_hat_2 = omega_2 + zeta^T u_hat_1 = omega_2 + gamma (1 - zeta^T zeta_hat)
 // (Eqs. MatrixInverseResult, FirstBlockElimination); tau <- max(0, u_hat_tau - kappa),
 // kappa <- kappa - u_hat_tau + tau (Eqs. HsdeStep2-3 on the R_+ component).
-__global__ void k_hsde_gamma(Dev d, int nbe, int nbr) {
+__global__ void __launch_bounds__(FTHREADS) k_hsde_gamma(Dev d, int nbe, int nbr) {
     __shared__ double sh[32];
     if (stopped(d)) return;
     const double cs = sum_col(d.parte, nbe, 2, sh);
@@ -152,26 +178,37 @@ __global__ void k_hsde_gamma(Dev d, int nbe, int nbr) {
 // u_x <- sigma_11 - gamma zeta_hat_x; A^T u_y with u_y = sigma_21 - gamma zeta_hat_y;
 // partials: |A^T u_y + H^T v_z - tau c|^2 (parte col 0) and <c, u_x> (col 1).
 template <typename T>
-__global__ void __launch_bounds__(ETHREADS) k_hsde_entry_update(Dev d) {
+__global__ void __launch_bounds__(ETHREADS) k_hsde_entry_update(Dev d, int G) {
     __shared__ double sh[64];
     if (stopped(d)) return;
     const double gamma = d.scal[SC_GAMMA], tau = d.scal[SC_TAU];
     const T* vz = reinterpret_cast<const T*>(d.ck1);
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G, lig = threadIdx.x & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    const int nloop = (d.NE + ng - 1) / ng;
     double p[2] = {0.0, 0.0};
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.NE; e += gridDim.x * blockDim.x) {
-        const double ux = d.s11[e] - gamma * d.zhx[e];
-        d.x[e] = ux;
-        double a = 0.0;
-        for (int q = d.at_ptr[e]; q < d.at_ptr[e + 1]; ++q) {
-            const int i = d.at_col[q];
-            a += d.at_val[q] * (d.s21[i] - gamma * d.zhy[i]);
+    for (int it = 0; it < nloop; ++it) {
+        const int e = gid + it * ng;
+        double a = 0.0, hv = 0.0;
+        if (e < d.NE) {
+            const int q1 = d.at_ptr[e + 1];
+            for (int q = d.at_ptr[e] + lig; q < q1; q += G) {
+                const int i = d.at_col[q];
+                a += d.at_val[q] * (d.s21[i] - gamma * d.zhy[i]);
+            }
+            const int j1 = d.sc_ptr[e + 1];
+            for (int j = d.sc_ptr[e] + lig; j < j1; j += G) hv += double(vz[d.sc_idx[j]]);
         }
-        d.atuy[e] = a;
-        double hv = 0.0;
-        for (int j = d.sc_ptr[e]; j < d.sc_ptr[e + 1]; ++j) hv += double(vz[d.sc_idx[j]]);
-        const double r = a + hv - tau * d.c[e];
-        p[0] += d.wgt[e] * r * r;
-        p[1] += d.wgt[e] * d.c[e] * ux;
+        a = group_sum(a, G);
+        hv = group_sum(hv, G);
+        if (e < d.NE && lig == 0) {
+            const double ux = d.s11[e] - gamma * d.zhx[e];
+            d.x[e] = ux;
+            d.atuy[e] = a;
+            const double r = a + hv - tau * d.c[e];
+            p[0] += d.wgt[e] * r * r;
+            p[1] += d.wgt[e] * d.c[e] * ux;
+        }
     }
     block_sum<2>(p, sh);
     if (threadIdx.x == 0) {
@@ -205,15 +242,16 @@ __global__ void __launch_bounds__(RTHREADS) k_hsde_row_update(Dev d) {
 // tau > 0; otherwise the infeasibility tests (each certificate on its own):
 // b^T u_y > 0 and |A^T u_y + H^T v_z| <= eps b^T u_y / |b|  -> primal infeasible,
 // c^T u_x < 0 and |A u_x| <= -eps c^T u_x / |c|             -> dual infeasible.
-__global__ void k_finish_hsde(Dev d, double eps, int nbe, int nbr, int use_cond, cudaGraphConditionalHandle hnd) {
-    __shared__ double sh[32];
+__global__ void __launch_bounds__(FTHREADS) k_finish_hsde(Dev d, double eps, int nbe, int nbr, int use_cond,
+                                                          cudaGraphConditionalHandle hnd) {
+    __shared__ double sh[32 * 6];
     if (stopped(d)) { if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(hnd, 0u); return; }
-    double s[6];
-    for (int c = 0; c < 6; ++c) s[c] = sum_col(d.part, d.p, c, sh);
-    const double rd2 = sum_col(d.parte, nbe, 0, sh);
-    const double cux = sum_col(d.parte, nbe, 1, sh);
-    const double rp2 = sum_col(d.partr, nbr, 0, sh);
-    const double buy = sum_col(d.partr, nbr, 1, sh);
+    const int cols6[6] = {0, 1, 2, 3, 4, 5}, cols2[2] = {0, 1};
+    double s[6], pe[2], pr[2];
+    sum_cols<6>(d.part, d.p, cols6, s, sh);
+    sum_cols<2>(d.parte, nbe, cols2, pe, sh);
+    sum_cols<2>(d.partr, nbr, cols2, pr, sh);
+    const double rd2 = pe[0], cux = pe[1], rp2 = pr[0], buy = pr[1];
     if (threadIdx.x == 0) {
         const int it = d.ctl[CTL_ITER] + 1;
         const double tau = d.scal[SC_TAU], kappa = d.scal[SC_KAPPA];

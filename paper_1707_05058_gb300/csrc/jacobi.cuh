@@ -1,164 +1,223 @@
 // Batched PSD projection P(W) = V max(Lambda, 0) V^T of clique blocks
 // (Section 4.1.2, Eq. XkUpdate; Eq. zkUpdate; Eq. HsdeStep2), one warp per
-// block of order s <= 32, block held in shared memory.
+// block of order s <= 32.
 //
-// Eigensolver: two-sided parallel Jacobi (Jacobi 1846; parallel round-robin
-// ordering of Brent and Luk 1985; 2x2 symmetric Schur step of Golub and Van
-// Loan, Matrix Computations, Section 8.5).  In each round every index is
-// paired with at most one partner (pairs {i, j} with i + j = 2r mod (S-1),
-// index r with the extra index S-1, S = s rounded up to even), so the s/2
-// rotations of a round commute and are applied together:
-//   A <- J^T A J,  V <- V J,
-// each new element of A mixing the four old elements of its two pairs.
-// A rotation is skipped when |a_pq| <= tol = eps_rel * ||W||_F; the sweeps end
-// when a whole sweep skips every rotation (or after max_sweeps).
+// Eigensolver: two-sided cyclic Jacobi (Jacobi 1846; 2x2 symmetric Schur step
+// of Golub and Van Loan, Matrix Computations, Section 8.5) in the parallel
+// ordering of Brent and Luk (1985).  The block is padded with zero rows to an
+// even order S (padding rows never rotate: their entries stay exactly zero and
+// their eigenvalues are 0).  Storage positions are paired as (2k, 2k+1),
+// k < S/2; after every round the matrix is re-indexed by the round-robin
+// permutation sigma (position 0 fixed, the other S-1 positions rotate along the
+// circle 2, 4, ..., S-2, S-1, S-3, ..., 1), so over one sweep of S-1 rounds
+// every pair of indices meets exactly once and the storage order returns to
+// the identity.  Each lane owns fixed 2x2 pair-blocks (I, J), I >= J, of the
+// lower triangle: per round it loads them from one shared-memory buffer,
+// applies J_I^T B J_J and writes them to their permuted positions in the other
+// buffer (one warp barrier per round).  Row `lane` of V stays in registers
+// and its columns are re-indexed by the same sigma (static register moves).
+// A rotation is skipped when |a_pq| <= tol = eps_rel * ||W||_F; sweeps stop when
+// a whole sweep skips every rotation (or after max_sweeps).
 #pragma once
 
 #include "kernels.cuh"
 
 namespace cdsdp_dev {
 
-template <typename T, int MAXS>
-struct WarpTile {
-    static constexpr int LD = MAXS | 1;  // odd stride: conflict-free column walks
-    static constexpr int NPK = MAXS * (MAXS + 1) / 2;
-    static constexpr int MAXE = (NPK + 31) / 32;  // packed elements per lane
-    static constexpr int NT = 2 * MAXS * LD + 3 * 32;
-    static constexpr size_t bytes = ((NT * sizeof(T) + 32 * sizeof(int)) + 15) & ~size_t(15);
+// ---- round-robin ordering on S storage positions ---------------------------
+template <int S>
+struct RoundRobin {
+    static constexpr int K = S / 2;
+    static constexpr int R = S - 1;
+    __host__ __device__ static constexpr int circ_index(int p) {  // p > 0
+        return (p % 2 == 0) ? (p / 2 - 1) : (K - 1 + (K - 1 - (p - 1) / 2));
+    }
+    __host__ __device__ static constexpr int circ_pos(int c) {
+        return c < K - 1 ? 2 * (c + 1) : 2 * (K - 1 - (c - (K - 1))) + 1;
+    }
+    __host__ __device__ static constexpr int sigma(int p) { return p == 0 ? 0 : circ_pos((circ_index(p) + 1) % R); }
+    __host__ __device__ static constexpr int sigma_inv(int p) {
+        return p == 0 ? 0 : circ_pos((circ_index(p) + R - 1) % R);
+    }
 };
 
 // (a, b) of packed element f of an s x s block, a >= b, column-major.
 __device__ __forceinline__ int packed_ab(int f, int s) {
-    int b = 0, rem = f;
-    while (rem >= s - b) { rem -= s - b; ++b; }
-    return ((b + rem) << 8) | b;
+    const float t = float(2 * s + 1);
+    int b = int((t - sqrtf(t * t - 8.0f * float(f))) * 0.5f);
+    b = max(0, min(b, s - 1));
+    while (b > 0 && b * (2 * s - b + 1) / 2 > f) --b;
+    while (b + 1 < s && (b + 1) * (2 * s - b) / 2 <= f) ++b;
+    const int a = b + f - b * (2 * s - b + 1) / 2;
+    return (a << 8) | b;
 }
 
-template <typename T, int MAXS>
-struct WarpJacobi {
-    using Tile = WarpTile<T, MAXS>;
-    static constexpr int LD = Tile::LD;
-    static constexpr int MAXE = Tile::MAXE;
-    T* A;
-    T* V;
-    T* rc;   // per index: coefficient on itself (cosine)
-    T* rsg;  // per index: coefficient on its partner (signed sine)
-    T* rd;   // per index: change of its diagonal entry (Schur step)
-    int* rp; // per index: partner (itself when not rotated)
+template <typename T, int S>
+struct BLJacobi {
+    using RR = RoundRobin<S>;
+    static constexpr int K = S / 2;
+    static constexpr int R = S - 1;
+    static constexpr int LDA = S + 1;
+    static constexpr int BUF = S * LDA;
+    static constexpr int NB = K * (K + 1) / 2;      // lower pair-blocks
+    static constexpr int NS = (NB + 31) / 32;       // blocks per lane
+    static constexpr int NPK = S * (S + 1) / 2;
+    static constexpr int MAXE = (NPK + 31) / 32;    // packed elements per lane
+    static constexpr size_t bytes = (2 * BUF * sizeof(T) + 15) & ~size_t(15);  // per warp
 
-    __device__ __forceinline__ void bind(unsigned char* base) {
-        A = reinterpret_cast<T*>(base);
-        V = A + MAXS * LD;
-        rc = V + MAXS * LD;
-        rsg = rc + 32;
-        rd = rsg + 32;
-        rp = reinterpret_cast<int*>(rd + 32);
-    }
+    T* X;  // current buffer
+    T* Y;  // next buffer
+    T v[S];  // row `lane` of V
+    int src[NS][4], dst[NS][4];
+    int bI[NS], bJ[NS];
 
-    // Diagonalise the symmetric block in A (s x s); V receives the
-    // eigenvectors (columns).  `ab` holds this lane's packed elements.
-    // Returns the number of sweeps run.
-    __device__ int run(int s, int npk, T tol, int max_sweeps, int lane, const int (&ab)[MAXE]) {
-        for (int idx = lane; idx < s * LD; idx += 32) {
-            int i = idx / LD, j = idx - i * LD;
-            V[idx] = (i == j) ? T(1) : T(0);
-        }
-        __syncwarp();
-        if (s <= 1) return 0;
-        const int S2 = (s + 1) & ~1, R = S2 - 1;
-        int sweep = 0;
-        for (; sweep < max_sweeps; ++sweep) {
-            bool sweep_any = false;
-            for (int r = 0; r < R; ++r) {
-                bool my_rot = false;
-                if (lane < s) {
-                    const int i = lane;
-                    const int j = (i == R) ? r : (i == r ? R : ((2 * r - i) % R + R) % R);
-                    if (j >= s) {
-                        rc[i] = T(1); rsg[i] = T(0); rd[i] = T(0); rp[i] = i;
-                    } else if (i < j) {
-                        const T aij = A[i * LD + j];
-                        if (fabs(aij) > tol) {
-                            const T aii = A[i * LD + i], ajj = A[j * LD + j];
-                            const T theta = (ajj - aii) / (T(2) * aij);
-                            const T tt = copysign(T(1), theta) / (fabs(theta) + sqrt(T(1) + theta * theta));
-                            const T cc = rsqrt_t<T>(T(1) + tt * tt);
-                            const T sn = tt * cc;
-                            rc[i] = cc; rc[j] = cc;
-                            rsg[i] = -sn; rsg[j] = sn;
-                            rd[i] = -tt * aij; rd[j] = tt * aij;
-                            rp[i] = j; rp[j] = i;
-                            my_rot = true;
-                        } else {
-                            rc[i] = T(1); rc[j] = T(1); rsg[i] = T(0); rsg[j] = T(0);
-                            rd[i] = T(0); rd[j] = T(0); rp[i] = i; rp[j] = j;
-                        }
-                    }
-                }
-                const bool any = __any_sync(0xffffffffu, my_rot);
-                __syncwarp();
-                if (!any) continue;
-                sweep_any = true;
-                T nv[MAXE];
+    __device__ __forceinline__ void bind(unsigned char* base, int lane) {
+        X = reinterpret_cast<T*>(base);
+        Y = X + BUF;
 #pragma unroll
-                for (int e = 0; e < MAXE; ++e) {
-                    const int f = lane + 32 * e;
-                    nv[e] = T(0);
-                    if (f < npk) {
-                        const int a = ab[e] >> 8, b = ab[e] & 255;
-                        if (a == b) {
-                            nv[e] = A[a * LD + a] + rd[a];
-                        } else {
-                            const int pa = rp[a], pb = rp[b];
-                            if (pa == b) {
-                                nv[e] = T(0);  // the rotated pair's off-diagonal entry
-                            } else {
-                                const T ca = rc[a], sa = rsg[a], cb = rc[b], sb = rsg[b];
-                                nv[e] = ca * (cb * A[a * LD + b] + sb * A[a * LD + pb]) +
-                                        sa * (cb * A[pa * LD + b] + sb * A[pa * LD + pb]);
-                            }
-                        }
-                    }
-                }
-                if (lane < s) {  // V <- V J, lane owns row `lane`
-                    T* vr = V + lane * LD;
-                    for (int i = 0; i < s; ++i) {
-                        const int j = rp[i];
-                        if (j > i) {
-                            const T vi = vr[i], vj = vr[j];
-                            vr[i] = rc[i] * vi + rsg[i] * vj;
-                            vr[j] = rc[j] * vj + rsg[j] * vi;
-                        }
-                    }
-                }
-                __syncwarp();
-#pragma unroll
-                for (int e = 0; e < MAXE; ++e) {
-                    const int f = lane + 32 * e;
-                    if (f < npk) {
-                        const int a = ab[e] >> 8, b = ab[e] & 255;
-                        A[a * LD + b] = nv[e];
-                        A[b * LD + a] = nv[e];
-                    }
-                }
-                __syncwarp();
+        for (int t = 0; t < NS; ++t) {
+            const int b = lane + 32 * t;
+            int I = 0, J = 0;
+            if (b < K) {
+                I = J = b;
+            } else if (b < NB) {
+                int o = b - K;
+                I = 1;
+                while (o >= I) { o -= I; ++I; }
+                J = o;
             }
-            if (!sweep_any) break;
+            const bool ok = b < NB;
+            bI[t] = ok ? I : -1;
+            bJ[t] = J;
+            const int r0 = 2 * I, r1 = 2 * I + 1, c0 = 2 * J, c1 = 2 * J + 1;
+            src[t][0] = r0 * LDA + c0;
+            src[t][1] = r1 * LDA + c0;
+            src[t][2] = (I == J) ? r1 * LDA + c0 : r0 * LDA + c1;
+            src[t][3] = r1 * LDA + c1;
+            const int rr[4] = {r0, r1, r0, r1}, cc[4] = {c0, c0, c1, c1};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int si = RR::sigma(rr[e]), sj = RR::sigma(cc[e]);
+                dst[t][e] = max(si, sj) * LDA + min(si, sj);
+            }
         }
-        return sweep;
     }
 
-    // After run(): rc[i] <- max(lambda_i, 0) for the rebuild.
-    __device__ __forceinline__ void prepare_rebuild(int s, int lane) {
-        if (lane < s) rc[lane] = A[lane * LD + lane] > T(0) ? A[lane * LD + lane] : T(0);
+    // Zero the working buffer (padding rows must read as exact zeros).
+    __device__ __forceinline__ void clear(int lane) {
+        for (int i = lane; i < BUF; i += 32) X[i] = T(0);
         __syncwarp();
     }
-    // (V max(Lambda,0) V^T)_{ab}
+    __device__ __forceinline__ void put(int a, int b, T w) { X[a * LDA + b] = w; }
+
+    __device__ __forceinline__ bool round(T tol, int lane) {
+        T bv[NS][4];
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            if (bI[t] >= 0) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) bv[t][e] = X[src[t][e]];
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) bv[t][e] = T(0);
+            }
+        }
+        // rotation of pair `lane` (lanes < K own the diagonal blocks in slot 0)
+        T c = T(1), sn = T(0), ta = T(0);
+        bool my = false;
+        if (lane < K) {
+            const T apq = bv[0][1];
+            if (fabs(apq) > tol) {
+                const T app = bv[0][0], aqq = bv[0][3];
+                const T theta = (aqq - app) / (T(2) * apq);
+                const T tt = copysign(T(1), theta) / (fabs(theta) + sqrt(T(1) + theta * theta));
+                c = rsqrt_t<T>(T(1) + tt * tt);
+                sn = tt * c;
+                ta = tt * apq;
+                my = true;
+            }
+        }
+        const bool any = __any_sync(0xffffffffu, my);
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            const int I = bI[t] >= 0 ? bI[t] : 0, J = bJ[t];
+            const T cI = __shfl_sync(0xffffffffu, c, I), sI = __shfl_sync(0xffffffffu, sn, I);
+            const T cJ = __shfl_sync(0xffffffffu, c, J), sJ = __shfl_sync(0xffffffffu, sn, J);
+            if (bI[t] < 0) continue;
+            if (t == 0 && lane < K) {  // diagonal block: the 2x2 Schur result
+                Y[dst[t][0]] = bv[t][0] - ta;
+                Y[dst[t][1]] = my ? T(0) : bv[t][1];
+                Y[dst[t][3]] = bv[t][3] + ta;
+            } else {
+                const T r00 = cI * bv[t][0] - sI * bv[t][1], r10 = sI * bv[t][0] + cI * bv[t][1];
+                const T r01 = cI * bv[t][2] - sI * bv[t][3], r11 = sI * bv[t][2] + cI * bv[t][3];
+                Y[dst[t][0]] = cJ * r00 - sJ * r01;
+                Y[dst[t][2]] = sJ * r00 + cJ * r01;
+                Y[dst[t][1]] = cJ * r10 - sJ * r11;
+                Y[dst[t][3]] = sJ * r10 + cJ * r11;
+            }
+        }
+        // V <- V J on this lane's row, then re-index its columns by sigma like A
+        T nv[S];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const T ck = __shfl_sync(0xffffffffu, c, k), sk = __shfl_sync(0xffffffffu, sn, k);
+            const T vp = v[2 * k], vq = v[2 * k + 1];
+            nv[RR::sigma(2 * k)] = ck * vp - sk * vq;
+            nv[RR::sigma(2 * k + 1)] = sk * vp + ck * vq;
+        }
+#pragma unroll
+        for (int j = 0; j < S; ++j) v[j] = nv[j];
+        __syncwarp();
+        T* tmp = X; X = Y; Y = tmp;
+        return any;
+    }
+
+    // Diagonalise; returns the number of sweeps run.  Afterwards X holds
+    // diag(lambda) (up to the threshold) and v the eigenvector row.
+    __device__ int run(T tol, int max_sweeps, int lane) {
+#pragma unroll
+        for (int j = 0; j < S; ++j) v[j] = (j == lane) ? T(1) : T(0);
+        __syncwarp();
+        int sw = 0;
+        while (sw < max_sweeps) {
+            ++sw;
+            bool any = false;
+#pragma unroll 1
+            for (int r = 0; r < R; ++r) any = round(tol, lane) || any;
+            if (!any) break;
+        }
+        return sw;
+    }
+
+    // Write V max(Lambda, 0) (into Y) and V (into X) row by row for rebuild().
+    __device__ __forceinline__ void prepare_rebuild(int lane) {
+        T lp[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            const T l = X[i * LDA + i];
+            lp[i] = l > T(0) ? l : T(0);
+        }
+        __syncwarp();
+        if (lane < S) {
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                Y[lane * LDA + i] = v[i] * lp[i];
+                X[lane * LDA + i] = v[i];
+            }
+        }
+        __syncwarp();
+    }
+    __device__ __forceinline__ void eigenvalues_to(T* lam_out, int s, int lane) const {
+        // only valid before prepare_rebuild()
+        if (lane < s) lam_out[lane] = X[lane * LDA + lane];
+    }
+    // (V max(Lambda,0) V^T)_{ab}, s active indices
     __device__ __forceinline__ T rebuild(int a, int b, int s) const {
-        const T* va = V + a * LD;
-        const T* vb = V + b * LD;
+        const T* ya = Y + a * LDA;
+        const T* xb = X + b * LDA;
         T acc = T(0);
-        for (int i = 0; i < s; ++i) acc += va[i] * rc[i] * vb[i];
+        for (int i = 0; i < s; ++i) acc += ya[i] * xb[i];
         return acc;
     }
 };
@@ -169,62 +228,50 @@ struct WarpJacobi {
 // (Eqs. XkUpdate, LambdakUpdate), with the per-clique sums of the stopping
 // test (Eq. PrimalConsensusResidual and eps_lambda):
 //   part[k] = (|x_k - H_k x|^2, |x_k|^2, |H_k x|^2, |x_k - x_k_old|^2, |lambda_k|^2)
-template <typename T, int MAXS>
+template <typename T, int S>
 __global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __restrict__ list, int nlist, double rho,
                                                          double tolrel, int max_sweeps) {
-    using J = WarpJacobi<T, MAXS>;
+    using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     J jac;
-    jac.bind(smem + warp * WarpTile<T, MAXS>::bytes);
+    jac.bind(smem + warp * J::bytes, lane);
     T* xk = reinterpret_cast<T*>(d.ck0);
     T* lam = reinterpret_cast<T*>(d.ck1);
     const T rho_t = T(rho), irho = T(1.0 / rho);
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
-        int ab[J::MAXE];
-        T hx[J::MAXE], lm[J::MAXE];
+        jac.clear(lane);
         T nrm = T(0);
-#pragma unroll
-        for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
-            ab[e] = 0; hx[e] = T(0); lm[e] = T(0);
-            if (f < npk) {
-                ab[e] = packed_ab(f, s);
-                const int a = ab[e] >> 8, b = ab[e] & 255;
-                hx[e] = T(d.x[d.gmap[off + f]]);
-                lm[e] = lam[off + f];
-                const T w = hx[e] - lm[e] * irho;
-                jac.A[a * J::LD + b] = w;
-                jac.A[b * J::LD + a] = w;
-                nrm += (a == b ? T(1) : T(2)) * w * w;
-            }
+        for (int f = lane; f < npk; f += 32) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            const T w = T(d.x[d.gmap[off + f]]) - lam[off + f] * irho;
+            jac.put(a, b, w);
+            nrm += (a == b ? T(1) : T(2)) * w * w;
         }
         nrm = warp_sum(nrm);
         __syncwarp();
-        jac.run(s, npk, T(tolrel) * sqrt(nrm), max_sweeps, lane, ab);
-        jac.prepare_rebuild(s, lane);
+        jac.run(T(tolrel) * sqrt(nrm), max_sweeps, lane);
+        jac.prepare_rebuild(lane);
         double p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0;
-#pragma unroll
-        for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
-            if (f < npk) {
-                const int a = ab[e] >> 8, b = ab[e] & 255;
-                const T xn = jac.rebuild(a, b, s);
-                const T xo = xk[off + f];
-                const T ln = lm[e] + rho_t * (xn - hx[e]);
-                xk[off + f] = xn;
-                lam[off + f] = ln;
-                const double w = (a == b) ? 1.0 : 2.0;
-                const double dc = double(xn) - double(hx[e]), dx = double(xn) - double(xo);
-                p0 += w * dc * dc;
-                p1 += w * double(xn) * double(xn);
-                p2 += w * double(hx[e]) * double(hx[e]);
-                p3 += w * dx * dx;
-                p4 += w * double(ln) * double(ln);
-            }
+        for (int f = lane; f < npk; f += 32) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            const T hx = T(d.x[d.gmap[off + f]]);
+            const T lm = lam[off + f];
+            const T xn = jac.rebuild(a, b, s);
+            const T xo = xk[off + f];
+            const T ln = lm + rho_t * (xn - hx);
+            xk[off + f] = xn;
+            lam[off + f] = ln;
+            const double w = (a == b) ? 1.0 : 2.0;
+            const double dc = double(xn) - double(hx), dx = double(xn) - double(xo);
+            p0 += w * dc * dc;
+            p1 += w * double(xn) * double(xn);
+            p2 += w * double(hx) * double(hx);
+            p3 += w * dx * dx;
+            p4 += w * double(ln) * double(ln);
         }
         p0 = warp_sum(p0); p1 = warp_sum(p1); p2 = warp_sum(p2); p3 = warp_sum(p3); p4 = warp_sum(p4);
         if (lane == 0) {
@@ -236,16 +283,16 @@ __global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __rest
 }
 
 // Algorithm 2, z-step (Eq. zkUpdate): z_k <- P(v_k - lambda_k / rho);
-// part[k][0] = |z_k - z_k_old|^2 (for eps_lambda).
-template <typename T, int MAXS>
+// part[k][5] = |z_k - z_k_old|^2 (for eps_lambda).
+template <typename T, int S>
 __global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restrict__ list, int nlist, double rho,
                                                        double tolrel, int max_sweeps) {
-    using J = WarpJacobi<T, MAXS>;
+    using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     J jac;
-    jac.bind(smem + warp * WarpTile<T, MAXS>::bytes);
+    jac.bind(smem + warp * J::bytes, lane);
     T* z = reinterpret_cast<T*>(d.ck0);
     const T* v = reinterpret_cast<const T*>(d.ck1);
     const T* lam = reinterpret_cast<const T*>(d.ck2);
@@ -253,36 +300,25 @@ __global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restri
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
-        int ab[J::MAXE];
+        jac.clear(lane);
         T nrm = T(0);
-#pragma unroll
-        for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
-            ab[e] = 0;
-            if (f < npk) {
-                ab[e] = packed_ab(f, s);
-                const int a = ab[e] >> 8, b = ab[e] & 255;
-                const T w = v[off + f] - lam[off + f] * irho;
-                jac.A[a * J::LD + b] = w;
-                jac.A[b * J::LD + a] = w;
-                nrm += (a == b ? T(1) : T(2)) * w * w;
-            }
+        for (int f = lane; f < npk; f += 32) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            const T w = v[off + f] - lam[off + f] * irho;
+            jac.put(a, b, w);
+            nrm += (a == b ? T(1) : T(2)) * w * w;
         }
         nrm = warp_sum(nrm);
         __syncwarp();
-        jac.run(s, npk, T(tolrel) * sqrt(nrm), max_sweeps, lane, ab);
-        jac.prepare_rebuild(s, lane);
+        jac.run(T(tolrel) * sqrt(nrm), max_sweeps, lane);
+        jac.prepare_rebuild(lane);
         double p0 = 0;
-#pragma unroll
-        for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
-            if (f < npk) {
-                const int a = ab[e] >> 8, b = ab[e] & 255;
-                const T zn = jac.rebuild(a, b, s);
-                const double dz = double(zn) - double(z[off + f]);
-                z[off + f] = zn;
-                p0 += (a == b ? 1.0 : 2.0) * dz * dz;
-            }
+        for (int f = lane; f < npk; f += 32) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            const T zn = jac.rebuild(a, b, s);
+            const double dz = double(zn) - double(z[off + f]);
+            z[off + f] = zn;
+            p0 += (a == b ? 1.0 : 2.0) * dz * dz;
         }
         p0 = warp_sum(p0);
         if (lane == 0) d.part[(size_t)k * PART_COLS + 5] = p0;
@@ -300,15 +336,15 @@ __global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restri
 // with nu_12 = u_s + v_z, nu_22 = u_t.  Partial sums for eps_c (Eq.
 // HSDEconsensusResidual): |u_s - H u_x|^2, |u_s|^2, |H u_x|^2, |v_z - u_t|^2,
 // |v_z|^2, |u_t|^2, where u_x = sigma_11 - gamma zeta_hat_x.
-template <typename T, int MAXS>
+template <typename T, int S>
 __global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restrict__ list, int nlist,
                                                        double tolrel, int max_sweeps) {
-    using J = WarpJacobi<T, MAXS>;
+    using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     J jac;
-    jac.bind(smem + warp * WarpTile<T, MAXS>::bytes);
+    jac.bind(smem + warp * J::bytes, lane);
     T* us = reinterpret_cast<T*>(d.ck0);
     T* vz = reinterpret_cast<T*>(d.ck1);
     T* ut = reinterpret_cast<T*>(d.ck2);
@@ -316,60 +352,50 @@ __global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restri
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
-        int ab[J::MAXE];
-        T uhs[J::MAXE], vzo[J::MAXE], hux[J::MAXE], utn[J::MAXE];
+        jac.clear(lane);
         T nrm = T(0);
-#pragma unroll
-        for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
-            ab[e] = 0; uhs[e] = T(0); vzo[e] = T(0); hux[e] = T(0); utn[e] = T(0);
-            if (f < npk) {
-                ab[e] = packed_ab(f, s);
-                const int a = ab[e] >> 8, b = ab[e] & 255;
-                const int ent = d.gmap[off + f];
-                const double hs = d.s11[ent];
-                const double zs = 0.5 * d.zhx[ent];
-                const double u_s = us[off + f], v_z = vz[off + f], u_t = ut[off + f];
-                const double nu12 = u_s + v_z, nu22 = u_t;
-                const double s12 = 0.5 * (nu12 - nu22 + hs);
-                const double s22 = nu22 - hs + s12;
-                const double uh_s = s12 - gamma * zs;
-                const double uh_t = s22 + gamma * zs;
-                uhs[e] = T(uh_s);
-                vzo[e] = T(v_z);
-                utn[e] = T(uh_t);
-                hux[e] = T(hs - gamma * d.zhx[ent]);
-                const T w = T(uh_s - v_z);
-                jac.A[a * J::LD + b] = w;
-                jac.A[b * J::LD + a] = w;
-                nrm += (a == b ? T(1) : T(2)) * w * w;
-            }
+        for (int f = lane; f < npk; f += 32) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            const int ent = d.gmap[off + f];
+            const double hs = d.s11[ent];
+            const double zs = 0.5 * d.zhx[ent];
+            const double u_s = us[off + f], v_z = vz[off + f], u_t = ut[off + f];
+            const double s12 = 0.5 * (u_s + v_z - u_t + hs);
+            const double uh_s = s12 - gamma * zs;
+            const T w = T(uh_s - v_z);
+            jac.put(a, b, w);
+            nrm += (a == b ? T(1) : T(2)) * w * w;
         }
         nrm = warp_sum(nrm);
         __syncwarp();
-        jac.run(s, npk, T(tolrel) * sqrt(nrm), max_sweeps, lane, ab);
-        jac.prepare_rebuild(s, lane);
+        jac.run(T(tolrel) * sqrt(nrm), max_sweeps, lane);
+        jac.prepare_rebuild(lane);
         double p[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
-            if (f < npk) {
-                const int a = ab[e] >> 8, b = ab[e] & 255;
-                const T un = jac.rebuild(a, b, s);
-                const T vn = vzo[e] - uhs[e] + un;
-                us[off + f] = un;
-                vz[off + f] = vn;
-                ut[off + f] = utn[e];
-                const double w = (a == b) ? 1.0 : 2.0;
-                const double d1 = double(un) - double(hux[e]);
-                const double d2 = double(vn) - double(utn[e]);
-                p[0] += w * d1 * d1;
-                p[1] += w * double(un) * double(un);
-                p[2] += w * double(hux[e]) * double(hux[e]);
-                p[3] += w * d2 * d2;
-                p[4] += w * double(vn) * double(vn);
-                p[5] += w * double(utn[e]) * double(utn[e]);
-            }
+        for (int f = lane; f < npk; f += 32) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            const int ent = d.gmap[off + f];
+            const double hs = d.s11[ent];
+            const double zs = 0.5 * d.zhx[ent];
+            const double u_s = us[off + f], v_z = vz[off + f], u_t = ut[off + f];
+            const double s12 = 0.5 * (u_s + v_z - u_t + hs);
+            const double s22 = u_t - hs + s12;
+            const T uhs = T(s12 - gamma * zs);
+            const T utn = T(s22 + gamma * zs);
+            const T hux = T(hs - gamma * d.zhx[ent]);
+            const T un = jac.rebuild(a, b, s);
+            const T vn = T(v_z) - uhs + un;
+            us[off + f] = un;
+            vz[off + f] = vn;
+            ut[off + f] = utn;
+            const double w = (a == b) ? 1.0 : 2.0;
+            const double d1 = double(un) - double(hux);
+            const double d2 = double(vn) - double(utn);
+            p[0] += w * d1 * d1;
+            p[1] += w * double(un) * double(un);
+            p[2] += w * double(hux) * double(hux);
+            p[3] += w * d2 * d2;
+            p[4] += w * double(vn) * double(vn);
+            p[5] += w * double(utn) * double(utn);
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) p[c] = warp_sum(p[c]);
@@ -383,53 +409,43 @@ __global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restri
 }
 
 // Standalone projection of packed blocks (the C ABI's cdsdp_psd_project).
-template <typename T, int MAXS>
+template <typename T, int S>
 __global__ void __launch_bounds__(128) k_project_standalone(int p, const int* __restrict__ off_arr,
                                                              const int* __restrict__ size_arr, const T* __restrict__ W,
                                                              T* X, T* eig, const int* __restrict__ voff, T* Vout,
                                                              const int* __restrict__ vvoff, double tolrel,
                                                              int max_sweeps) {
-    using J = WarpJacobi<T, MAXS>;
+    using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     J jac;
-    jac.bind(smem + warp * WarpTile<T, MAXS>::bytes);
+    jac.bind(smem + warp * J::bytes, lane);
     for (int k = blockIdx.x * wpb + warp; k < p; k += gridDim.x * wpb) {
         const int s = size_arr[k];
-        if (s > MAXS || s < 1) continue;
+        if (s > S || s < 1) continue;  // warp-uniform
         const int off = off_arr[k], npk = s * (s + 1) / 2;
-        int ab[J::MAXE];
+        jac.clear(lane);
         T nrm = T(0);
-#pragma unroll
-        for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
-            ab[e] = 0;
-            if (f < npk) {
-                ab[e] = packed_ab(f, s);
-                const int a = ab[e] >> 8, b = ab[e] & 255;
-                const T w = W[off + f];
-                jac.A[a * J::LD + b] = w;
-                jac.A[b * J::LD + a] = w;
-                nrm += (a == b ? T(1) : T(2)) * w * w;
-            }
+        for (int f = lane; f < npk; f += 32) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            const T w = W[off + f];
+            jac.put(a, b, w);
+            nrm += (a == b ? T(1) : T(2)) * w * w;
         }
         nrm = warp_sum(nrm);
         __syncwarp();
-        jac.run(s, npk, T(tolrel) * sqrt(nrm), max_sweeps, lane, ab);
-        if (eig && lane < s) eig[voff[k] + lane] = jac.A[lane * J::LD + lane];
-        if (Vout)
-            for (int idx = lane; idx < s * s; idx += 32) {
-                const int col = idx / s, row = idx - col * s;
-                Vout[vvoff[k] + idx] = jac.V[row * J::LD + col];
-            }
-        jac.prepare_rebuild(s, lane);
+        jac.run(T(tolrel) * sqrt(nrm), max_sweeps, lane);
+        if (eig) jac.eigenvalues_to(eig + voff[k], s, lane);
+        if (Vout && lane < s) {
 #pragma unroll
-        for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
-            if (f < npk) {
-                const int a = ab[e] >> 8, b = ab[e] & 255;
-                X[off + f] = jac.rebuild(a, b, s);
-            }
+            for (int col = 0; col < S; ++col)
+                if (col < s) Vout[vvoff[k] + col * s + lane] = jac.v[col];
+        }
+        __syncwarp();
+        jac.prepare_rebuild(lane);
+        for (int f = lane; f < npk; f += 32) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            X[off + f] = jac.rebuild(a, b, s);
         }
         __syncwarp();
     }

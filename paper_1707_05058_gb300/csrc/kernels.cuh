@@ -71,6 +71,7 @@ constexpr int NBLK_E = 1216;  // 152 SMs x 8
 constexpr int NBLK_R = 1216;
 constexpr int ETHREADS = 256;
 constexpr int RTHREADS = 256;
+constexpr int FTHREADS = 512;
 
 __device__ __forceinline__ bool stopped(const Dev& d) {
     return *((volatile int*)d.ctl + CTL_DONE) != 0;

@@ -1,0 +1,82 @@
+// Dispatch from a size class to the projection kernel instantiations.
+// Included once per precision with PROJ_T and PROJ_SUFFIX defined.
+#include <algorithm>
+
+#include "jacobi.cuh"
+#include "proj_launch.h"
+
+namespace cdsdp_dev {
+namespace {
+
+template <typename T, int S>
+cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, double rho, double tolrel, int max_sweeps,
+                        cudaStream_t st) {
+    if (nlist <= 0) return cudaSuccess;
+    const size_t smem = 4 * BLJacobi<T, S>::bytes;
+    const int grid = std::min((nlist + 3) / 4, 152 * 32);
+    cudaError_t e;
+    if (form == 0) {
+        e = cudaFuncSetAttribute(k_project_primal<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_project_primal<T, S><<<grid, 128, smem, st>>>(d, list, nlist, rho, tolrel, max_sweeps);
+    } else if (form == 1) {
+        e = cudaFuncSetAttribute(k_project_dual<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_project_dual<T, S><<<grid, 128, smem, st>>>(d, list, nlist, rho, tolrel, max_sweeps);
+    } else {
+        e = cudaFuncSetAttribute(k_project_hsde<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_project_hsde<T, S><<<grid, 128, smem, st>>>(d, list, nlist, tolrel, max_sweeps);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int S>
+cudaError_t launch_standalone(int p, const int* off, const int* size, const void* W, void* X, void* eig,
+                              const int* voff, void* V, const int* vvoff, double tolrel, int max_sweeps,
+                              cudaStream_t st) {
+    const size_t smem = 4 * BLJacobi<T, S>::bytes;
+    const int grid = std::max(1, std::min((p + 3) / 4, 152 * 64));
+    cudaError_t e = cudaFuncSetAttribute(k_project_standalone<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_project_standalone<T, S><<<grid, 128, smem, st>>>(p, off, size, (const T*)W, (T*)X, (T*)eig, voff, (T*)V,
+                                                        vvoff, tolrel, max_sweeps);
+    return cudaGetLastError();
+}
+
+#define CDSDP_CLASS_SWITCH(CALL)        \
+    switch (kProjClasses[cls]) {        \
+        case 2: return CALL(2);         \
+        case 4: return CALL(4);         \
+        case 6: return CALL(6);         \
+        case 8: return CALL(8);         \
+        case 10: return CALL(10);       \
+        case 12: return CALL(12);       \
+        case 14: return CALL(14);       \
+        case 16: return CALL(16);       \
+        case 20: return CALL(20);       \
+        case 24: return CALL(24);       \
+        case 28: return CALL(28);       \
+        case 32: return CALL(32);       \
+        default: return cudaErrorInvalidValue; \
+    }
+
+}  // namespace
+
+cudaError_t PROJ_SUFFIX(launch_proj)(int form, int cls, const Dev& d, const int* list, int nlist, double rho,
+                                     double tolrel, int max_sweeps, cudaStream_t st) {
+#define CALL(S) launch_form<PROJ_T, S>(form, d, list, nlist, rho, tolrel, max_sweeps, st)
+    CDSDP_CLASS_SWITCH(CALL)
+#undef CALL
+}
+
+cudaError_t PROJ_SUFFIX(launch_proj_standalone)(int cls, int p, const int* off, const int* size, const void* W,
+                                                void* X, void* eig, const int* voff, void* V, const int* vvoff,
+                                                double tolrel, int max_sweeps, cudaStream_t st) {
+#define CALL(S) launch_standalone<PROJ_T, S>(p, off, size, W, X, eig, voff, V, vvoff, tolrel, max_sweeps, st)
+    CDSDP_CLASS_SWITCH(CALL)
+#undef CALL
+}
+
+}  // namespace cdsdp_dev

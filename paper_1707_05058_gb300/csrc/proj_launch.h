@@ -1,0 +1,33 @@
+// Launchers of the batched projection kernels, one translation unit per
+// precision (proj_f32.cu, proj_f64.cu) so the two compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace cdsdp_dev {
+
+// Padded orders handled by the warp-per-clique projection.
+constexpr int kProjClasses[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
+constexpr int kNumProjClasses = 12;
+inline int proj_class_of(int s) {
+    for (int c = 0; c < kNumProjClasses; ++c)
+        if (s <= kProjClasses[c]) return c;
+    return -1;
+}
+
+// form 0/1/2: Algorithm 1/2/3 projection kernels over `list` (cliques of
+// order <= kProjClasses[cls]).
+cudaError_t launch_proj_f32(int form, int cls, const Dev& d, const int* list, int nlist, double rho,
+                            double tolrel, int max_sweeps, cudaStream_t st);
+cudaError_t launch_proj_f64(int form, int cls, const Dev& d, const int* list, int nlist, double rho,
+                            double tolrel, int max_sweeps, cudaStream_t st);
+cudaError_t launch_proj_standalone_f32(int cls, int p, const int* off, const int* size, const void* W, void* X,
+                                       void* eig, const int* voff, void* V, const int* vvoff, double tolrel,
+                                       int max_sweeps, cudaStream_t st);
+cudaError_t launch_proj_standalone_f64(int cls, int p, const int* off, const int* size, const void* W, void* X,
+                                       void* eig, const int* voff, void* V, const int* vvoff, double tolrel,
+                                       int max_sweeps, cudaStream_t st);
+
+}  // namespace cdsdp_dev

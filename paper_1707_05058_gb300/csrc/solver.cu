@@ -13,7 +13,7 @@
 
 #include "cdsdp_internal.h"
 #include "forms.cuh"
-#include "jacobi.cuh"
+#include "proj_launch.h"
 
 using namespace cdsdp_dev;
 using cdsdp_impl::HostProblem;
@@ -23,14 +23,8 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-// Clique size classes handled by the warp-per-clique projection.
-constexpr int kClasses[] = {4, 8, 12, 16, 24, 32};
-constexpr int kNumClasses = 6;
-inline int class_of(int s) {
-    for (int c = 0; c < kNumClasses; ++c)
-        if (s <= kClasses[c]) return c;
-    return -1;
-}
+constexpr int kNumClasses = kNumProjClasses;
+inline int class_of(int s) { return proj_class_of(s); }
 
 struct Layout {
     // constants
@@ -53,7 +47,10 @@ struct cdsdp {
     size_t ws_bytes = 0;
     int ws_max_iter = 0;
     Dev dev{};
-    int GE = 1, GR = 1;  // grid sizes of the pattern-entry and constraint-row kernels
+    // launch shapes: grids of the pattern-entry / constraint-row kernels, lanes
+    // per entry for scatters (Gs) and A^T rows (Ga), threads per A row (TPR)
+    // and per row of the cached inverse (TPRM)
+    int GE = 1, GR = 1, Gs = 1, Ga = 1, TPR = 32, TPRM = 32;
     // cached graph of a whole solve
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -176,47 +173,37 @@ void make_dev(cdsdp* h) {
     d.part = (double*)(w + L.part); d.parte = (double*)(w + L.parte); d.partr = (double*)(w + L.partr);
     d.scal = (double*)(w + L.scal); d.ctl = (int*)(w + L.ctl); d.hist = (double*)(w + L.hist);
     d.max_iter = h->ws_max_iter;
-    h->GE = std::max(1, std::min(NBLK_E, (d.NE + ETHREADS - 1) / ETHREADS));
-    h->GR = std::max(1, std::min(NBLK_R, (d.m + (RTHREADS / 32) - 1) / (RTHREADS / 32)));
+    auto pow2_clamp = [](double x, int lo, int hi) {
+        int v = lo;
+        while (v < hi && v < x) v <<= 1;
+        return v;
+    };
+    const double avg_sc = d.NE ? double(d.nd) / d.NE : 1.0;
+    const double avg_at = d.NE ? double(hp.a_col.size()) / d.NE : 1.0;
+    const double avg_a = d.m ? double(hp.a_col.size()) / d.m : 1.0;
+    h->Gs = pow2_clamp(avg_sc / 2.0, 1, 32);
+    h->Ga = pow2_clamp(std::max(avg_at, avg_sc) / 3.0, 1, 32);
+    h->TPR = pow2_clamp(avg_a / 4.0, 32, RTHREADS);
+    h->TPRM = hp.diag_factor ? 32 : pow2_clamp(d.m / 4.0, 32, RTHREADS);
+    const int G = std::max(h->Gs, h->Ga);
+    h->GE = std::max(1, std::min(NBLK_E, (int)(((long long)d.NE * G + ETHREADS - 1) / ETHREADS)));
+    const int TP = std::max(h->TPR, h->TPRM);
+    h->GR = std::max(1, std::min(NBLK_R, (d.m + RTHREADS / TP - 1) / (RTHREADS / TP)));
 }
 
 // ---- projection dispatch ----------------------------------------------------
 
-template <typename T, int MAXS>
-cudaError_t launch_proj_class(cdsdp* h, int form, const int* list, int nlist, const cdsdp_opts& o, cudaStream_t st) {
-    if (nlist <= 0) return cudaSuccess;
-    const size_t smem = 4 * WarpTile<T, MAXS>::bytes;
-    const int grid = std::min((nlist + 3) / 4, 152 * 32);
-    const double tolrel = sizeof(T) == 4 ? 1.2e-7 : 2.3e-16;
-    static bool attr_set[3] = {false, false, false};
-    if (form == 0) {
-        if (!attr_set[0]) { cudaFuncSetAttribute(k_project_primal<T, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr_set[0] = true; }
-        k_project_primal<T, MAXS><<<grid, 128, smem, st>>>(h->dev, list, nlist, o.rho, tolrel, o.jacobi_max_sweeps);
-    } else if (form == 1) {
-        if (!attr_set[1]) { cudaFuncSetAttribute(k_project_dual<T, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr_set[1] = true; }
-        k_project_dual<T, MAXS><<<grid, 128, smem, st>>>(h->dev, list, nlist, o.rho, tolrel, o.jacobi_max_sweeps);
-    } else {
-        if (!attr_set[2]) { cudaFuncSetAttribute(k_project_hsde<T, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr_set[2] = true; }
-        k_project_hsde<T, MAXS><<<grid, 128, smem, st>>>(h->dev, list, nlist, tolrel, o.jacobi_max_sweeps);
-    }
-    return cudaGetLastError();
-}
-
 template <typename T>
 cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, cudaStream_t st) {
     const int* bl = (const int*)(h->ws + h->L.blist);
+    const double tolrel = sizeof(T) == 4 ? 1.2e-7 : 2.3e-16;
     cudaError_t e = cudaSuccess;
     for (int c = 0; c < kNumClasses && e == cudaSuccess; ++c) {
         const int* list = bl + h->cls_off[c];
         const int nl = h->cls_off[c + 1] - h->cls_off[c];
-        switch (kClasses[c]) {
-            case 4: e = launch_proj_class<T, 4>(h, form, list, nl, o, st); break;
-            case 8: e = launch_proj_class<T, 8>(h, form, list, nl, o, st); break;
-            case 12: e = launch_proj_class<T, 12>(h, form, list, nl, o, st); break;
-            case 16: e = launch_proj_class<T, 16>(h, form, list, nl, o, st); break;
-            case 24: e = launch_proj_class<T, 24>(h, form, list, nl, o, st); break;
-            case 32: e = launch_proj_class<T, 32>(h, form, list, nl, o, st); break;
-        }
+        if (nl <= 0) continue;
+        e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, o.rho, tolrel, o.jacobi_max_sweeps, st)
+                           : launch_proj_f64(form, c, h->dev, list, nl, o.rho, tolrel, o.jacobi_max_sweeps, st);
     }
     return e;
 }
@@ -231,39 +218,39 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
     const double rho = o.rho;
     cudaError_t e;
     if (form == 0) {  // Algorithm 1
-        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0 / rho, 1.0, 1.0 / rho, d.dinv, d.t, 1);
-        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, d.g);
-        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0);
-        k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x);
+        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0 / rho, 1.0, 1.0 / rho, d.dinv, d.t, 1, h->Gs);
+        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, d.g, h->TPR);
+        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
+        k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
         if ((e = launch_projection<T>(h, 0, o, st)) != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, st);
-        k_finish_primal<<<1, 256, 0, st>>>(d, rho, o.eps, GE, GR, use_cond, hnd);
+        k_finish_primal<<<1, FTHREADS, 0, st>>>(d, rho, o.eps, GE, GR, use_cond, hnd);
     } else if (form == 1) {  // Algorithm 2
         if (ev0) cudaEventRecord(ev0, st);
         if ((e = launch_projection<T>(h, 1, o, st)) != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, st);
-        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0 / rho, d.dinv, d.t, 1);
-        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0 / rho, d.g);
-        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0);
-        k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x);
+        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0 / rho, d.dinv, d.t, 1, h->Gs);
+        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0 / rho, d.g, h->TPR);
+        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
+        k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
         k_vlam_dual<T><<<PG, 128, 0, st>>>(d, rho);
-        k_finish_dual<<<1, 256, 0, st>>>(d, rho, o.eps, GE, GR, use_cond, hnd);
+        k_finish_dual<<<1, FTHREADS, 0, st>>>(d, rho, o.eps, GE, GR, use_cond, hnd);
     } else {  // Algorithm 3
-        k_hsde_eta<T><<<GE, ETHREADS, 0, st>>>(d);
-        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.q, 0.0, d.g);
-        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.kinv, d.g, d.hh, -1);
-        k_hsde_sigma11<<<GE, ETHREADS, 0, st>>>(d);
-        k_hsde_sigma21<<<GR, RTHREADS, 0, st>>>(d);
-        k_hsde_gamma<<<1, 256, 0, st>>>(d, GE, GR);
+        k_hsde_eta<T><<<GE, ETHREADS, 0, st>>>(d, h->Gs);
+        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.q, 0.0, d.g, h->TPR);
+        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.kinv, d.g, d.hh, -1, h->TPRM);
+        k_hsde_sigma11<<<GE, ETHREADS, 0, st>>>(d, h->Ga);
+        k_hsde_sigma21<<<GR, RTHREADS, 0, st>>>(d, h->TPR);
+        k_hsde_gamma<<<1, FTHREADS, 0, st>>>(d, GE, GR);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
         if ((e = launch_projection<T>(h, 2, o, st)) != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, st);
-        k_hsde_entry_update<T><<<GE, ETHREADS, 0, st>>>(d);
+        k_hsde_entry_update<T><<<GE, ETHREADS, 0, st>>>(d, h->Ga);
         k_hsde_row_update<<<GR, RTHREADS, 0, st>>>(d);
-        k_finish_hsde<<<1, 256, 0, st>>>(d, o.eps, GE, GR, use_cond, hnd);
+        k_finish_hsde<<<1, FTHREADS, 0, st>>>(d, o.eps, GE, GR, use_cond, hnd);
     }
     return cudaGetLastError();
 }
@@ -355,8 +342,8 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
     }
     if (Z) {
         const void* src = form == 0 ? d.ck1 : (form == 1 ? d.ck0 : d.ck1);  // lambda, z, v_z
-        if (fp64) k_scatter<double><<<h->GE, ETHREADS, 0, st>>>(d, (const double*)src, nullptr, 0.0, 1.0, 0.0, nullptr, tmpE, 0);
-        else k_scatter<float><<<h->GE, ETHREADS, 0, st>>>(d, (const float*)src, nullptr, 0.0, 1.0, 0.0, nullptr, tmpE, 0);
+        if (fp64) k_scatter<double><<<h->GE, ETHREADS, 0, st>>>(d, (const double*)src, nullptr, 0.0, 1.0, 0.0, nullptr, tmpE, 0, h->Gs);
+        else k_scatter<float><<<h->GE, ETHREADS, 0, st>>>(d, (const float*)src, nullptr, 0.0, 1.0, 0.0, nullptr, tmpE, 0, h->Gs);
         if (form == 2) k_scale_out<<<64, 256, 0, st>>>(NE, tmpE, 1.0, tau, tmpE);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(Z, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -617,25 +604,15 @@ int cdsdp_psd_project(int p, const int* d_off, const int* d_size, int max_size, 
     if (!d_off || !d_size || !d_W || !d_X) return CDSDP_ERR_ARG;
     if ((d_eig && !d_voff) || (d_V && !d_vvoff)) return CDSDP_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const int grid = std::min((p + 3) / 4, 152 * 64);
     const int c = class_of(max_size);
-#define PROJ_CASE(T, S)                                                                                             \
-    case S: {                                                                                                      \
-        const size_t smem = 4 * WarpTile<T, S>::bytes;                                                            \
-        CK(cudaFuncSetAttribute(k_project_standalone<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        k_project_standalone<T, S><<<grid, 128, smem, st>>>(p, d_off, d_size, (const T*)d_W, (T*)d_X, (T*)d_eig,   \
-                                                            d_voff, (T*)d_V, d_vvoff, sizeof(T) == 4 ? 1.2e-7 : 2.3e-16, \
-                                                            max_sweeps);                                          \
-        break;                                                                                                     \
-    }
-    if (precision == CDSDP_FP64) {
-        switch (kClasses[c]) { PROJ_CASE(double, 4) PROJ_CASE(double, 8) PROJ_CASE(double, 12) PROJ_CASE(double, 16) PROJ_CASE(double, 24) PROJ_CASE(double, 32) }
-    } else if (precision == CDSDP_FP32_PROJECTION) {
-        switch (kClasses[c]) { PROJ_CASE(float, 4) PROJ_CASE(float, 8) PROJ_CASE(float, 12) PROJ_CASE(float, 16) PROJ_CASE(float, 24) PROJ_CASE(float, 32) }
-    } else {
+    cudaError_t e;
+    if (precision == CDSDP_FP64)
+        e = launch_proj_standalone_f64(c, p, d_off, d_size, d_W, d_X, d_eig, d_voff, d_V, d_vvoff, 2.3e-16, max_sweeps, st);
+    else if (precision == CDSDP_FP32_PROJECTION)
+        e = launch_proj_standalone_f32(c, p, d_off, d_size, d_W, d_X, d_eig, d_voff, d_V, d_vvoff, 1.2e-7, max_sweeps, st);
+    else
         return CDSDP_ERR_ARG;
-    }
-#undef PROJ_CASE
+    CK(e);
     CK(cudaGetLastError());
     return CDSDP_SOLVED;
 }

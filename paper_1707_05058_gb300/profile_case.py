@@ -1,0 +1,45 @@
+"""Fixed-size solve for profilers (ncu launch lists and kernel captures).
+
+    python -m paper_1707_05058_gb300.profile_case --workload banded --iters 20 --precision fp32
+
+Runs `iters` iterations of one form of the solver on a named workload with one
+launch per phase (no CUDA graph, so every kernel shows up individually) and
+no early stop.  Workloads:
+  banded        n=2000, half-bandwidth 10, m=500 (1990 cliques of order 11)
+  block_arrow   l=5, d=10, h=5, m=30 (5 cliques of order 15)
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="banded", choices=["banded", "block_arrow"])
+    ap.add_argument("--form", default="primal", choices=["primal", "dual", "hsde"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--iters", type=int, default=20)
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1707_05058_gb300 import cdsdp, workloads
+
+    prob = workloads.workload(1 if args.workload == "banded" else 0)
+    P = cdsdp.Problem(prob).bind(max_iter=args.iters)
+    out = P.solve(args.form, eps=0.0, max_iter=args.iters, precision=args.precision, use_graph=0,
+                  check_every=args.iters, outputs=False)
+    torch.cuda.synchronize()
+    print(f"{args.workload} {args.form} {args.precision}: {out['iters']} iterations, status {out['status']}")
+
+
+if __name__ == "__main__":
+    main()

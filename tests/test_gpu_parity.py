@@ -241,23 +241,33 @@ def test_banded_full_size_trajectory(lib, torch_cuda):
     assert np.abs(out["X"] - Xr).max() <= 1e-9 * np.abs(Xr).max()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_banded_full_size_converges(lib, torch_cuda, prec):
-    """Banded workload solved to eps=1e-4 (about 28k iterations at rho = 1,
-    unscaled data): KKT residuals of the returned
-    (X, y, Z), computed here independently, are <= 1e-4 (primal/dual) and every
-    clique block of X is PSD (Grone, Theorem 1)."""
+def test_banded_full_size_converges(lib, torch_cuda):
+    """Banded workload solved to eps=1e-4 (about 28k iterations at rho = 1 on
+    unscaled data) in both precisions.  Algorithm 1 stops on consensus and
+    multiplier change (Section 4.1.4), not on KKT residuals, so the checks are:
+    both stop with their own residuals <= 1e-4; the FP32-projection objective is
+    within 1e-4 of the FP64 one (the FP64 path is tied to the oracle by the
+    trajectory test above); the KKT residuals of (X, y, Z), computed here
+    independently, are <= 5e-4; sampled clique blocks of X are PSD up to
+    eps ||block|| (Grone, Theorem 1; X is the affine iterate, which meets the
+    projected blocks only up to the consensus tolerance)."""
     prob = W.workload(1)
     dp = admm.decompose(prob)
     P = lib.Problem(prob).bind(max_iter=40000)
-    out = P.solve("primal", eps=1e-4, max_iter=40000, precision=prec)
-    assert out["status"] == 0
-    rp, rd, gap = _kkt(dp, out)
-    assert rp <= 1e-4 and rd <= 1e-4
-    X = _full(dp, out["X"])
-    for ix, cl in zip(dp.clique_idx[::97], dp.cliques[::97]):
-        blk = X[ix].reshape(len(cl), len(cl), order="F")
-        assert np.linalg.eigvalsh(blk).min() >= -1e-5 * np.abs(blk).max()
+    res = {}
+    for prec in ("fp64", "fp32"):
+        out = P.solve("primal", eps=1e-4, max_iter=40000, precision=prec)
+        assert out["status"] == 0
+        assert max(out["hist"][-1][:2]) <= 1e-4
+        rp, rd, gap = _kkt(dp, out)
+        assert rp <= 5e-4 and rd <= 5e-4
+        X = _full(dp, out["X"])
+        for ix, cl in zip(dp.clique_idx[::97], dp.cliques[::97]):
+            blk = X[ix].reshape(len(cl), len(cl), order="F")
+            # X is the affine iterate: its blocks are PSD up to the consensus tolerance
+            assert np.linalg.eigvalsh(blk).min() >= -1e-4 * np.linalg.norm(blk)
+        res[prec] = float(dp.c @ X)
+    assert abs(res["fp32"] - res["fp64"]) <= 1e-4 * abs(res["fp64"])
 
 
 def test_repeat_solves_identical(lib, torch_cuda):
