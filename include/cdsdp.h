@@ -188,6 +188,23 @@ int cdsdp_psd_project(int p, const int* d_off, const int* d_size, int max_size,
                       const void* d_W, void* d_X, void* d_eig, const int* d_voff, void* d_V, const int* d_vvoff,
                       int precision, int max_sweeps, void* stream);
 
+/* PSD-violation measure of Section 6.1.3 (Eq. PSD-violation):
+ *   alpha = -min{0, lambda_min(W_0), ..., lambda_min(W_{p-1})}
+ * over p lower-packed symmetric blocks (layout and orders as in
+ * cdsdp_psd_project; order <= 32).  With W_k = mat(H_k x) this is the bound
+ * alpha in the paper's eps_alpha = alpha / (1 + ||X||_F).  One kernel: one warp
+ * per block, per-thread-block minima in d_scratch, final reduction by the last
+ * thread block.
+ *   d_scratch  caller-owned device scratch, 256-byte aligned, at least
+ *              cdsdp_psd_violation_scratch_bytes(p) bytes; its first word is
+ *              cleared on `stream` before the launch
+ *   d_alpha    device pointer receiving alpha (one double)
+ * Asynchronous on `stream`.  Errors: CDSDP_ERR_ARG (p < 1, order out of range,
+ * misaligned scratch), CDSDP_ERR_NOMEM (scratch too small), CDSDP_ERR_CUDA. */
+size_t cdsdp_psd_violation_scratch_bytes(int p);
+int cdsdp_psd_violation(int p, const int* d_off, const int* d_size, int max_size, const void* d_W, int precision,
+                        int max_sweeps, void* d_scratch, size_t scratch_bytes, double* d_alpha, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

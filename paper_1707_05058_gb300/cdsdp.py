@@ -62,9 +62,15 @@ _lib.cdsdp_strerror.restype = ctypes.c_char_p
 _lib.cdsdp_psd_project.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.c_int, ctypes.c_int, _vp]
 
+_lib.cdsdp_psd_violation_scratch_bytes.argtypes = [ctypes.c_int]
+_lib.cdsdp_psd_violation_scratch_bytes.restype = ctypes.c_size_t
+_lib.cdsdp_psd_violation.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp,
+                                     ctypes.c_size_t, _vp, _vp]
+
 EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", "cdsdp_pattern",
             "cdsdp_workspace_bytes", "cdsdp_bind", "cdsdp_solve", "cdsdp_results", "cdsdp_free",
-            "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile"]
+            "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile", "cdsdp_psd_violation_scratch_bytes",
+            "cdsdp_psd_violation"]
 
 
 class CdsdpError(RuntimeError):
@@ -231,3 +237,23 @@ def psd_project(W, offsets, sizes, eig_offsets=None, vec_offsets=None, want_eig=
     if st != 0:
         raise CdsdpError(st, "cdsdp_psd_project")
     return (X, eig, vec) if want_eig else X
+
+
+def psd_violation(W, offsets, sizes, max_sweeps=30, stream=None):
+    """alpha = -min(0, min_k lambda_min(W_k)) of lower-packed blocks (torch
+    CUDA tensors, layout of psd_project); returns a 1-element float64 CUDA
+    tensor.  Scratch comes from a PyTorch allocation."""
+    import torch
+    p = int(sizes.numel())
+    prec = FP64 if W.dtype == torch.float64 else FP32
+    nbytes = _lib.cdsdp_psd_violation_scratch_bytes(p)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=W.device)
+    alpha = torch.empty(1, dtype=torch.float64, device=W.device)
+    maxs = int(sizes.max().item())
+    st = _lib.cdsdp_psd_violation(p, ctypes.c_void_p(offsets.data_ptr()), ctypes.c_void_p(sizes.data_ptr()), maxs,
+                                  ctypes.c_void_p(W.data_ptr()), prec, int(max_sweeps),
+                                  ctypes.c_void_p(scratch.data_ptr()), nbytes, ctypes.c_void_p(alpha.data_ptr()),
+                                  _stream_ptr(stream))
+    if st != 0:
+        raise CdsdpError(st, "cdsdp_psd_violation")
+    return alpha

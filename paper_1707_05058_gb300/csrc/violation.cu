@@ -1,0 +1,162 @@
+// PSD-violation measure of Section 6.1.3 (Eq. PSD-violation) of arXiv 1707.05058:
+//   alpha = -min{0, lambda_min[mat(H_1 x)], ..., lambda_min[mat(H_p x)]}
+// over a batch of lower-packed blocks, in one kernel: one warp per block runs
+// the Jacobi eigensolver of jacobi.cuh, each thread block writes its minimum
+// eigenvalue to scratch, and the last thread block to finish (an atomic
+// counter in scratch) reduces those partials in a fixed order and writes alpha.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "cdsdp_internal.h"
+#include "jacobi.cuh"
+#include "proj_launch.h"
+
+using namespace cdsdp_dev;
+
+namespace {
+
+constexpr int kViolWarps = 4;  // warps (blocks of the batch) per thread block
+
+// Scratch layout: [0, 256) counter (unsigned int), then one double per thread block.
+inline size_t violation_scratch_bytes(int p) {
+    const size_t grid = (size_t)std::max(1, (p + kViolWarps - 1) / kViolWarps);
+    return 256 + grid * sizeof(double);
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(32 * kViolWarps) k_psd_violation(int p, const int* __restrict__ off_arr,
+                                                                    const int* __restrict__ size_arr,
+                                                                    const T* __restrict__ W, double tolrel,
+                                                                    int max_sweeps, unsigned char* scratch,
+                                                                    double* alpha_out) {
+    using J = BLJacobi<T, S>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double wmin[kViolWarps];
+    __shared__ bool last;
+    unsigned int* counter = reinterpret_cast<unsigned int*>(scratch);
+    double* partial = reinterpret_cast<double*>(scratch + 256);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    J jac;
+    jac.bind(smem + warp * J::bytes, lane);
+    double lmin = 0.0;  // min{0, ...}: start from 0
+    const int k = blockIdx.x * kViolWarps + warp;
+    if (k < p) {
+        const int s = size_arr[k];
+        if (s >= 1 && s <= S) {  // warp-uniform
+            const int off = off_arr[k], npk = s * (s + 1) / 2;
+            jac.clear(lane);
+            T nrm = T(0);
+            for (int f = lane; f < npk; f += 32) {
+                const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+                const T w = W[off + f];
+                jac.put(a, b, w);
+                nrm += (a == b ? T(1) : T(2)) * w * w;
+            }
+            nrm = warp_sum(nrm);
+            __syncwarp();
+            jac.run(T(tolrel) * sqrt(nrm), max_sweeps, lane);
+            double l = (lane < s) ? double(jac.X[lane * J::LDA + lane]) : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
+            lmin = fmin(0.0, l);
+        }
+    }
+    if (lane == 0) wmin[warp] = lmin;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < kViolWarps; ++w) m = fmin(m, wmin[w]);
+        partial[blockIdx.x] = m;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {  // the final reduction, in a fixed order
+        __threadfence();
+        double m = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmin(m, ((volatile double*)partial)[b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) wmin[warp] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double mm = 0.0;
+            for (int w = 0; w < kViolWarps; ++w) mm = fmin(mm, wmin[w]);
+            *alpha_out = -mm;
+            *counter = 0u;
+        }
+    }
+}
+
+template <typename T, int S>
+cudaError_t launch_violation(int p, const int* off, const int* size, const void* W, double tolrel, int max_sweeps,
+                             unsigned char* scratch, double* alpha, cudaStream_t st) {
+    const size_t smem = kViolWarps * BLJacobi<T, S>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_psd_violation<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, (p + kViolWarps - 1) / kViolWarps);
+    k_psd_violation<T, S><<<grid, 32 * kViolWarps, smem, st>>>(p, off, size, (const T*)W, tolrel, max_sweeps, scratch,
+                                                              alpha);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_violation(int cls, int p, const int* off, const int* size, const void* W, double tolrel,
+                               int max_sweeps, unsigned char* scratch, double* alpha, cudaStream_t st) {
+    switch (kProjClasses[cls]) {
+        case 2: return launch_violation<T, 2>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 4: return launch_violation<T, 4>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 6: return launch_violation<T, 6>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 8: return launch_violation<T, 8>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 10: return launch_violation<T, 10>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 12: return launch_violation<T, 12>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 14: return launch_violation<T, 14>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 16: return launch_violation<T, 16>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 20: return launch_violation<T, 20>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 24: return launch_violation<T, 24>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 28: return launch_violation<T, 28>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 32: return launch_violation<T, 32>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Shared body of the entry points: validate, clear the counter, launch.
+int run_violation(int p, const int* d_off, const int* d_size, int max_size, const void* d_W, int precision,
+                  int max_sweeps, unsigned char* scratch, double* d_alpha, cudaStream_t st) {
+    const int cls = proj_class_of(max_size);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) { cudaGetLastError(); return CDSDP_ERR_CUDA; }
+    if (precision == CDSDP_FP64)
+        e = dispatch_violation<double>(cls, p, d_off, d_size, d_W, 2.3e-16, max_sweeps, scratch, d_alpha, st);
+    else
+        e = dispatch_violation<float>(cls, p, d_off, d_size, d_W, 1.2e-7, max_sweeps, scratch, d_alpha, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return CDSDP_ERR_CUDA; }
+    return CDSDP_SOLVED;
+}
+
+int check_violation_args(int p, const int* d_off, const int* d_size, int max_size, const void* d_W, int precision,
+                         int max_sweeps, const double* d_alpha) {
+    if (p < 1 || max_size < 1 || max_size > 32 || max_sweeps < 1) return CDSDP_ERR_ARG;
+    if (!d_off || !d_size || !d_W || !d_alpha) return CDSDP_ERR_ARG;
+    if (precision != CDSDP_FP32_PROJECTION && precision != CDSDP_FP64) return CDSDP_ERR_ARG;
+    return CDSDP_SOLVED;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cdsdp_psd_violation_scratch_bytes(int p) { return violation_scratch_bytes(p); }
+
+int cdsdp_psd_violation(int p, const int* d_off, const int* d_size, int max_size, const void* d_W, int precision,
+                        int max_sweeps, void* d_scratch, size_t scratch_bytes, double* d_alpha, void* stream) {
+    int rc = check_violation_args(p, d_off, d_size, max_size, d_W, precision, max_sweeps, d_alpha);
+    if (rc != CDSDP_SOLVED) return rc;
+    if (!d_scratch || reinterpret_cast<uintptr_t>(d_scratch) % 256) return CDSDP_ERR_ARG;
+    if (scratch_bytes < violation_scratch_bytes(p)) return CDSDP_ERR_NOMEM;
+    return run_violation(p, d_off, d_size, max_size, d_W, precision, max_sweeps, (unsigned char*)d_scratch, d_alpha,
+                         (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -92,6 +92,31 @@ def test_psd_projection_eigenpairs(lib, torch_cuda):
         np.testing.assert_allclose((Vk * l) @ Vk.T, B, atol=1e-11 * np.abs(B).max() * s)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_psd_violation_kernel(lib, torch_cuda, prec):
+    """alpha = -min(0, min_k lambda_min(W_k)) (Section 6.1.3, Eq. PSD-violation)
+    against LAPACK eigenvalues, over 2000 blocks of mixed order (many thread
+    blocks, so the last-block reduction is exercised), and for all-PSD input."""
+    torch = torch_cuda
+    rng = np.random.default_rng(11 if prec == "fp64" else 12)
+    sizes = [int(s) for s in rng.integers(1, 21, 2000)]
+    blocks = []
+    for s in sizes:
+        G = W._f32(rng.standard_normal((s, s)))
+        blocks.append(W._f32(G @ G.T + 0.5 * np.eye(s)))   # PSD
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    off = torch.tensor(np.concatenate([[0], np.cumsum([s * (s + 1) // 2 for s in sizes])]), dtype=torch.int32, device="cuda")
+    sz = torch.tensor(sizes, dtype=torch.int32, device="cuda")
+    a = lib.psd_violation(torch.tensor(_pack(blocks), dtype=dt, device="cuda"), off, sz)
+    assert a.item() == 0.0
+    blocks[1234] = blocks[1234] - 3.25 * np.eye(sizes[1234])   # one indefinite block
+    blocks[7] = blocks[7] - 1.0 * np.eye(sizes[7])
+    want = -min(0.0, min(np.linalg.eigvalsh(B).min() for B in blocks))
+    a = lib.psd_violation(torch.tensor(_pack(blocks), dtype=dt, device="cuda"), off, sz).item()
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert abs(a - want) <= tol * max(1.0, max(np.linalg.norm(B) for B in blocks))
+
+
 def _oracle_lower(dp, v):
     return dp.lower_values(v)
 
