@@ -205,6 +205,24 @@ size_t cdsdp_psd_violation_scratch_bytes(int p);
 int cdsdp_psd_violation(int p, const int* d_off, const int* d_size, int max_size, const void* d_W, int precision,
                         int max_sweeps, void* d_scratch, size_t scratch_bytes, double* d_alpha, void* stream);
 
+/* cdsdp_psd_violation for callers that cannot allocate device memory.  The
+ * paper has no counterpart; this exists for callers that cannot call
+ * cudaMalloc when they need the measure: code recording a CUDA graph by stream
+ * capture, code running inside a framework whose caching allocator owns the
+ * device memory, or real-time loops that forbid allocation.  Same arguments,
+ * result and errors as cdsdp_psd_violation, minus the scratch: the scratch is
+ * a fixed 1 MiB array inside the library, present on every GPU that loads it
+ * until the process exits.  Limit: p <= 524160 blocks (131040 thread blocks of
+ * 4); larger p returns CDSDP_ERR_UNSUPPORTED.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) and should therefore
+ * come before any stream capture on that device.  Every call shares the array
+ * and clears its counter word on `stream` before launching; calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * the array and must be serialised by the caller.  Allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library routine. */
+int cdsdp_psd_violation_noalloc(int p, const int* d_off, const int* d_size, int max_size, const void* d_W,
+                                int precision, int max_sweeps, double* d_alpha, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,11 +66,13 @@ _lib.cdsdp_psd_violation_scratch_bytes.argtypes = [ctypes.c_int]
 _lib.cdsdp_psd_violation_scratch_bytes.restype = ctypes.c_size_t
 _lib.cdsdp_psd_violation.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                      ctypes.c_size_t, _vp, _vp]
+_lib.cdsdp_psd_violation_noalloc.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
+                                             _vp, _vp]
 
 EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", "cdsdp_pattern",
             "cdsdp_workspace_bytes", "cdsdp_bind", "cdsdp_solve", "cdsdp_results", "cdsdp_free",
             "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile", "cdsdp_psd_violation_scratch_bytes",
-            "cdsdp_psd_violation"]
+            "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc"]
 
 
 class CdsdpError(RuntimeError):
@@ -256,4 +258,19 @@ def psd_violation(W, offsets, sizes, max_sweeps=30, stream=None):
                                   _stream_ptr(stream))
     if st != 0:
         raise CdsdpError(st, "cdsdp_psd_violation")
+    return alpha
+
+
+def psd_violation_noalloc(W, offsets, sizes, alpha, max_sweeps=30, stream=None):
+    """As psd_violation, through the entry point that allocates nothing: the
+    caller passes the output `alpha` (1-element float64 CUDA tensor) and the
+    scratch is the library's fixed device array."""
+    p = int(sizes.numel())
+    prec = FP64 if str(W.dtype) == "torch.float64" else FP32
+    maxs = int(sizes.max().item())
+    st = _lib.cdsdp_psd_violation_noalloc(p, ctypes.c_void_p(offsets.data_ptr()), ctypes.c_void_p(sizes.data_ptr()),
+                                          maxs, ctypes.c_void_p(W.data_ptr()), prec, int(max_sweeps),
+                                          ctypes.c_void_p(alpha.data_ptr()), _stream_ptr(stream))
+    if st != 0:
+        raise CdsdpError(st, "cdsdp_psd_violation_noalloc")
     return alpha

@@ -160,3 +160,55 @@ int cdsdp_psd_violation(int p, const int* d_off, const int* d_size, int max_size
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Variant for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc at the moment they need this measure:
+// code recording a CUDA graph by stream capture (allocation is not a
+// capturable operation), code inside a framework whose caching allocator owns
+// the device memory, or a real-time loop that forbids allocation latency.  For
+// them the scratch lives in a fixed array in the library's device image,
+// held on every GPU that loads the library until the process exits.
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;  // 1 MiB: counter + 131040 per-block minima
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_violation_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_violation_scratch on the current device (the host-side
+// name is only a stand-in, never a device pointer).  Looked up once per device.
+int scratch_address(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return CDSDP_ERR_CUDA; }
+    if (dev < 0 || dev >= kMaxDevices) return CDSDP_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_violation_scratch);
+        if (e != cudaSuccess || !ptr) { cudaGetLastError(); return CDSDP_ERR_CUDA; }
+        g_scratch_addr[dev] = ptr;
+    }
+    *out = g_scratch_addr[dev];
+    return CDSDP_SOLVED;
+}
+
+}  // namespace
+
+extern "C" int cdsdp_psd_violation_noalloc(int p, const int* d_off, const int* d_size, int max_size, const void* d_W,
+                                           int precision, int max_sweeps, double* d_alpha, void* stream) {
+    int rc = check_violation_args(p, d_off, d_size, max_size, d_W, precision, max_sweeps, d_alpha);
+    if (rc != CDSDP_SOLVED) return rc;
+    if (violation_scratch_bytes(p) > kNoAllocScratchBytes) return CDSDP_ERR_UNSUPPORTED;
+    void* scratch = nullptr;
+    rc = scratch_address(&scratch);
+    if (rc != CDSDP_SOLVED) return rc;
+    return run_violation(p, d_off, d_size, max_size, d_W, precision, max_sweeps, (unsigned char*)scratch, d_alpha,
+                         (cudaStream_t)stream);
+}
