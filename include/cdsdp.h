@@ -67,7 +67,9 @@ typedef struct {
                               loop; 0: one launch per phase, host polls every check_every */
     int check_every;       /* host poll period when use_graph = 0                       */
     int jacobi_max_sweeps; /* cap on Jacobi sweeps per projection                       */
-    int warm_start;        /* reserved, must be 0                                        */
+    int warm_start;        /* 0: every eigensolve starts from the identity; N > 0: each
+                              clique's Jacobi starts from its eigenvectors of the previous
+                              iteration, with a cold start every N iterations          */
     int profile;           /* 1: run the use_graph = 0 path and bracket every projection
                               launch with CUDA events on `stream` (see cdsdp_profile)      */
 } cdsdp_opts;
@@ -86,7 +88,8 @@ typedef struct {
 } cdsdp_info_t;
 
 /* Fill `o` with defaults: eps 1e-4, max_iter 2000, rho 1, FP32 projection,
- * graph on, check_every 50, 30 Jacobi sweeps, no profiling. */
+ * graph on, check_every 50, 30 Jacobi sweeps, warm start with a cold start every
+ * 16 iterations, no profiling. */
 void cdsdp_default_opts(cdsdp_opts* o);
 
 /* Data preprocessing of Algorithms 1-3 (host only, no GPU call):

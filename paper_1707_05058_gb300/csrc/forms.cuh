@@ -9,8 +9,10 @@ namespace cdsdp_dev {
 // Algorithm 2, after the KKT solve: v_k = z_k + lambda_k/rho + H_k x (Eq. vkEqn),
 // lambda_k <- lambda_k + rho (z_k - v_k) (Eq. MultUpdateDualSDP), one warp per
 // clique; part[k][0..3] = |z_k - v_k|^2, |z_k|^2, |v_k|^2, |lambda_k|^2.
+__device__ void finish_dual_block(const Dev& d, const FinishArgs& fa);
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho) {
+__global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho, FinishArgs fa) {
     if (stopped(d)) return;
     const int lane = threadIdx.x & 31;
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -40,26 +42,27 @@ __global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho) {
             pk[0] = p0; pk[1] = p1; pk[2] = p2; pk[3] = p3;
         }
     }
+    if (last_block_arrival(d)) finish_dual_block(d, fa);
 }
 
-// Algorithm 2 stopping test (Eq. DualConsensusResidual, eps_lambda).
-__global__ void __launch_bounds__(FTHREADS) k_finish_dual(Dev d, double rho, double eps, int nbe, int nbr,
-                                                          int use_cond, cudaGraphConditionalHandle hnd) {
+// Algorithm 2 stopping test (Eq. DualConsensusResidual, eps_lambda), run by
+// every thread of the block that finishes the iteration.
+__device__ void finish_dual_block(const Dev& d, const FinishArgs& fa) {
     __shared__ double sh[32 * 5];
-    if (stopped(d)) { if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(hnd, 0u); return; }
     const int cols[5] = {0, 1, 2, 3, 5};
     double s[5];
     sum_cols<5>(d.part, d.p, cols, s, sh);
-    const double cx = sum_col(d.parte, nbe, 0, sh);
-    const double by = sum_col(d.partr, nbr, 0, sh);
+    const double cx = sum_col(d.parte, fa.nbe, 0, sh);
+    const double by = sum_col(d.partr, fa.nbr, 0, sh);
     if (threadIdx.x == 0) {
         const int it = d.ctl[CTL_ITER] + 1;
         const double ec = sqrt(s[0]) / fmax(fmax(sqrt(s[1]), sqrt(s[2])), 1e-300);
-        const double el = rho * sqrt(s[4]) / fmax(sqrt(s[3]), 1e-300);
+        const double el = fa.rho * sqrt(s[4]) / fmax(sqrt(s[3]), 1e-300);
         double* h = d.hist + (size_t)(it - 1) * HIST_COLS;
-        h[0] = ec; h[1] = el; h[2] = 0; h[3] = 0; h[4] = -rho * cx; h[5] = by; h[6] = 0; h[7] = 0;
+        h[0] = ec; h[1] = el; h[2] = 0; h[3] = 0; h[4] = -fa.rho * cx; h[5] = by; h[6] = 0; h[7] = 0;
         const bool bad = !isfinite(ec) || !isfinite(el);
-        finish_common(d, bad, it > 1 && fmax(ec, el) <= eps, it, use_cond, hnd);
+        d.ctl[CTL_COUNTER] = 0;
+        finish_common(d, bad, it > 1 && fmax(ec, el) <= fa.eps, it, fa.use_cond, fa.hnd);
     }
 }
 
@@ -127,7 +130,9 @@ __global__ void __launch_bounds__(ETHREADS) k_hsde_sigma11(Dev d, int G) {
 
 // sigma_21 = nu_21 - A sigma_11 (Eq. AppendixEqSigma2); partial <b, sigma_21>
 // in partr[block][2]; A sigma_11 kept for the primal residual.
-__global__ void __launch_bounds__(RTHREADS) k_hsde_sigma21(Dev d, int TPR) {
+__device__ void hsde_gamma_block(const Dev& d, int nbe, int nbr);
+
+__global__ void __launch_bounds__(RTHREADS) k_hsde_sigma21(Dev d, int TPR, int nbe) {
     __shared__ double sh[RTHREADS / 32];
     __shared__ double sh2[32];
     if (stopped(d)) return;
@@ -152,14 +157,14 @@ __global__ void __launch_bounds__(RTHREADS) k_hsde_sigma21(Dev d, int TPR) {
     }
     block_sum<1>(bs, sh2);
     if (threadIdx.x == 0) d.partr[blockIdx.x * PART_COLS + 2] = bs[0];
+    if (last_block_arrival(d)) hsde_gamma_block(d, nbe, gridDim.x);
 }
 
 // gamma = zeta^T sigma, u_hat_2 = omega_2 + zeta^T u_hat_1 = omega_2 + gamma (1 - zeta^T zeta_hat)
 // (Eqs. MatrixInverseResult, FirstBlockElimination); tau <- max(0, u_hat_tau - kappa),
 // kappa <- kappa - u_hat_tau + tau (Eqs. HsdeStep2-3 on the R_+ component).
-__global__ void __launch_bounds__(FTHREADS) k_hsde_gamma(Dev d, int nbe, int nbr) {
+__device__ void hsde_gamma_block(const Dev& d, int nbe, int nbr) {
     __shared__ double sh[32];
-    if (stopped(d)) return;
     const double cs = sum_col(d.parte, nbe, 2, sh);
     const double bs = sum_col(d.partr, nbr, 2, sh);
     if (threadIdx.x == 0) {
@@ -172,6 +177,7 @@ __global__ void __launch_bounds__(FTHREADS) k_hsde_gamma(Dev d, int nbe, int nbr
         d.scal[SC_TAUHAT] = tauhat;
         d.scal[SC_TAU] = tn;
         d.scal[SC_KAPPA] = kappa - tauhat + tn;
+        d.ctl[CTL_COUNTER] = 0;
     }
 }
 
@@ -219,7 +225,9 @@ __global__ void __launch_bounds__(ETHREADS) k_hsde_entry_update(Dev d, int G) {
 
 // u_y <- sigma_21 - gamma zeta_hat_y; A u_x = A sigma_11 - gamma A zeta_hat_x;
 // partials |A u_x - tau b|^2 (partr col 0) and <b, u_y> (col 1).
-__global__ void __launch_bounds__(RTHREADS) k_hsde_row_update(Dev d) {
+__device__ void finish_hsde_block(const Dev& d, const FinishArgs& fa);
+
+__global__ void __launch_bounds__(RTHREADS) k_hsde_row_update(Dev d, FinishArgs fa) {
     __shared__ double sh[64];
     if (stopped(d)) return;
     const double gamma = d.scal[SC_GAMMA], tau = d.scal[SC_TAU];
@@ -236,16 +244,17 @@ __global__ void __launch_bounds__(RTHREADS) k_hsde_row_update(Dev d) {
         d.partr[blockIdx.x * PART_COLS + 0] = p[0];
         d.partr[blockIdx.x * PART_COLS + 1] = p[1];
     }
+    if (last_block_arrival(d)) finish_hsde_block(d, fa);
 }
 
 // Algorithm 3 stopping tests: Eqs. HSDEerror and HSDEconsensusResidual when
 // tau > 0; otherwise the infeasibility tests (each certificate on its own):
 // b^T u_y > 0 and |A^T u_y + H^T v_z| <= eps b^T u_y / |b|  -> primal infeasible,
 // c^T u_x < 0 and |A u_x| <= -eps c^T u_x / |c|             -> dual infeasible.
-__global__ void __launch_bounds__(FTHREADS) k_finish_hsde(Dev d, double eps, int nbe, int nbr, int use_cond,
-                                                          cudaGraphConditionalHandle hnd) {
+__device__ void finish_hsde_block(const Dev& d, const FinishArgs& fa) {
     __shared__ double sh[32 * 6];
-    if (stopped(d)) { if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(hnd, 0u); return; }
+    const double eps = fa.eps;
+    const int nbe = fa.nbe, nbr = fa.nbr;
     const int cols6[6] = {0, 1, 2, 3, 4, 5}, cols2[2] = {0, 1};
     double s[6], pe[2], pr[2];
     sum_cols<6>(d.part, d.p, cols6, s, sh);
@@ -282,8 +291,9 @@ __global__ void __launch_bounds__(FTHREADS) k_finish_hsde(Dev d, double eps, int
         else if (stop) done = 1;
         else if (it >= d.max_iter) { d.ctl[CTL_STATUS] = 1; done = 1; }
         d.ctl[CTL_ITER] = it;
+        d.ctl[CTL_COUNTER] = 0;
         if (done) d.ctl[CTL_DONE] = 1;
-        if (use_cond) cudaGraphSetConditional(hnd, done ? 0u : 1u);
+        if (fa.use_cond) cudaGraphSetConditional(fa.hnd, done ? 0u : 1u);
     }
 }
 

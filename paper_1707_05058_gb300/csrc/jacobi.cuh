@@ -16,11 +16,17 @@
 // applies J_I^T B J_J and writes them to their permuted positions in the other
 // buffer (one warp barrier per round).  Row `lane` of V stays in registers
 // and its columns are re-indexed by the same sigma (static register moves).
-// A rotation is skipped when |a_pq| <= tol = eps_rel * ||W||_F; sweeps stop when
-// a whole sweep skips every rotation (or after max_sweeps).
+// A rotation is skipped when |a_pq| <= tol = eps_rel * ||W||_F; a sweep starts
+// only while some off-diagonal entry exceeds tol (or until max_sweeps).
+// Warm start (ADMM iterates move little between iterations): each clique keeps
+// its eigenvectors V from the previous iteration; the new block W is first
+// rotated into that basis (A = V^T W V, two warp-level products) and the
+// sweeps continue from V, which typically needs one sweep instead of five or
+// six.  Every `restart` iterations the eigensolve starts from the identity, so
+// rounding in the accumulated V cannot drift.
 #pragma once
 
-#include "kernels.cuh"
+#include "reduce.cuh"
 
 namespace cdsdp_dev {
 
@@ -108,9 +114,89 @@ struct BLJacobi {
         for (int i = lane; i < BUF; i += 32) X[i] = T(0);
         __syncwarp();
     }
-    __device__ __forceinline__ void put(int a, int b, T w) { X[a * LDA + b] = w; }
+    __device__ __forceinline__ void put(int a, int b, T w) {
+        X[a * LDA + b] = w;
+        X[b * LDA + a] = w;
+    }
 
-    __device__ __forceinline__ bool round(T tol, int lane) {
+    // Largest |off-diagonal entry| of the lower triangle in X (same in all lanes).
+    __device__ __forceinline__ T off_max(int lane) const {
+        T m = T(0);
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            if (bI[t] < 0) continue;
+            if (t == 0 && lane < K) {
+                m = fmax(m, fabs(X[src[0][1]]));
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) m = fmax(m, fabs(X[src[t][e]]));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        return m;
+    }
+
+    // Warm start: v holds the rows of an orthogonal V (lane r: row r), X the
+    // symmetric block W (both triangles).  Replace X by V^T W V, so that the
+    // sweeps continue from the basis V (the final eigenvectors are V J_1 J_2 ...).
+    // Y is used as scratch.
+    __device__ void rotate_into_basis(int lane) {
+        if (lane < S) {
+#pragma unroll
+            for (int j = 0; j < S; ++j) Y[lane * LDA + j] = v[j];
+        }
+        __syncwarp();
+        T acc[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) acc[j] = T(0);
+        if (lane < S) {  // row `lane` of W V
+            for (int i = 0; i < S; ++i) {
+                const T w = X[lane * LDA + i];
+                const T* yi = Y + i * LDA;
+#pragma unroll
+                for (int j = 0; j < S; ++j) acc[j] += w * yi[j];
+            }
+        }
+        __syncwarp();
+        if (lane < S) {
+#pragma unroll
+            for (int j = 0; j < S; ++j) X[lane * LDA + j] = acc[j];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < S; ++j) acc[j] = T(0);
+        if (lane < S) {  // row `lane` of V^T (W V)
+            for (int r = 0; r < S; ++r) {
+                const T vr = Y[r * LDA + lane];
+                const T* xr = X + r * LDA;
+#pragma unroll
+                for (int j = 0; j < S; ++j) acc[j] += vr * xr[j];
+            }
+        }
+        __syncwarp();
+        if (lane < S) {
+#pragma unroll
+            for (int j = 0; j < S; ++j) X[lane * LDA + j] = acc[j];
+        }
+        __syncwarp();
+    }
+
+    // v <- rows of the stored s x s eigenvector matrix (row-major at Vc), padded
+    // with the identity on indices s..S-1.
+    __device__ __forceinline__ void load_basis(const T* __restrict__ Vc, int s, int lane) {
+#pragma unroll
+        for (int j = 0; j < S; ++j) v[j] = (lane < s && j < s) ? Vc[lane * s + j] : (j == lane ? T(1) : T(0));
+    }
+    __device__ __forceinline__ void store_basis(T* __restrict__ Vc, int s, int lane) const {
+        if (lane < s) {
+#pragma unroll
+            for (int j = 0; j < S; ++j)
+                if (j < s) Vc[lane * s + j] = v[j];
+        }
+    }
+
+    __device__ __forceinline__ void round(T tol, int lane) {
         T bv[NS][4];
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
@@ -137,7 +223,6 @@ struct BLJacobi {
                 my = true;
             }
         }
-        const bool any = __any_sync(0xffffffffu, my);
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
             const int I = bI[t] >= 0 ? bI[t] : 0, J = bJ[t];
@@ -170,22 +255,24 @@ struct BLJacobi {
         for (int j = 0; j < S; ++j) v[j] = nv[j];
         __syncwarp();
         T* tmp = X; X = Y; Y = tmp;
-        return any;
     }
 
     // Diagonalise; returns the number of sweeps run.  Afterwards X holds
-    // diag(lambda) (up to the threshold) and v the eigenvector row.
-    __device__ int run(T tol, int max_sweeps, int lane) {
+    // diag(lambda) (up to the threshold) and v the eigenvector row.  With
+    // v_preset the sweeps start from the basis already in v (see
+    // rotate_into_basis); otherwise from the identity.  A sweep runs only while
+    // some off-diagonal entry exceeds tol.
+    __device__ int run(T tol, int max_sweeps, int lane, bool v_preset = false) {
+        if (!v_preset) {
 #pragma unroll
-        for (int j = 0; j < S; ++j) v[j] = (j == lane) ? T(1) : T(0);
+            for (int j = 0; j < S; ++j) v[j] = (j == lane) ? T(1) : T(0);
+        }
         __syncwarp();
         int sw = 0;
-        while (sw < max_sweeps) {
+        while (sw < max_sweeps && off_max(lane) > tol) {
             ++sw;
-            bool any = false;
 #pragma unroll 1
-            for (int r = 0; r < R; ++r) any = round(tol, lane) || any;
-            if (!any) break;
+            for (int r = 0; r < R; ++r) round(tol, lane);
         }
         return sw;
     }
@@ -229,8 +316,8 @@ struct BLJacobi {
 // test (Eq. PrimalConsensusResidual and eps_lambda):
 //   part[k] = (|x_k - H_k x|^2, |x_k|^2, |H_k x|^2, |x_k - x_k_old|^2, |lambda_k|^2)
 template <typename T, int S>
-__global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __restrict__ list, int nlist, double rho,
-                                                         double tolrel, int max_sweeps) {
+__global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
+                                                         FinishArgs fa) {
     using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
@@ -239,7 +326,9 @@ __global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __rest
     jac.bind(smem + warp * J::bytes, lane);
     T* xk = reinterpret_cast<T*>(d.ck0);
     T* lam = reinterpret_cast<T*>(d.ck1);
-    const T rho_t = T(rho), irho = T(1.0 / rho);
+    T* vc = reinterpret_cast<T*>(d.vcache);
+    const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
+    const T rho_t = T(pa.rho), irho = T(1.0 / pa.rho);
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
@@ -253,7 +342,12 @@ __global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __rest
         }
         nrm = warp_sum(nrm);
         __syncwarp();
-        jac.run(T(tolrel) * sqrt(nrm), max_sweeps, lane);
+        if (warm) {
+            jac.load_basis(vc + d.vv_off[k], s, lane);
+            jac.rotate_into_basis(lane);
+        }
+        jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm);
+        if (pa.warm_start) jac.store_basis(vc + d.vv_off[k], s, lane);
         jac.prepare_rebuild(lane);
         double p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0;
         for (int f = lane; f < npk; f += 32) {
@@ -280,13 +374,13 @@ __global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __rest
         }
         __syncwarp();
     }
+    if (fa.enabled && last_block_arrival(d)) finish_primal_block(d, fa);
 }
 
 // Algorithm 2, z-step (Eq. zkUpdate): z_k <- P(v_k - lambda_k / rho);
 // part[k][5] = |z_k - z_k_old|^2 (for eps_lambda).
 template <typename T, int S>
-__global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restrict__ list, int nlist, double rho,
-                                                       double tolrel, int max_sweeps) {
+__global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa) {
     using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
@@ -296,7 +390,9 @@ __global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restri
     T* z = reinterpret_cast<T*>(d.ck0);
     const T* v = reinterpret_cast<const T*>(d.ck1);
     const T* lam = reinterpret_cast<const T*>(d.ck2);
-    const T irho = T(1.0 / rho);
+    T* vc = reinterpret_cast<T*>(d.vcache);
+    const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
+    const T irho = T(1.0 / pa.rho);
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
@@ -310,7 +406,12 @@ __global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restri
         }
         nrm = warp_sum(nrm);
         __syncwarp();
-        jac.run(T(tolrel) * sqrt(nrm), max_sweeps, lane);
+        if (warm) {
+            jac.load_basis(vc + d.vv_off[k], s, lane);
+            jac.rotate_into_basis(lane);
+        }
+        jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm);
+        if (pa.warm_start) jac.store_basis(vc + d.vv_off[k], s, lane);
         jac.prepare_rebuild(lane);
         double p0 = 0;
         for (int f = lane; f < npk; f += 32) {
@@ -337,8 +438,7 @@ __global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restri
 // HSDEconsensusResidual): |u_s - H u_x|^2, |u_s|^2, |H u_x|^2, |v_z - u_t|^2,
 // |v_z|^2, |u_t|^2, where u_x = sigma_11 - gamma zeta_hat_x.
 template <typename T, int S>
-__global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restrict__ list, int nlist,
-                                                       double tolrel, int max_sweeps) {
+__global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa) {
     using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
@@ -348,6 +448,8 @@ __global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restri
     T* us = reinterpret_cast<T*>(d.ck0);
     T* vz = reinterpret_cast<T*>(d.ck1);
     T* ut = reinterpret_cast<T*>(d.ck2);
+    T* vc = reinterpret_cast<T*>(d.vcache);
+    const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     const double gamma = d.scal[SC_GAMMA];
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
@@ -368,7 +470,12 @@ __global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restri
         }
         nrm = warp_sum(nrm);
         __syncwarp();
-        jac.run(T(tolrel) * sqrt(nrm), max_sweeps, lane);
+        if (warm) {
+            jac.load_basis(vc + d.vv_off[k], s, lane);
+            jac.rotate_into_basis(lane);
+        }
+        jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm);
+        if (pa.warm_start) jac.store_basis(vc + d.vv_off[k], s, lane);
         jac.prepare_rebuild(lane);
         double p[6] = {0, 0, 0, 0, 0, 0};
         for (int f = lane; f < npk; f += 32) {

@@ -11,7 +11,7 @@
 
 namespace cdsdp_dev {
 
-enum { CTL_DONE = 0, CTL_ITER = 1, CTL_STATUS = 2, CTL_NAN = 3, CTL_WORDS = 16 };
+enum { CTL_DONE = 0, CTL_ITER = 1, CTL_STATUS = 2, CTL_NAN = 3, CTL_COUNTER = 4, CTL_WORDS = 16 };
 // iteration scalars of Algorithm 3
 enum { SC_TAU = 0, SC_KAPPA = 1, SC_OMEGA2 = 2, SC_GAMMA = 3, SC_TAUHAT = 4, SC_WORDS = 32 };
 enum { HIST_COLS = 8, PART_COLS = 8 };
@@ -58,6 +58,8 @@ struct Dev {
     void* ck0;            // [nd] clique vectors (float or double)
     void* ck1;
     void* ck2;
+    void* vcache;         // [sum_k s_k^2] eigenvectors of the previous iteration (warm start)
+    const int* vv_off;    // [p+1] offsets into vcache
     double* part;         // [p * PART_COLS] per-clique partial sums
     double* parte;        // [NBLK_E * PART_COLS] per-block partials, pattern-entry kernels
     double* partr;        // [NBLK_R * PART_COLS] per-block partials, constraint-row kernels
@@ -72,6 +74,23 @@ constexpr int NBLK_R = 1216;
 constexpr int ETHREADS = 256;
 constexpr int RTHREADS = 256;
 constexpr int FTHREADS = 512;
+
+// Stopping-test arguments handed to the kernel whose last block finishes an iteration.
+struct FinishArgs {
+    double rho, eps;
+    int nbe, nbr;        // rows of the per-block partial tables to reduce
+    int enabled;         // 0: this launch does not finish the iteration
+    int use_cond;        // 1: inside the graph while loop (set its condition)
+    cudaGraphConditionalHandle hnd;
+};
+
+// Eigensolver options of the projection kernels.
+struct ProjArgs {
+    double rho, tolrel;
+    int max_sweeps;
+    int warm_start;      // reuse the previous iteration's eigenvectors
+    int restart;         // cold start every `restart` iterations
+};
 
 __device__ __forceinline__ bool stopped(const Dev& d) {
     return *((volatile int*)d.ctl + CTL_DONE) != 0;
@@ -106,6 +125,23 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
         for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
     }
     __syncthreads();
+}
+
+// Every thread of a block calls this after writing its partial sums; it
+// returns true in the block that arrives last (in which the other blocks'
+// writes are then visible).  The counter lives in ctl and is reset by the
+// finishing block.
+__device__ __forceinline__ bool last_block_arrival(const Dev& d) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int ticket = atomicAdd(reinterpret_cast<unsigned int*>(d.ctl + CTL_COUNTER), 1u);
+        s_last = (ticket == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
 }
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);

@@ -9,7 +9,7 @@ namespace cdsdp_dev {
 namespace {
 
 template <typename T, int S>
-cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, double rho, double tolrel, int max_sweeps,
+cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, const ProjArgs& pa, const FinishArgs& fa,
                         cudaStream_t st) {
     if (nlist <= 0) return cudaSuccess;
     const size_t smem = 4 * BLJacobi<T, S>::bytes;
@@ -18,15 +18,15 @@ cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, doub
     if (form == 0) {
         e = cudaFuncSetAttribute(k_project_primal<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_project_primal<T, S><<<grid, 128, smem, st>>>(d, list, nlist, rho, tolrel, max_sweeps);
+        k_project_primal<T, S><<<grid, 128, smem, st>>>(d, list, nlist, pa, fa);
     } else if (form == 1) {
         e = cudaFuncSetAttribute(k_project_dual<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_project_dual<T, S><<<grid, 128, smem, st>>>(d, list, nlist, rho, tolrel, max_sweeps);
+        k_project_dual<T, S><<<grid, 128, smem, st>>>(d, list, nlist, pa);
     } else {
         e = cudaFuncSetAttribute(k_project_hsde<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_project_hsde<T, S><<<grid, 128, smem, st>>>(d, list, nlist, tolrel, max_sweeps);
+        k_project_hsde<T, S><<<grid, 128, smem, st>>>(d, list, nlist, pa);
     }
     return cudaGetLastError();
 }
@@ -64,9 +64,9 @@ cudaError_t launch_standalone(int p, const int* off, const int* size, const void
 
 }  // namespace
 
-cudaError_t PROJ_SUFFIX(launch_proj)(int form, int cls, const Dev& d, const int* list, int nlist, double rho,
-                                     double tolrel, int max_sweeps, cudaStream_t st) {
-#define CALL(S) launch_form<PROJ_T, S>(form, d, list, nlist, rho, tolrel, max_sweeps, st)
+cudaError_t PROJ_SUFFIX(launch_proj)(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
+                                     const FinishArgs& fa, cudaStream_t st) {
+#define CALL(S) launch_form<PROJ_T, S>(form, d, list, nlist, pa, fa, st)
     CDSDP_CLASS_SWITCH(CALL)
 #undef CALL
 }

@@ -19,10 +19,11 @@ inline int proj_class_of(int s) {
 
 // form 0/1/2: Algorithm 1/2/3 projection kernels over `list` (cliques of
 // order <= kProjClasses[cls]).
-cudaError_t launch_proj_f32(int form, int cls, const Dev& d, const int* list, int nlist, double rho,
-                            double tolrel, int max_sweeps, cudaStream_t st);
-cudaError_t launch_proj_f64(int form, int cls, const Dev& d, const int* list, int nlist, double rho,
-                            double tolrel, int max_sweeps, cudaStream_t st);
+// `fa` is used by the primal form only (its last block finishes the iteration).
+cudaError_t launch_proj_f32(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
+                            const FinishArgs& fa, cudaStream_t st);
+cudaError_t launch_proj_f64(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
+                            const FinishArgs& fa, cudaStream_t st);
 cudaError_t launch_proj_standalone_f32(int cls, int p, const int* off, const int* size, const void* W, void* X,
                                        void* eig, const int* voff, void* V, const int* vvoff, double tolrel,
                                        int max_sweeps, cudaStream_t st);

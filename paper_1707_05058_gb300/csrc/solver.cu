@@ -29,10 +29,10 @@ inline int class_of(int s) { return proj_class_of(s); }
 struct Layout {
     // constants
     size_t c, dinv, pinv, wgt, a_ptr, a_col, a_valw, at_ptr, at_col, at_val, b, minv, kinv, gmap, pk_off, csize,
-        sc_ptr, sc_idx, zhx, zhy, atb, azhx, blist;
+        sc_ptr, sc_idx, zhx, zhy, atb, azhx, blist, vv_off;
     size_t const_end;
     // state
-    size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, part, parte, partr, scal, ctl, hist;
+    size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, vcache, part, parte, partr, scal, ctl, hist;
     size_t total;
 };
 
@@ -94,10 +94,17 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     L.sc_ptr = take((NE + 1) * 4); L.sc_idx = take(nd * 4);
     L.zhx = take(NE * 8); L.zhy = take(m * 8); L.atb = take(NE * 8); L.azhx = take(m * 8);
     L.blist = take(p * 4);
+    L.vv_off = take((p + 1) * 4);
     L.const_end = o;
     L.x = take(NE * 8); L.t = take(NE * 8); L.q = take(NE * 8); L.s11 = take(NE * 8); L.atuy = take(NE * 8);
     L.y = take(m * 8); L.g = take(m * 8); L.hh = take(m * 8); L.s21 = take(m * 8); L.as11 = take(m * 8);
     L.ck0 = take(nd * 8); L.ck1 = take(nd * 8); L.ck2 = take(nd * 8);
+    size_t nvv = 0;
+    for (size_t k = 0; k + 1 < hp.cl_off.size(); ++k) {
+        const size_t sk = hp.cl_off[k + 1] - hp.cl_off[k];
+        nvv += sk * sk;
+    }
+    L.vcache = take(nvv * 8);
     L.part = take(p * PART_COLS * 8);
     L.parte = take((size_t)NBLK_E * PART_COLS * 8);
     L.partr = take((size_t)NBLK_R * PART_COLS * 8);
@@ -146,6 +153,9 @@ void build_image(cdsdp* h) {
     }
     h->cls_off[kNumClasses] = (int)blist.size();
     put(img, L.blist, blist);
+    std::vector<int> vv(p + 1, 0);
+    for (int k = 0; k < p; ++k) vv[k + 1] = vv[k] + cs[k] * cs[k];
+    put(img, L.vv_off, vv);
 }
 
 void make_dev(cdsdp* h) {
@@ -170,6 +180,7 @@ void make_dev(cdsdp* h) {
     d.y = (double*)(w + L.y); d.g = (double*)(w + L.g); d.hh = (double*)(w + L.hh); d.s21 = (double*)(w + L.s21);
     d.as11 = (double*)(w + L.as11);
     d.ck0 = w + L.ck0; d.ck1 = w + L.ck1; d.ck2 = w + L.ck2;
+    d.vcache = w + L.vcache; d.vv_off = (const int*)(w + L.vv_off);
     d.part = (double*)(w + L.part); d.parte = (double*)(w + L.parte); d.partr = (double*)(w + L.partr);
     d.scal = (double*)(w + L.scal); d.ctl = (int*)(w + L.ctl); d.hist = (double*)(w + L.hist);
     d.max_iter = h->ws_max_iter;
@@ -194,16 +205,26 @@ void make_dev(cdsdp* h) {
 // ---- projection dispatch ----------------------------------------------------
 
 template <typename T>
-cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, cudaStream_t st) {
+cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const FinishArgs& fa, cudaStream_t st) {
     const int* bl = (const int*)(h->ws + h->L.blist);
-    const double tolrel = sizeof(T) == 4 ? 1.2e-7 : 2.3e-16;
+    ProjArgs pa;
+    pa.rho = o.rho;
+    pa.tolrel = sizeof(T) == 4 ? 1.2e-7 : 2.3e-16;
+    pa.max_sweeps = o.jacobi_max_sweeps;
+    pa.warm_start = o.warm_start > 0 ? 1 : 0;
+    pa.restart = o.warm_start > 0 ? o.warm_start : 1;
+    int last = -1;
+    for (int c = 0; c < kNumClasses; ++c)
+        if (h->cls_off[c + 1] > h->cls_off[c]) last = c;
     cudaError_t e = cudaSuccess;
     for (int c = 0; c < kNumClasses && e == cudaSuccess; ++c) {
         const int* list = bl + h->cls_off[c];
         const int nl = h->cls_off[c + 1] - h->cls_off[c];
         if (nl <= 0) continue;
-        e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, o.rho, tolrel, o.jacobi_max_sweeps, st)
-                           : launch_proj_f64(form, c, h->dev, list, nl, o.rho, tolrel, o.jacobi_max_sweeps, st);
+        FinishArgs f = fa;
+        f.enabled = (c == last) ? fa.enabled : 0;  // the last launch finishes the iteration
+        e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, pa, f, st)
+                           : launch_proj_f64(form, c, h->dev, list, nl, pa, f, st);
     }
     return e;
 }
@@ -216,41 +237,49 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
     Dev& d = h->dev;
     const int GE = h->GE, GR = h->GR, PG = std::max(1, std::min((d.p + 3) / 4, 152 * 32));
     const double rho = o.rho;
+    FinishArgs fa;
+    fa.rho = rho;
+    fa.eps = o.eps;
+    fa.nbe = GE;
+    fa.nbr = GR;
+    fa.enabled = 1;
+    fa.use_cond = use_cond;
+    fa.hnd = hnd;
     cudaError_t e;
-    if (form == 0) {  // Algorithm 1
+    if (form == 0) {  // Algorithm 1; the projection's last block runs the stopping test
         k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0 / rho, 1.0, 1.0 / rho, d.dinv, d.t, 1, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
         k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
-        if ((e = launch_projection<T>(h, 0, o, st)) != cudaSuccess) return e;
+        if ((e = launch_projection<T>(h, 0, o, fa, st)) != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, st);
-        k_finish_primal<<<1, FTHREADS, 0, st>>>(d, rho, o.eps, GE, GR, use_cond, hnd);
-    } else if (form == 1) {  // Algorithm 2
+    } else if (form == 1) {  // Algorithm 2; the v/lambda kernel's last block runs the stopping test
         if (ev0) cudaEventRecord(ev0, st);
-        if ((e = launch_projection<T>(h, 1, o, st)) != cudaSuccess) return e;
+        FinishArgs none = fa;
+        none.enabled = 0;
+        if ((e = launch_projection<T>(h, 1, o, none, st)) != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, st);
         k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0 / rho, d.dinv, d.t, 1, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0 / rho, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
         k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
-        k_vlam_dual<T><<<PG, 128, 0, st>>>(d, rho);
-        k_finish_dual<<<1, FTHREADS, 0, st>>>(d, rho, o.eps, GE, GR, use_cond, hnd);
-    } else {  // Algorithm 3
+        k_vlam_dual<T><<<PG, 128, 0, st>>>(d, rho, fa);
+    } else {  // Algorithm 3; gamma/tau/kappa in sigma21's last block, stopping test in row_update's
         k_hsde_eta<T><<<GE, ETHREADS, 0, st>>>(d, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.q, 0.0, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.kinv, d.g, d.hh, -1, h->TPRM);
         k_hsde_sigma11<<<GE, ETHREADS, 0, st>>>(d, h->Ga);
-        k_hsde_sigma21<<<GR, RTHREADS, 0, st>>>(d, h->TPR);
-        k_hsde_gamma<<<1, FTHREADS, 0, st>>>(d, GE, GR);
+        k_hsde_sigma21<<<GR, RTHREADS, 0, st>>>(d, h->TPR, GE);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
-        if ((e = launch_projection<T>(h, 2, o, st)) != cudaSuccess) return e;
+        FinishArgs none = fa;
+        none.enabled = 0;
+        if ((e = launch_projection<T>(h, 2, o, none, st)) != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, st);
         k_hsde_entry_update<T><<<GE, ETHREADS, 0, st>>>(d, h->Ga);
-        k_hsde_row_update<<<GR, RTHREADS, 0, st>>>(d);
-        k_finish_hsde<<<1, FTHREADS, 0, st>>>(d, o.eps, GE, GR, use_cond, hnd);
+        k_hsde_row_update<<<GR, RTHREADS, 0, st>>>(d, fa);
     }
     return cudaGetLastError();
 }
@@ -264,7 +293,7 @@ cudaError_t launch_iteration_any(cdsdp* h, int form, const cdsdp_opts& o, cudaSt
 
 bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
     return a.eps == b.eps && a.max_iter == b.max_iter && a.rho == b.rho && a.precision == b.precision &&
-           a.jacobi_max_sweeps == b.jacobi_max_sweeps;
+           a.jacobi_max_sweeps == b.jacobi_max_sweeps && a.warm_start == b.warm_start;
 }
 
 void drop_graph(cdsdp* h) {
@@ -311,7 +340,7 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     if (!(o.eps >= 0) || o.max_iter < 1 || !(o.rho > 0) || o.jacobi_max_sweeps < 1 || o.check_every < 1) return CDSDP_ERR_ARG;
     if (o.precision != CDSDP_FP32_PROJECTION && o.precision != CDSDP_FP64) return CDSDP_ERR_ARG;
     if (o.max_iter > h->ws_max_iter) return CDSDP_ERR_ARG;
-    if (o.warm_start != 0) return CDSDP_ERR_ARG;
+    if (o.warm_start < 0) return CDSDP_ERR_ARG;
     return CDSDP_SOLVED;
 }
 
@@ -388,7 +417,7 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->use_graph = 1;
     o->check_every = 50;
     o->jacobi_max_sweeps = 30;
-    o->warm_start = 0;
+    o->warm_start = 16;
     o->profile = 0;
 }
 
