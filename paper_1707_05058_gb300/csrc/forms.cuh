@@ -8,7 +8,8 @@ namespace cdsdp_dev {
 
 // Algorithm 2, after the KKT solve: v_k = z_k + lambda_k/rho + H_k x (Eq. vkEqn),
 // lambda_k <- lambda_k + rho (z_k - v_k) (Eq. MultUpdateDualSDP), one warp per
-// clique; part[k][0..3] = |z_k - v_k|^2, |z_k|^2, |v_k|^2, |lambda_k|^2.
+// clique; per-block sums of |z_k - v_k|^2, |z_k|^2, |v_k|^2, |lambda_k|^2 in
+// columns 0-3 of the partial table.
 __device__ void finish_dual_block(const Dev& d, const FinishArgs& fa);
 
 template <typename T>
@@ -19,6 +20,7 @@ __global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho, FinishArgs
     const T* z = reinterpret_cast<const T*>(d.ck0);
     T* v = reinterpret_cast<T*>(d.ck1);
     T* lam = reinterpret_cast<T*>(d.ck2);
+    double acc[4] = {0, 0, 0, 0};
     for (int k = w0; k < d.p; k += nw) {
         const int off = d.pk_off[k], s = d.csize[k], npk = s * (s + 1) / 2;
         double p0 = 0, p1 = 0, p2 = 0, p3 = 0;
@@ -36,13 +38,11 @@ __global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho, FinishArgs
             p2 += w * double(vn) * double(vn);
             p3 += w * double(ln) * double(ln);
         }
-        p0 = warp_sum(p0); p1 = warp_sum(p1); p2 = warp_sum(p2); p3 = warp_sum(p3);
-        if (lane == 0) {
-            double* pk = d.part + (size_t)k * PART_COLS;
-            pk[0] = p0; pk[1] = p1; pk[2] = p2; pk[3] = p3;
-        }
+        acc[0] += warp_sum(p0); acc[1] += warp_sum(p1); acc[2] += warp_sum(p2); acc[3] += warp_sum(p3);
     }
-    if (last_block_arrival(d)) finish_dual_block(d, fa);
+    const int cols[4] = {0, 1, 2, 3};
+    block_partial_row<4>(acc, d.part, blockIdx.x, cols);
+    if (last_block_single_writer(d)) finish_dual_block(d, fa);
 }
 
 // Algorithm 2 stopping test (Eq. DualConsensusResidual, eps_lambda), run by
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(RTHREADS) k_hsde_sigma21(Dev d, int TPR, int n
     }
     block_sum<1>(bs, sh2);
     if (threadIdx.x == 0) d.partr[blockIdx.x * PART_COLS + 2] = bs[0];
-    if (last_block_arrival(d)) hsde_gamma_block(d, nbe, gridDim.x);
+    if (last_block_single_writer(d)) hsde_gamma_block(d, nbe, gridDim.x);
 }
 
 // gamma = zeta^T sigma, u_hat_2 = omega_2 + zeta^T u_hat_1 = omega_2 + gamma (1 - zeta^T zeta_hat)
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(RTHREADS) k_hsde_row_update(Dev d, FinishArgs 
         d.partr[blockIdx.x * PART_COLS + 0] = p[0];
         d.partr[blockIdx.x * PART_COLS + 1] = p[1];
     }
-    if (last_block_arrival(d)) finish_hsde_block(d, fa);
+    if (last_block_single_writer(d)) finish_hsde_block(d, fa);
 }
 
 // Algorithm 3 stopping tests: Eqs. HSDEerror and HSDEconsensusResidual when

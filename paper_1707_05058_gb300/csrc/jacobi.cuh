@@ -140,44 +140,56 @@ struct BLJacobi {
     // Warm start: v holds the rows of an orthogonal V (lane r: row r), X the
     // symmetric block W (both triangles).  Replace X by V^T W V, so that the
     // sweeps continue from the basis V (the final eigenvectors are V J_1 J_2 ...).
-    // Y is used as scratch.
+    // Both products are spread element-wise over the 32 lanes; Y is scratch.
     __device__ void rotate_into_basis(int lane) {
+        constexpr int NE1 = (S * S + 31) / 32;
         if (lane < S) {
 #pragma unroll
             for (int j = 0; j < S; ++j) Y[lane * LDA + j] = v[j];
         }
         __syncwarp();
-        T acc[S];
+        T acc[NE1];
 #pragma unroll
-        for (int j = 0; j < S; ++j) acc[j] = T(0);
-        if (lane < S) {  // row `lane` of W V
-            for (int i = 0; i < S; ++i) {
-                const T w = X[lane * LDA + i];
-                const T* yi = Y + i * LDA;
-#pragma unroll
-                for (int j = 0; j < S; ++j) acc[j] += w * yi[j];
-            }
-        }
-        __syncwarp();
-        if (lane < S) {
-#pragma unroll
-            for (int j = 0; j < S; ++j) X[lane * LDA + j] = acc[j];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < S; ++j) acc[j] = T(0);
-        if (lane < S) {  // row `lane` of V^T (W V)
-            for (int r = 0; r < S; ++r) {
-                const T vr = Y[r * LDA + lane];
+        for (int e = 0; e < NE1; ++e) {  // (W V)_{rj}
+            const int idx = lane + 32 * e;
+            T a = T(0);
+            if (idx < S * S) {
+                const int r = idx / S, j = idx - r * S;
                 const T* xr = X + r * LDA;
 #pragma unroll
-                for (int j = 0; j < S; ++j) acc[j] += vr * xr[j];
+                for (int i = 0; i < S; ++i) a += xr[i] * Y[i * LDA + j];
+            }
+            acc[e] = a;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < NE1; ++e) {
+            const int idx = lane + 32 * e;
+            if (idx < S * S) {
+                const int r = idx / S, j = idx - r * S;
+                X[r * LDA + j] = acc[e];
             }
         }
         __syncwarp();
-        if (lane < S) {
 #pragma unroll
-            for (int j = 0; j < S; ++j) X[lane * LDA + j] = acc[j];
+        for (int e = 0; e < NE1; ++e) {  // (V^T (W V))_{ij}
+            const int idx = lane + 32 * e;
+            T a = T(0);
+            if (idx < S * S) {
+                const int i = idx / S, j = idx - i * S;
+#pragma unroll
+                for (int r = 0; r < S; ++r) a += Y[r * LDA + i] * X[r * LDA + j];
+            }
+            acc[e] = a;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < NE1; ++e) {
+            const int idx = lane + 32 * e;
+            if (idx < S * S) {
+                const int i = idx / S, j = idx - i * S;
+                X[i * LDA + j] = acc[e];
+            }
         }
         __syncwarp();
     }
@@ -329,6 +341,7 @@ __global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __rest
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     const T rho_t = T(pa.rho), irho = T(1.0 / pa.rho);
+    double acc[5] = {0, 0, 0, 0, 0};
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
@@ -367,14 +380,13 @@ __global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __rest
             p3 += w * dx * dx;
             p4 += w * double(ln) * double(ln);
         }
-        p0 = warp_sum(p0); p1 = warp_sum(p1); p2 = warp_sum(p2); p3 = warp_sum(p3); p4 = warp_sum(p4);
-        if (lane == 0) {
-            double* pk = d.part + (size_t)k * PART_COLS;
-            pk[0] = p0; pk[1] = p1; pk[2] = p2; pk[3] = p3; pk[4] = p4;
-        }
+        acc[0] += warp_sum(p0); acc[1] += warp_sum(p1); acc[2] += warp_sum(p2);
+        acc[3] += warp_sum(p3); acc[4] += warp_sum(p4);
         __syncwarp();
     }
-    if (fa.enabled && last_block_arrival(d)) finish_primal_block(d, fa);
+    const int cols[5] = {0, 1, 2, 3, 4};
+    block_partial_row<5>(acc, d.part, pa.row_off + blockIdx.x, cols);
+    if (fa.enabled && last_block_single_writer(d)) finish_primal_block(d, fa);
 }
 
 // Algorithm 2, z-step (Eq. zkUpdate): z_k <- P(v_k - lambda_k / rho);
@@ -393,6 +405,7 @@ __global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restri
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     const T irho = T(1.0 / pa.rho);
+    double acc[1] = {0};
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
@@ -421,10 +434,11 @@ __global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restri
             z[off + f] = zn;
             p0 += (a == b ? 1.0 : 2.0) * dz * dz;
         }
-        p0 = warp_sum(p0);
-        if (lane == 0) d.part[(size_t)k * PART_COLS + 5] = p0;
+        acc[0] += warp_sum(p0);
         __syncwarp();
     }
+    const int cols[1] = {5};
+    block_partial_row<1>(acc, d.part, pa.row_off + blockIdx.x, cols);
 }
 
 // Algorithm 3, cone step on the s block (Eqs. HsdeStep2-3) with the pieces of
@@ -451,6 +465,7 @@ __global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restri
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     const double gamma = d.scal[SC_GAMMA];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
@@ -505,14 +520,11 @@ __global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restri
             p[5] += w * double(utn) * double(utn);
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) p[c] = warp_sum(p[c]);
-        if (lane == 0) {
-            double* pk = d.part + (size_t)k * PART_COLS;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) pk[c] = p[c];
-        }
+        for (int c = 0; c < 6; ++c) acc[c] += warp_sum(p[c]);
         __syncwarp();
     }
+    const int cols[6] = {0, 1, 2, 3, 4, 5};
+    block_partial_row<6>(acc, d.part, pa.row_off + blockIdx.x, cols);
 }
 
 // Standalone projection of packed blocks (the C ABI's cdsdp_psd_project).

@@ -90,6 +90,7 @@ struct ProjArgs {
     int max_sweeps;
     int warm_start;      // reuse the previous iteration's eigenvectors
     int restart;         // cold start every `restart` iterations
+    int row_off;         // first row of this launch in the per-block partial table
 };
 
 __device__ __forceinline__ bool stopped(const Dev& d) {
@@ -127,21 +128,40 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
     __syncthreads();
 }
 
-// Every thread of a block calls this after writing its partial sums; it
-// returns true in the block that arrives last (in which the other blocks'
-// writes are then visible).  The counter lives in ctl and is reset by the
-// finishing block.
-__device__ __forceinline__ bool last_block_arrival(const Dev& d) {
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
+// Called by every thread of a block after thread 0 (the only writer of the
+// block's partial sums) has written them; returns true in the block that
+// arrives last, which then sees every block's partials (read them through L2).
+// The counter lives in ctl and is reset by the finishing block.
+__device__ __forceinline__ bool last_block_single_writer(const Dev& d) {
+    __shared__ int s_last1;
     if (threadIdx.x == 0) {
+        __threadfence();
         const unsigned int ticket = atomicAdd(reinterpret_cast<unsigned int*>(d.ctl + CTL_COUNTER), 1u);
-        s_last = (ticket == gridDim.x - 1) ? 1 : 0;
+        s_last1 = (ticket == gridDim.x - 1) ? 1 : 0;
     }
     __syncthreads();
-    if (s_last) __threadfence();
-    return s_last != 0;
+    return s_last1 != 0;
+}
+
+// Per-block sum of NV per-warp values (each warp's value valid in its lane 0);
+// thread 0 writes row `row` of the partial table at the listed columns.
+template <int NV>
+__device__ __forceinline__ void block_partial_row(const double (&v)[NV], double* part, int row, const int (&cols)[NV]) {
+    __shared__ double wsum[32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) wsum[warp][c] = v[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double* pr = part + (size_t)row * PART_COLS;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += wsum[w][c];
+            pr[cols[c]] = s;
+        }
+    }
 }
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);

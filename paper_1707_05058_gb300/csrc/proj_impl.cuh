@@ -13,7 +13,7 @@ cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, cons
                         cudaStream_t st) {
     if (nlist <= 0) return cudaSuccess;
     const size_t smem = 4 * BLJacobi<T, S>::bytes;
-    const int grid = std::min((nlist + 3) / 4, 152 * 32);
+    const int grid = proj_grid(nlist);
     cudaError_t e;
     if (form == 0) {
         e = cudaFuncSetAttribute(k_project_primal<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -11,6 +11,10 @@ namespace cdsdp_dev {
 // Padded orders handled by the warp-per-clique projection.
 constexpr int kProjClasses[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
 constexpr int kNumProjClasses = 12;
+// Grid of a projection launch over `nlist` cliques (4 warps per block, one
+// clique per warp, grid-stride beyond 152 x 32 blocks).
+inline int proj_grid(int nlist) { return nlist < 1 ? 1 : (nlist + 3) / 4 < 152 * 32 ? (nlist + 3) / 4 : 152 * 32; }
+
 inline int proj_class_of(int s) {
     for (int c = 0; c < kNumProjClasses; ++c)
         if (s <= kProjClasses[c]) return c;

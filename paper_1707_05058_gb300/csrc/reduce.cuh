@@ -39,11 +39,22 @@ __device__ __forceinline__ void sum_cols(const double* part, int rows, const int
                                          double* sh) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) out[c] = 0.0;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-        const double* pr = part + (size_t)r * PART_COLS;
+    const int stride = blockDim.x;
+    int r = threadIdx.x;
+    for (; r + 3 * stride < rows; r += 4 * stride) {  // four rows in flight per thread
+        double v[4][NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) out[c] += __ldcg(pr + cols[c]);  // L2: written by other blocks
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[u][c] = __ldcg(part + (size_t)(r + u * stride) * PART_COLS + cols[c]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) out[c] += v[u][c];
     }
+    for (; r < rows; r += stride)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c] += __ldcg(part + (size_t)r * PART_COLS + cols[c]);
     block_sum<NC>(out, sh);
 }
 

@@ -217,6 +217,7 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
     for (int c = 0; c < kNumClasses; ++c)
         if (h->cls_off[c + 1] > h->cls_off[c]) last = c;
     cudaError_t e = cudaSuccess;
+    pa.row_off = 0;
     for (int c = 0; c < kNumClasses && e == cudaSuccess; ++c) {
         const int* list = bl + h->cls_off[c];
         const int nl = h->cls_off[c + 1] - h->cls_off[c];
@@ -225,6 +226,7 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
         f.enabled = (c == last) ? fa.enabled : 0;  // the last launch finishes the iteration
         e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, pa, f, st)
                            : launch_proj_f64(form, c, h->dev, list, nl, pa, f, st);
+        pa.row_off += proj_grid(nl);  // rows [row_off, row_off + grid) of the partial table
     }
     return e;
 }
