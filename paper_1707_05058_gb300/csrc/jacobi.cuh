@@ -16,8 +16,12 @@
 // applies J_I^T B J_J and writes them to their permuted positions in the other
 // buffer (one warp barrier per round).  Row `lane` of V stays in registers
 // and its columns are re-indexed by the same sigma (static register moves).
-// A rotation is skipped when |a_pq| <= tol = eps_rel * ||W||_F; a sweep starts
-// only while some off-diagonal entry exceeds tol (or until max_sweeps).
+// A rotation is skipped when |a_pq| <= tol = eps_rel * ||W||_F, and a sweep
+// starts only while some off-diagonal entry exceeds tol (or until max_sweeps).
+// eps_rel = 4 S u (u the unit roundoff): eigenvalues clustered within rounding
+// noise of each other (typical near zero at ADMM convergence) keep
+// off-diagonal entries at about S u ||W||_F, and a lower threshold would make
+// those blocks rotate noise until max_sweeps.
 // Warm start (ADMM iterates move little between iterations): each clique keeps
 // its eigenvectors V from the previous iteration; the new block W is first
 // rotated into that basis (A = V^T W V, two warp-level products) and the
@@ -156,7 +160,7 @@ struct BLJacobi {
             if (idx < S * S) {
                 const int r = idx / S, j = idx - r * S;
                 const T* xr = X + r * LDA;
-#pragma unroll
+#pragma unroll 4
                 for (int i = 0; i < S; ++i) a += xr[i] * Y[i * LDA + j];
             }
             acc[e] = a;
@@ -177,7 +181,7 @@ struct BLJacobi {
             T a = T(0);
             if (idx < S * S) {
                 const int i = idx / S, j = idx - i * S;
-#pragma unroll
+#pragma unroll 4
                 for (int r = 0; r < S; ++r) a += Y[r * LDA + i] * X[r * LDA + j];
             }
             acc[e] = a;
@@ -208,7 +212,9 @@ struct BLJacobi {
         }
     }
 
-    __device__ __forceinline__ void round(T tol, int lane) {
+    // One round: A (shared memory) from X into Y with the pair rotations, and
+    // V's row from vin into vout (columns re-indexed by sigma).
+    __device__ __forceinline__ void round(T tol, int lane, const T (&vin)[S], T (&vout)[S]) {
         T bv[NS][4];
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
@@ -220,15 +226,18 @@ struct BLJacobi {
                 for (int e = 0; e < 4; ++e) bv[t][e] = T(0);
             }
         }
-        // rotation of pair `lane` (lanes < K own the diagonal blocks in slot 0)
+        // rotation of pair `lane` (lanes < K own the diagonal blocks in slot 0):
+        // t = sign(zeta) a_pq / (|zeta| + sqrt(zeta^2 + a_pq^2)), zeta = (a_qq - a_pp)/2
+        // (Rutishauser's form of the 2x2 Schur step), c = 1/sqrt(1+t^2), s = t c.
         T c = T(1), sn = T(0), ta = T(0);
         bool my = false;
         if (lane < K) {
             const T apq = bv[0][1];
             if (fabs(apq) > tol) {
-                const T app = bv[0][0], aqq = bv[0][3];
-                const T theta = (aqq - app) / (T(2) * apq);
-                const T tt = copysign(T(1), theta) / (fabs(theta) + sqrt(T(1) + theta * theta));
+                const T zeta = T(0.5) * (bv[0][3] - bv[0][0]);
+                const T r2 = zeta * zeta + apq * apq;
+                const T r = r2 * rsqrt_t<T>(r2);
+                const T tt = copysign(T(1), zeta) * div_t<T>(apq, fabs(zeta) + r);
                 c = rsqrt_t<T>(T(1) + tt * tt);
                 sn = tt * c;
                 ta = tt * apq;
@@ -255,16 +264,13 @@ struct BLJacobi {
             }
         }
         // V <- V J on this lane's row, then re-index its columns by sigma like A
-        T nv[S];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const T ck = __shfl_sync(0xffffffffu, c, k), sk = __shfl_sync(0xffffffffu, sn, k);
-            const T vp = v[2 * k], vq = v[2 * k + 1];
-            nv[RR::sigma(2 * k)] = ck * vp - sk * vq;
-            nv[RR::sigma(2 * k + 1)] = sk * vp + ck * vq;
+            const T vp = vin[2 * k], vq = vin[2 * k + 1];
+            vout[RR::sigma(2 * k)] = ck * vp - sk * vq;
+            vout[RR::sigma(2 * k + 1)] = sk * vp + ck * vq;
         }
-#pragma unroll
-        for (int j = 0; j < S; ++j) v[j] = nv[j];
         __syncwarp();
         T* tmp = X; X = Y; Y = tmp;
     }
@@ -281,10 +287,18 @@ struct BLJacobi {
         }
         __syncwarp();
         int sw = 0;
+        T w[S];
         while (sw < max_sweeps && off_max(lane) > tol) {
             ++sw;
+            // rounds in pairs, V ping-ponging between v and w (R = S - 1 is odd)
 #pragma unroll 1
-            for (int r = 0; r < R; ++r) round(tol, lane);
+            for (int r = 0; r + 1 < R; r += 2) {
+                round(tol, lane, v, w);
+                round(tol, lane, w, v);
+            }
+            round(tol, lane, v, w);
+#pragma unroll
+            for (int j = 0; j < S; ++j) v[j] = w[j];
         }
         return sw;
     }

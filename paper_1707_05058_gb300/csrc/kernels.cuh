@@ -167,5 +167,13 @@ __device__ __forceinline__ void block_partial_row(const double (&v)[NV], double*
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+template <typename T> __device__ __forceinline__ T div_t(T a, T b);
+template <> __device__ __forceinline__ float div_t<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double div_t<double>(double a, double b) { return a / b; }
+
+// Jacobi threshold relative to ||W||_F for padded order S (see jacobi.cuh).
+__host__ __device__ constexpr double jacobi_tolrel(int S, bool fp32) {
+    return 4.0 * S * (fp32 ? 5.9604644775390625e-8 : 1.1102230246251565e-16);
+}
 
 }  // namespace cdsdp_dev

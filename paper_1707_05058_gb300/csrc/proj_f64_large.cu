@@ -1,0 +1,5 @@
+// double instantiations of the batched projection kernels, padded orders 20..32.
+#define PROJ_T double
+#define PROJ_PART 1
+#define PROJ_SUFFIX(name) name##_f64_large
+#include "proj_impl.cuh"

@@ -9,11 +9,13 @@ namespace cdsdp_dev {
 namespace {
 
 template <typename T, int S>
-cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, const ProjArgs& pa, const FinishArgs& fa,
-                        cudaStream_t st) {
+cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, const ProjArgs& pa_in,
+                        const FinishArgs& fa, cudaStream_t st) {
     if (nlist <= 0) return cudaSuccess;
     const size_t smem = 4 * BLJacobi<T, S>::bytes;
     const int grid = proj_grid(nlist);
+    ProjArgs pa = pa_in;
+    pa.tolrel = jacobi_tolrel(S, sizeof(T) == 4);
     cudaError_t e;
     if (form == 0) {
         e = cudaFuncSetAttribute(k_project_primal<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -41,10 +43,12 @@ cudaError_t launch_standalone(int p, const int* off, const int* size, const void
                                          (int)smem);
     if (e != cudaSuccess) return e;
     k_project_standalone<T, S><<<grid, 128, smem, st>>>(p, off, size, (const T*)W, (T*)X, (T*)eig, voff, (T*)V,
-                                                        vvoff, tolrel, max_sweeps);
+                                                        vvoff, jacobi_tolrel(S, sizeof(T) == 4), max_sweeps);
     return cudaGetLastError();
 }
 
+// PROJ_PART 0 instantiates orders 2..16, PROJ_PART 1 orders 20..32.
+#if PROJ_PART == 0
 #define CDSDP_CLASS_SWITCH(CALL)        \
     switch (kProjClasses[cls]) {        \
         case 2: return CALL(2);         \
@@ -55,12 +59,18 @@ cudaError_t launch_standalone(int p, const int* off, const int* size, const void
         case 12: return CALL(12);       \
         case 14: return CALL(14);       \
         case 16: return CALL(16);       \
+        default: return cudaErrorInvalidValue; \
+    }
+#else
+#define CDSDP_CLASS_SWITCH(CALL)        \
+    switch (kProjClasses[cls]) {        \
         case 20: return CALL(20);       \
         case 24: return CALL(24);       \
         case 28: return CALL(28);       \
         case 32: return CALL(32);       \
         default: return cudaErrorInvalidValue; \
     }
+#endif
 
 }  // namespace
 

@@ -24,15 +24,42 @@ inline int proj_class_of(int s) {
 // form 0/1/2: Algorithm 1/2/3 projection kernels over `list` (cliques of
 // order <= kProjClasses[cls]).
 // `fa` is used by the primal form only (its last block finishes the iteration).
-cudaError_t launch_proj_f32(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
-                            const FinishArgs& fa, cudaStream_t st);
-cudaError_t launch_proj_f64(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
-                            const FinishArgs& fa, cudaStream_t st);
-cudaError_t launch_proj_standalone_f32(int cls, int p, const int* off, const int* size, const void* W, void* X,
-                                       void* eig, const int* voff, void* V, const int* vvoff, double tolrel,
-                                       int max_sweeps, cudaStream_t st);
-cudaError_t launch_proj_standalone_f64(int cls, int p, const int* off, const int* size, const void* W, void* X,
-                                       void* eig, const int* voff, void* V, const int* vvoff, double tolrel,
-                                       int max_sweeps, cudaStream_t st);
+// Instantiations live in proj_{f32,f64}_{small,large}.cu (orders 2..16 / 20..32).
+#define CDSDP_DECLARE_PROJ(SUF)                                                                                 \
+    cudaError_t launch_proj_##SUF(int form, int cls, const Dev& d, const int* list, int nlist,                 \
+                                  const ProjArgs& pa, const FinishArgs& fa, cudaStream_t st);                    \
+    cudaError_t launch_proj_standalone_##SUF(int cls, int p, const int* off, const int* size, const void* W,   \
+                                             void* X, void* eig, const int* voff, void* V, const int* vvoff,  \
+                                             double tolrel, int max_sweeps, cudaStream_t st);
+CDSDP_DECLARE_PROJ(f32_small)
+CDSDP_DECLARE_PROJ(f32_large)
+CDSDP_DECLARE_PROJ(f64_small)
+CDSDP_DECLARE_PROJ(f64_large)
+#undef CDSDP_DECLARE_PROJ
+
+inline cudaError_t launch_proj_f32(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
+                                   const FinishArgs& fa, cudaStream_t st) {
+    return kProjClasses[cls] <= 16 ? launch_proj_f32_small(form, cls, d, list, nlist, pa, fa, st)
+                                   : launch_proj_f32_large(form, cls, d, list, nlist, pa, fa, st);
+}
+inline cudaError_t launch_proj_f64(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
+                                   const FinishArgs& fa, cudaStream_t st) {
+    return kProjClasses[cls] <= 16 ? launch_proj_f64_small(form, cls, d, list, nlist, pa, fa, st)
+                                   : launch_proj_f64_large(form, cls, d, list, nlist, pa, fa, st);
+}
+inline cudaError_t launch_proj_standalone_f32(int cls, int p, const int* off, const int* size, const void* W, void* X,
+                                              void* eig, const int* voff, void* V, const int* vvoff, double tolrel,
+                                              int max_sweeps, cudaStream_t st) {
+    return kProjClasses[cls] <= 16
+               ? launch_proj_standalone_f32_small(cls, p, off, size, W, X, eig, voff, V, vvoff, tolrel, max_sweeps, st)
+               : launch_proj_standalone_f32_large(cls, p, off, size, W, X, eig, voff, V, vvoff, tolrel, max_sweeps, st);
+}
+inline cudaError_t launch_proj_standalone_f64(int cls, int p, const int* off, const int* size, const void* W, void* X,
+                                              void* eig, const int* voff, void* V, const int* vvoff, double tolrel,
+                                              int max_sweeps, cudaStream_t st) {
+    return kProjClasses[cls] <= 16
+               ? launch_proj_standalone_f64_small(cls, p, off, size, W, X, eig, voff, V, vvoff, tolrel, max_sweeps, st)
+               : launch_proj_standalone_f64_large(cls, p, off, size, W, X, eig, voff, V, vvoff, tolrel, max_sweeps, st);
+}
 
 }  // namespace cdsdp_dev

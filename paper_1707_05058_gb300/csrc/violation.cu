@@ -96,7 +96,9 @@ cudaError_t launch_violation(int p, const int* off, const int* size, const void*
     cudaError_t e = cudaFuncSetAttribute(k_psd_violation<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, (p + kViolWarps - 1) / kViolWarps);
-    k_psd_violation<T, S><<<grid, 32 * kViolWarps, smem, st>>>(p, off, size, (const T*)W, tolrel, max_sweeps, scratch,
+    (void)tolrel;
+    k_psd_violation<T, S><<<grid, 32 * kViolWarps, smem, st>>>(p, off, size, (const T*)W,
+                                                              jacobi_tolrel(S, sizeof(T) == 4), max_sweeps, scratch,
                                                               alpha);
     return cudaGetLastError();
 }
