@@ -16,12 +16,13 @@
 // applies J_I^T B J_J and writes them to their permuted positions in the other
 // buffer (one warp barrier per round).  Row `lane` of V stays in registers
 // and its columns are re-indexed by the same sigma (static register moves).
-// A rotation is skipped when |a_pq| <= tol = eps_rel * ||W||_F, and a sweep
-// starts only while some off-diagonal entry exceeds tol (or until max_sweeps).
-// eps_rel = 4 S u (u the unit roundoff): eigenvalues clustered within rounding
-// noise of each other (typical near zero at ADMM convergence) keep
-// off-diagonal entries at about S u ||W||_F, and a lower threshold would make
-// those blocks rotate noise until max_sweeps.
+// A rotation is skipped when |a_pq| <= tol = 2 u ||W||_F (u the unit
+// roundoff), and a sweep starts only while some off-diagonal entry exceeds tol
+// (or until max_sweeps).  Eigenvalues clustered within rounding noise of each
+// other (typical near zero at ADMM convergence) can keep off-diagonal entries
+// at about S u ||W||_F forever; a block whose largest off-diagonal entry is
+// below 4 S u ||W||_F and did not halve over the last sweep has reached that
+// floor and stops.
 // Warm start (ADMM iterates move little between iterations): each clique keeps
 // its eigenvectors V from the previous iteration; the new block W is first
 // rotated into that basis (A = V^T W V, two warp-level products) and the
@@ -281,6 +282,7 @@ struct BLJacobi {
     // rotate_into_basis); otherwise from the identity.  A sweep runs only while
     // some off-diagonal entry exceeds tol.
     __device__ int run(T tol, int max_sweeps, int lane, bool v_preset = false) {
+        const T noise = tol * T(2 * S);  // 4 S u ||W||_F when tol = 2 u ||W||_F
         if (!v_preset) {
 #pragma unroll
             for (int j = 0; j < S; ++j) v[j] = (j == lane) ? T(1) : T(0);
@@ -288,7 +290,12 @@ struct BLJacobi {
         __syncwarp();
         int sw = 0;
         T w[S];
-        while (sw < max_sweeps && off_max(lane) > tol) {
+        T prev = T(3.0e38);
+        while (sw < max_sweeps) {
+            const T off = off_max(lane);
+            if (off <= tol) break;
+            if (off <= noise && off > T(0.5) * prev) break;  // stagnated at the rounding-noise level
+            prev = off;
             ++sw;
             // rounds in pairs, V ping-ponging between v and w (R = S - 1 is odd)
 #pragma unroll 1

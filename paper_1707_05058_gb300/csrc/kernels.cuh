@@ -171,9 +171,9 @@ template <typename T> __device__ __forceinline__ T div_t(T a, T b);
 template <> __device__ __forceinline__ float div_t<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double div_t<double>(double a, double b) { return a / b; }
 
-// Jacobi threshold relative to ||W||_F for padded order S (see jacobi.cuh).
+// Jacobi rotation threshold relative to ||W||_F: twice the unit roundoff (see jacobi.cuh).
 __host__ __device__ constexpr double jacobi_tolrel(int S, bool fp32) {
-    return 4.0 * S * (fp32 ? 5.9604644775390625e-8 : 1.1102230246251565e-16);
+    return (void)S, 2.0 * (fp32 ? 5.9604644775390625e-8 : 1.1102230246251565e-16);
 }
 
 }  // namespace cdsdp_dev
