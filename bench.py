@@ -241,7 +241,7 @@ def main():
                        "sample": f"{n_it} iterations of the FP64 oracle (Algorithm 1) on {WORKLOAD}, 1 thread, {sec:.1f} s"}
             except Exception as exc:  # report, do not hide
                 cpu = {"value": None, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
-        launches_per_iter = 5  # scatter, A W t, cached-inverse GEMV, x update, projection (+ stopping test)
+        launches_per_iter = 4  # scatter, A W t, cached-inverse GEMV, projection (+ x update, stopping test)
         gpu_launches = sum(it32) * launches_per_iter + len(it32)
         line = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,

@@ -32,6 +32,7 @@
 #pragma once
 
 #include "reduce.cuh"
+#include "proj_launch.h"
 
 namespace cdsdp_dev {
 
@@ -343,13 +344,16 @@ struct BLJacobi {
 };
 
 // ---------------------------------------------------------------------------
-// Algorithm 1, projection and multiplier step for every clique in `list`:
+// Algorithm 1, affine x-update, projection and multiplier step for every
+// clique in `list`:
+//   x_e = t_e - (A^T y)_e / D_e on the clique's entries (Appendix A, Eq. KKTflops_s1),
 //   W = H_k x - lambda_k / rho,  x_k <- P(W),  lambda_k <- lambda_k + rho (x_k - H_k x)
-// (Eqs. XkUpdate, LambdakUpdate), with the per-clique sums of the stopping
-// test (Eq. PrimalConsensusResidual and eps_lambda):
-//   part[k] = (|x_k - H_k x|^2, |x_k|^2, |H_k x|^2, |x_k - x_k_old|^2, |lambda_k|^2)
+// (Eqs. XkUpdate, LambdakUpdate).  The first clique covering an entry stores
+// x_e and its term of <c, x>.  Per-block sums of the stopping test (Eq.
+// PrimalConsensusResidual and eps_lambda) go to the partial table:
+//   |x_k - H_k x|^2, |x_k|^2, |H_k x|^2, |x_k - x_k_old|^2, |lambda_k|^2, <c, x>.
 template <typename T, int S>
-__global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
+__global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_project_primal(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
                                                          FinishArgs fa) {
     using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -362,19 +366,38 @@ __global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __rest
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     const T rho_t = T(pa.rho), irho = T(1.0 / pa.rho);
-    double acc[5] = {0, 0, 0, 0, 0};
+    double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
         jac.clear(lane);
         T nrm = T(0);
-        for (int f = lane; f < npk; f += 32) {
-            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
-            const T w = T(d.x[d.gmap[off + f]]) - lam[off + f] * irho;
-            jac.put(a, b, w);
-            nrm += (a == b ? T(1) : T(2)) * w * w;
+        T hx[J::MAXE];
+        double cx = 0.0;
+#pragma unroll
+        for (int e = 0; e < J::MAXE; ++e) {
+            const int f = lane + 32 * e;
+            hx[e] = T(0);
+            if (f < npk) {
+                const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+                const int ent = d.gmap[off + f];
+                double aty = 0.0;
+                const int q1 = d.at_ptr[ent + 1];
+#pragma unroll 4
+                for (int q = d.at_ptr[ent]; q < q1; ++q) aty += d.at_val[q] * d.y[d.at_col[q]];
+                const double xe = d.t[ent] - d.dinv[ent] * aty;
+                if (d.owner[off + f]) {
+                    d.x[ent] = xe;
+                    cx += d.wgt[ent] * d.c[ent] * xe;
+                }
+                hx[e] = T(xe);
+                const T w = hx[e] - lam[off + f] * irho;
+                jac.put(a, b, w);
+                nrm += (a == b ? T(1) : T(2)) * w * w;
+            }
         }
         nrm = warp_sum(nrm);
+        acc[5] += warp_sum(cx);
         __syncwarp();
         if (warm) {
             jac.load_basis(vc + d.vv_off[k], s, lane);
@@ -384,36 +407,39 @@ __global__ void __launch_bounds__(128) k_project_primal(Dev d, const int* __rest
         if (pa.warm_start) jac.store_basis(vc + d.vv_off[k], s, lane);
         jac.prepare_rebuild(lane);
         double p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0;
-        for (int f = lane; f < npk; f += 32) {
-            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
-            const T hx = T(d.x[d.gmap[off + f]]);
-            const T lm = lam[off + f];
-            const T xn = jac.rebuild(a, b, s);
-            const T xo = xk[off + f];
-            const T ln = lm + rho_t * (xn - hx);
-            xk[off + f] = xn;
-            lam[off + f] = ln;
-            const double w = (a == b) ? 1.0 : 2.0;
-            const double dc = double(xn) - double(hx), dx = double(xn) - double(xo);
-            p0 += w * dc * dc;
-            p1 += w * double(xn) * double(xn);
-            p2 += w * double(hx) * double(hx);
-            p3 += w * dx * dx;
-            p4 += w * double(ln) * double(ln);
+#pragma unroll
+        for (int e = 0; e < J::MAXE; ++e) {
+            const int f = lane + 32 * e;
+            if (f < npk) {
+                const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+                const T lm = lam[off + f];
+                const T xn = jac.rebuild(a, b, s);
+                const T xo = xk[off + f];
+                const T ln = lm + rho_t * (xn - hx[e]);
+                xk[off + f] = xn;
+                lam[off + f] = ln;
+                const double w = (a == b) ? 1.0 : 2.0;
+                const double dc = double(xn) - double(hx[e]), dx = double(xn) - double(xo);
+                p0 += w * dc * dc;
+                p1 += w * double(xn) * double(xn);
+                p2 += w * double(hx[e]) * double(hx[e]);
+                p3 += w * dx * dx;
+                p4 += w * double(ln) * double(ln);
+            }
         }
         acc[0] += warp_sum(p0); acc[1] += warp_sum(p1); acc[2] += warp_sum(p2);
         acc[3] += warp_sum(p3); acc[4] += warp_sum(p4);
         __syncwarp();
     }
-    const int cols[5] = {0, 1, 2, 3, 4};
-    block_partial_row<5>(acc, d.part, pa.row_off + blockIdx.x, cols);
+    const int cols[6] = {0, 1, 2, 3, 4, 5};
+    block_partial_row<6>(acc, d.part, pa.row_off + blockIdx.x, cols);
     if (fa.enabled && last_block_single_writer(d)) finish_primal_block(d, fa);
 }
 
 // Algorithm 2, z-step (Eq. zkUpdate): z_k <- P(v_k - lambda_k / rho);
 // part[k][5] = |z_k - z_k_old|^2 (for eps_lambda).
 template <typename T, int S>
-__global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa) {
+__global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_project_dual(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa) {
     using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
@@ -473,7 +499,7 @@ __global__ void __launch_bounds__(128) k_project_dual(Dev d, const int* __restri
 // HSDEconsensusResidual): |u_s - H u_x|^2, |u_s|^2, |H u_x|^2, |v_z - u_t|^2,
 // |v_z|^2, |u_t|^2, where u_x = sigma_11 - gamma zeta_hat_x.
 template <typename T, int S>
-__global__ void __launch_bounds__(128) k_project_hsde(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa) {
+__global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_project_hsde(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa) {
     using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;

@@ -12,23 +12,29 @@ template <typename T, int S>
 cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, const ProjArgs& pa_in,
                         const FinishArgs& fa, cudaStream_t st) {
     if (nlist <= 0) return cudaSuccess;
-    const size_t smem = 4 * BLJacobi<T, S>::bytes;
-    const int grid = proj_grid(nlist);
+    constexpr int MW = proj_max_warps(S, sizeof(T) == 4);
+    const ProjShape sh = proj_shape(nlist, MW);
+    const size_t smem = (size_t)sh.wpb * BLJacobi<T, S>::bytes;
+    const size_t smem_max = (size_t)MW * BLJacobi<T, S>::bytes;
     ProjArgs pa = pa_in;
     pa.tolrel = jacobi_tolrel(S, sizeof(T) == 4);
-    cudaError_t e;
+    static bool attr_done[3] = {false, false, false};  // per instantiation; setting twice is harmless
+    cudaError_t e = cudaSuccess;
     if (form == 0) {
-        e = cudaFuncSetAttribute(k_project_primal<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (!attr_done[0]) e = cudaFuncSetAttribute(k_project_primal<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e != cudaSuccess) return e;
-        k_project_primal<T, S><<<grid, 128, smem, st>>>(d, list, nlist, pa, fa);
+        attr_done[0] = true;
+        k_project_primal<T, S><<<sh.grid, 32 * sh.wpb, smem, st>>>(d, list, nlist, pa, fa);
     } else if (form == 1) {
-        e = cudaFuncSetAttribute(k_project_dual<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (!attr_done[1]) e = cudaFuncSetAttribute(k_project_dual<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e != cudaSuccess) return e;
-        k_project_dual<T, S><<<grid, 128, smem, st>>>(d, list, nlist, pa);
+        attr_done[1] = true;
+        k_project_dual<T, S><<<sh.grid, 32 * sh.wpb, smem, st>>>(d, list, nlist, pa);
     } else {
-        e = cudaFuncSetAttribute(k_project_hsde<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (!attr_done[2]) e = cudaFuncSetAttribute(k_project_hsde<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e != cudaSuccess) return e;
-        k_project_hsde<T, S><<<grid, 128, smem, st>>>(d, list, nlist, pa);
+        attr_done[2] = true;
+        k_project_hsde<T, S><<<sh.grid, 32 * sh.wpb, smem, st>>>(d, list, nlist, pa);
     }
     return cudaGetLastError();
 }

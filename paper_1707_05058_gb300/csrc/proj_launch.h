@@ -11,9 +11,24 @@ namespace cdsdp_dev {
 // Padded orders handled by the warp-per-clique projection.
 constexpr int kProjClasses[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
 constexpr int kNumProjClasses = 12;
-// Grid of a projection launch over `nlist` cliques (4 warps per block, one
-// clique per warp, grid-stride beyond 152 x 32 blocks).
-inline int proj_grid(int nlist) { return nlist < 1 ? 1 : (nlist + 3) / 4 < 152 * 32 ? (nlist + 3) / 4 : 152 * 32; }
+// Warps per block allowed for a projection kernel of padded order S
+// (registers: 16 warps only while a thread needs <= 128 registers).
+__host__ __device__ constexpr int proj_max_warps(int S, bool fp32) { return S <= 16 ? 16 : (fp32 ? 8 : 4); }
+
+// Launch shape of a projection over `nlist` cliques, one clique per warp:
+// the grid is a multiple of the 152 SMs when it can be, and blocks are made as
+// wide as allowed so that every SM receives the same number of warps.
+struct ProjShape { int wpb, grid; };
+inline ProjShape proj_shape(int nlist, int max_warps) {
+    constexpr int kSMs = 152;
+    if (nlist < 1) return {1, 1};
+    const int mult = (nlist + kSMs * max_warps - 1) / (kSMs * max_warps);
+    int grid = kSMs * mult;
+    const int wpb = (nlist + grid - 1) / grid;
+    grid = (nlist + wpb - 1) / wpb;
+    if (grid > kSMs * 32) grid = kSMs * 32;  // grid-stride beyond this
+    return {wpb, grid};
+}
 
 inline int proj_class_of(int s) {
     for (int c = 0; c < kNumProjClasses; ++c)

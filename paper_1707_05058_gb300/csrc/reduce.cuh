@@ -79,11 +79,11 @@ __device__ __forceinline__ void finish_common(Dev d, bool nan_seen, bool converg
 // Algorithm 1 stopping test (Eq. PrimalConsensusResidual, eps_lambda), run by
 // every thread of the block that finishes the iteration.
 __device__ __forceinline__ void finish_primal_block(const Dev& d, const FinishArgs& fa) {
-    __shared__ double sh[32 * 5];
-    const int cols[5] = {0, 1, 2, 3, 4};
-    double s[5];
-    sum_cols<5>(d.part, d.p, cols, s, sh);
-    const double cx = sum_col(d.parte, fa.nbe, 0, sh);
+    __shared__ double sh[32 * 6];
+    const int cols[6] = {0, 1, 2, 3, 4, 5};
+    double s[6];
+    sum_cols<6>(d.part, d.p, cols, s, sh);
+    const double cx = s[5];
     const double by = sum_col(d.partr, fa.nbr, 0, sh);
     if (threadIdx.x == 0) {
         const int it = d.ctl[CTL_ITER] + 1;

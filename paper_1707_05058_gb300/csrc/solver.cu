@@ -29,7 +29,7 @@ inline int class_of(int s) { return proj_class_of(s); }
 struct Layout {
     // constants
     size_t c, dinv, pinv, wgt, a_ptr, a_col, a_valw, at_ptr, at_col, at_val, b, minv, kinv, gmap, pk_off, csize,
-        sc_ptr, sc_idx, zhx, zhy, atb, azhx, blist, vv_off;
+        sc_ptr, sc_idx, zhx, zhy, atb, azhx, blist, vv_off, owner;
     size_t const_end;
     // state
     size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, vcache, part, parte, partr, scal, ctl, hist;
@@ -95,6 +95,7 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     L.zhx = take(NE * 8); L.zhy = take(m * 8); L.atb = take(NE * 8); L.azhx = take(m * 8);
     L.blist = take(p * 4);
     L.vv_off = take((p + 1) * 4);
+    L.owner = take(nd);
     L.const_end = o;
     L.x = take(NE * 8); L.t = take(NE * 8); L.q = take(NE * 8); L.s11 = take(NE * 8); L.atuy = take(NE * 8);
     L.y = take(m * 8); L.g = take(m * 8); L.hh = take(m * 8); L.s21 = take(m * 8); L.as11 = take(m * 8);
@@ -156,6 +157,10 @@ void build_image(cdsdp* h) {
     std::vector<int> vv(p + 1, 0);
     for (int k = 0; k < p; ++k) vv[k + 1] = vv[k] + cs[k] * cs[k];
     put(img, L.vv_off, vv);
+    std::vector<unsigned char> own(hp.gmap.size(), 0);
+    for (int e = 0; e < NE; ++e)
+        if (hp.sc_ptr[e + 1] > hp.sc_ptr[e]) own[hp.sc_idx[hp.sc_ptr[e]]] = 1;
+    put(img, L.owner, own);
 }
 
 void make_dev(cdsdp* h) {
@@ -181,6 +186,7 @@ void make_dev(cdsdp* h) {
     d.as11 = (double*)(w + L.as11);
     d.ck0 = w + L.ck0; d.ck1 = w + L.ck1; d.ck2 = w + L.ck2;
     d.vcache = w + L.vcache; d.vv_off = (const int*)(w + L.vv_off);
+    d.owner = (const unsigned char*)(w + L.owner);
     d.part = (double*)(w + L.part); d.parte = (double*)(w + L.parte); d.partr = (double*)(w + L.partr);
     d.scal = (double*)(w + L.scal); d.ctl = (int*)(w + L.ctl); d.hist = (double*)(w + L.hist);
     d.max_iter = h->ws_max_iter;
@@ -226,7 +232,8 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
         f.enabled = (c == last) ? fa.enabled : 0;  // the last launch finishes the iteration
         e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, pa, f, st)
                            : launch_proj_f64(form, c, h->dev, list, nl, pa, f, st);
-        pa.row_off += proj_grid(nl);  // rows [row_off, row_off + grid) of the partial table
+        const int S = kProjClasses[c];
+        pa.row_off += proj_shape(nl, proj_max_warps(S, sizeof(T) == 4)).grid;  // rows of this launch
     }
     return e;
 }
@@ -248,11 +255,10 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
     fa.use_cond = use_cond;
     fa.hnd = hnd;
     cudaError_t e;
-    if (form == 0) {  // Algorithm 1; the projection's last block runs the stopping test
+    if (form == 0) {  // Algorithm 1; the projection computes x on the fly and its last block the stopping test
         k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0 / rho, 1.0, 1.0 / rho, d.dinv, d.t, 1, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
-        k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
         if ((e = launch_projection<T>(h, 0, o, fa, st)) != cudaSuccess) return e;
