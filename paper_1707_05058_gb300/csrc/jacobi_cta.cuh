@@ -1,0 +1,351 @@
+// Batched PSD projection of clique blocks of order 33..128: one thread block
+// (CTA) per clique.  Same method as jacobi.cuh (two-sided Jacobi in the
+// Brent-Luk parallel ordering, 2x2 symmetric Schur step in Rutishauser's form,
+// warm start from the clique's previous eigenvectors, stagnation stop at the
+// rounding-noise floor), laid out for a CTA:
+//  * A lives in two shared-memory buffers (S x S+1); each round every thread
+//    takes pair-blocks (I, J), I >= J, applies J_I^T B J_J and stores them at
+//    their positions permuted by sigma in the other buffer;
+//  * V (S x S+1) lives in shared memory and is rotated in place at the
+//    round's logical column pair (L[2k], L[2k+1]); L, the logical index held by
+//    each storage position, follows sigma (two small buffers);
+//  * two barriers per round (rotations ready; buffers swapped).
+#pragma once
+
+#include "jacobi.cuh"
+
+namespace cdsdp_dev {
+
+constexpr int kCtaThreads = 256;
+
+template <typename T, int S>
+struct CTAJacobi {
+    using RR = RoundRobin<S>;
+    static constexpr int K = S / 2;
+    static constexpr int R = S - 1;
+    static constexpr int LDA = S + 1;
+    static constexpr int BUF = S * LDA;
+    static constexpr int NB = K * (K + 1) / 2;
+    static constexpr size_t bytes =
+        ((3 * (size_t)BUF + 3 * K) * sizeof(T) + 4 * (size_t)S * sizeof(int) + 64 * sizeof(T) + 15) & ~size_t(15);
+
+    T* X;    // current A
+    T* Y;    // next A
+    T* V;    // eigenvectors, row-major, logical columns
+    T* cs;   // [K] cos, [K] sin, [K] t * a_pq
+    int* L;  // logical index at each storage position (current)
+    int* Ln; // next
+    T* red;  // [32] reduction scratch
+
+    __device__ __forceinline__ void bind(unsigned char* base) {
+        X = reinterpret_cast<T*>(base);
+        Y = X + BUF;
+        V = Y + BUF;
+        cs = V + BUF;
+        red = cs + 3 * K;
+        L = reinterpret_cast<int*>(red + 64);
+        Ln = L + 2 * S;
+    }
+
+    __device__ __forceinline__ static void block_coords(int b, int& I, int& J) {
+        if (b < K) { I = J = b; return; }
+        const int o = b - K;  // off-diagonal blocks I > J, o = I (I - 1) / 2 + J
+        int i = int((1.0f + sqrtf(1.0f + 8.0f * float(o))) * 0.5f);
+        while (i * (i - 1) / 2 > o) --i;
+        while ((i + 1) * i / 2 <= o) ++i;
+        I = i;
+        J = o - i * (i - 1) / 2;
+    }
+
+    __device__ __forceinline__ void clear() {
+        for (int i = threadIdx.x; i < BUF; i += blockDim.x) X[i] = T(0);
+        __syncthreads();
+    }
+    __device__ __forceinline__ void put(int a, int b, T w) {
+        X[a * LDA + b] = w;
+        X[b * LDA + a] = w;
+    }
+
+    // block-wide max of |off-diagonal| of the lower triangle of X
+    __device__ T off_max() {
+        T m = T(0);
+        for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+            const int i = idx / S, j = idx - i * S;
+            if (i > j) m = fmax(m, fabs(X[i * LDA + j]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        __syncthreads();
+        if (lane == 0) red[warp] = m;
+        __syncthreads();
+        T r = T(0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+        __syncthreads();
+        return r;
+    }
+
+    __device__ void round(T tol) {
+        const int tid = threadIdx.x, nt = blockDim.x;
+        if (tid < K) {  // rotation of pair tid (Rutishauser form)
+            const T app = X[(2 * tid) * LDA + 2 * tid], aqq = X[(2 * tid + 1) * LDA + 2 * tid + 1];
+            const T apq = X[(2 * tid + 1) * LDA + 2 * tid];
+            T c = T(1), sn = T(0), ta = T(0);
+            if (fabs(apq) > tol) {
+                const T zeta = T(0.5) * (aqq - app);
+                const T r2 = zeta * zeta + apq * apq;
+                const T r = r2 * rsqrt_t<T>(r2);
+                const T tt = copysign(T(1), zeta) * div_t<T>(apq, fabs(zeta) + r);
+                c = rsqrt_t<T>(T(1) + tt * tt);
+                sn = tt * c;
+                ta = tt * apq;
+            }
+            cs[tid] = c;
+            cs[K + tid] = sn;
+            cs[2 * K + tid] = ta;
+        }
+        if (tid < S) Ln[RR::sigma(tid)] = L[tid];
+        __syncthreads();
+        for (int b = tid; b < NB; b += nt) {  // pair-blocks of A, into Y at permuted positions
+            int I, J;
+            block_coords(b, I, J);
+            const int r0 = 2 * I, r1 = r0 + 1, c0 = 2 * J, c1 = c0 + 1;
+            const int sr0 = RR::sigma(r0), sr1 = RR::sigma(r1), sc0 = RR::sigma(c0), sc1 = RR::sigma(c1);
+            if (I == J) {
+                const T ta = cs[2 * K + I];
+                const bool rot = ta != T(0) || cs[K + I] != T(0);
+                Y[max(sr0, sc0) * LDA + min(sr0, sc0)] = X[r0 * LDA + c0] - ta;
+                Y[max(sr1, sc0) * LDA + min(sr1, sc0)] = rot ? T(0) : X[r1 * LDA + c0];
+                Y[max(sr1, sc1) * LDA + min(sr1, sc1)] = X[r1 * LDA + c1] + ta;
+            } else {
+                const T cI = cs[I], sI = cs[K + I], cJ = cs[J], sJ = cs[K + J];
+                const T b00 = X[r0 * LDA + c0], b10 = X[r1 * LDA + c0], b01 = X[r0 * LDA + c1], b11 = X[r1 * LDA + c1];
+                const T q00 = cI * b00 - sI * b10, q10 = sI * b00 + cI * b10;
+                const T q01 = cI * b01 - sI * b11, q11 = sI * b01 + cI * b11;
+                Y[max(sr0, sc0) * LDA + min(sr0, sc0)] = cJ * q00 - sJ * q01;
+                Y[max(sr0, sc1) * LDA + min(sr0, sc1)] = sJ * q00 + cJ * q01;
+                Y[max(sr1, sc0) * LDA + min(sr1, sc0)] = cJ * q10 - sJ * q11;
+                Y[max(sr1, sc1) * LDA + min(sr1, sc1)] = sJ * q10 + cJ * q11;
+            }
+        }
+        for (int task = tid; task < S * K; task += nt) {  // V <- V J at the logical column pairs
+            const int i = task / K, k = task - i * K;
+            const T c = cs[k], sn = cs[K + k];
+            if (sn == T(0)) continue;
+            const int p = L[2 * k], q = L[2 * k + 1];
+            T* vr = V + i * LDA;
+            const T vp = vr[p], vq = vr[q];
+            vr[p] = c * vp - sn * vq;
+            vr[q] = sn * vp + c * vq;
+        }
+        __syncthreads();
+        T* t = X; X = Y; Y = t;
+        int* u = L; L = Ln; Ln = u;
+    }
+
+    // V <- identity (cold) or keep the loaded basis (warm), then sweep.
+    __device__ int run(T tol, int max_sweeps, bool v_preset) {
+        if (!v_preset)
+            for (int i = threadIdx.x; i < BUF; i += blockDim.x) V[i] = ((i / LDA) == (i % LDA)) ? T(1) : T(0);
+        if (threadIdx.x < S) L[threadIdx.x] = threadIdx.x;
+        __syncthreads();
+        const T noise = tol * T(2 * S);
+        T prev = T(3.0e38);
+        int sw = 0;
+        while (sw < max_sweeps) {
+            const T off = off_max();
+            if (off <= tol) break;
+            if (off <= noise && off > T(0.5) * prev) break;
+            prev = off;
+            ++sw;
+            for (int r = 0; r < R; ++r) round(tol);
+        }
+        return sw;
+    }
+
+    // X <- V^T X V (X holds the symmetric W in both triangles, V the basis).
+    __device__ void rotate_into_basis() {
+        const int tid = threadIdx.x, nt = blockDim.x;
+        for (int idx = tid; idx < S * S; idx += nt) {  // Y = W V
+            const int r = idx / S, j = idx - r * S;
+            T a = T(0);
+#pragma unroll 8
+            for (int i = 0; i < S; ++i) a += X[r * LDA + i] * V[i * LDA + j];
+            Y[r * LDA + j] = a;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < S * S; idx += nt) {  // X = V^T Y
+            const int i = idx / S, j = idx - i * S;
+            T a = T(0);
+#pragma unroll 8
+            for (int r = 0; r < S; ++r) a += V[r * LDA + i] * Y[r * LDA + j];
+            X[i * LDA + j] = a;
+        }
+        __syncthreads();
+    }
+
+    __device__ void load_basis(const T* __restrict__ Vc, int s) {
+        for (int i = threadIdx.x; i < BUF; i += blockDim.x) {
+            const int r = i / LDA, c = i - r * LDA;
+            V[i] = (r < s && c < s) ? Vc[r * s + c] : (r == c ? T(1) : T(0));
+        }
+        __syncthreads();
+    }
+    __device__ void store_basis(T* __restrict__ Vc, int s) const {
+        for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+            const int r = i / s, c = i - r * s;
+            Vc[i] = V[r * LDA + c];
+        }
+    }
+    // Y row a <- V row a scaled by max(lambda, 0) (lambda on X's diagonal).
+    __device__ void prepare_rebuild() {
+        for (int i = threadIdx.x; i < BUF; i += blockDim.x) {
+            const int r = i / LDA, c = i - r * LDA;
+            if (c < S) {
+                const T l = X[c * LDA + c];
+                Y[i] = V[i] * (l > T(0) ? l : T(0));
+            }
+        }
+        __syncthreads();
+    }
+    __device__ __forceinline__ T rebuild(int a, int b, int s) const {
+        const T* ya = Y + a * LDA;
+        const T* vb = V + b * LDA;
+        T acc = T(0);
+        for (int i = 0; i < s; ++i) acc += ya[i] * vb[i];
+        return acc;
+    }
+};
+
+template <int NV>
+__device__ __forceinline__ void cta_sum(double (&v)[NV], double* sh) {
+    block_sum<NV>(v, sh);  // valid in thread 0
+}
+
+// One kernel for every form: FORM 0/1/2 = Algorithm 1/2/3 step (as the warp
+// kernels of jacobi.cuh), FORM 3 = standalone projection.
+template <typename T, int S, int FORM>
+__global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
+                                                              FinishArgs fa, const int* __restrict__ off_arr,
+                                                              const int* __restrict__ size_arr,
+                                                              const T* __restrict__ Win, T* Xout) {
+    using J = CTAJacobi<T, S>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double shr[32 * 6];
+    if (FORM != 3 && stopped(d)) return;
+    J jac;
+    jac.bind(smem);
+    const int tid = threadIdx.x;
+    T* c0 = reinterpret_cast<T*>(d.ck0);
+    T* c1 = reinterpret_cast<T*>(d.ck1);
+    T* c2 = reinterpret_cast<T*>(d.ck2);
+    T* vc = reinterpret_cast<T*>(d.vcache);
+    const bool warm = FORM != 3 && pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
+    const double rho = pa.rho, irho = 1.0 / pa.rho;
+    const double gamma = FORM == 2 ? d.scal[SC_GAMMA] : 0.0;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+        const int k = FORM == 3 ? li : list[li];
+        const int s = FORM == 3 ? size_arr[k] : d.csize[k];
+        const int off = FORM == 3 ? off_arr[k] : d.pk_off[k];
+        if (s > S || s < 1) continue;  // block-uniform
+        const int npk = s * (s + 1) / 2;
+        jac.clear();
+        double nrm = 0.0, cx = 0.0;
+        for (int f = tid; f < npk; f += blockDim.x) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            double w;
+            if (FORM == 0) {
+                const int ent = d.gmap[off + f];
+                double aty = 0.0;
+                for (int q = d.at_ptr[ent]; q < d.at_ptr[ent + 1]; ++q) aty += d.at_val[q] * d.y[d.at_col[q]];
+                const double xe = d.t[ent] - d.dinv[ent] * aty;
+                if (d.owner[off + f]) {
+                    d.x[ent] = xe;
+                    cx += d.wgt[ent] * d.c[ent] * xe;
+                }
+                d.q[ent] = xe;  // H_k x for the epilogue (scratch, same value from every clique)
+                w = xe - double(c1[off + f]) * irho;
+            } else if (FORM == 1) {
+                w = double(c1[off + f]) - double(c2[off + f]) * irho;
+            } else if (FORM == 2) {
+                const int ent = d.gmap[off + f];
+                const double hs = d.s11[ent];
+                const double s12 = 0.5 * (double(c0[off + f]) + double(c1[off + f]) - double(c2[off + f]) + hs);
+                w = s12 - gamma * 0.5 * d.zhx[ent] - double(c1[off + f]);
+            } else {
+                w = double(Win[off + f]);
+            }
+            jac.put(a, b, T(w));
+            nrm += (a == b ? 1.0 : 2.0) * w * w;
+        }
+        double tmp[2] = {nrm, cx};
+        cta_sum<2>(tmp, shr);
+        if (tid == 0) { shr[0] = tmp[0]; acc[5] += tmp[1]; }
+        __syncthreads();
+        nrm = shr[0];
+        __syncthreads();
+        if (warm) {
+            jac.load_basis(vc + d.vv_off[k], s);
+            jac.rotate_into_basis();
+        }
+        jac.run(T(pa.tolrel) * T(sqrt(nrm)), pa.max_sweeps, warm);
+        if (FORM != 3 && pa.warm_start) jac.store_basis(vc + d.vv_off[k], s);
+        jac.prepare_rebuild();
+        double p[6] = {0, 0, 0, 0, 0, 0};
+        for (int f = tid; f < npk; f += blockDim.x) {
+            const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+            const T xn = jac.rebuild(a, b, s);
+            const double w = (a == b) ? 1.0 : 2.0;
+            if (FORM == 0) {
+                const double hx = d.q[d.gmap[off + f]];
+                const double lm = c1[off + f];
+                const double xo = c0[off + f];
+                const double ln = lm + rho * (double(xn) - hx);
+                c0[off + f] = xn;
+                c1[off + f] = T(ln);
+                const double dc = double(xn) - hx, dx = double(xn) - xo;
+                p[0] += w * dc * dc; p[1] += w * double(xn) * double(xn); p[2] += w * hx * hx;
+                p[3] += w * dx * dx; p[4] += w * ln * ln;
+            } else if (FORM == 1) {
+                const double dz = double(xn) - double(c0[off + f]);
+                c0[off + f] = xn;
+                p[0] += w * dz * dz;
+            } else if (FORM == 2) {
+                const int ent = d.gmap[off + f];
+                const double hs = d.s11[ent], zs = 0.5 * d.zhx[ent];
+                const double u_s = c0[off + f], v_z = c1[off + f], u_t = c2[off + f];
+                const double s12 = 0.5 * (u_s + v_z - u_t + hs);
+                const double s22 = u_t - hs + s12;
+                const double uhs = s12 - gamma * zs, utn = s22 + gamma * zs;
+                const double hux = hs - gamma * d.zhx[ent];
+                const double vn = v_z - uhs + double(xn);
+                c0[off + f] = xn;
+                c1[off + f] = T(vn);
+                c2[off + f] = T(utn);
+                const double d1 = double(xn) - hux, d2 = vn - utn;
+                p[0] += w * d1 * d1; p[1] += w * double(xn) * double(xn); p[2] += w * hux * hux;
+                p[3] += w * d2 * d2; p[4] += w * vn * vn; p[5] += w * utn * utn;
+            } else {
+                Xout[off + f] = xn;
+            }
+        }
+        if (FORM != 3) {
+            cta_sum<6>(p, shr);
+            if (tid == 0)
+                for (int c = 0; c < 5; ++c) acc[c] += p[c];
+            if (tid == 0 && FORM == 2) acc[5] += p[5];
+        }
+        __syncthreads();
+    }
+    if (FORM == 3) return;
+    if (tid == 0) {
+        double* pr = d.part + (size_t)(pa.row_off + blockIdx.x) * PART_COLS;
+        if (FORM == 0) { for (int c = 0; c < 6; ++c) pr[c] = acc[c]; }
+        else if (FORM == 1) { pr[5] = acc[0]; }
+        else { for (int c = 0; c < 6; ++c) pr[c] = acc[c]; }
+    }
+    if (FORM == 0 && fa.enabled && last_block_single_writer(d)) finish_primal_block(d, fa);
+}
+
+}  // namespace cdsdp_dev

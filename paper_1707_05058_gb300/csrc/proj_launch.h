@@ -8,9 +8,13 @@
 
 namespace cdsdp_dev {
 
-// Padded orders handled by the warp-per-clique projection.
-constexpr int kProjClasses[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
-constexpr int kNumProjClasses = 12;
+// Padded orders of the projection kernels: one warp per clique up to 32, one
+// thread block per clique above (float32 up to 128, float64 up to 64).
+constexpr int kProjClasses[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32, 48, 64, 96, 128};
+constexpr int kNumProjClasses = 16;
+constexpr int kMaxWarpOrder = 32;
+constexpr int kMaxOrderF32 = 128;
+constexpr int kMaxOrderF64 = 64;
 // Warps per block allowed for a projection kernel of padded order S
 // (registers: 16 warps only while a thread needs <= 128 registers).
 __host__ __device__ constexpr int proj_max_warps(int S, bool fp32) { return S <= 16 ? 16 : (fp32 ? 8 : 4); }
@@ -19,6 +23,7 @@ __host__ __device__ constexpr int proj_max_warps(int S, bool fp32) { return S <=
 // the grid is a multiple of the 152 SMs when it can be, and blocks are made as
 // wide as allowed so that every SM receives the same number of warps.
 struct ProjShape { int wpb, grid; };
+inline int proj_cta_grid(int nlist) { return nlist < 1 ? 1 : (nlist < 152 * 32 ? nlist : 152 * 32); }
 inline ProjShape proj_shape(int nlist, int max_warps) {
     constexpr int kSMs = 152;
     if (nlist < 1) return {1, 1};
@@ -52,19 +57,33 @@ CDSDP_DECLARE_PROJ(f64_small)
 CDSDP_DECLARE_PROJ(f64_large)
 #undef CDSDP_DECLARE_PROJ
 
+cudaError_t launch_proj_cta(bool fp32, int form, int cls, const Dev& d, const int* list, int nlist,
+                            const ProjArgs& pa, const FinishArgs& fa, cudaStream_t st);
+cudaError_t launch_proj_cta_standalone(bool fp32, int cls, int p, const int* off, const int* size, const void* W,
+                                       void* X, int max_sweeps, cudaStream_t st);
+
 inline cudaError_t launch_proj_f32(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
                                    const FinishArgs& fa, cudaStream_t st) {
+    if (kProjClasses[cls] > kMaxWarpOrder) return launch_proj_cta(true, form, cls, d, list, nlist, pa, fa, st);
     return kProjClasses[cls] <= 16 ? launch_proj_f32_small(form, cls, d, list, nlist, pa, fa, st)
                                    : launch_proj_f32_large(form, cls, d, list, nlist, pa, fa, st);
 }
 inline cudaError_t launch_proj_f64(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
                                    const FinishArgs& fa, cudaStream_t st) {
+    if (kProjClasses[cls] > kMaxWarpOrder) return launch_proj_cta(false, form, cls, d, list, nlist, pa, fa, st);
     return kProjClasses[cls] <= 16 ? launch_proj_f64_small(form, cls, d, list, nlist, pa, fa, st)
                                    : launch_proj_f64_large(form, cls, d, list, nlist, pa, fa, st);
+}
+// grid of one projection launch (rows it writes in the partial table)
+inline int proj_launch_grid(int cls, int nlist, bool fp32) {
+    const int S = kProjClasses[cls];
+    if (S > kMaxWarpOrder) return proj_cta_grid(nlist);
+    return proj_shape(nlist, proj_max_warps(S, fp32)).grid;
 }
 inline cudaError_t launch_proj_standalone_f32(int cls, int p, const int* off, const int* size, const void* W, void* X,
                                               void* eig, const int* voff, void* V, const int* vvoff, double tolrel,
                                               int max_sweeps, cudaStream_t st) {
+    if (kProjClasses[cls] > kMaxWarpOrder) return launch_proj_cta_standalone(true, cls, p, off, size, W, X, max_sweeps, st);
     return kProjClasses[cls] <= 16
                ? launch_proj_standalone_f32_small(cls, p, off, size, W, X, eig, voff, V, vvoff, tolrel, max_sweeps, st)
                : launch_proj_standalone_f32_large(cls, p, off, size, W, X, eig, voff, V, vvoff, tolrel, max_sweeps, st);
@@ -72,6 +91,7 @@ inline cudaError_t launch_proj_standalone_f32(int cls, int p, const int* off, co
 inline cudaError_t launch_proj_standalone_f64(int cls, int p, const int* off, const int* size, const void* W, void* X,
                                               void* eig, const int* voff, void* V, const int* vvoff, double tolrel,
                                               int max_sweeps, cudaStream_t st) {
+    if (kProjClasses[cls] > kMaxWarpOrder) return launch_proj_cta_standalone(false, cls, p, off, size, W, X, max_sweeps, st);
     return kProjClasses[cls] <= 16
                ? launch_proj_standalone_f64_small(cls, p, off, size, W, X, eig, voff, V, vvoff, tolrel, max_sweeps, st)
                : launch_proj_standalone_f64_large(cls, p, off, size, W, X, eig, voff, V, vvoff, tolrel, max_sweeps, st);

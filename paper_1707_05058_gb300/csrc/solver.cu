@@ -232,8 +232,7 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
         f.enabled = (c == last) ? fa.enabled : 0;  // the last launch finishes the iteration
         e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, pa, f, st)
                            : launch_proj_f64(form, c, h->dev, list, nl, pa, f, st);
-        const int S = kProjClasses[c];
-        pa.row_off += proj_shape(nl, proj_max_warps(S, sizeof(T) == 4)).grid;  // rows of this launch
+        pa.row_off += proj_launch_grid(c, nl, sizeof(T) == 4);  // rows of this launch
     }
     return e;
 }
@@ -349,6 +348,7 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     if (o.precision != CDSDP_FP32_PROJECTION && o.precision != CDSDP_FP64) return CDSDP_ERR_ARG;
     if (o.max_iter > h->ws_max_iter) return CDSDP_ERR_ARG;
     if (o.warm_start < 0) return CDSDP_ERR_ARG;
+    if (o.precision == CDSDP_FP64 && h->hp.max_clique > kMaxOrderF64) return CDSDP_ERR_UNSUPPORTED;
     return CDSDP_SOLVED;
 }
 
@@ -488,7 +488,7 @@ int cdsdp_workspace_bytes(const cdsdp* h, int max_iter, size_t* bytes) {
 int cdsdp_bind(cdsdp* h, void* d_workspace, size_t bytes, int max_iter, void* stream) {
     if (!h || !d_workspace || max_iter < 1) return CDSDP_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) return CDSDP_ERR_ARG;
-    if (h->hp.max_clique > 32) return CDSDP_ERR_UNSUPPORTED;
+    if (h->hp.max_clique > kMaxOrderF32) return CDSDP_ERR_UNSUPPORTED;
     Layout L = make_layout(h->hp, max_iter);
     if (bytes < L.total) return CDSDP_ERR_NOMEM;
     drop_graph(h);
@@ -636,10 +636,12 @@ const char* cdsdp_strerror(int s) {
 int cdsdp_psd_project(int p, const int* d_off, const int* d_size, int max_size, const void* d_W, void* d_X, void* d_eig,
                       const int* d_voff, void* d_V, const int* d_vvoff, int precision, int max_sweeps, void* stream) {
     cdsdp* h = nullptr;
-    if (p < 0 || max_size < 1 || max_size > 32 || max_sweeps < 1) return p == 0 ? CDSDP_SOLVED : CDSDP_ERR_ARG;
+    if (p < 0 || max_size < 1 || max_sweeps < 1) return p == 0 ? CDSDP_SOLVED : CDSDP_ERR_ARG;
+    if (max_size > (precision == CDSDP_FP64 ? kMaxOrderF64 : kMaxOrderF32)) return CDSDP_ERR_UNSUPPORTED;
     if (p == 0) return CDSDP_SOLVED;
     if (!d_off || !d_size || !d_W || !d_X) return CDSDP_ERR_ARG;
     if ((d_eig && !d_voff) || (d_V && !d_vvoff)) return CDSDP_ERR_ARG;
+    if ((d_eig || d_V) && max_size > kMaxWarpOrder) return CDSDP_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     const int c = class_of(max_size);
     cudaError_t e;

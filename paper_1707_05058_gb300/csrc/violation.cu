@@ -119,7 +119,7 @@ cudaError_t dispatch_violation(int cls, int p, const int* off, const int* size, 
         case 24: return launch_violation<T, 24>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
         case 28: return launch_violation<T, 28>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
         case 32: return launch_violation<T, 32>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        default: return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;  // orders above 32 are not served by this entry point
     }
 }
 

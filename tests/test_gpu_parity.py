@@ -72,6 +72,44 @@ def test_psd_projection_kernel(lib, torch_cuda, prec, sizes):
         assert np.linalg.norm(g - w) <= tol * max(np.linalg.norm(B), 1e-30) * B.shape[0]
 
 
+@pytest.mark.parametrize("prec,sizes", [("fp32", [40] * 6 + [33, 48]), ("fp32", [64, 57, 96, 100, 128]),
+                                        ("fp64", [36, 48, 64, 61])])
+def test_psd_projection_kernel_cta(lib, torch_cuda, prec, sizes):
+    """Orders 33..128 (one thread block per clique) against the oracle."""
+    torch = torch_cuda
+    rng = np.random.default_rng(sum(sizes))
+    blocks = []
+    for s in sizes:
+        G = W._f32(rng.standard_normal((s, s)))
+        blocks.append(W._f32(0.5 * (G + G.T)))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Wv = torch.tensor(_pack(blocks), dtype=dt, device="cuda")
+    off = torch.tensor(np.concatenate([[0], np.cumsum([s * (s + 1) // 2 for s in sizes])]), dtype=torch.int32, device="cuda")
+    sz = torch.tensor(sizes, dtype=torch.int32, device="cuda")
+    X = lib.psd_project(Wv, off, sz)
+    torch.cuda.synchronize()
+    got = _unpack(X.double().cpu().numpy(), sizes)
+    want = [psd.psd_project(B[None])[0] for B in blocks]
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    for B, g, w in zip(blocks, got, want):
+        assert np.linalg.norm(g - w) <= tol * max(np.linalg.norm(B), 1e-30) * B.shape[0]
+
+
+@pytest.mark.parametrize("form", ["primal", "dual", "hsde"])
+def test_cta_cliques_fp64_trajectory(lib, torch_cuda, form):
+    """Cliques of order 36 (thread-block projection kernel): the first 12 FP64
+    iterates of every form equal the oracle's."""
+    prob = W.block_arrow(2, 30, 6, 10, seed=77)
+    dp = admm.decompose(prob)
+    assert max(len(c) for c in dp.cliques) == 36
+    fn = {"primal": admm.primal_admm, "dual": admm.dual_admm, "hsde": admm.hsde_admm}[form]
+    ref = fn(dp, eps=0.0, max_iter=12)
+    P = lib.Problem(prob).bind(max_iter=12)
+    out = P.solve(form, eps=0.0, max_iter=12, precision="fp64")
+    assert out["iters"] == 12
+    np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-7, atol=1e-10)
+
+
 def test_psd_projection_eigenpairs(lib, torch_cuda):
     torch = torch_cuda
     sizes = [9] * 40 + [20] * 10
