@@ -98,8 +98,11 @@ def test_psd_projection_kernel_cta(lib, torch_cuda, prec, sizes):
 @pytest.mark.parametrize("form", ["primal", "dual", "hsde"])
 def test_cta_cliques_fp64_trajectory(lib, torch_cuda, form):
     """Cliques of order 36 (thread-block projection kernel): the first 12 FP64
-    iterates of every form equal the oracle's."""
+    iterates of every form equal the oracle's (HSDE on the normalised
+    instance, see test_hsde_fp64_block_arrow_unscaled)."""
     prob = W.block_arrow(2, 30, 6, 10, seed=77)
+    if form == "hsde":
+        prob = _normalised(prob)
     dp = admm.decompose(prob)
     assert max(len(c) for c in dp.cliques) == 36
     fn = {"primal": admm.primal_admm, "dual": admm.dual_admm, "hsde": admm.hsde_admm}[form]
