@@ -332,3 +332,85 @@ def solve(prob, form="primal", **kw):
     dp = decompose(prob)
     fn = {"primal": primal_admm, "dual": dual_admm, "hsde": hsde_admm}[form]
     return dp, fn(dp, **kw)
+
+
+# ---------------------------------------------------------------------------
+# Differentiation through unrolled Algorithm 1 (not in the paper; the
+# projection's derivative is the Daleckii-Krein formula, oracle/psd.py).
+
+def primal_unrolled(dp: Decomposed, c, b, iters, rho=1.0, keep=False):
+    """`iters` iterations of Algorithm 1 from the zero start with data (c, b)
+    in place of the problem's (full vec over E*, m).  Returns x after the last
+    affine step; with keep=True also the projection inputs W_n of every
+    iteration (for the adjoint)."""
+    A, D = dp.A, dp.D
+    AT = A.T.tocsr()
+    fac = _cholesky((A @ scipy.sparse.diags(1.0 / D) @ A.T).toarray())
+    xk = np.zeros(dp.nd)
+    lam = np.zeros(dp.nd)
+    Ws = []
+    x = None
+    for _ in range(iters):
+        bhat = dp.HT(xk + lam / rho) - c / rho
+        y = scipy.linalg.cho_solve(fac, A @ (bhat / D) - b)
+        x = (bhat - AT @ y) / D
+        Hx = dp.H(x)
+        Wn = Hx - lam / rho
+        if keep:
+            Ws.append(Wn.copy())
+        xk_new = dp.project_cliques(Wn)
+        lam = lam + rho * (xk_new - Hx)
+        xk = xk_new
+    return (x, Ws) if keep else x
+
+
+def _project_cliques_vjp(dp: Decomposed, Wn, gbar):
+    """Adjoint of the stacked clique projection at W_n (Daleckii-Krein)."""
+    from .psd import daleckii_krein_vjp, jacobi_eigh
+    out = np.empty_like(gbar)
+    for k, cl in enumerate(dp.cliques):
+        s = len(cl)
+        sl = slice(dp.offsets[k], dp.offsets[k + 1])
+        lam, V = jacobi_eigh(Wn[sl].reshape(s, s, order="F"))
+        out[sl] = daleckii_krein_vjp(lam, V, gbar[sl].reshape(s, s, order="F")).reshape(-1, order="F")
+    return out
+
+
+def primal_unrolled_vjp(dp: Decomposed, c, b, iters, xbar, rho=1.0):
+    """Reverse-mode adjoint of primal_unrolled: given the upstream gradient
+    xbar of the returned x, the gradients (cbar, bbar) with respect to c and b.
+    Each step of Algorithm 1 is linear except the projection, so the reverse
+    pass transposes the steps in reverse order (plain transposes in the full
+    vec coordinates)."""
+    A, D = dp.A, dp.D
+    AT = A.T.tocsr()
+    fac = _cholesky((A @ scipy.sparse.diags(1.0 / D) @ A.T).toarray())
+    _, Ws = primal_unrolled(dp, c, b, iters, rho, keep=True)
+    xk_bar = np.zeros(dp.nd)
+    lam_bar = np.zeros(dp.nd)
+    cbar = np.zeros(dp.N)
+    bbar = np.zeros(dp.m)
+    for n in range(iters - 1, -1, -1):
+        # lambda' = lambda + rho (x_k' - Hx)
+        xkp_bar = xk_bar + rho * lam_bar
+        hx_bar = -rho * lam_bar
+        lam_prev_bar = lam_bar.copy()
+        # x_k' = P(W),  W = Hx - lambda / rho
+        W_bar = _project_cliques_vjp(dp, Ws[n], xkp_bar)
+        hx_bar = hx_bar + W_bar
+        lam_prev_bar = lam_prev_bar - W_bar / rho
+        # Hx = H x
+        x_bar = dp.HT(hx_bar) + (xbar if n == iters - 1 else 0.0)
+        # x = (bhat - A^T y) / D
+        bhat_bar = x_bar / D
+        y_bar = -(A @ (x_bar / D))
+        # y = (A D^-1 A^T)^-1 (A D^-1 bhat - b)
+        r_bar = scipy.linalg.cho_solve(fac, y_bar)
+        bhat_bar = bhat_bar + (AT @ r_bar) / D
+        bbar -= r_bar
+        # bhat = H^T (x_k + lambda / rho) - c / rho
+        g = dp.H(bhat_bar)
+        xk_bar = g
+        lam_bar = lam_prev_bar + g / rho
+        cbar -= bhat_bar / rho
+    return cbar, bbar
