@@ -191,6 +191,31 @@ int cdsdp_psd_project(int p, const int* d_off, const int* d_size, int max_size,
                       const void* d_W, void* d_X, void* d_eig, const int* d_voff, void* d_V, const int* d_vvoff,
                       int precision, int max_sweeps, void* stream);
 
+/* Differentiation through unrolled Algorithm 1 (not in the paper).  The map
+ * (c, b) -> x_N runs `iters` iterations of Algorithm 1 from the zero start
+ * with the bound problem's A, cliques and cached factor but with the data c
+ * (lower pattern order, nnz_pattern values, the off-diagonal value standing
+ * for both entries) and b (m values) given on the device.  The forward stores
+ * the clique state every `ckpt_every` iterations in the caller-owned device
+ * buffer d_gws (cdsdp_grad_workspace_bytes); the backward replays each
+ * segment from its checkpoint, recording the projection inputs, and runs the
+ * reverse pass: the Daleckii-Krein adjoint of every clique projection on the
+ * GPU (eigenpairs recomputed by the same Jacobi), the linear steps transposed.
+ * Warm start is off and the solve never stops early, so the replay repeats
+ * the forward bit for bit.  Only opts->rho, precision and jacobi_max_sweeps
+ * are used.  Cliques of order > 32 return CDSDP_ERR_UNSUPPORTED; ckpt_every
+ * must not exceed the bound max_iter.
+ *   d_x     out [nnz_pattern] x_N (device)
+ *   d_xbar  [nnz_pattern] dL/dx_N in the same coordinates (device)
+ *   d_cbar  out [nnz_pattern] dL/dc;  d_bbar  out [m] dL/db (device)
+ * The backward must follow a forward with the same arguments and d_gws. */
+int cdsdp_grad_workspace_bytes(const cdsdp* h, int iters, int ckpt_every, int precision, size_t* bytes);
+int cdsdp_unrolled_forward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckpt_every, const double* d_c,
+                           const double* d_b, void* d_gws, size_t gws_bytes, double* d_x, void* stream);
+int cdsdp_unrolled_backward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckpt_every, const double* d_c,
+                            const double* d_b, void* d_gws, size_t gws_bytes, const double* d_xbar, double* d_cbar,
+                            double* d_bbar, void* stream);
+
 /* PSD-violation measure of Section 6.1.3 (Eq. PSD-violation):
  *   alpha = -min{0, lambda_min(W_0), ..., lambda_min(W_{p-1})}
  * over p lower-packed symmetric blocks (layout and orders as in

@@ -66,13 +66,19 @@ _lib.cdsdp_psd_violation_scratch_bytes.argtypes = [ctypes.c_int]
 _lib.cdsdp_psd_violation_scratch_bytes.restype = ctypes.c_size_t
 _lib.cdsdp_psd_violation.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                      ctypes.c_size_t, _vp, _vp]
+_lib.cdsdp_grad_workspace_bytes.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+_lib.cdsdp_unrolled_forward.argtypes = [_vp, ctypes.POINTER(Opts), ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
+                                        ctypes.c_size_t, _vp, _vp]
+_lib.cdsdp_unrolled_backward.argtypes = [_vp, ctypes.POINTER(Opts), ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
+                                         ctypes.c_size_t, _vp, _vp, _vp, _vp]
 _lib.cdsdp_psd_violation_noalloc.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
                                              _vp, _vp]
 
 EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", "cdsdp_pattern",
             "cdsdp_workspace_bytes", "cdsdp_bind", "cdsdp_solve", "cdsdp_results", "cdsdp_free",
             "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile", "cdsdp_psd_violation_scratch_bytes",
-            "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc"]
+            "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc", "cdsdp_grad_workspace_bytes",
+            "cdsdp_unrolled_forward", "cdsdp_unrolled_backward"]
 
 
 class CdsdpError(RuntimeError):
@@ -206,6 +212,62 @@ class Problem:
             raise CdsdpError(st, "cdsdp_profile")
         return a.value, n.value, c.value
 
+    # ---- differentiation through unrolled Algorithm 1 ----
+
+    def problem_data(self, device="cuda"):
+        """(c, b) of the problem as CUDA float64 tensors in the solver's
+        coordinates (c on the lower pattern, pattern order)."""
+        import torch
+        r, cpat = self.pattern()
+        index = {(int(i), int(j)): e for e, (i, j) in enumerate(zip(r, cpat))}
+        c = np.zeros(len(r))
+        (_, _, _, _, b, C_row, C_col, C_val, _, _) = self._keep
+        for i, j, v in zip(C_row, C_col, C_val):
+            c[index[(int(i), int(j))]] += v
+        return (torch.tensor(c, dtype=torch.float64, device=device),
+                torch.tensor(np.asarray(b), dtype=torch.float64, device=device))
+
+    def _grad_ws(self, iters, ckpt_every, precision, device):
+        import torch
+        n = ctypes.c_size_t()
+        st = _lib.cdsdp_grad_workspace_bytes(self._h, int(iters), int(ckpt_every),
+                                             FP64 if precision == "fp64" else FP32, ctypes.byref(n))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_grad_workspace_bytes")
+        return torch.empty(n.value, dtype=torch.uint8, device=device)
+
+    def unrolled_forward(self, c, b, iters, ckpt_every, precision="fp32", rho=1.0, gws=None, stream=None):
+        import torch
+        if self.workspace is None or self.max_iter < ckpt_every:
+            self.bind(max(ckpt_every, self.max_iter))
+        if gws is None:
+            gws = self._grad_ws(iters, ckpt_every, precision, c.device)
+        o = default_opts(precision=precision, rho=rho)
+        x = torch.empty(int(self.info["nnz_pattern"]), dtype=torch.float64, device=c.device)
+        c = c.contiguous(); b = b.contiguous()
+        st = _lib.cdsdp_unrolled_forward(self._h, ctypes.byref(o), int(iters), int(ckpt_every),
+                                         ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                         ctypes.c_void_p(gws.data_ptr()), gws.numel(), ctypes.c_void_p(x.data_ptr()),
+                                         _stream_ptr(stream))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_unrolled_forward")
+        return x, gws
+
+    def unrolled_backward(self, c, b, xbar, iters, ckpt_every, gws, precision="fp32", rho=1.0, stream=None):
+        import torch
+        o = default_opts(precision=precision, rho=rho)
+        cbar = torch.empty_like(c)
+        bbar = torch.empty_like(b)
+        c = c.contiguous(); b = b.contiguous(); xbar = xbar.contiguous().to(torch.float64)
+        st = _lib.cdsdp_unrolled_backward(self._h, ctypes.byref(o), int(iters), int(ckpt_every),
+                                          ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                          ctypes.c_void_p(gws.data_ptr()), gws.numel(),
+                                          ctypes.c_void_p(xbar.data_ptr()), ctypes.c_void_p(cbar.data_ptr()),
+                                          ctypes.c_void_p(bbar.data_ptr()), _stream_ptr(stream))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_unrolled_backward")
+        return cbar, bbar
+
     def results(self, stream=None):
         nz, m = int(self.info["nnz_pattern"]), int(self.info["m"])
         X, y, Z = np.zeros(nz), np.zeros(m), np.zeros(nz)
@@ -274,3 +336,26 @@ def psd_violation_noalloc(W, offsets, sizes, alpha, max_sweeps=30, stream=None):
     if st != 0:
         raise CdsdpError(st, "cdsdp_psd_violation_noalloc")
     return alpha
+
+
+def unrolled_primal(problem, c, b, iters=500, ckpt_every=50, precision="fp32", rho=1.0):
+    """x_N of `iters` unrolled iterations of Algorithm 1 as a differentiable
+    function of c (lower pattern values) and b: gradients flow back through
+    the library's reverse pass (Daleckii-Krein adjoint of the projections)."""
+    import torch
+
+    class _Unrolled(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, c_, b_):
+            x, gws = problem.unrolled_forward(c_.detach(), b_.detach(), iters, ckpt_every, precision, rho)
+            ctx.save_for_backward(c_.detach(), b_.detach())
+            ctx.gws = gws
+            return x
+
+        @staticmethod
+        def backward(ctx, xbar):
+            c_, b_ = ctx.saved_tensors
+            cbar, bbar = problem.unrolled_backward(c_, b_, xbar, iters, ckpt_every, ctx.gws, precision, rho)
+            return cbar, bbar
+
+    return _Unrolled.apply(c, b)

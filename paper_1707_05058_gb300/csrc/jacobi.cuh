@@ -200,6 +200,53 @@ struct BLJacobi {
         __syncwarp();
     }
 
+    // X <- V X V^T (inverse of rotate_into_basis; X symmetric, both triangles).
+    __device__ void rotate_out_of_basis(int lane) {
+        constexpr int NE1 = (S * S + 31) / 32;
+        if (lane < S) {
+#pragma unroll
+            for (int j = 0; j < S; ++j) Y[lane * LDA + j] = v[j];
+        }
+        __syncwarp();
+        T acc[NE1];
+#pragma unroll
+        for (int e = 0; e < NE1; ++e) {  // (X V^T)_{ib} = sum_j X_ij V_bj
+            const int idx = lane + 32 * e;
+            T a = T(0);
+            if (idx < S * S) {
+                const int i = idx / S, b = idx - i * S;
+#pragma unroll 4
+                for (int j = 0; j < S; ++j) a += X[i * LDA + j] * Y[b * LDA + j];
+            }
+            acc[e] = a;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < NE1; ++e) {
+            const int idx = lane + 32 * e;
+            if (idx < S * S) X[(idx / S) * LDA + idx % S] = acc[e];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < NE1; ++e) {  // (V (X V^T))_{ab} = sum_i V_ai (X V^T)_ib
+            const int idx = lane + 32 * e;
+            T a = T(0);
+            if (idx < S * S) {
+                const int ar = idx / S, b = idx - ar * S;
+#pragma unroll 4
+                for (int i = 0; i < S; ++i) a += Y[ar * LDA + i] * X[i * LDA + b];
+            }
+            acc[e] = a;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < NE1; ++e) {
+            const int idx = lane + 32 * e;
+            if (idx < S * S) X[(idx / S) * LDA + idx % S] = acc[e];
+        }
+        __syncwarp();
+    }
+
     // v <- rows of the stored s x s eigenvector matrix (row-major at Vc), padded
     // with the identity on indices s..S-1.
     __device__ __forceinline__ void load_basis(const T* __restrict__ Vc, int s, int lane) {
@@ -392,6 +439,10 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
                 }
                 hx[e] = T(xe);
                 const T w = hx[e] - lam[off + f] * irho;
+                if (d.wstore) {
+                    const int slot = d.ctl[CTL_ITER];
+                    if (slot < d.wstore_count) reinterpret_cast<T*>(d.wstore)[(size_t)slot * d.nd + off + f] = w;
+                }
                 jac.put(a, b, w);
                 nrm += (a == b ? T(1) : T(2)) * w * w;
             }

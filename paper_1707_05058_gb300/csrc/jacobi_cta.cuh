@@ -266,6 +266,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* _
                 }
                 d.q[ent] = xe;  // H_k x for the epilogue (scratch, same value from every clique)
                 w = xe - double(c1[off + f]) * irho;
+                if (d.wstore) {
+                    const int slot = d.ctl[CTL_ITER];
+                    if (slot < d.wstore_count) reinterpret_cast<T*>(d.wstore)[(size_t)slot * d.nd + off + f] = T(w);
+                }
             } else if (FORM == 1) {
                 w = double(c1[off + f]) - double(c2[off + f]) * irho;
             } else if (FORM == 2) {

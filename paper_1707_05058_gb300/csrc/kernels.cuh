@@ -61,6 +61,9 @@ struct Dev {
     void* vcache;         // [sum_k s_k^2] eigenvectors of the previous iteration (warm start)
     const int* vv_off;    // [p+1] offsets into vcache
     const unsigned char* owner;  // [nd] 1 at the first packed position of each pattern entry
+    const double* a_valu; // [nnzA] A_ie unweighted, CSR by rows (reverse pass)
+    void* wstore;         // when set, primal projections record W of iteration n at wstore + n * nd
+    int wstore_count;     // iterations that fit in wstore
     double* part;         // [p * PART_COLS] per-clique partial sums
     double* parte;        // [NBLK_E * PART_COLS] per-block partials, pattern-entry kernels
     double* partr;        // [NBLK_R * PART_COLS] per-block partials, constraint-row kernels

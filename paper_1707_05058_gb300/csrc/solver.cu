@@ -14,6 +14,8 @@
 #include "cdsdp_internal.h"
 #include "forms.cuh"
 #include "proj_launch.h"
+#include "grad.cuh"
+#include "grad_launch.h"
 
 using namespace cdsdp_dev;
 using cdsdp_impl::HostProblem;
@@ -28,7 +30,7 @@ inline int class_of(int s) { return proj_class_of(s); }
 
 struct Layout {
     // constants
-    size_t c, dinv, pinv, wgt, a_ptr, a_col, a_valw, at_ptr, at_col, at_val, b, minv, kinv, gmap, pk_off, csize,
+    size_t c, dinv, pinv, wgt, a_ptr, a_col, a_valw, a_valu, at_ptr, at_col, at_val, b, minv, kinv, gmap, pk_off, csize,
         sc_ptr, sc_idx, zhx, zhy, atb, azhx, blist, vv_off, owner;
     size_t const_end;
     // state
@@ -87,7 +89,7 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     const size_t nnzA = hp.a_col.size();
     const size_t minv_n = hp.diag_factor ? m : m * m;
     L.c = take(NE * 8); L.dinv = take(NE * 8); L.pinv = take(NE * 8); L.wgt = take(NE * 8);
-    L.a_ptr = take((m + 1) * 4); L.a_col = take(nnzA * 4); L.a_valw = take(nnzA * 8);
+    L.a_ptr = take((m + 1) * 4); L.a_col = take(nnzA * 4); L.a_valw = take(nnzA * 8); L.a_valu = take(nnzA * 8);
     L.at_ptr = take((NE + 1) * 4); L.at_col = take(nnzA * 4); L.at_val = take(nnzA * 8);
     L.b = take(m * 8); L.minv = take(minv_n * 8); L.kinv = take(minv_n * 8);
     L.gmap = take(nd * 4); L.pk_off = take((p + 1) * 4); L.csize = take(p * 4);
@@ -136,7 +138,7 @@ void build_image(cdsdp* h) {
     }
     for (size_t q = 0; q < hp.a_val.size(); ++q) aw[q] = wgt[hp.a_col[q]] * hp.a_val[q];
     put(img, L.dinv, dinv); put(img, L.pinv, pinv); put(img, L.wgt, wgt);
-    put(img, L.a_ptr, hp.a_ptr); put(img, L.a_col, hp.a_col); put(img, L.a_valw, aw);
+    put(img, L.a_ptr, hp.a_ptr); put(img, L.a_col, hp.a_col); put(img, L.a_valw, aw); put(img, L.a_valu, hp.a_val);
     put(img, L.at_ptr, hp.at_ptr); put(img, L.at_col, hp.at_col); put(img, L.at_val, hp.at_val);
     put(img, L.b, hp.b); put(img, L.minv, hp.minv); put(img, L.kinv, hp.kinv);
     put(img, L.gmap, hp.gmap); put(img, L.pk_off, hp.pk_off);
@@ -173,6 +175,8 @@ void make_dev(cdsdp* h) {
     d.c = (const double*)(w + L.c); d.dinv = (const double*)(w + L.dinv); d.pinv = (const double*)(w + L.pinv);
     d.wgt = (const double*)(w + L.wgt);
     d.a_ptr = (const int*)(w + L.a_ptr); d.a_col = (const int*)(w + L.a_col); d.a_valw = (const double*)(w + L.a_valw);
+    d.a_valu = (const double*)(w + L.a_valu);
+    d.wstore = nullptr; d.wstore_count = 0;
     d.at_ptr = (const int*)(w + L.at_ptr); d.at_col = (const int*)(w + L.at_col); d.at_val = (const double*)(w + L.at_val);
     d.b = (const double*)(w + L.b); d.minv = (const double*)(w + L.minv); d.kinv = (const double*)(w + L.kinv);
     d.gmap = (const int*)(w + L.gmap); d.pk_off = (const int*)(w + L.pk_off); d.csize = (const int*)(w + L.csize);
@@ -410,6 +414,59 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
 }
 
 }  // namespace
+
+// ---- differentiation through unrolled Algorithm 1 -------------------------
+
+struct GradLayout {
+    size_t ckpt, wstore, xkbar, lambar, hxbar, lamprev, xbar, u, sbar, ybar, rbar, total;
+    int nseg;
+};
+
+GradLayout make_grad_layout(const Dev& d, int iters, int ckpt_every, bool fp32) {
+    GradLayout G{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1)); return r; };
+    const size_t ts = fp32 ? 4 : 8, nd = d.nd, NE = d.NE, m = d.m;
+    G.nseg = (iters + ckpt_every - 1) / ckpt_every;
+    G.ckpt = take((size_t)G.nseg * 2 * nd * ts);
+    G.wstore = take((size_t)ckpt_every * nd * ts);
+    G.xkbar = take(nd * 8); G.lambar = take(nd * 8); G.hxbar = take(nd * 8); G.lamprev = take(nd * 8);
+    G.xbar = take(NE * 8); G.u = take(NE * 8); G.sbar = take(NE * 8);
+    G.ybar = take(m * 8); G.rbar = take(m * 8);
+    G.total = o;
+    return G;
+}
+
+int check_unrolled(cdsdp* h, const cdsdp_opts& o, int iters, int ckpt_every) {
+    if (!h->ws) return CDSDP_ERR_STATE;
+    if (iters < 1 || ckpt_every < 1 || !(o.rho > 0) || o.jacobi_max_sweeps < 1) return CDSDP_ERR_ARG;
+    if (o.precision != CDSDP_FP32_PROJECTION && o.precision != CDSDP_FP64) return CDSDP_ERR_ARG;
+    if (h->hp.max_clique > kMaxWarpOrder) return CDSDP_ERR_UNSUPPORTED;
+    if (ckpt_every > h->ws_max_iter) return CDSDP_ERR_ARG;
+    return CDSDP_SOLVED;
+}
+
+// Run `len` iterations of Algorithm 1 (no early stop) with the device view dd.
+int run_segment(cdsdp* h, Dev dd, const cdsdp_opts& o, int len, cudaStream_t st) {
+    const Dev saved = h->dev;
+    h->dev = dd;
+    k_reset_ctl<<<1, 32, 0, st>>>(dd);
+    cudaError_t e = cudaGetLastError();
+    for (int it = 0; it < len && e == cudaSuccess; ++it)
+        e = launch_iteration_any(h, 0, o, st, 0, cudaGraphConditionalHandle{});
+    h->dev = saved;
+    return e == cudaSuccess ? CDSDP_SOLVED : fail_cuda(h, e, "unrolled iteration");
+}
+
+cdsdp_opts unrolled_opts(const cdsdp_opts* opts) {
+    cdsdp_opts o;
+    if (opts) o = *opts; else cdsdp_default_opts(&o);
+    o.eps = 0.0;        // fixed number of iterations
+    o.warm_start = 0;   // replays must repeat the forward bit for bit
+    o.use_graph = 0;
+    o.profile = 0;
+    return o;
+}
 
 // =============================================================================
 // C ABI
@@ -653,6 +710,110 @@ int cdsdp_psd_project(int p, const int* d_off, const int* d_size, int max_size, 
         return CDSDP_ERR_ARG;
     CK(e);
     CK(cudaGetLastError());
+    return CDSDP_SOLVED;
+}
+
+
+int cdsdp_grad_workspace_bytes(const cdsdp* h, int iters, int ckpt_every, int precision, size_t* bytes) {
+    if (!h || !bytes || iters < 1 || ckpt_every < 1) return CDSDP_ERR_ARG;
+    if (!h->ws) return CDSDP_ERR_STATE;
+    *bytes = make_grad_layout(h->dev, iters, ckpt_every, precision != CDSDP_FP64).total;
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_unrolled_forward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckpt_every, const double* d_c,
+                           const double* d_b, void* d_gws, size_t gws_bytes, double* d_x, void* stream) {
+    if (!h || !d_c || !d_b || !d_gws || !d_x) return CDSDP_ERR_ARG;
+    const cdsdp_opts o = unrolled_opts(opts);
+    int rc = check_unrolled(h, o, iters, ckpt_every);
+    if (rc != CDSDP_SOLVED) return rc;
+    const bool fp32 = o.precision != CDSDP_FP64;
+    const GradLayout G = make_grad_layout(h->dev, iters, ckpt_every, fp32);
+    if (gws_bytes < G.total) return CDSDP_ERR_NOMEM;
+    if (reinterpret_cast<uintptr_t>(d_gws) % kAlign) return CDSDP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* g = (unsigned char*)d_gws;
+    Dev dd = h->dev;
+    dd.c = d_c;
+    dd.b = d_b;
+    dd.max_iter = ckpt_every;
+    const size_t ts = fp32 ? 4 : 8, nd = dd.nd;
+    CK(cudaMemsetAsync(h->ws + h->L.const_end, 0, h->L.total - h->L.const_end, st));
+    for (int sg = 0; sg < G.nseg; ++sg) {
+        unsigned char* ck = g + G.ckpt + (size_t)sg * 2 * nd * ts;
+        CK(cudaMemcpyAsync(ck, dd.ck0, nd * ts, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ck + nd * ts, dd.ck1, nd * ts, cudaMemcpyDeviceToDevice, st));
+        const int len = std::min(ckpt_every, iters - sg * ckpt_every);
+        rc = run_segment(h, dd, o, len, st);
+        if (rc != CDSDP_SOLVED) return rc;
+    }
+    CK(cudaMemcpyAsync(d_x, dd.x, (size_t)dd.NE * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_unrolled_backward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckpt_every, const double* d_c,
+                            const double* d_b, void* d_gws, size_t gws_bytes, const double* d_xbar, double* d_cbar,
+                            double* d_bbar, void* stream) {
+    if (!h || !d_c || !d_b || !d_gws || !d_xbar || !d_cbar || !d_bbar) return CDSDP_ERR_ARG;
+    const cdsdp_opts o = unrolled_opts(opts);
+    int rc = check_unrolled(h, o, iters, ckpt_every);
+    if (rc != CDSDP_SOLVED) return rc;
+    const bool fp32 = o.precision != CDSDP_FP64;
+    const GradLayout G = make_grad_layout(h->dev, iters, ckpt_every, fp32);
+    if (gws_bytes < G.total) return CDSDP_ERR_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* g = (unsigned char*)d_gws;
+    Dev dd = h->dev;
+    dd.c = d_c;
+    dd.b = d_b;
+    dd.max_iter = ckpt_every;
+    dd.wstore = g + G.wstore;
+    dd.wstore_count = ckpt_every;
+    const size_t ts = fp32 ? 4 : 8, nd = dd.nd;
+    double* xkbar = (double*)(g + G.xkbar);
+    double* lambar = (double*)(g + G.lambar);
+    double* hxbar = (double*)(g + G.hxbar);
+    double* lamprev = (double*)(g + G.lamprev);
+    double* xbar = (double*)(g + G.xbar);
+    double* u = (double*)(g + G.u);
+    double* sbar = (double*)(g + G.sbar);
+    double* ybar = (double*)(g + G.ybar);
+    double* rbar = (double*)(g + G.rbar);
+    CK(cudaMemsetAsync(xkbar, 0, nd * 8, st));
+    CK(cudaMemsetAsync(lambar, 0, nd * 8, st));
+    CK(cudaMemsetAsync(d_cbar, 0, (size_t)dd.NE * 8, st));
+    CK(cudaMemsetAsync(d_bbar, 0, (size_t)dd.m * 8, st));
+    const int* bl = (const int*)(h->ws + h->L.blist);
+    const int GE = std::max(1, std::min(NBLK_E, (dd.NE + ETHREADS - 1) / ETHREADS));
+    const int GR = std::max(1, std::min(NBLK_R, (dd.m + 7) / 8));
+    const int GN = std::max(1, std::min(NBLK_E, (dd.nd + ETHREADS - 1) / ETHREADS));
+    GradArgs ga;
+    ga.xkbar = xkbar; ga.lambar = lambar; ga.hxbar = hxbar; ga.lamprev = lamprev;
+    ga.rho = o.rho; ga.tolrel = 0.0; ga.max_sweeps = o.jacobi_max_sweeps;
+    for (int sg = G.nseg - 1; sg >= 0; --sg) {
+        unsigned char* ck = g + G.ckpt + (size_t)sg * 2 * nd * ts;
+        CK(cudaMemsetAsync(h->ws + h->L.const_end, 0, h->L.total - h->L.const_end, st));
+        CK(cudaMemcpyAsync(dd.ck0, ck, nd * ts, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(dd.ck1, ck + nd * ts, nd * ts, cudaMemcpyDeviceToDevice, st));
+        const int len = std::min(ckpt_every, iters - sg * ckpt_every);
+        rc = run_segment(h, dd, o, len, st);  // replay, recording W of every iteration
+        if (rc != CDSDP_SOLVED) return rc;
+        for (int n = len - 1; n >= 0; --n) {
+            ga.slot = n;
+            for (int c = 0; c < kNumClasses; ++c) {
+                const int nl = h->cls_off[c + 1] - h->cls_off[c];
+                if (nl <= 0) continue;
+                CK(launch_bwd_proj(fp32, c, dd, bl + h->cls_off[c], nl, ga, st));
+            }
+            const bool last = (sg * ckpt_every + n == iters - 1);
+            k_bwd_scatter<<<GE, ETHREADS, 0, st>>>(dd, hxbar, last ? d_xbar : nullptr, xbar, u);
+            k_bwd_ybar<<<GR, RTHREADS, 0, st>>>(dd, u, ybar);
+            k_bwd_rbar<<<GR, RTHREADS, 0, st>>>(dd, ybar, rbar, d_bbar);
+            k_bwd_tbar<<<GE, ETHREADS, 0, st>>>(dd, xbar, rbar, sbar, d_cbar, o.rho);
+            k_bwd_state<<<GN, ETHREADS, 0, st>>>(dd, sbar, lamprev, xkbar, lambar, o.rho);
+            CK(cudaGetLastError());
+        }
+    }
     return CDSDP_SOLVED;
 }
 
