@@ -128,7 +128,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -199,7 +199,7 @@ def main():
     time_to_eps_ms = statistics.median(ms32)
 
     # ---- plain FP64 form (FP64 everywhere, one launch per phase, no graph)
-    ms64, it64 = timed_solves(1, 0, precision="fp64", use_graph=0, check_every=10)
+    ms64, it64 = timed_solves(1, 0, precision="fp64", use_graph=0, check_every=10, warm_start=0)
 
     # ---- profiled FP32 solve: per-launch projection time from CUDA events
     P.solve("primal", outputs=False, eps=1e-4, max_iter=max_iter, precision="fp32", profile=1, check_every=50)
@@ -254,7 +254,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_eps_ms": time_to_eps_ms, "iters_to_eps": int(statistics.median(it32)),
             "fp64_plain": {"iters_per_s": sum(it64) / (sum(ms64) / 1e3), "time_to_eps_ms": statistics.median(ms64),
-                           "iters_to_eps": int(statistics.median(it64))},
+                           "iters_to_eps": int(statistics.median(it64)),
+                           "form": "float64 everywhere, cold Jacobi every iteration, one launch per phase, no graph"},
             "speedup_time_to_eps_fp32_graph_vs_fp64_plain": statistics.median(ms64) / time_to_eps_ms,
             "clique_proj_gflops": gflops,
             "setup_ms": setup_s * 1e3,
