@@ -72,6 +72,12 @@ typedef struct {
                               iteration, with a cold start every N iterations          */
     int profile;           /* 1: run the use_graph = 0 path and bracket every projection
                               launch with CUDA events on `stream` (see cdsdp_profile)      */
+    int component_stop;    /* Algorithms 1-2 on a problem with independent components
+                              (see cdsdp_components): 1 = each component runs its own
+                              stopping test and is frozen once it holds, so its result
+                              is that of a solve of the component alone; 0 = one test
+                              over the whole problem.  HSDE always uses one test (tau
+                              and kappa are shared).                                   */
 } cdsdp_opts;
 
 typedef struct {
@@ -85,11 +91,12 @@ typedef struct {
     int chordal;             /* 1 if the aggregate pattern was already chordal       */
     int diag_factor;         /* 1 if A D^-1 A^T is diagonal (e.g. MaxCut, Section 4.1.2) */
     long long upload_bytes;  /* size of the one host-to-device copy cdsdp_bind makes   */
+    int ncomp;               /* independent components (see cdsdp_components)        */
 } cdsdp_info_t;
 
 /* Fill `o` with defaults: eps 1e-4, max_iter 2000, rho 1, FP32 projection,
  * graph on, check_every 50, 30 Jacobi sweeps, warm start with a cold start every
- * 16 iterations, no profiling. */
+ * 16 iterations, no profiling, per-component stopping. */
 void cdsdp_default_opts(cdsdp_opts* o);
 
 /* Data preprocessing of Algorithms 1-3 (host only, no GPU call):
@@ -126,6 +133,26 @@ int cdsdp_cliques(const cdsdp* h, int* offsets, int* vertices);
  * rows[nnz_pattern], cols[nnz_pattern].  X and Z are returned in this order. */
 int cdsdp_pattern(const cdsdp* h, int* rows, int* cols);
 
+/* Independent components: connected components of the extended pattern in
+ * which every constraint also joins the vertices it touches.  A direct sum of
+ * SDPs (a batch of independent problems given as one block-diagonal problem)
+ * has one component per summand; A D^-1 A^T is then block diagonal and the
+ * library caches one dense inverse block per component.  Components are
+ * numbered by their smallest vertex.
+ *   vertex_comp      [n] component of each vertex (may be NULL)
+ *   constraint_comp  [m] component of each constraint (may be NULL)
+ * Host only, valid right after cdsdp_setup. */
+int cdsdp_components(const cdsdp* h, int* vertex_comp, int* constraint_comp);
+
+/* Per-component outcome of the last solve (each output may be NULL):
+ *   iters   [ncomp] iterations the component ran
+ *   status  [ncomp] its outcome (CDSDP_SOLVED, CDSDP_MAX_ITER, CDSDP_ERR_NUMERIC)
+ *   res     [ncomp x 8] its last stopping-test row (columns as in cdsdp_solve's hist)
+ * When the last solve ran one test over the whole problem (component_stop = 0,
+ * HSDE, or a single component) every component reports the global values.
+ * Errors: CDSDP_ERR_STATE before the first solve. */
+int cdsdp_component_results(cdsdp* h, void* stream, int* iters, int* status, double* res);
+
 /* Device workspace the caller must provide for solves of up to max_iter
  * iterations (history included). */
 int cdsdp_workspace_bytes(const cdsdp* h, int max_iter, size_t* bytes);
@@ -148,7 +175,10 @@ int cdsdp_bind(cdsdp* h, void* d_workspace, size_t bytes, int max_iter, void* st
  *         primal/dual: eps_c, eps_lambda, 0, 0, <C,X>, b^T y, 0, 0
  *         HSDE tau>0:  eps_p, eps_d, eps_g, eps_c, <C,X>, b^T y, tau, kappa
  *         HSDE tau=0:  ||A^T u_y + H^T v_z||, ||A u_x||, b^T u_y, c^T u_x, 0, 0, tau, kappa
- *   iters number of iterations run
+ *   iters number of iterations run (with per-component stopping: the largest
+ *         over the components; hist then holds, per iteration, the largest
+ *         eps_c and eps_lambda over the components tested, the summed
+ *         objectives and, in column 6, the number of components still running)
  *   cert  HSDE certificate: [m] (primal infeasible) or [nnz_pattern] (dual
  *         infeasible); must hold max(m, nnz_pattern) doubles
  * Returns the outcome (CDSDP_SOLVED, CDSDP_MAX_ITER, CDSDP_*_INFEASIBLE) or

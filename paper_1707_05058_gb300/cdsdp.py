@@ -35,13 +35,15 @@ _ll = ctypes.c_longlong
 class Opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_iter", ctypes.c_int), ("rho", ctypes.c_double),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("jacobi_max_sweeps", ctypes.c_int), ("warm_start", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("jacobi_max_sweeps", ctypes.c_int), ("warm_start", ctypes.c_int), ("profile", ctypes.c_int),
+                ("component_stop", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int), ("max_clique", ctypes.c_int),
                 ("nnz_pattern", _ll), ("n_d_lower", _ll), ("nnz_A", _ll), ("n_fill", _ll),
-                ("chordal", ctypes.c_int), ("diag_factor", ctypes.c_int), ("upload_bytes", _ll)]
+                ("chordal", ctypes.c_int), ("diag_factor", ctypes.c_int), ("upload_bytes", _ll),
+                ("ncomp", ctypes.c_int)]
 
 
 _lib.cdsdp_default_opts.argtypes = [ctypes.POINTER(Opts)]
@@ -51,6 +53,8 @@ _lib.cdsdp_setup.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32
 _lib.cdsdp_info.argtypes = [_vp, ctypes.POINTER(Info)]
 _lib.cdsdp_cliques.argtypes = [_vp, _i32p, _i32p]
 _lib.cdsdp_pattern.argtypes = [_vp, _i32p, _i32p]
+_lib.cdsdp_components.argtypes = [_vp, _i32p, _i32p]
+_lib.cdsdp_component_results.argtypes = [_vp, _vp, _i32p, _i32p, _f64p]
 _lib.cdsdp_workspace_bytes.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
 _lib.cdsdp_bind.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.c_int, _vp]
 _lib.cdsdp_solve.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, _f64p, _f64p, _f64p, _f64p, _i32p, _f64p]
@@ -78,7 +82,8 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_workspace_bytes", "cdsdp_bind", "cdsdp_solve", "cdsdp_results", "cdsdp_free",
             "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile", "cdsdp_psd_violation_scratch_bytes",
             "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc", "cdsdp_grad_workspace_bytes",
-            "cdsdp_unrolled_forward", "cdsdp_unrolled_backward"]
+            "cdsdp_unrolled_forward", "cdsdp_unrolled_backward", "cdsdp_components",
+            "cdsdp_component_results"]
 
 
 class CdsdpError(RuntimeError):
@@ -157,6 +162,28 @@ class Problem:
         c = np.zeros(nz, np.int32)
         _lib.cdsdp_pattern(self._h, _ptr(r, ctypes.c_int), _ptr(c, ctypes.c_int))
         return r, c
+
+    def components(self):
+        """(component of each vertex [n], component of each constraint [m])."""
+        vc = np.zeros(int(self.info["n"]), np.int32)
+        rc = np.zeros(int(self.info["m"]), np.int32)
+        st = _lib.cdsdp_components(self._h, _ptr(vc, ctypes.c_int), _ptr(rc, ctypes.c_int))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_components")
+        return vc, rc
+
+    def component_results(self, stream=None):
+        """Per-component (iterations, status, last stopping-test row [ncomp, 8])
+        of the last solve."""
+        nc = int(self.info["ncomp"])
+        it = np.zeros(nc, np.int32)
+        stt = np.zeros(nc, np.int32)
+        res = np.zeros((nc, 8))
+        st = _lib.cdsdp_component_results(self._h, _stream_ptr(stream), _ptr(it, ctypes.c_int),
+                                          _ptr(stt, ctypes.c_int), _ptr(res, ctypes.c_double))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_component_results")
+        return it, stt, res
 
     def workspace_bytes(self, max_iter):
         n = ctypes.c_size_t()

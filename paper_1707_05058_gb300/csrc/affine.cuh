@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(ETHREADS) k_scatter(Dev d, const T* __restrict
     for (int it = 0; it < nloop; ++it) {  // uniform trip count: every lane reaches the shuffles
         const int e = gid + it * ng;
         double acc = 0.0;
-        if (e < d.NE) {
+        const bool live = e < d.NE && !(check_stop && frozen_entry(d, e));
+        if (live) {
             const int j1 = d.sc_ptr[e + 1];
             for (int j = d.sc_ptr[e] + lig; j < j1; j += G) {
                 const int q = d.sc_idx[j];
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(ETHREADS) k_scatter(Dev d, const T* __restrict
             }
         }
         acc = group_sum(acc, G);
-        if (e < d.NE && lig == 0) {
+        if (live && lig == 0) {
             const double r = alpha * d.c[e] + beta * acc;
             out[e] = scale ? r * scale[e] : r;
         }
@@ -61,12 +62,13 @@ __global__ void __launch_bounds__(ETHREADS) k_xupd(Dev d, const double* __restri
     for (int it = 0; it < nloop; ++it) {
         const int e = gid + it * ng;
         double s = 0.0;
-        if (e < d.NE) {
+        const bool live = e < d.NE && !frozen_entry(d, e);
+        if (live) {
             const int q1 = d.at_ptr[e + 1];
             for (int q = d.at_ptr[e] + lig; q < q1; q += G) s += d.at_val[q] * y[d.at_col[q]];
         }
         s = group_sum(s, G);
-        if (e < d.NE && lig == 0) {
+        if (live && lig == 0) {
             const double xe = t[e] - d.dinv[e] * s;
             x[e] = xe;
             cx[0] += d.wgt[e] * d.c[e] * xe;
@@ -88,17 +90,19 @@ __global__ void __launch_bounds__(RTHREADS) k_rows_aw(Dev d, const double* __res
     for (int it = 0; it < nloop; ++it) {
         const int i = (it * gridDim.x + blockIdx.x) * rpb + gi;
         double s = 0.0;
-        if (i < d.m) {
+        const bool live = i < d.m && !frozen_row(d, i);
+        if (live) {
             const int q1 = d.a_ptr[i + 1];
             for (int q = d.a_ptr[i] + tig; q < q1; q += TPR) s += d.a_valw[q] * v[d.a_col[q]];
         }
         s = row_group_sum(s, TPR, sh);
-        if (i < d.m && tig == 0) out[i] = s + delta * d.b[i];
+        if (live && tig == 0) out[i] = s + delta * d.b[i];
     }
 }
 
 // y = Minv g, Minv the cached inverse (Appendix A item (iii); the paper
-// allows a factorisation or the inverse).  Partial of <b, y> in partr[block][col].
+// allows a factorisation or the inverse), block diagonal over independent
+// components.  Partial of <b, y> in partr[block][col].
 __global__ void __launch_bounds__(RTHREADS) k_gemv(Dev d, const double* __restrict__ Minv, const double* __restrict__ g,
                                                    double* __restrict__ y, int col, int TPR) {
     __shared__ double sh[RTHREADS / 32];
@@ -110,16 +114,16 @@ __global__ void __launch_bounds__(RTHREADS) k_gemv(Dev d, const double* __restri
     for (int it = 0; it < nloop; ++it) {
         const int i = (it * gridDim.x + blockIdx.x) * rpb + gi;
         double s = 0.0;
-        if (i < d.m) {
+        const bool live = i < d.m && !frozen_row(d, i);
+        if (live) {
             if (d.diag_factor) {
                 if (tig == 0) s = Minv[i] * g[i];
             } else {
-                const double* row = Minv + (size_t)i * d.m;
-                for (int j = tig; j < d.m; j += TPR) s += row[j] * g[j];
+                s = factor_row_dot(d, Minv, i, g, tig, TPR);
             }
         }
         s = row_group_sum(s, TPR, sh);
-        if (i < d.m && tig == 0) {
+        if (live && tig == 0) {
             y[i] = s;
             by[0] += d.b[i] * s;
         }

@@ -36,7 +36,18 @@ struct HostProblem {
     long long nfill = 0;
     bool chordal = false;
     bool diag_factor = false;
-    // cached inverses (dense row-major m x m, or the diagonal when diag_factor)
+    // Independent components (connected components of the extended pattern with
+    // every constraint joining the vertices of its entries): a direct sum of
+    // SDPs has one per summand.  A D^-1 A^T is block diagonal over them.
+    int ncomp = 1;
+    std::vector<int> comp_of_vertex, comp_of_entry, comp_of_clique, comp_of_row;  // [n], [NE], [p], [m]
+    bool rows_contiguous = true;       // constraints of each component form one index range
+    std::vector<int> lrow;             // [m] index of a constraint within its component
+    std::vector<int> crow_ptr, crow_idx;  // constraints of each component (ascending)
+    std::vector<int> ccl_ptr, ccl_idx;    // cliques of each component (ascending)
+    std::vector<long long> minv_off;   // [ncomp] offset of each dense block in minv / kinv
+    // cached inverses: per component a dense row-major m_c x m_c block (or, when
+    // diag_factor, one value per constraint)
     std::vector<double> minv;         // (A W D^-1 A^T)^-1, Algorithms 1-2
     std::vector<double> kinv;         // (I + A W P^-1 A^T)^-1, P = I + D/2, Algorithm 3
     // HSDE constants (Proposition 2): zeta_hat = M^-1 zeta / (1 + zeta^T M^-1 zeta);

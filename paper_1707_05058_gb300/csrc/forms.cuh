@@ -22,10 +22,12 @@ __global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho, FinishArgs
     T* lam = reinterpret_cast<T*>(d.ck2);
     double acc[4] = {0, 0, 0, 0};
     for (int k = w0; k < d.p; k += nw) {
+        if (frozen_clique(d, k)) continue;  // warp-uniform
         const int off = d.pk_off[k], s = d.csize[k], npk = s * (s + 1) / 2;
-        double p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+        double p0 = 0, p1 = 0, p2 = 0, p3 = 0, cx = 0;
         for (int f = lane; f < npk; f += 32) {
             const int ent = d.gmap[off + f];
+            if (d.comp_mode && d.owner[off + f]) cx += d.wgt[ent] * d.c[ent] * d.x[ent];
             const double zz = z[off + f], ll = lam[off + f];
             const T vn = T(zz + ll / rho + d.x[ent]);
             const T ln = T(ll + rho * (zz - double(vn)));
@@ -38,11 +40,22 @@ __global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho, FinishArgs
             p2 += w * double(vn) * double(vn);
             p3 += w * double(ln) * double(ln);
         }
-        acc[0] += warp_sum(p0); acc[1] += warp_sum(p1); acc[2] += warp_sum(p2); acc[3] += warp_sum(p3);
+        const double q[4] = {warp_sum(p0), warp_sum(p1), warp_sum(p2), warp_sum(p3)};
+        if (d.comp_mode) {  // per-clique row (column 6: <c, x> over the entries the clique owns)
+            const double cxk = warp_sum(cx);
+            if (lane == 0) {
+                double* pr = d.part + (size_t)k * PART_COLS;
+                for (int c = 0; c < 4; ++c) pr[c] = q[c];
+                pr[6] = cxk;
+            }
+        } else {
+            for (int c = 0; c < 4; ++c) acc[c] += q[c];
+        }
     }
+    if (d.comp_mode) return;
     const int cols[4] = {0, 1, 2, 3};
     block_partial_row<4>(acc, d.part, blockIdx.x, cols);
-    if (last_block_single_writer(d)) finish_dual_block(d, fa);
+    if (fa.enabled && last_block_single_writer(d)) finish_dual_block(d, fa);
 }
 
 // Algorithm 2 stopping test (Eq. DualConsensusResidual, eps_lambda), run by
@@ -63,6 +76,110 @@ __device__ void finish_dual_block(const Dev& d, const FinishArgs& fa) {
         const bool bad = !isfinite(ec) || !isfinite(el);
         d.ctl[CTL_COUNTER] = 0;
         finish_common(d, bad, it > 1 && fmax(ec, el) <= fa.eps, it, fa.use_cond, fa.hnd);
+    }
+}
+
+// Stopping tests of Algorithms 1-2 per independent component (one block per
+// component).  A direct sum of SDPs decouples: every step of the iteration
+// acts on each summand separately, so each component's iterates are those of
+// a solve of that component alone, and its test (Eq. PrimalConsensusResidual /
+// DualConsensusResidual with eps_lambda) uses its own clique rows of the
+// partial table (columns as in the single-problem tests; <c, x> in column 5
+// for Algorithm 1, column 6 for Algorithm 2) and its own <b, y>.  A component
+// that passes, reaches max_iter or meets a NaN is frozen from the next
+// iteration on.  The block that arrives last sets the global state: the solve
+// ends once every component has stopped; the history row holds the largest
+// eps_c and eps_lambda over the components tested in this iteration, the
+// summed objectives, and (column 6) the number of components still running.
+__global__ void __launch_bounds__(256) k_finish_components(Dev d, int form, FinishArgs fa) {
+    __shared__ double sh[32 * 8];
+    __shared__ int s_was_done;
+    if (stopped(d)) return;
+    const int c = blockIdx.x;
+    const int it = d.ctl[CTL_ITER] + 1;
+    if (threadIdx.x == 0) s_was_done = d.comp_done[c];
+    __syncthreads();
+    if (!s_was_done) {
+        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int j = d.ccl_ptr[c] + threadIdx.x; j < d.ccl_ptr[c + 1]; j += blockDim.x) {
+            const double* pr = d.part + (size_t)d.ccl_idx[j] * PART_COLS;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) v[q] += __ldcg(pr + q);
+        }
+        for (int j = d.crow_ptr[c] + threadIdx.x; j < d.crow_ptr[c + 1]; j += blockDim.x) {
+            const int i = d.crow_idx[j];
+            v[7] += d.b[i] * __ldcg(d.y + i);
+        }
+        block_sum<8>(v, sh);
+        if (threadIdx.x == 0) {
+            double ec, el, cost, dobj;
+            ec = sqrt(v[0]) / fmax(fmax(sqrt(v[1]), sqrt(v[2])), 1e-300);
+            if (form == 0) {
+                el = fa.rho * sqrt(v[3]) / fmax(sqrt(v[4]), 1e-300);
+                cost = v[5];
+                dobj = -fa.rho * v[7];
+            } else {
+                el = fa.rho * sqrt(v[5]) / fmax(sqrt(v[3]), 1e-300);
+                cost = -fa.rho * v[6];
+                dobj = v[7];
+            }
+            double* r = d.comp_res + (size_t)c * HIST_COLS;
+            r[0] = ec; r[1] = el; r[2] = 0; r[3] = 0; r[4] = cost; r[5] = dobj; r[6] = 0; r[7] = 0;
+            int st = 1, done = 0;
+            if (!isfinite(ec) || !isfinite(el)) { st = -6; done = 1; }
+            else if (it > 1 && fmax(ec, el) <= fa.eps) { st = 0; done = 1; }
+            else if (it >= d.max_iter) { st = 1; done = 1; }
+            d.comp_iter[c] = it;
+            if (done) {
+                d.comp_status[c] = st;
+                d.comp_done[c] = 1;
+            }
+        }
+    }
+    if (!last_block_single_writer(d)) return;
+    // last block: global state
+    __shared__ int s_nan, s_maxit;
+    __shared__ double shm[32 * 2];
+    if (threadIdx.x == 0) { s_nan = 0; s_maxit = 0; }
+    __syncthreads();
+    double mx[2] = {0.0, 0.0};     // largest eps_c, eps_lambda tested in this iteration
+    double sm[3] = {0.0, 0.0, 0.0};  // summed objectives, components still running
+    for (int j = threadIdx.x; j < d.ncomp; j += blockDim.x) {
+        const volatile double* r = d.comp_res + (size_t)j * HIST_COLS;
+        if (*((volatile int*)d.comp_iter + j) == it) {
+            mx[0] = fmax(mx[0], r[0]);
+            mx[1] = fmax(mx[1], r[1]);
+        }
+        sm[0] += r[4];
+        sm[1] += r[5];
+        if (!*((volatile int*)d.comp_done + j)) {
+            sm[2] += 1.0;
+        } else {
+            const int st = *((volatile int*)d.comp_status + j);
+            if (st == -6) s_nan = 1;
+            if (st == 1) s_maxit = 1;
+        }
+    }
+    block_sum<3>(sm, sh);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        mx[0] = fmax(mx[0], __shfl_xor_sync(0xffffffffu, mx[0], o));
+        mx[1] = fmax(mx[1], __shfl_xor_sync(0xffffffffu, mx[1], o));
+    }
+    if (lane == 0) { shm[warp * 2] = mx[0]; shm[warp * 2 + 1] = mx[1]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) { mx[0] = fmax(mx[0], shm[w * 2]); mx[1] = fmax(mx[1], shm[w * 2 + 1]); }
+        double* h = d.hist + (size_t)(it - 1) * HIST_COLS;
+        h[0] = mx[0]; h[1] = mx[1]; h[2] = 0; h[3] = 0; h[4] = sm[0]; h[5] = sm[1]; h[6] = sm[2]; h[7] = 0;
+        const int done = sm[2] == 0.0;
+        d.ctl[CTL_COUNTER] = 0;
+        d.ctl[CTL_ITER] = it;
+        if (done) {
+            d.ctl[CTL_STATUS] = s_nan ? -6 : (s_maxit ? 1 : 0);
+            d.ctl[CTL_DONE] = 1;
+        }
+        if (fa.use_cond) cudaGraphSetConditional(fa.hnd, done ? 0u : 1u);
     }
 }
 

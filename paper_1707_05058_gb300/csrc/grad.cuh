@@ -46,10 +46,7 @@ __global__ void __launch_bounds__(RTHREADS) k_bwd_rbar(Dev d, const double* __re
         if (d.diag_factor) {
             s = d.minv[i] * ybar[i];
         } else {
-            s = 0.0;
-            const double* row = d.minv + (size_t)i * d.m;
-            for (int j = lane; j < d.m; j += 32) s += row[j] * ybar[j];
-            s = warp_sum(s);
+            s = warp_sum(factor_row_dot(d, d.minv, i, ybar, lane, 32));
         }
         if (lane == 0) {
             rbar[i] = s;

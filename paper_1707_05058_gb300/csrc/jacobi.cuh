@@ -416,6 +416,7 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
+        if (frozen_clique(d, k)) continue;  // warp-uniform
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
         jac.clear(lane);
         T nrm = T(0);
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
             }
         }
         nrm = warp_sum(nrm);
-        acc[5] += warp_sum(cx);
+        const double cxk = warp_sum(cx);
         __syncwarp();
         if (warm) {
             jac.load_basis(vc + d.vv_off[k], s, lane);
@@ -478,10 +479,18 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
                 p4 += w * double(ln) * double(ln);
             }
         }
-        acc[0] += warp_sum(p0); acc[1] += warp_sum(p1); acc[2] += warp_sum(p2);
-        acc[3] += warp_sum(p3); acc[4] += warp_sum(p4);
+        const double q[6] = {warp_sum(p0), warp_sum(p1), warp_sum(p2), warp_sum(p3), warp_sum(p4), cxk};
+        if (d.comp_mode) {  // per-clique row, reduced per component
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) d.part[(size_t)k * PART_COLS + c] = q[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[c] += q[c];
+        }
         __syncwarp();
     }
+    if (d.comp_mode) return;
     const int cols[6] = {0, 1, 2, 3, 4, 5};
     block_partial_row<6>(acc, d.part, pa.row_off + blockIdx.x, cols);
     if (fa.enabled && last_block_single_writer(d)) finish_primal_block(d, fa);
@@ -506,6 +515,7 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
     double acc[1] = {0};
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
+        if (frozen_clique(d, k)) continue;  // warp-uniform
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
         jac.clear(lane);
         T nrm = T(0);
@@ -532,9 +542,15 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
             z[off + f] = zn;
             p0 += (a == b ? 1.0 : 2.0) * dz * dz;
         }
-        acc[0] += warp_sum(p0);
+        const double q0 = warp_sum(p0);
+        if (d.comp_mode) {
+            if (lane == 0) d.part[(size_t)k * PART_COLS + 5] = q0;
+        } else {
+            acc[0] += q0;
+        }
         __syncwarp();
     }
+    if (d.comp_mode) return;
     const int cols[1] = {5};
     block_partial_row<1>(acc, d.part, pa.row_off + blockIdx.x, cols);
 }

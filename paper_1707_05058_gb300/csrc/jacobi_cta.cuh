@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* _
         const int s = FORM == 3 ? size_arr[k] : d.csize[k];
         const int off = FORM == 3 ? off_arr[k] : d.pk_off[k];
         if (s > S || s < 1) continue;  // block-uniform
+        if (FORM != 3 && frozen_clique(d, k)) continue;
         const int npk = s * (s + 1) / 2;
         jac.clear();
         double nrm = 0.0, cx = 0.0;
@@ -285,7 +286,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* _
         }
         double tmp[2] = {nrm, cx};
         cta_sum<2>(tmp, shr);
-        if (tid == 0) { shr[0] = tmp[0]; acc[5] += tmp[1]; }
+        double cxk = 0.0;
+        if (tid == 0) { shr[0] = tmp[0]; cxk = tmp[1]; }
         __syncthreads();
         nrm = shr[0];
         __syncthreads();
@@ -336,13 +338,20 @@ __global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* _
         }
         if (FORM != 3) {
             cta_sum<6>(p, shr);
-            if (tid == 0)
+            if (FORM != 2) p[5] = cxk;
+            if (tid == 0 && d.comp_mode) {  // per-clique row, reduced per component
+                double* pr = d.part + (size_t)k * PART_COLS;
+                if (FORM == 0) { for (int c = 0; c < 6; ++c) pr[c] = p[c]; }
+                else if (FORM == 1) { pr[5] = p[0]; }
+            } else if (tid == 0) {
                 for (int c = 0; c < 5; ++c) acc[c] += p[c];
-            if (tid == 0 && FORM == 2) acc[5] += p[5];
+                if (FORM != 1) acc[5] += p[5];
+            }
         }
         __syncthreads();
     }
     if (FORM == 3) return;
+    if (d.comp_mode) return;
     if (tid == 0) {
         double* pr = d.part + (size_t)(pa.row_off + blockIdx.x) * PART_COLS;
         if (FORM == 0) { for (int c = 0; c < 6; ++c) pr[c] = acc[c]; }

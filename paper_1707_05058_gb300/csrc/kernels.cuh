@@ -71,6 +71,25 @@ struct Dev {
     int* ctl;             // [CTL_WORDS]
     double* hist;         // [max_iter * HIST_COLS]
     int max_iter;
+    // independent components (summands of a direct sum).  The cached inverses
+    // are block diagonal: row i of component c is the dense row lrow[i] of
+    // the m_c x m_c block at minv_off[c], over the constraints crow_idx[crow_ptr[c] ..].
+    int ncomp;
+    int rows_contig;      // crow_idx is the identity
+    int comp_mode;        // 1: each component stops and freezes on its own test
+    const int* comp_of_entry;   // [NE]
+    const int* comp_of_clique;  // [p]
+    const int* comp_of_row;     // [m]
+    const int* lrow;            // [m]
+    const int* crow_ptr;        // [ncomp+1]
+    const int* crow_idx;        // [m]
+    const int* ccl_ptr;         // [ncomp+1]
+    const int* ccl_idx;         // [p]
+    const long long* minv_off;  // [ncomp]
+    int* comp_done;             // [ncomp] 1 once the component has stopped
+    int* comp_iter;             // [ncomp] iterations run by the component
+    int* comp_status;           // [ncomp] cdsdp_status of the component
+    double* comp_res;           // [ncomp * HIST_COLS] last stopping-test row of the component
 };
 
 constexpr int NBLK_E = 1216;  // 152 SMs x 8
@@ -99,6 +118,39 @@ struct ProjArgs {
 
 __device__ __forceinline__ bool stopped(const Dev& d) {
     return *((volatile int*)d.ctl + CTL_DONE) != 0;
+}
+
+// Component freeze: a stopped component's entries, rows and cliques are left alone.
+__device__ __forceinline__ bool frozen_clique(const Dev& d, int k) {
+    return d.comp_mode && d.comp_done[d.comp_of_clique[k]];
+}
+__device__ __forceinline__ bool frozen_entry(const Dev& d, int e) {
+    return d.comp_mode && d.comp_done[d.comp_of_entry[e]];
+}
+__device__ __forceinline__ bool frozen_row(const Dev& d, int i) {
+    return d.comp_mode && d.comp_done[d.comp_of_row[i]];
+}
+
+// Partial dot product of row i of a cached inverse (dense m x m, or block
+// diagonal over components) with g, over the row positions t0, t0+step, ...
+__device__ __forceinline__ double factor_row_dot(const Dev& d, const double* __restrict__ M, int i,
+                                                 const double* __restrict__ g, int t0, int step) {
+    double s = 0.0;
+    if (d.ncomp <= 1) {
+        const double* row = M + (size_t)i * d.m;
+        for (int j = t0; j < d.m; j += step) s += row[j] * g[j];
+        return s;
+    }
+    const int c = d.comp_of_row[i], r0 = d.crow_ptr[c], mc = d.crow_ptr[c + 1] - r0;
+    const double* row = M + d.minv_off[c] + (size_t)d.lrow[i] * mc;
+    if (d.rows_contig) {
+        const double* gc = g + r0;
+        for (int j = t0; j < mc; j += step) s += row[j] * gc[j];
+    } else {
+        const int* idx = d.crow_idx + r0;
+        for (int j = t0; j < mc; j += step) s += row[j] * g[idx[j]];
+    }
+    return s;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -299,12 +299,78 @@ int build_host_problem(int n, int m,
     }
     hp.b.assign(bvec, bvec + m);
 
-    // ---- cached inverses: S(d) = A W diag(d)^-1 A^T (+ I for HSDE)
+    // ---- independent components (union-find over vertices)
+    {
+        std::vector<int> parent(n);
+        for (int v = 0; v < n; ++v) parent[v] = v;
+        auto find = [&](int v) {
+            while (parent[v] != v) { parent[v] = parent[parent[v]]; v = parent[v]; }
+            return v;
+        };
+        auto unite = [&](int a, int b2) {
+            a = find(a); b2 = find(b2);
+            if (a != b2) parent[std::max(a, b2)] = std::min(a, b2);
+        };
+        for (int e = 0; e < NE; ++e) unite(hp.prow[e], hp.pcol[e]);
+        for (int i = 0; i < m; ++i)
+            for (int q = hp.a_ptr[i] + 1; q < hp.a_ptr[i + 1]; ++q) unite(hp.pcol[hp.a_col[q]], hp.pcol[hp.a_col[hp.a_ptr[i]]]);
+        // components numbered by their smallest vertex
+        std::vector<int> id(n, -1);
+        hp.ncomp = 0;
+        for (int v = 0; v < n; ++v) {
+            const int r = find(v);
+            if (id[r] < 0) id[r] = hp.ncomp++;
+        }
+        auto comp = [&](int v) { return id[find(v)]; };
+        hp.comp_of_vertex.resize(n);
+        for (int v = 0; v < n; ++v) hp.comp_of_vertex[v] = comp(v);
+        hp.comp_of_entry.resize(NE);
+        for (int e = 0; e < NE; ++e) hp.comp_of_entry[e] = comp(hp.pcol[e]);
+        hp.comp_of_clique.resize(p);
+        for (int k = 0; k < p; ++k) hp.comp_of_clique[k] = comp(hp.cl_vert[hp.cl_off[k]]);
+        hp.comp_of_row.assign(m, 0);
+        for (int i = 0; i < m; ++i)
+            if (hp.a_ptr[i + 1] > hp.a_ptr[i]) hp.comp_of_row[i] = hp.comp_of_entry[hp.a_col[hp.a_ptr[i]]];
+        const int C = hp.ncomp;
+        hp.crow_ptr.assign(C + 1, 0);
+        for (int i = 0; i < m; ++i) ++hp.crow_ptr[hp.comp_of_row[i] + 1];
+        for (int c = 0; c < C; ++c) hp.crow_ptr[c + 1] += hp.crow_ptr[c];
+        hp.crow_idx.resize(m);
+        hp.lrow.resize(m);
+        {
+            std::vector<int> fill(hp.crow_ptr.begin(), hp.crow_ptr.end() - 1);
+            for (int i = 0; i < m; ++i) {
+                const int c = hp.comp_of_row[i];
+                hp.lrow[i] = fill[c] - hp.crow_ptr[c];
+                hp.crow_idx[fill[c]++] = i;
+            }
+        }
+        hp.rows_contiguous = true;
+        for (int i = 0; i < m; ++i)
+            if (hp.crow_idx[i] != i) hp.rows_contiguous = false;
+        hp.ccl_ptr.assign(C + 1, 0);
+        for (int k = 0; k < p; ++k) ++hp.ccl_ptr[hp.comp_of_clique[k] + 1];
+        for (int c = 0; c < C; ++c) hp.ccl_ptr[c + 1] += hp.ccl_ptr[c];
+        hp.ccl_idx.resize(p);
+        {
+            std::vector<int> fill(hp.ccl_ptr.begin(), hp.ccl_ptr.end() - 1);
+            for (int k = 0; k < p; ++k) hp.ccl_idx[fill[hp.comp_of_clique[k]]++] = k;
+        }
+    }
+
+    // ---- cached inverses: S(d) = A W diag(d)^-1 A^T (+ I for HSDE), block diagonal over components
     auto wgt = [&](int e) { return hp.prow[e] == hp.pcol[e] ? 1.0 : 2.0; };
     bool structurally_diag = true;
     for (int e = 0; e < NE && structurally_diag; ++e)
         if (hp.at_ptr[e + 1] - hp.at_ptr[e] > 1) structurally_diag = false;
-    if (!structurally_diag && m > 8192) return CDSDP_ERR_UNSUPPORTED;
+    hp.minv_off.assign(hp.ncomp, 0);
+    long long tot = 0;
+    for (int c = 0; c < hp.ncomp; ++c) {
+        const long long mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+        if (!structurally_diag && mc > 8192) return CDSDP_ERR_UNSUPPORTED;
+        hp.minv_off[c] = tot;
+        tot += mc * mc;
+    }
     auto build = [&](bool hsde, std::vector<double>& inv) -> int {
         if (structurally_diag) {
             inv.assign(m, hsde ? 1.0 : 0.0);
@@ -319,17 +385,31 @@ int build_host_problem(int n, int m,
             }
             return CDSDP_SOLVED;
         }
-        std::vector<double> S((size_t)m * m, 0.0);
-        for (int i = 0; hsde && i < m; ++i) S[(size_t)i * m + i] = 1.0;
+        inv.assign((size_t)tot, 0.0);
+        std::vector<std::vector<double>> blocks(hp.ncomp);
+        for (int c = 0; c < hp.ncomp; ++c) {
+            const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+            blocks[c].assign((size_t)mc * mc, 0.0);
+            for (int i = 0; hsde && i < mc; ++i) blocks[c][(size_t)i * mc + i] = 1.0;
+        }
         for (int e = 0; e < NE; ++e) {
-            double f = wgt(e) / (hsde ? 1.0 + 0.5 * hp.D[e] : hp.D[e]);
+            const int c = hp.comp_of_entry[e];
+            const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+            double* S = blocks[c].data();
+            const double f = wgt(e) / (hsde ? 1.0 + 0.5 * hp.D[e] : hp.D[e]);
             for (int q1 = hp.at_ptr[e]; q1 < hp.at_ptr[e + 1]; ++q1) {
-                double v1 = f * hp.at_val[q1];
-                double* row = &S[(size_t)hp.at_col[q1] * m];
-                for (int q2 = hp.at_ptr[e]; q2 < hp.at_ptr[e + 1]; ++q2) row[hp.at_col[q2]] += v1 * hp.at_val[q2];
+                const double v1 = f * hp.at_val[q1];
+                double* row = S + (size_t)hp.lrow[hp.at_col[q1]] * mc;
+                for (int q2 = hp.at_ptr[e]; q2 < hp.at_ptr[e + 1]; ++q2) row[hp.lrow[hp.at_col[q2]]] += v1 * hp.at_val[q2];
             }
         }
-        return spd_inverse(S, m, inv) ? CDSDP_SOLVED : CDSDP_ERR_RANK;
+        for (int c = 0; c < hp.ncomp; ++c) {
+            const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+            std::vector<double> bi;
+            if (!spd_inverse(blocks[c], mc, bi)) return CDSDP_ERR_RANK;
+            std::copy(bi.begin(), bi.end(), inv.begin() + hp.minv_off[c]);
+        }
+        return CDSDP_SOLVED;
     };
     hp.diag_factor = structurally_diag;
     int st = build(false, hp.minv);
@@ -343,8 +423,10 @@ int build_host_problem(int n, int m,
             out.assign(m, 0.0);
             if (hp.diag_factor) { for (int i = 0; i < m; ++i) out[i] = hp.kinv[i] * r[i]; return; }
             for (int i = 0; i < m; ++i) {
+                const int c = hp.comp_of_row[i], mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+                const double* row = hp.kinv.data() + hp.minv_off[c] + (size_t)hp.lrow[i] * mc;
                 double s = 0.0;
-                for (int j = 0; j < m; ++j) s += hp.kinv[(size_t)i * m + j] * r[j];
+                for (int j = 0; j < mc; ++j) s += row[j] * r[hp.crow_idx[hp.crow_ptr[c] + j]];
                 out[i] = s;
             }
         };

@@ -31,10 +31,12 @@ inline int class_of(int s) { return proj_class_of(s); }
 struct Layout {
     // constants
     size_t c, dinv, pinv, wgt, a_ptr, a_col, a_valw, a_valu, at_ptr, at_col, at_val, b, minv, kinv, gmap, pk_off, csize,
-        sc_ptr, sc_idx, zhx, zhy, atb, azhx, blist, vv_off, owner;
+        sc_ptr, sc_idx, zhx, zhy, atb, azhx, blist, vv_off, owner, comp_of_entry, comp_of_clique, comp_of_row, lrow,
+        crow_ptr, crow_idx, ccl_ptr, ccl_idx, minv_off;
     size_t const_end;
     // state
-    size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, vcache, part, parte, partr, scal, ctl, hist;
+    size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, vcache, part, parte, partr, scal, ctl, hist,
+        comp_done, comp_iter, comp_status, comp_res;
     size_t total;
 };
 
@@ -59,7 +61,7 @@ struct cdsdp {
     int g_form = -1;
     cdsdp_opts g_opts{};
     // last solve
-    int last_form = -1, last_iters = 0, last_status = CDSDP_ERR_STATE;
+    int last_form = -1, last_iters = 0, last_status = CDSDP_ERR_STATE, last_comp_mode = 0;
     std::string err;
     // profiling: event pairs around projection launches and whole iterations
     std::vector<cudaEvent_t> ev;
@@ -87,7 +89,8 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     const size_t NE = hp.prow.size(), m = hp.m, nd = hp.gmap.size(), p = hp.cl_off.size() - 1;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1)); return r; };
     const size_t nnzA = hp.a_col.size();
-    const size_t minv_n = hp.diag_factor ? m : m * m;
+    const size_t minv_n = hp.minv.size();
+    const size_t nc = hp.ncomp;
     L.c = take(NE * 8); L.dinv = take(NE * 8); L.pinv = take(NE * 8); L.wgt = take(NE * 8);
     L.a_ptr = take((m + 1) * 4); L.a_col = take(nnzA * 4); L.a_valw = take(nnzA * 8); L.a_valu = take(nnzA * 8);
     L.at_ptr = take((NE + 1) * 4); L.at_col = take(nnzA * 4); L.at_val = take(nnzA * 8);
@@ -98,6 +101,9 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     L.blist = take(p * 4);
     L.vv_off = take((p + 1) * 4);
     L.owner = take(nd);
+    L.comp_of_entry = take(NE * 4); L.comp_of_clique = take(p * 4); L.comp_of_row = take(m * 4); L.lrow = take(m * 4);
+    L.crow_ptr = take((nc + 1) * 4); L.crow_idx = take(m * 4); L.ccl_ptr = take((nc + 1) * 4); L.ccl_idx = take(p * 4);
+    L.minv_off = take(nc * 8);
     L.const_end = o;
     L.x = take(NE * 8); L.t = take(NE * 8); L.q = take(NE * 8); L.s11 = take(NE * 8); L.atuy = take(NE * 8);
     L.y = take(m * 8); L.g = take(m * 8); L.hh = take(m * 8); L.s21 = take(m * 8); L.as11 = take(m * 8);
@@ -114,6 +120,8 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     L.scal = take(SC_WORDS * 8);
     L.ctl = take(CTL_WORDS * 4);
     L.hist = take((size_t)std::max(max_iter, 1) * HIST_COLS * 8);
+    L.comp_done = take(nc * 4); L.comp_iter = take(nc * 4); L.comp_status = take(nc * 4);
+    L.comp_res = take(nc * HIST_COLS * 8);
     L.total = o;
     return L;
 }
@@ -163,6 +171,10 @@ void build_image(cdsdp* h) {
     for (int e = 0; e < NE; ++e)
         if (hp.sc_ptr[e + 1] > hp.sc_ptr[e]) own[hp.sc_idx[hp.sc_ptr[e]]] = 1;
     put(img, L.owner, own);
+    put(img, L.comp_of_entry, hp.comp_of_entry); put(img, L.comp_of_clique, hp.comp_of_clique);
+    put(img, L.comp_of_row, hp.comp_of_row); put(img, L.lrow, hp.lrow);
+    put(img, L.crow_ptr, hp.crow_ptr); put(img, L.crow_idx, hp.crow_idx);
+    put(img, L.ccl_ptr, hp.ccl_ptr); put(img, L.ccl_idx, hp.ccl_idx); put(img, L.minv_off, hp.minv_off);
 }
 
 void make_dev(cdsdp* h) {
@@ -194,6 +206,16 @@ void make_dev(cdsdp* h) {
     d.part = (double*)(w + L.part); d.parte = (double*)(w + L.parte); d.partr = (double*)(w + L.partr);
     d.scal = (double*)(w + L.scal); d.ctl = (int*)(w + L.ctl); d.hist = (double*)(w + L.hist);
     d.max_iter = h->ws_max_iter;
+    d.ncomp = hp.ncomp;
+    d.rows_contig = hp.rows_contiguous ? 1 : 0;
+    d.comp_mode = 0;
+    d.comp_of_entry = (const int*)(w + L.comp_of_entry); d.comp_of_clique = (const int*)(w + L.comp_of_clique);
+    d.comp_of_row = (const int*)(w + L.comp_of_row); d.lrow = (const int*)(w + L.lrow);
+    d.crow_ptr = (const int*)(w + L.crow_ptr); d.crow_idx = (const int*)(w + L.crow_idx);
+    d.ccl_ptr = (const int*)(w + L.ccl_ptr); d.ccl_idx = (const int*)(w + L.ccl_idx);
+    d.minv_off = (const long long*)(w + L.minv_off);
+    d.comp_done = (int*)(w + L.comp_done); d.comp_iter = (int*)(w + L.comp_iter);
+    d.comp_status = (int*)(w + L.comp_status); d.comp_res = (double*)(w + L.comp_res);
     auto pow2_clamp = [](double x, int lo, int hi) {
         int v = lo;
         while (v < hi && v < x) v <<= 1;
@@ -205,7 +227,9 @@ void make_dev(cdsdp* h) {
     h->Gs = pow2_clamp(avg_sc / 2.0, 1, 32);
     h->Ga = pow2_clamp(std::max(avg_at, avg_sc) / 3.0, 1, 32);
     h->TPR = pow2_clamp(avg_a / 4.0, 32, RTHREADS);
-    h->TPRM = hp.diag_factor ? 32 : pow2_clamp(d.m / 4.0, 32, RTHREADS);
+    int max_mc = 0;
+    for (int c = 0; c < hp.ncomp; ++c) max_mc = std::max(max_mc, hp.crow_ptr[c + 1] - hp.crow_ptr[c]);
+    h->TPRM = hp.diag_factor ? 32 : pow2_clamp(max_mc / 4.0, 32, RTHREADS);
     const int G = std::max(h->Gs, h->Ga);
     h->GE = std::max(1, std::min(NBLK_E, (int)(((long long)d.NE * G + ETHREADS - 1) / ETHREADS)));
     const int TP = std::max(h->TPR, h->TPRM);
@@ -257,6 +281,10 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
     fa.enabled = 1;
     fa.use_cond = use_cond;
     fa.hnd = hnd;
+    // with independent components stopping on their own, a separate kernel
+    // (one block per component) runs the tests after the last update
+    FinishArgs fin = fa;
+    if (d.comp_mode) fin.enabled = 0;
     cudaError_t e;
     if (form == 0) {  // Algorithm 1; the projection computes x on the fly and its last block the stopping test
         k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0 / rho, 1.0, 1.0 / rho, d.dinv, d.t, 1, h->Gs);
@@ -264,8 +292,9 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
-        if ((e = launch_projection<T>(h, 0, o, fa, st)) != cudaSuccess) return e;
+        if ((e = launch_projection<T>(h, 0, o, fin, st)) != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, st);
+        if (d.comp_mode) k_finish_components<<<d.ncomp, 256, 0, st>>>(d, 0, fa);
     } else if (form == 1) {  // Algorithm 2; the v/lambda kernel's last block runs the stopping test
         if (ev0) cudaEventRecord(ev0, st);
         FinishArgs none = fa;
@@ -276,7 +305,8 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0 / rho, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
         k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
-        k_vlam_dual<T><<<PG, 128, 0, st>>>(d, rho, fa);
+        k_vlam_dual<T><<<PG, 128, 0, st>>>(d, rho, fin);
+        if (d.comp_mode) k_finish_components<<<d.ncomp, 256, 0, st>>>(d, 1, fa);
     } else {  // Algorithm 3; gamma/tau/kappa in sigma21's last block, stopping test in row_update's
         k_hsde_eta<T><<<GE, ETHREADS, 0, st>>>(d, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.q, 0.0, d.g, h->TPR);
@@ -304,7 +334,8 @@ cudaError_t launch_iteration_any(cdsdp* h, int form, const cdsdp_opts& o, cudaSt
 
 bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
     return a.eps == b.eps && a.max_iter == b.max_iter && a.rho == b.rho && a.precision == b.precision &&
-           a.jacobi_max_sweeps == b.jacobi_max_sweeps && a.warm_start == b.warm_start;
+           a.jacobi_max_sweeps == b.jacobi_max_sweeps && a.warm_start == b.warm_start &&
+           a.component_stop == b.component_stop;
 }
 
 void drop_graph(cdsdp* h) {
@@ -352,6 +383,7 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     if (o.precision != CDSDP_FP32_PROJECTION && o.precision != CDSDP_FP64) return CDSDP_ERR_ARG;
     if (o.max_iter > h->ws_max_iter) return CDSDP_ERR_ARG;
     if (o.warm_start < 0) return CDSDP_ERR_ARG;
+    if (o.component_stop != 0 && o.component_stop != 1) return CDSDP_ERR_ARG;
     if (o.precision == CDSDP_FP64 && h->hp.max_clique > kMaxOrderF64) return CDSDP_ERR_UNSUPPORTED;
     return CDSDP_SOLVED;
 }
@@ -484,6 +516,7 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->jacobi_max_sweeps = 30;
     o->warm_start = 16;
     o->profile = 0;
+    o->component_stop = 1;
 }
 
 int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
@@ -519,6 +552,7 @@ int cdsdp_info(const cdsdp* h, cdsdp_info_t* info) {
     info->chordal = hp.chordal ? 1 : 0;
     info->diag_factor = hp.diag_factor ? 1 : 0;
     info->upload_bytes = (long long)make_layout(hp, 1).const_end;
+    info->ncomp = hp.ncomp;
     return CDSDP_SOLVED;
 }
 
@@ -533,6 +567,41 @@ int cdsdp_pattern(const cdsdp* h, int* rows, int* cols) {
     if (!h || !rows || !cols) return CDSDP_ERR_ARG;
     std::copy(h->hp.prow.begin(), h->hp.prow.end(), rows);
     std::copy(h->hp.pcol.begin(), h->hp.pcol.end(), cols);
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_components(const cdsdp* h, int* vertex_comp, int* constraint_comp) {
+    if (!h) return CDSDP_ERR_ARG;
+    if (vertex_comp) std::copy(h->hp.comp_of_vertex.begin(), h->hp.comp_of_vertex.end(), vertex_comp);
+    if (constraint_comp) std::copy(h->hp.comp_of_row.begin(), h->hp.comp_of_row.end(), constraint_comp);
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_component_results(cdsdp* h, void* stream, int* iters, int* status, double* res) {
+    if (!h) return CDSDP_ERR_ARG;
+    if (!h->ws || h->last_form < 0) return CDSDP_ERR_STATE;
+    const int nc = h->hp.ncomp;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Dev& d = h->dev;
+    if (h->last_comp_mode) {
+        if (iters) CK(cudaMemcpyAsync(iters, d.comp_iter, nc * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (status) CK(cudaMemcpyAsync(status, d.comp_status, nc * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (res) CK(cudaMemcpyAsync(res, d.comp_res, (size_t)nc * HIST_COLS * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return CDSDP_SOLVED;
+    }
+    // one test over the whole problem: every component shares it
+    double last[HIST_COLS] = {0};
+    if (res && h->last_iters > 0) {
+        CK(cudaMemcpyAsync(last, d.hist + (size_t)(h->last_iters - 1) * HIST_COLS, sizeof(last),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    for (int c = 0; c < nc; ++c) {
+        if (iters) iters[c] = h->last_iters;
+        if (status) status[c] = h->last_status;
+        if (res) std::copy(last, last + HIST_COLS, res + (size_t)c * HIST_COLS);
+    }
     return CDSDP_SOLVED;
 }
 
@@ -578,6 +647,7 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     cudaStream_t st = (cudaStream_t)stream;
     Dev& d = h->dev;
     d.max_iter = o.max_iter;
+    d.comp_mode = (h->hp.ncomp > 1 && form != 2 && o.component_stop) ? 1 : 0;
     // zero the state (clique vectors, iterates, partials, history)
     CK(cudaMemsetAsync(h->ws + h->L.const_end, 0, h->L.total - h->L.const_end, st));
     k_init<<<1, 32, 0, st>>>(d, form);
@@ -643,6 +713,7 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     h->last_form = form;
     h->last_iters = ctl[CTL_ITER];
     h->last_status = ctl[CTL_STATUS];
+    h->last_comp_mode = d.comp_mode;
     if (iters) *iters = h->last_iters;
     rc = copy_results(h, st, X, y, Z, hist, cert);
     if (rc != CDSDP_SOLVED) return rc;
@@ -737,6 +808,7 @@ int cdsdp_unrolled_forward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckpt
     dd.c = d_c;
     dd.b = d_b;
     dd.max_iter = ckpt_every;
+    dd.comp_mode = 0;
     const size_t ts = fp32 ? 4 : 8, nd = dd.nd;
     CK(cudaMemsetAsync(h->ws + h->L.const_end, 0, h->L.total - h->L.const_end, st));
     for (int sg = 0; sg < G.nseg; ++sg) {
@@ -769,6 +841,7 @@ int cdsdp_unrolled_backward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckp
     dd.max_iter = ckpt_every;
     dd.wstore = g + G.wstore;
     dd.wstore_count = ckpt_every;
+    dd.comp_mode = 0;
     const size_t ts = fp32 ? 4 : 8, nd = dd.nd;
     double* xkbar = (double*)(g + G.xkbar);
     double* lambar = (double*)(g + G.lambar);

@@ -86,17 +86,22 @@ def _lower_pairs_banded(n, w):
     return np.array(rows, dtype=np.int64), np.array(cols, dtype=np.int64)
 
 
-def _feasible_data(rng, n, m, prow, pcol, A_con, A_ent, A_val):
+def _feasible_data(rng, n, m, prow, pcol, A_con, A_ent, A_val, x0_of=None):
     """b from a strictly feasible X0 = G G^T + I and C = Z0 + sum y0_i A_i with
-    Z0 = W + alpha I (W N(0,1) on the pattern, alpha a Gershgorin bound)."""
+    Z0 = W + alpha I (W N(0,1) on the pattern, alpha a Gershgorin bound).
+    `x0_of(G)`, when given, returns G G^T on the pattern entries (a faster
+    route for structured patterns)."""
     npat = prow.size
     wgt = np.where(prow == pcol, 1.0, 2.0)
     G = rng.standard_normal((n, n))
-    x0 = np.empty(npat)
-    chunk = 1 << 14
-    for s in range(0, npat, chunk):
-        e = slice(s, s + chunk)
-        x0[e] = np.einsum("ij,ij->i", G[prow[e]], G[pcol[e]])
+    if x0_of is not None:
+        x0 = x0_of(G)
+    else:
+        x0 = np.empty(npat)
+        chunk = 1 << 14
+        for s in range(0, npat, chunk):
+            e = slice(s, s + chunk)
+            x0[e] = np.einsum("ij,ij->i", G[prow[e]], G[pcol[e]])
     x0 += (prow == pcol)
     b = np.bincount(A_con, weights=wgt[A_ent] * A_val * x0[A_ent], minlength=m)
     W = rng.standard_normal(npat)
@@ -109,17 +114,46 @@ def _feasible_data(rng, n, m, prow, pcol, A_con, A_ent, A_val):
     return _f32(b), _f32(c)
 
 
-def block_arrow(l, d, h, m, seed, name=None):
+def _bernoulli_positions(rng, total, density):
+    """Sorted positions in [0, total) of a Bernoulli(density) process, drawn
+    as geometric gaps (O(density * total) draws instead of `total`)."""
+    est = int(total * density * 1.1) + 64
+    pos = np.cumsum(rng.geometric(density, size=est)) - 1
+    while pos[-1] < total:
+        more = pos[-1] + np.cumsum(rng.geometric(density, size=est))
+        pos = np.concatenate([pos, more])
+    return pos[pos < total]
+
+
+def block_arrow(l, d, h, m, seed, name=None, density=None):
     """Random block-arrow SDP (Section 6.3 recipe, N(0,1) draws): every A_i is
-    dense on the lower block-arrow pattern."""
+    dense on the lower block-arrow pattern, or, with `density`, each lower
+    pattern entry of each A_i is nonzero with that probability."""
     rng = np.random.default_rng(seed)
     n = l * d + h
     prow, pcol = _lower_pairs_block_arrow(l, d, h)
     npat = prow.size
-    A_val = _f32(rng.standard_normal((m, npat))).ravel()
-    A_con = np.repeat(np.arange(m), npat)
-    A_ent = np.tile(np.arange(npat), m)
-    b, c = _feasible_data(rng, n, m, prow, pcol, A_con, A_ent, A_val)
+    if density is None:
+        A_val = _f32(rng.standard_normal((m, npat))).ravel()
+        A_con = np.repeat(np.arange(m), npat)
+        A_ent = np.tile(np.arange(npat), m)
+    else:
+        pos = _bernoulli_positions(rng, m * npat, density)
+        A_con, A_ent = pos // npat, pos % npat
+        A_val = _f32(rng.standard_normal(pos.size))
+
+    def x0_of(G):  # G G^T on the pattern from l diagonal-block products and the head rows
+        x0 = np.empty(npat)
+        nb = l * d
+        for blk in range(l):
+            sel = (pcol >= blk * d) & (pcol < (blk + 1) * d) & (prow < nb)
+            B = G[blk * d:(blk + 1) * d]
+            x0[sel] = (B @ B.T)[prow[sel] - blk * d, pcol[sel] - blk * d]
+        sel = prow >= nb
+        x0[sel] = (G[nb:] @ G.T)[prow[sel] - nb, pcol[sel]]
+        return x0
+
+    b, c = _feasible_data(rng, n, m, prow, pcol, A_con, A_ent, A_val, x0_of if density is not None else None)
     return SDPProblem(n, m, A_con.astype(np.int32), prow[A_ent].astype(np.int32),
                       pcol[A_ent].astype(np.int32), A_val, b,
                       prow.astype(np.int32), pcol.astype(np.int32), c,
@@ -167,13 +201,33 @@ def maxcut(n, avg_degree, seed, name=None):
                       _empty_i32(), _empty_i32(), name or f"maxcut_n{n}_deg{avg_degree}")
 
 
-def block_arrow_batch(count, seed):
-    """Batch of block-arrow SDPs of uneven size: l in [10,100], d in [10,40],
-    h in [10,20], m in [50,400], each with its own seed."""
+def block_arrow_batch(count, seed, density=0.05, l_range=(10, 100), d_range=(10, 40), h_range=(10, 20),
+                      m_range=(50, 400)):
+    """Batch of block-arrow SDPs of uneven size: l, d, h, m uniform on the
+    given inclusive ranges, each problem with its own seed; A_i sparse on the
+    pattern with the given density (None: dense on the pattern)."""
     rng = np.random.default_rng(seed)
-    shapes = [(int(rng.integers(10, 101)), int(rng.integers(10, 41)),
-               int(rng.integers(10, 21)), int(rng.integers(50, 401))) for _ in range(count)]
-    return [block_arrow(l, d, h, m, seed + 1 + i) for i, (l, d, h, m) in enumerate(shapes)]
+    shapes = [(int(rng.integers(l_range[0], l_range[1] + 1)), int(rng.integers(d_range[0], d_range[1] + 1)),
+               int(rng.integers(h_range[0], h_range[1] + 1)), int(rng.integers(m_range[0], m_range[1] + 1)))
+              for _ in range(count)]
+    return [block_arrow(l, d, h, m, seed + 1 + i, density=density) for i, (l, d, h, m) in enumerate(shapes)]
+
+
+def direct_sum(problems, name=None):
+    """The block-diagonal SDP whose summands are `problems`: vertices and
+    constraints of problem j are shifted past those of problems 0..j-1.  Its
+    optimum is the sum of theirs."""
+    vo = np.cumsum([0] + [p.n for p in problems])
+    mo = np.cumsum([0] + [p.m for p in problems])
+    cat = lambda f, sh: np.concatenate([getattr(p, f).astype(np.int64) + s for p, s in zip(problems, sh)]).astype(np.int32)
+    opt = None
+    if all(p.optimum is not None for p in problems):
+        opt = float(sum(p.optimum for p in problems))
+    return SDPProblem(int(vo[-1]), int(mo[-1]), cat("A_con", mo), cat("A_row", vo), cat("A_col", vo),
+                      np.concatenate([p.A_val for p in problems]), np.concatenate([p.b for p in problems]),
+                      cat("C_row", vo), cat("C_col", vo), np.concatenate([p.C_val for p in problems]),
+                      cat("P_row", vo), cat("P_col", vo),
+                      name or "direct_sum_" + "+".join(p.name for p in problems), opt)
 
 
 def banded_batch(count, n, w, m, seed):

@@ -103,3 +103,76 @@ def test_workspace_bytes_without_gpu(lib):
     P = lib.Problem(W.workload(0))
     a, b = P.workspace_bytes(10), P.workspace_bytes(2000)
     assert 0 < a < b and a % 256 == 0
+
+
+def _summands():
+    return [W.block_arrow(3, 4, 2, 6, seed=21), W.banded(15, 3, 7, seed=22, density=0.4),
+            W.lovasz_theta_cycle(5), W.block_arrow(2, 5, 3, 9, seed=23, density=0.5)]
+
+
+def test_components_of_direct_sum(lib):
+    """A direct sum has one independent component per summand, numbered in
+    vertex order; its cliques are the summands' cliques, shifted."""
+    parts = _summands()
+    prob = W.direct_sum(parts)
+    P = _compare(prob)
+    assert P.info["ncomp"] == len(parts)
+    vc, rc = P.components()
+    np.testing.assert_array_equal(vc, np.repeat(np.arange(len(parts)), [p.n for p in parts]))
+    np.testing.assert_array_equal(rc, np.repeat(np.arange(len(parts)), [p.m for p in parts]))
+    shifted, vo = [], 0
+    for q in parts:
+        shifted += [tuple(v + vo for v in cl) for cl in lib.Problem(q).clique_list()]
+        vo += q.n
+    assert sorted(P.clique_list()) == sorted(shifted)
+
+
+def test_components_joined_by_a_constraint(lib):
+    """A constraint whose entries touch two summands merges them (the pattern
+    alone would not): A D^-1 A^T then couples their constraints."""
+    import dataclasses
+    a, b = W.block_arrow(2, 3, 2, 4, seed=31), W.block_arrow(2, 4, 1, 5, seed=32)
+    s = W.direct_sum([a, b, W.lovasz_theta_cycle(5)])
+    # constraint 0 gets one more (diagonal) entry in the second summand
+    s = dataclasses.replace(s, A_con=np.append(s.A_con, 0).astype(np.int32),
+                            A_row=np.append(s.A_row, a.n).astype(np.int32),
+                            A_col=np.append(s.A_col, a.n).astype(np.int32), A_val=np.append(s.A_val, 1.0))
+    P = lib.Problem(s)
+    assert P.info["ncomp"] == 2
+    vc, rc = P.components()
+    assert set(vc[:a.n + b.n].tolist()) == {0} and set(vc[a.n + b.n:].tolist()) == {1}
+    assert set(rc[:a.m + b.m].tolist()) == {0} and set(rc[a.m + b.m:].tolist()) == {1}
+
+
+def test_components_interleaved_numbering(lib):
+    """Components are found from the structure, not from index ranges: with
+    the vertices of two summands interleaved and the constraints shuffled,
+    each vertex and constraint still lands in its summand's component."""
+    import dataclasses
+    a, b = W.banded(10, 2, 4, seed=41, density=0.5), W.block_arrow(2, 3, 2, 5, seed=42)
+    s = W.direct_sum([a, b])
+    rng = np.random.default_rng(0)
+    vperm = rng.permutation(s.n).astype(np.int32)  # new label of each vertex
+    cperm = rng.permutation(s.m).astype(np.int32)
+
+    def relabel(r, c):
+        r2, c2 = vperm[r], vperm[c]
+        return np.maximum(r2, c2).astype(np.int32), np.minimum(r2, c2).astype(np.int32)
+
+    Ar, Ac = relabel(s.A_row, s.A_col)
+    Cr, Cc = relabel(s.C_row, s.C_col)
+    b_new = np.empty_like(s.b)
+    b_new[cperm] = s.b
+    t = dataclasses.replace(s, A_row=Ar, A_col=Ac, C_row=Cr, C_col=Cc, A_con=cperm[s.A_con], b=b_new)
+    P = _compare(t)
+    assert P.info["ncomp"] == 2
+    vc, rc = P.components()
+    owner = np.repeat([0, 1], [a.n, b.n])
+    first = owner[np.argmin(vperm)]  # the summand holding new vertex 0 is component 0
+    want_v = np.empty(s.n, np.int64)
+    want_v[vperm] = (owner != first).astype(np.int64)
+    np.testing.assert_array_equal(vc, want_v)
+    cowner = np.repeat([0, 1], [a.m, b.m])
+    want_c = np.empty(s.m, np.int64)
+    want_c[cperm] = (cowner != first).astype(np.int64)
+    np.testing.assert_array_equal(rc, want_c)
