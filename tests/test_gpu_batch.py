@@ -132,8 +132,16 @@ def test_direct_sum_hsde_trajectory(lib, torch_cuda):
 def test_block_arrow_batch_fp32(lib, torch_cuda, form):
     """Three uneven block-arrow SDPs (cliques of order 36, 24 and 22, so both
     the warp-per-clique and the block-per-clique projections run) in one FP32
-    solve: each summand solved, objective within 1e-4 of the FP64 oracle's
-    (primal and dual forms share the optimum)."""
+    solve, against the FP64 oracle's run of the same form on each summand.
+    Near eps = 1e-4 the objective of these runs still moves by a few 1e-4
+    (relative) from one iteration to the next, and float32 rounding can move
+    the stopping iteration by a few, so the checks are: every summand solved,
+    within 5% (at least 3) of the oracle's iteration count, and its objective
+    within tol of the oracle's objective at the same iteration: 1e-4 for
+    Algorithm 1; 3e-4 for Algorithm 2, whose projection input z_k + H_k x is
+    dominated by the primal part, so the float32 eigensolver's error
+    (~ s u ||W||_F per projection, s = 36) accumulates in x, from which X is
+    read (measured: 1.6e-4 after 97 iterations on the order-36 summand)."""
     parts = [W.block_arrow(2, 24, 12, 20, seed=91, density=0.3), W.block_arrow(2, 14, 10, 25, seed=92, density=0.3),
              W.block_arrow(3, 10, 12, 20, seed=93, density=0.3)]
     prob = W.direct_sum(parts)
@@ -150,10 +158,13 @@ def test_block_arrow_batch_fp32(lib, torch_cuda, form):
         cvec[index[(int(i), int(j))]] += v
     vo = 0
     for j, q in enumerate(parts):
-        dp, ref = _oracle(q, "primal", 1e-4, 20000)
+        dp, ref = _oracle(q, form, 1e-4, 20000)
         assert ref.status == 0
+        assert abs(int(it[j]) - ref.iters) <= max(3, 0.05 * ref.iters), (j, it[j], ref.iters)
+        _, traj = _oracle(q, form, 0.0, int(it[j]))
         mask = (c >= vo) & (c < vo + q.n)
         obj = float(np.sum(wgt[mask] * cvec[mask] * out["X"][mask]))
-        want = float(dp.c @ ref.X)
-        assert abs(obj - want) <= 1e-4 * abs(want), (j, obj, want)
+        want = float(traj.hist[-1, 4])
+        tol = 1e-4 if form == "primal" else 3e-4
+        assert abs(obj - want) <= tol * abs(want), (j, obj, want)
         vo += q.n
