@@ -140,13 +140,29 @@ class Result:
     state: dict | None = None
 
 
-def primal_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None):
+def adapt_rho(rho, eps_p, eps_d, mu, nu):
+    """Adaptive penalty rule of Section 7.1.2: multiply rho by mu when the
+    primal residual is at least nu times the dual one, divide by mu in the
+    opposite case, keep it otherwise.  For Algorithms 1-2 the residual pair
+    is (eps_c, eps_lambda) of their stopping tests."""
+    if eps_p >= nu * eps_d:
+        return rho * mu
+    if eps_d >= nu * eps_p:
+        return rho / mu
+    return rho
+
+
+def primal_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None, adapt_every=0, mu=2.0, nu=10.0):
     """Algorithm 1 (ADMM for the domain-space decomposition).
     x-step: KKT system Eq. OptCondMinYPrimal by block elimination with the
     cached Cholesky factor of A D^-1 A^T (Eq. ADMMprimalFatorization, and
     Appendix A: L L^T y = A D^-1 bhat - b, x = D^-1 (bhat - A^T y));
     x_k-step: Eq. XkUpdate; multipliers: Eq. LambdakUpdate; stopping:
-    Eq. PrimalConsensusResidual and eps_lambda (Section 4.1.4)."""
+    Eq. PrimalConsensusResidual and eps_lambda (Section 4.1.4).
+    adapt_every = N > 0 applies the adaptive penalty rule (Section 7.1.2,
+    `adapt_rho`) after every N-th iteration whose stopping test failed; the
+    multipliers are unscaled, so nothing else changes with rho.  History
+    column 2 holds the rho of each iteration."""
     A, b, c, D = dp.A, dp.b, dp.c, dp.D
     AT = A.T.tocsr()
     fac = _cholesky((A @ scipy.sparse.diags(1.0 / D) @ A.T).toarray())
@@ -164,21 +180,25 @@ def primal_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None)
         eps_c = _norm(xk_new - Hx) / max(_norm(xk_new), _norm(Hx), 1e-300)
         eps_l = rho * _norm(xk_new - xk) / max(_norm(lam), 1e-300)
         xk = xk_new
-        hist.append([eps_c, eps_l, 0.0, 0.0, float(c @ x), float(-rho * (b @ y)), 0.0, 0.0])
+        hist.append([eps_c, eps_l, rho, 0.0, float(c @ x), float(-rho * (b @ y)), 0.0, 0.0])
         if callback is not None:
             callback(it, dict(x=x, y=y, xk=xk, lam=lam))
+        rho_it = rho  # the penalty this iteration ran with
         if it > 1 and max(eps_c, eps_l) <= eps:
             status = SOLVED
             break
-    return Result(status, it, x, -rho * y, dp.HT(lam), np.array(hist),
-                  state=dict(x=x, y_kkt=y, xk=xk, lam=lam))
+        if adapt_every > 0 and it % adapt_every == 0:
+            rho = adapt_rho(rho, eps_c, eps_l, mu, nu)
+    return Result(status, it, x, -rho_it * y, dp.HT(lam), np.array(hist),
+                  state=dict(x=x, y_kkt=y, xk=xk, lam=lam, rho=rho_it))
 
 
-def dual_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None):
+def dual_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None, adapt_every=0, mu=2.0, nu=10.0):
     """Algorithm 2 (ADMM for the range-space decomposition).
     z-step Eq. zkUpdate; (y, x) from the KKT system Eq. OptCondMinYDual with the
     same cached factor of A D^-1 A^T; v_k from Eq. vkEqn; lambda_k from the
-    generic rule Eq. MultUpdateDualSDP; stopping Section 4.2.4."""
+    generic rule Eq. MultUpdateDualSDP; stopping Section 4.2.4.  Adaptive
+    penalty and history column 2 as in `primal_admm`."""
     A, b, c, D = dp.A, dp.b, dp.c, dp.D
     AT = A.T.tocsr()
     fac = _cholesky((A @ scipy.sparse.diags(1.0 / D) @ A.T).toarray())
@@ -199,14 +219,17 @@ def dual_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None):
         eps_c = _norm(z_new - v) / max(_norm(z_new), _norm(v), 1e-300)
         eps_l = rho * _norm(z_new - z) / max(_norm(lam), 1e-300)
         z = z_new
-        hist.append([eps_c, eps_l, 0.0, 0.0, float(-rho * (c @ x)), float(b @ y), 0.0, 0.0])
+        hist.append([eps_c, eps_l, rho, 0.0, float(-rho * (c @ x)), float(b @ y), 0.0, 0.0])
         if callback is not None:
             callback(it, dict(x=x, y=y, z=z, v=v, lam=lam))
+        rho_it = rho  # the penalty this iteration ran with
         if it > 1 and max(eps_c, eps_l) <= eps:
             status = SOLVED
             break
-    return Result(status, it, -rho * x, y, dp.HT(z), np.array(hist),
-                  state=dict(x=x, y=y, z=z, v=v, lam=lam))
+        if adapt_every > 0 and it % adapt_every == 0:
+            rho = adapt_rho(rho, eps_c, eps_l, mu, nu)
+    return Result(status, it, -rho_it * x, y, dp.HT(z), np.array(hist),
+                  state=dict(x=x, y=y, z=z, v=v, lam=lam, rho=rho_it))
 
 
 class HSDEOperator:

@@ -185,3 +185,48 @@ def test_block_arrow_workload_converges():
         assert r.status == admm.SOLVED
         objs.append(dp.c @ r.X)
     assert abs(objs[0] - objs[1]) <= 1e-4 * abs(objs[0])
+
+
+# ---- adaptive penalty (Section 7.1.2) ---------------------------------------
+
+def test_adapt_rho_rule_cases():
+    """mu = 2, nu = 10: primal residual >= 10x dual -> double; dual >= 10x
+    primal -> halve; otherwise keep (boundaries inclusive as printed)."""
+    assert admm.adapt_rho(1.0, 1e-2, 1e-3, 2.0, 10.0) == 2.0
+    assert admm.adapt_rho(1.0, 1e-3, 1e-2, 2.0, 10.0) == 0.5
+    assert admm.adapt_rho(1.0, 1e-3, 2e-3, 2.0, 10.0) == 1.0
+    assert admm.adapt_rho(4.0, 5.0, 0.5, 2.0, 10.0) == 8.0
+    assert admm.adapt_rho(4.0, 0.0, 0.0, 2.0, 10.0) == 8.0  # 0 >= 10 * 0
+
+
+@pytest.mark.parametrize("form", ["primal", "dual"])
+@pytest.mark.parametrize("prob", CLOSED[:4], ids=lambda p: p.name)
+def test_closed_form_optimum_adaptive_rho(prob, form):
+    """With the adaptive penalty the iteration still reaches the closed-form
+    optimum (the rule only changes the path, not the fixed point)."""
+    dp, r = admm.solve(prob, form, eps=1e-8, max_iter=20000, adapt_every=1)
+    assert r.status == admm.SOLVED
+    obj = float(dp.c @ r.X)
+    assert abs(obj - prob.optimum) <= 1e-6 * max(1.0, abs(prob.optimum))
+
+
+@pytest.mark.parametrize("form", ["primal", "dual"])
+def test_adaptive_rho_same_optimum(form):
+    """Banded instance: with the adaptive rule applied every 5 iterations the
+    iteration reaches the objective of the fixed-rho run (within 1e-5 at
+    eps = 1e-6); the penalty recorded in history column 2 follows the rule
+    applied to columns 0-1 of the same row, and does change."""
+    prob = W.banded(60, 4, 15, seed=11, density=0.3)
+    dp = admm.decompose(prob)
+    fn = admm.primal_admm if form == "primal" else admm.dual_admm
+    fixed = fn(dp, eps=1e-6, max_iter=30000)
+    adapt = fn(dp, eps=1e-6, max_iter=30000, adapt_every=5)
+    assert fixed.status == admm.SOLVED and adapt.status == admm.SOLVED
+    o1, o2 = float(dp.c @ fixed.X), float(dp.c @ adapt.X)
+    assert abs(o1 - o2) <= 1e-5 * abs(o1)
+    h = adapt.hist
+    assert np.all(fixed.hist[:, 2] == 1.0)
+    for n in range(len(h) - 1):
+        want = admm.adapt_rho(h[n, 2], h[n, 0], h[n, 1], 2.0, 10.0) if (n + 1) % 5 == 0 else h[n, 2]
+        assert h[n + 1, 2] == want
+    assert len(set(h[:, 2])) > 1
