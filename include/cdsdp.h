@@ -78,6 +78,14 @@ typedef struct {
                               is that of a solve of the component alone; 0 = one test
                               over the whole problem.  HSDE always uses one test (tau
                               and kappa are shared).                                   */
+    int adaptive_rho;      /* Algorithms 1-2: 0 = fixed rho; N > 0 = after every N-th
+                              iteration whose stopping test failed, apply the adaptive
+                              penalty rule of Section 7.1.2 to (eps_c, eps_lambda):
+                              rho *= rho_mu if eps_c >= rho_nu eps_lambda, rho /= rho_mu
+                              if eps_lambda >= rho_nu eps_c (per component with
+                              component_stop).  The cached factor does not involve rho. */
+    double rho_mu;         /* >= 1; the paper's default 2                              */
+    double rho_nu;         /* >= 1; the paper's default 10                             */
 } cdsdp_opts;
 
 typedef struct {
@@ -96,7 +104,8 @@ typedef struct {
 
 /* Fill `o` with defaults: eps 1e-4, max_iter 2000, rho 1, FP32 projection,
  * graph on, check_every 50, 30 Jacobi sweeps, warm start with a cold start every
- * 16 iterations, no profiling, per-component stopping. */
+ * 16 iterations, no profiling, per-component stopping, fixed rho (adaptive
+ * rule off; rho_mu 2, rho_nu 10 when switched on). */
 void cdsdp_default_opts(cdsdp_opts* o);
 
 /* Data preprocessing of Algorithms 1-3 (host only, no GPU call):
@@ -172,7 +181,7 @@ int cdsdp_bind(cdsdp* h, void* d_workspace, size_t bytes, int max_iter, void* st
  *   y     [m]           dual multipliers
  *   Z     [nnz_pattern] dual slack on E*
  *   hist  [iters x 8]   per-iteration residuals, row-major:
- *         primal/dual: eps_c, eps_lambda, 0, 0, <C,X>, b^T y, 0, 0
+ *         primal/dual: eps_c, eps_lambda, rho, 0, <C,X>, b^T y, 0, 0
  *         HSDE tau>0:  eps_p, eps_d, eps_g, eps_c, <C,X>, b^T y, tau, kappa
  *         HSDE tau=0:  ||A^T u_y + H^T v_z||, ||A u_x||, b^T u_y, c^T u_x, 0, 0, tau, kappa
  *   iters number of iterations run (with per-component stopping: the largest

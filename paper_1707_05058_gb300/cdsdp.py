@@ -36,7 +36,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_iter", ctypes.c_int), ("rho", ctypes.c_double),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("jacobi_max_sweeps", ctypes.c_int), ("warm_start", ctypes.c_int), ("profile", ctypes.c_int),
-                ("component_stop", ctypes.c_int)]
+                ("component_stop", ctypes.c_int), ("adaptive_rho", ctypes.c_int), ("rho_mu", ctypes.c_double),
+                ("rho_nu", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

@@ -17,15 +17,16 @@ namespace cdsdp_dev {
 
 // ---- pattern-entry kernels ---------------------------------------------------
 
-// out_e = (alpha c_e + beta sum_{j in H^T(e)} (P_j + gamma Q_j)) * scale_e
+// out_e = (alpha c_e + beta sum_{j in H^T(e)} (P_j + gamma Q_j)) * scale_e, with
+// alpha (gamma) divided by the entry's rho when alpha_rho (gamma_rho) is set.
 // Algorithm 1: bhat / D with bhat = sum_k H_k^T (x_k + lambda_k/rho) - c/rho
 // (Appendix A, Eq. bnflopsdef); Algorithm 2: (c - sum_k H_k^T (z_k + lambda_k/rho)) / D
 // (right-hand side of Eq. OptCondMinYDual); output assembly: Z = sum_k H_k^T lambda_k.
 template <typename T>
 __global__ void __launch_bounds__(ETHREADS) k_scatter(Dev d, const T* __restrict__ P, const T* __restrict__ Q,
-                                                      double alpha, double beta, double gamma,
-                                                      const double* __restrict__ scale, double* __restrict__ out,
-                                                      int check_stop, int G) {
+                                                      double alpha, double beta, double gamma, int alpha_rho,
+                                                      int gamma_rho, const double* __restrict__ scale,
+                                                      double* __restrict__ out, int check_stop, int G) {
     if (check_stop && stopped(d)) return;
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G, lig = threadIdx.x & (G - 1);
     const int ng = (gridDim.x * blockDim.x) / G;
@@ -34,16 +35,22 @@ __global__ void __launch_bounds__(ETHREADS) k_scatter(Dev d, const T* __restrict
         const int e = gid + it * ng;
         double acc = 0.0;
         const bool live = e < d.NE && !(check_stop && frozen_entry(d, e));
+        double a = alpha, gm = gamma;
+        if (live && (alpha_rho || gamma_rho)) {
+            const double ir = 1.0 / rho_entry(d, e);
+            if (alpha_rho) a *= ir;
+            if (gamma_rho) gm *= ir;
+        }
         if (live) {
             const int j1 = d.sc_ptr[e + 1];
             for (int j = d.sc_ptr[e] + lig; j < j1; j += G) {
                 const int q = d.sc_idx[j];
-                acc += Q ? double(P[q]) + gamma * double(Q[q]) : double(P[q]);
+                acc += Q ? double(P[q]) + gm * double(Q[q]) : double(P[q]);
             }
         }
         acc = group_sum(acc, G);
         if (live && lig == 0) {
-            const double r = alpha * d.c[e] + beta * acc;
+            const double r = a * d.c[e] + beta * acc;
             out[e] = scale ? r * scale[e] : r;
         }
     }
@@ -80,9 +87,10 @@ __global__ void __launch_bounds__(ETHREADS) k_xupd(Dev d, const double* __restri
 
 // ---- constraint-row kernels ------------------------------------------------
 
-// out_i = (A W v)_i + delta b_i ; Appendix A item (ii): A D^-1 bhat - b.
+// out_i = (A W v)_i + delta b_i (delta / rho_i when delta_rho); Appendix A
+// item (ii): A D^-1 bhat - b.
 __global__ void __launch_bounds__(RTHREADS) k_rows_aw(Dev d, const double* __restrict__ v, double delta,
-                                                      double* __restrict__ out, int TPR) {
+                                                      int delta_rho, double* __restrict__ out, int TPR) {
     __shared__ double sh[RTHREADS / 32];
     if (stopped(d)) return;
     const int rpb = blockDim.x / TPR, gi = threadIdx.x / TPR, tig = threadIdx.x % TPR;
@@ -96,7 +104,7 @@ __global__ void __launch_bounds__(RTHREADS) k_rows_aw(Dev d, const double* __res
             for (int q = d.a_ptr[i] + tig; q < q1; q += TPR) s += d.a_valw[q] * v[d.a_col[q]];
         }
         s = row_group_sum(s, TPR, sh);
-        if (live && tig == 0) out[i] = s + delta * d.b[i];
+        if (live && tig == 0) out[i] = s + (delta_rho ? delta / rho_row(d, i) : delta) * d.b[i];
     }
 }
 

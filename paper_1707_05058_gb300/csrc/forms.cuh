@@ -13,7 +13,7 @@ namespace cdsdp_dev {
 __device__ void finish_dual_block(const Dev& d, const FinishArgs& fa);
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho, FinishArgs fa) {
+__global__ void __launch_bounds__(128) k_vlam_dual(Dev d, FinishArgs fa) {
     if (stopped(d)) return;
     const int lane = threadIdx.x & 31;
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(128) k_vlam_dual(Dev d, double rho, FinishArgs
     double acc[4] = {0, 0, 0, 0};
     for (int k = w0; k < d.p; k += nw) {
         if (frozen_clique(d, k)) continue;  // warp-uniform
+        const double rho = rho_clique(d, k);
         const int off = d.pk_off[k], s = d.csize[k], npk = s * (s + 1) / 2;
         double p0 = 0, p1 = 0, p2 = 0, p3 = 0, cx = 0;
         for (int f = lane; f < npk; f += 32) {
@@ -69,13 +70,16 @@ __device__ void finish_dual_block(const Dev& d, const FinishArgs& fa) {
     const double by = sum_col(d.partr, fa.nbr, 0, sh);
     if (threadIdx.x == 0) {
         const int it = d.ctl[CTL_ITER] + 1;
+        const double rho = d.rho[0];
         const double ec = sqrt(s[0]) / fmax(fmax(sqrt(s[1]), sqrt(s[2])), 1e-300);
-        const double el = fa.rho * sqrt(s[4]) / fmax(sqrt(s[3]), 1e-300);
+        const double el = rho * sqrt(s[4]) / fmax(sqrt(s[3]), 1e-300);
         double* h = d.hist + (size_t)(it - 1) * HIST_COLS;
-        h[0] = ec; h[1] = el; h[2] = 0; h[3] = 0; h[4] = -fa.rho * cx; h[5] = by; h[6] = 0; h[7] = 0;
+        h[0] = ec; h[1] = el; h[2] = rho; h[3] = 0; h[4] = -rho * cx; h[5] = by; h[6] = 0; h[7] = 0;
         const bool bad = !isfinite(ec) || !isfinite(el);
         d.ctl[CTL_COUNTER] = 0;
         finish_common(d, bad, it > 1 && fmax(ec, el) <= fa.eps, it, fa.use_cond, fa.hnd);
+        if (!d.ctl[CTL_DONE] && fa.adapt_every > 0 && it % fa.adapt_every == 0)
+            d.rho[0] = adapt_rho(rho, ec, el, fa.mu, fa.nu);
     }
 }
 
@@ -113,18 +117,19 @@ __global__ void __launch_bounds__(256) k_finish_components(Dev d, int form, Fini
         block_sum<8>(v, sh);
         if (threadIdx.x == 0) {
             double ec, el, cost, dobj;
+            const double rho = d.rho[c];
             ec = sqrt(v[0]) / fmax(fmax(sqrt(v[1]), sqrt(v[2])), 1e-300);
             if (form == 0) {
-                el = fa.rho * sqrt(v[3]) / fmax(sqrt(v[4]), 1e-300);
+                el = rho * sqrt(v[3]) / fmax(sqrt(v[4]), 1e-300);
                 cost = v[5];
-                dobj = -fa.rho * v[7];
+                dobj = -rho * v[7];
             } else {
-                el = fa.rho * sqrt(v[5]) / fmax(sqrt(v[3]), 1e-300);
-                cost = -fa.rho * v[6];
+                el = rho * sqrt(v[5]) / fmax(sqrt(v[3]), 1e-300);
+                cost = -rho * v[6];
                 dobj = v[7];
             }
             double* r = d.comp_res + (size_t)c * HIST_COLS;
-            r[0] = ec; r[1] = el; r[2] = 0; r[3] = 0; r[4] = cost; r[5] = dobj; r[6] = 0; r[7] = 0;
+            r[0] = ec; r[1] = el; r[2] = rho; r[3] = 0; r[4] = cost; r[5] = dobj; r[6] = 0; r[7] = 0;
             int st = 1, done = 0;
             if (!isfinite(ec) || !isfinite(el)) { st = -6; done = 1; }
             else if (it > 1 && fmax(ec, el) <= fa.eps) { st = 0; done = 1; }
@@ -133,6 +138,8 @@ __global__ void __launch_bounds__(256) k_finish_components(Dev d, int form, Fini
             if (done) {
                 d.comp_status[c] = st;
                 d.comp_done[c] = 1;
+            } else if (fa.adapt_every > 0 && it % fa.adapt_every == 0) {
+                d.rho[c] = adapt_rho(rho, ec, el, fa.mu, fa.nu);
             }
         }
     }
@@ -416,7 +423,8 @@ __device__ void finish_hsde_block(const Dev& d, const FinishArgs& fa) {
 
 // ---- set-up and result assembly --------------------------------------------
 
-__global__ void k_init(Dev d, int form) {
+__global__ void k_init(Dev d, int form, double rho0) {
+    for (int c = threadIdx.x; c < d.ncomp; c += blockDim.x) d.rho[c] = rho0;
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         d.scal[SC_TAU] = (form == 2) ? 1.0 : 0.0;
         d.scal[SC_KAPPA] = (form == 2) ? 1.0 : 0.0;
@@ -424,6 +432,15 @@ __global__ void k_init(Dev d, int form) {
         d.ctl[CTL_ITER] = 0;
         d.ctl[CTL_STATUS] = 1;
     }
+}
+
+// out_i = sign * rho_i * in_i, rho_i the penalty of entry i (rows = 0) or of
+// constraint row i (rows = 1): the variables of Algorithms 1-2 scaled back by
+// the penalty of their last iteration.
+__global__ void k_scale_rho(Dev d, int n, const double* __restrict__ in, double sign, int rows,
+                            double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = sign * (rows ? rho_row(d, i) : rho_entry(d, i)) * in[i];
 }
 
 // out = scale * in, or scale * in / *sptr: mode 1 divides only when *sptr > 0

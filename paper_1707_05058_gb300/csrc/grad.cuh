@@ -80,8 +80,9 @@ __global__ void __launch_bounds__(ETHREADS) k_bwd_state(Dev d, const double* __r
 }
 
 // Reset the per-segment iteration counters (the replay counts from 0).
-__global__ void k_reset_ctl(Dev d) {
+__global__ void k_reset_ctl(Dev d, double rho) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
+        d.rho[0] = rho;
         d.ctl[CTL_DONE] = 0;
         d.ctl[CTL_ITER] = 0;
         d.ctl[CTL_STATUS] = 1;

@@ -412,11 +412,12 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
     T* lam = reinterpret_cast<T*>(d.ck1);
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
-    const T rho_t = T(pa.rho), irho = T(1.0 / pa.rho);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         if (frozen_clique(d, k)) continue;  // warp-uniform
+        const double rho = rho_clique(d, k);
+        const T rho_t = T(rho), irho = T(1.0 / rho);
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
         jac.clear(lane);
         T nrm = T(0);
@@ -511,11 +512,11 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
     const T* lam = reinterpret_cast<const T*>(d.ck2);
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
-    const T irho = T(1.0 / pa.rho);
     double acc[1] = {0};
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
         if (frozen_clique(d, k)) continue;  // warp-uniform
+        const T irho = T(1.0 / rho_clique(d, k));
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
         jac.clear(lane);
         T nrm = T(0);

@@ -241,7 +241,6 @@ __global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* _
     T* c2 = reinterpret_cast<T*>(d.ck2);
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = FORM != 3 && pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
-    const double rho = pa.rho, irho = 1.0 / pa.rho;
     const double gamma = FORM == 2 ? d.scal[SC_GAMMA] : 0.0;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
@@ -250,6 +249,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* _
         const int off = FORM == 3 ? off_arr[k] : d.pk_off[k];
         if (s > S || s < 1) continue;  // block-uniform
         if (FORM != 3 && frozen_clique(d, k)) continue;
+        const double rho = (FORM == 0 || FORM == 1) ? rho_clique(d, k) : 1.0, irho = 1.0 / rho;
         const int npk = s * (s + 1) / 2;
         jac.clear();
         double nrm = 0.0, cx = 0.0;

@@ -90,6 +90,8 @@ struct Dev {
     int* comp_iter;             // [ncomp] iterations run by the component
     int* comp_status;           // [ncomp] cdsdp_status of the component
     double* comp_res;           // [ncomp * HIST_COLS] last stopping-test row of the component
+    double* rho;                // [ncomp] penalty of Algorithms 1-2: one per component when
+                                // components stop on their own, else entry 0 for the whole problem
 };
 
 constexpr int NBLK_E = 1216;  // 152 SMs x 8
@@ -100,7 +102,9 @@ constexpr int FTHREADS = 512;
 
 // Stopping-test arguments handed to the kernel whose last block finishes an iteration.
 struct FinishArgs {
-    double rho, eps;
+    double eps;
+    double mu, nu;       // adaptive penalty (Section 7.1.2): factor and balance ratio
+    int adapt_every;     // 0: fixed rho; N: apply the rule after every N-th iteration
     int nbe, nbr;        // rows of the per-block partial tables to reduce
     int enabled;         // 0: this launch does not finish the iteration
     int use_cond;        // 1: inside the graph while loop (set its condition)
@@ -109,7 +113,7 @@ struct FinishArgs {
 
 // Eigensolver options of the projection kernels.
 struct ProjArgs {
-    double rho, tolrel;
+    double tolrel;
     int max_sweeps;
     int warm_start;      // reuse the previous iteration's eigenvectors
     int restart;         // cold start every `restart` iterations
@@ -118,6 +122,23 @@ struct ProjArgs {
 
 __device__ __forceinline__ bool stopped(const Dev& d) {
     return *((volatile int*)d.ctl + CTL_DONE) != 0;
+}
+
+// Penalty of Algorithms 1-2 seen by a clique, pattern entry or constraint row.
+__device__ __forceinline__ double rho_clique(const Dev& d, int k) {
+    return d.rho[d.comp_mode ? d.comp_of_clique[k] : 0];
+}
+__device__ __forceinline__ double rho_entry(const Dev& d, int e) {
+    return d.rho[d.comp_mode ? d.comp_of_entry[e] : 0];
+}
+__device__ __forceinline__ double rho_row(const Dev& d, int i) {
+    return d.rho[d.comp_mode ? d.comp_of_row[i] : 0];
+}
+// Adaptive penalty rule (Section 7.1.2) on the residual pair (eps_c, eps_lambda).
+__device__ __forceinline__ double adapt_rho(double rho, double ep, double ed, double mu, double nu) {
+    if (ep >= nu * ed) return rho * mu;
+    if (ed >= nu * ep) return rho / mu;
+    return rho;
 }
 
 // Component freeze: a stopped component's entries, rows and cliques are left alone.

@@ -65,7 +65,6 @@ cudaError_t launch_proj_cta_standalone(bool fp32, int cls, int p, const int* off
     Dev d{};
     ProjArgs pa{};
     FinishArgs fa{};
-    pa.rho = 1.0;
     pa.restart = 1;
     if (fp32) {
         switch (S) {

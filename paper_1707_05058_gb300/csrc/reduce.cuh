@@ -87,13 +87,16 @@ __device__ __forceinline__ void finish_primal_block(const Dev& d, const FinishAr
     const double by = sum_col(d.partr, fa.nbr, 0, sh);
     if (threadIdx.x == 0) {
         const int it = d.ctl[CTL_ITER] + 1;
+        const double rho = d.rho[0];
         const double ec = sqrt(s[0]) / fmax(fmax(sqrt(s[1]), sqrt(s[2])), 1e-300);
-        const double el = fa.rho * sqrt(s[3]) / fmax(sqrt(s[4]), 1e-300);
+        const double el = rho * sqrt(s[3]) / fmax(sqrt(s[4]), 1e-300);
         double* h = d.hist + (size_t)(it - 1) * HIST_COLS;
-        h[0] = ec; h[1] = el; h[2] = 0; h[3] = 0; h[4] = cx; h[5] = -fa.rho * by; h[6] = 0; h[7] = 0;
+        h[0] = ec; h[1] = el; h[2] = rho; h[3] = 0; h[4] = cx; h[5] = -rho * by; h[6] = 0; h[7] = 0;
         const bool bad = !isfinite(ec) || !isfinite(el);
         d.ctl[CTL_COUNTER] = 0;
         finish_common(d, bad, it > 1 && fmax(ec, el) <= fa.eps, it, fa.use_cond, fa.hnd);
+        if (!d.ctl[CTL_DONE] && fa.adapt_every > 0 && it % fa.adapt_every == 0)
+            d.rho[0] = adapt_rho(rho, ec, el, fa.mu, fa.nu);
     }
 }
 

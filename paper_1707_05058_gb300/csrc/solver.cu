@@ -36,7 +36,7 @@ struct Layout {
     size_t const_end;
     // state
     size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, vcache, part, parte, partr, scal, ctl, hist,
-        comp_done, comp_iter, comp_status, comp_res;
+        comp_done, comp_iter, comp_status, comp_res, rho;
     size_t total;
 };
 
@@ -122,6 +122,7 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     L.hist = take((size_t)std::max(max_iter, 1) * HIST_COLS * 8);
     L.comp_done = take(nc * 4); L.comp_iter = take(nc * 4); L.comp_status = take(nc * 4);
     L.comp_res = take(nc * HIST_COLS * 8);
+    L.rho = take(nc * 8);
     L.total = o;
     return L;
 }
@@ -216,6 +217,7 @@ void make_dev(cdsdp* h) {
     d.minv_off = (const long long*)(w + L.minv_off);
     d.comp_done = (int*)(w + L.comp_done); d.comp_iter = (int*)(w + L.comp_iter);
     d.comp_status = (int*)(w + L.comp_status); d.comp_res = (double*)(w + L.comp_res);
+    d.rho = (double*)(w + L.rho);
     auto pow2_clamp = [](double x, int lo, int hi) {
         int v = lo;
         while (v < hi && v < x) v <<= 1;
@@ -242,7 +244,6 @@ template <typename T>
 cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const FinishArgs& fa, cudaStream_t st) {
     const int* bl = (const int*)(h->ws + h->L.blist);
     ProjArgs pa;
-    pa.rho = o.rho;
     pa.tolrel = sizeof(T) == 4 ? 1.2e-7 : 2.3e-16;
     pa.max_sweeps = o.jacobi_max_sweeps;
     pa.warm_start = o.warm_start > 0 ? 1 : 0;
@@ -272,10 +273,11 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
                              cudaGraphConditionalHandle hnd, cudaEvent_t ev0, cudaEvent_t ev1) {
     Dev& d = h->dev;
     const int GE = h->GE, GR = h->GR, PG = std::max(1, std::min((d.p + 3) / 4, 152 * 32));
-    const double rho = o.rho;
     FinishArgs fa;
-    fa.rho = rho;
     fa.eps = o.eps;
+    fa.mu = o.rho_mu;
+    fa.nu = o.rho_nu;
+    fa.adapt_every = o.adaptive_rho;
     fa.nbe = GE;
     fa.nbr = GR;
     fa.enabled = 1;
@@ -287,8 +289,8 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
     if (d.comp_mode) fin.enabled = 0;
     cudaError_t e;
     if (form == 0) {  // Algorithm 1; the projection computes x on the fly and its last block the stopping test
-        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0 / rho, 1.0, 1.0 / rho, d.dinv, d.t, 1, h->Gs);
-        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, d.g, h->TPR);
+        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0, 1.0, 1.0, 1, 1, d.dinv, d.t, 1, h->Gs);
+        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, 0, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
@@ -301,15 +303,15 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         none.enabled = 0;
         if ((e = launch_projection<T>(h, 1, o, none, st)) != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, st);
-        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0 / rho, d.dinv, d.t, 1, h->Gs);
-        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0 / rho, d.g, h->TPR);
+        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0, 0, 1, d.dinv, d.t, 1, h->Gs);
+        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0, 1, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
         k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
-        k_vlam_dual<T><<<PG, 128, 0, st>>>(d, rho, fin);
+        k_vlam_dual<T><<<PG, 128, 0, st>>>(d, fin);
         if (d.comp_mode) k_finish_components<<<d.ncomp, 256, 0, st>>>(d, 1, fa);
     } else {  // Algorithm 3; gamma/tau/kappa in sigma21's last block, stopping test in row_update's
         k_hsde_eta<T><<<GE, ETHREADS, 0, st>>>(d, h->Gs);
-        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.q, 0.0, d.g, h->TPR);
+        k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.q, 0.0, 0, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.kinv, d.g, d.hh, -1, h->TPRM);
         k_hsde_sigma11<<<GE, ETHREADS, 0, st>>>(d, h->Ga);
         k_hsde_sigma21<<<GR, RTHREADS, 0, st>>>(d, h->TPR, GE);
@@ -335,7 +337,8 @@ cudaError_t launch_iteration_any(cdsdp* h, int form, const cdsdp_opts& o, cudaSt
 bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
     return a.eps == b.eps && a.max_iter == b.max_iter && a.rho == b.rho && a.precision == b.precision &&
            a.jacobi_max_sweeps == b.jacobi_max_sweeps && a.warm_start == b.warm_start &&
-           a.component_stop == b.component_stop;
+           a.component_stop == b.component_stop && a.adaptive_rho == b.adaptive_rho && a.rho_mu == b.rho_mu &&
+           a.rho_nu == b.rho_nu;
 }
 
 void drop_graph(cdsdp* h) {
@@ -384,6 +387,7 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     if (o.max_iter > h->ws_max_iter) return CDSDP_ERR_ARG;
     if (o.warm_start < 0) return CDSDP_ERR_ARG;
     if (o.component_stop != 0 && o.component_stop != 1) return CDSDP_ERR_ARG;
+    if (o.adaptive_rho < 0 || !(o.rho_mu >= 1.0) || !(o.rho_nu >= 1.0)) return CDSDP_ERR_ARG;
     if (o.precision == CDSDP_FP64 && h->hp.max_clique > kMaxOrderF64) return CDSDP_ERR_UNSUPPORTED;
     return CDSDP_SOLVED;
 }
@@ -396,17 +400,16 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
     double* tmpE = d.t;  // scratch after the solve
     double* tmpM = d.g;
     const double* tau = d.scal + SC_TAU;
-    const double rho = h->g_opts.rho;
     if (X) {
         if (form == 0) k_scale_out<<<64, 256, 0, st>>>(NE, d.x, 1.0, nullptr, tmpE);
-        else if (form == 1) k_scale_out<<<64, 256, 0, st>>>(NE, d.x, -rho, nullptr, tmpE);
+        else if (form == 1) k_scale_rho<<<64, 256, 0, st>>>(d, NE, d.x, -1.0, 0, tmpE);
         else k_scale_out<<<64, 256, 0, st>>>(NE, d.x, 1.0, tau, tmpE);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(X, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
     if (y) {
-        if (form == 0) k_scale_out<<<8, 256, 0, st>>>(m, d.y, -rho, nullptr, tmpM);
+        if (form == 0) k_scale_rho<<<8, 256, 0, st>>>(d, m, d.y, -1.0, 1, tmpM);
         else if (form == 1) k_scale_out<<<8, 256, 0, st>>>(m, d.y, 1.0, nullptr, tmpM);
         else k_scale_out<<<8, 256, 0, st>>>(m, d.y, 1.0, tau, tmpM);
         CK(cudaGetLastError());
@@ -415,8 +418,8 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
     }
     if (Z) {
         const void* src = form == 0 ? d.ck1 : (form == 1 ? d.ck0 : d.ck1);  // lambda, z, v_z
-        if (fp64) k_scatter<double><<<h->GE, ETHREADS, 0, st>>>(d, (const double*)src, nullptr, 0.0, 1.0, 0.0, nullptr, tmpE, 0, h->Gs);
-        else k_scatter<float><<<h->GE, ETHREADS, 0, st>>>(d, (const float*)src, nullptr, 0.0, 1.0, 0.0, nullptr, tmpE, 0, h->Gs);
+        if (fp64) k_scatter<double><<<h->GE, ETHREADS, 0, st>>>(d, (const double*)src, nullptr, 0.0, 1.0, 0.0, 0, 0, nullptr, tmpE, 0, h->Gs);
+        else k_scatter<float><<<h->GE, ETHREADS, 0, st>>>(d, (const float*)src, nullptr, 0.0, 1.0, 0.0, 0, 0, nullptr, tmpE, 0, h->Gs);
         if (form == 2) k_scale_out<<<64, 256, 0, st>>>(NE, tmpE, 1.0, tau, tmpE);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(Z, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -482,7 +485,7 @@ int check_unrolled(cdsdp* h, const cdsdp_opts& o, int iters, int ckpt_every) {
 int run_segment(cdsdp* h, Dev dd, const cdsdp_opts& o, int len, cudaStream_t st) {
     const Dev saved = h->dev;
     h->dev = dd;
-    k_reset_ctl<<<1, 32, 0, st>>>(dd);
+    k_reset_ctl<<<1, 32, 0, st>>>(dd, o.rho);
     cudaError_t e = cudaGetLastError();
     for (int it = 0; it < len && e == cudaSuccess; ++it)
         e = launch_iteration_any(h, 0, o, st, 0, cudaGraphConditionalHandle{});
@@ -497,6 +500,7 @@ cdsdp_opts unrolled_opts(const cdsdp_opts* opts) {
     o.warm_start = 0;   // replays must repeat the forward bit for bit
     o.use_graph = 0;
     o.profile = 0;
+    o.adaptive_rho = 0;  // the reverse pass assumes one fixed rho
     return o;
 }
 
@@ -517,6 +521,9 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->warm_start = 16;
     o->profile = 0;
     o->component_stop = 1;
+    o->adaptive_rho = 0;
+    o->rho_mu = 2.0;
+    o->rho_nu = 10.0;
 }
 
 int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
@@ -650,7 +657,7 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     d.comp_mode = (h->hp.ncomp > 1 && form != 2 && o.component_stop) ? 1 : 0;
     // zero the state (clique vectors, iterates, partials, history)
     CK(cudaMemsetAsync(h->ws + h->L.const_end, 0, h->L.total - h->L.const_end, st));
-    k_init<<<1, 32, 0, st>>>(d, form);
+    k_init<<<1, 256, 0, st>>>(d, form, o.rho);
     CK(cudaGetLastError());
     h->last_profiled = false;
     if (o.profile) {

@@ -7,6 +7,9 @@ launch per phase (no CUDA graph, so every kernel shows up individually) and
 no early stop.  Workloads:
   banded        n=2000, half-bandwidth 10, m=500 (1990 cliques of order 11)
   block_arrow   l=5, d=10, h=5, m=30 (5 cliques of order 15)
+  batched       direct sum of `--count` uneven block-arrow SDPs (l in [10,100],
+                d in [10,40], h in [10,20], m in [50,400]; cliques of order
+                20..60); --count 256 is the full batch
 """
 from __future__ import annotations
 
@@ -21,7 +24,8 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="banded", choices=["banded", "block_arrow"])
+    ap.add_argument("--workload", default="banded", choices=["banded", "block_arrow", "batched"])
+    ap.add_argument("--count", type=int, default=256, help="problems in the batched workload")
     ap.add_argument("--form", default="primal", choices=["primal", "dual", "hsde"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--iters", type=int, default=20)
@@ -33,7 +37,10 @@ def main(argv=None):
     __graft_entry__.build_library()
     from paper_1707_05058_gb300 import cdsdp, workloads
 
-    prob = workloads.workload(1 if args.workload == "banded" else 0)
+    if args.workload == "batched":
+        prob = workloads.direct_sum(workloads.block_arrow_batch(args.count, 3707))
+    else:
+        prob = workloads.workload(1 if args.workload == "banded" else 0)
     P = cdsdp.Problem(prob).bind(max_iter=args.iters)
     out = P.solve(args.form, eps=0.0, max_iter=args.iters, precision=args.precision, use_graph=0,
                   check_every=args.iters, outputs=False)

@@ -34,10 +34,10 @@ def _parts():
 _CACHE = {}
 
 
-def _oracle(prob, form, eps, max_iter):
-    key = (prob.name, form, eps, max_iter)
+def _oracle(prob, form, eps, max_iter, adapt_every=0):
+    key = (prob.name, form, eps, max_iter, adapt_every)
     if key not in _CACHE:
-        _CACHE[key] = admm.solve(prob, form, eps=eps, max_iter=max_iter)
+        _CACHE[key] = admm.solve(prob, form, eps=eps, max_iter=max_iter, adapt_every=adapt_every)
     return _CACHE[key]
 
 
@@ -46,16 +46,16 @@ def _close(a, b, tol, what):
     assert np.abs(a - b).max() <= tol * scale, what
 
 
-def _check_components(P, out, parts, form, eps, max_iter, rows_perm=None):
+def _check_components(P, out, parts, form, eps, max_iter, rows_perm=None, adapt_every=0):
     it, st, res = P.component_results()
     r, c = P.pattern()
     vo = mo = 0
     for j, q in enumerate(parts):
-        dp, ref = _oracle(q, form, eps, max_iter)
+        dp, ref = _oracle(q, form, eps, max_iter, adapt_every)
         assert st[j] == ref.status, j
         assert abs(int(it[j]) - ref.iters) <= 1, (j, it[j], ref.iters)
         if it[j] == ref.iters:
-            np.testing.assert_allclose(res[j, :2], ref.hist[ref.iters - 1, :2], rtol=1e-6, atol=1e-12)
+            np.testing.assert_allclose(res[j, :3], ref.hist[ref.iters - 1, :3], rtol=1e-6, atol=1e-12)
         mask = (c >= vo) & (c < vo + q.n)
         rows = np.arange(mo, mo + q.m) if rows_perm is None else rows_perm[mo:mo + q.m]
         _close(out["X"][mask], dp.lower_values(ref.X), 1e-7, f"X[{j}]")
@@ -80,6 +80,16 @@ def test_direct_sum_per_component_fp64(lib, torch_cuda, form, use_graph):
     h = out["hist"]
     assert h[0, 6] == len(parts) and h[-1, 6] == 0
     assert np.all(np.diff(h[:, 6]) <= 0)
+
+
+@pytest.mark.parametrize("form", ["primal", "dual"])
+def test_direct_sum_per_component_adaptive_rho(lib, torch_cuda, form):
+    """Adaptive penalty per component (every 3 iterations): each summand's
+    penalty path and result equal the oracle's run of that summand alone."""
+    parts = _parts()
+    P = lib.Problem(W.direct_sum(parts)).bind(max_iter=5000)
+    out = P.solve(form, eps=1e-5, max_iter=5000, precision="fp64", adaptive_rho=3)
+    _check_components(P, out, parts, form, 1e-5, 5000, adapt_every=3)
 
 
 def test_direct_sum_shuffled_constraints(lib, torch_cuda):

@@ -344,3 +344,43 @@ def test_repeat_solves_identical(lib, torch_cuda):
     assert a["iters"] == b["iters"]
     np.testing.assert_array_equal(a["X"], b["X"])
     np.testing.assert_array_equal(a["hist"], b["hist"])
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+@pytest.mark.parametrize("form", ["primal", "dual"])
+def test_adaptive_rho_fp64_matches_oracle(lib, torch_cuda, form, use_graph):
+    """Adaptive penalty (Section 7.1.2) applied every 5 iterations: the FP64 GPU
+    run follows the oracle's, penalty history (column 2) included, to the
+    same iteration count and solution."""
+    prob = W.banded(60, 4, 15, seed=11, density=0.3)
+    dp = admm.decompose(prob)
+    fn = admm.primal_admm if form == "primal" else admm.dual_admm
+    ref = fn(dp, eps=1e-6, max_iter=5000, adapt_every=5)
+    P = lib.Problem(prob).bind(max_iter=5000)
+    out = P.solve(form, eps=1e-6, max_iter=5000, precision="fp64", adaptive_rho=5, use_graph=use_graph,
+                  check_every=9)
+    assert len(set(ref.hist[:, 2])) > 1
+    _assert_trajectory(dp, ref, out, k=ref.iters)
+    np.testing.assert_array_equal(out["hist"][:min(out["iters"], ref.iters), 2],
+                                  ref.hist[:min(out["iters"], ref.iters), 2])
+
+
+def test_banded_full_size_adaptive_rho(lib, torch_cuda):
+    """Banded n=2000, w=10, m=500 with the adaptive penalty applied every
+    iteration: both precisions stop at eps=1e-4 with KKT residuals of
+    (X, y, Z) <= 5e-4 and objectives within 1e-4 of each other, and the FP64
+    run's first 40 iterates equal the oracle's."""
+    prob = W.workload(1)
+    dp = admm.decompose(prob)
+    ref = admm.primal_admm(dp, eps=0.0, max_iter=40, adapt_every=1)
+    P = lib.Problem(prob).bind(max_iter=40000)
+    out = P.solve("primal", eps=0.0, max_iter=40, precision="fp64", adaptive_rho=1)
+    np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-9, atol=1e-12)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        out = P.solve("primal", eps=1e-4, max_iter=40000, precision=prec, adaptive_rho=1)
+        assert out["status"] == 0
+        rp, rd, gap = _kkt(dp, out)
+        assert rp <= 5e-4 and rd <= 5e-4
+        res[prec] = float(dp.c @ _full(dp, out["X"]))
+    assert abs(res["fp32"] - res["fp64"]) <= 1e-4 * abs(res["fp64"])
