@@ -1,16 +1,21 @@
 """Benchmark: decomposed ADMM (Algorithm 1) on the banded SDP workload
 (n=2000, half-bandwidth 10, m=500; 1990 cliques of order 11) on one GB300.
 
-A step is one full solve to eps = 1e-4 from a cold start (every §-step of the
+A step is one full solve to eps = 1e-4 from a cold start (every step of the
 iteration: scatter, affine projection with the cached inverse, clique gather,
-batched PSD projection, multiplier update, stopping reductions).
+batched PSD projection, multiplier update, stopping reductions), with the
+adaptive penalty of Section 7.1.2 applied every iteration (mu = 2, nu = 10,
+rho starting at 1).
 
   value     ADMM iterations/s of the FP32-projection form, whole solve as one
             CUDA graph (device-side while loop), inputs resident in HBM,
             L2 flushed (256 MiB write) before every timed step
   e2e       the same metric through the public API from host arrays:
             host preprocessing, one H2D upload, solve, D2H of X, y, Z
-  fp64_plain  FP64 everywhere, one launch per phase, no graph
+  fp64_plain  FP64 everywhere, cold Jacobi, one launch per phase, no graph
+  fixed_rho   both forms again with rho = 1 throughout
+  batched   256 independent uneven block-arrow SDPs (cliques of order
+            20..60) solved as one direct sum, each stopping on its own test
   roofline  the batched projection kernel (FP32 ALU bound), launch durations
             from CUDA events in a profiled solve on the solve's stream
   cpu_baseline  the FP64 oracle on a bounded sample (host cores, 1 thread)
@@ -92,7 +97,7 @@ def _cpu_baseline(iters, timeout=600):
         "from paper_1707_05058_gb300 import workloads as W\n"
         "dp=admm.decompose(W.workload(1))\n"
         "t=time.perf_counter()\n"
-        f"r=admm.primal_admm(dp,eps=0.0,max_iter={iters})\n"
+        f"r=admm.primal_admm(dp,eps=0.0,max_iter={iters},adapt_every=1)\n"
         "dt=time.perf_counter()-t\n"
         "print(json.dumps({'iters':r.iters,'sec':dt}))\n")
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
@@ -118,11 +123,63 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "primal", "sample": f"{iters} ADMM iterations per step"},
+            "config": {"workload": WORKLOAD, "form": "primal", "rho": "adaptive every iteration",
+                       "sample": f"{iters} ADMM iterations per step"},
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
                              "sample": f"{iters} iterations of the FP64 oracle (Algorithm 1) on {WORKLOAD} per step, 1 thread"},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _batched(cdsdp, workloads, torch, flush, stream):
+    """256 uneven block-arrow SDPs (l in [10,100], d in [10,40], h in [10,20],
+    m in [50,400]; A_i with 5% density on the pattern) as one direct sum, each
+    component stopping and freezing on its own test; FP32 graph with the
+    adaptive penalty to eps = 1e-4, then per-iteration times of the first 50
+    iterations (every component active) for the FP32 graph form, the profiled
+    projection launches, and the plain FP64 form."""
+    import numpy as np
+    t0 = time.perf_counter()
+    prob = workloads.direct_sum(workloads.workload(2))
+    t1 = time.perf_counter()
+    P = cdsdp.Problem(prob)
+    t2 = time.perf_counter()
+    P.bind(max_iter=10000)
+    info = P.info
+
+    def timed(**kw):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = P.solve("primal", outputs=False, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    kw = dict(eps=1e-4, max_iter=10000, precision="fp32", use_graph=1, adaptive_rho=1)
+    P.solve("primal", outputs=False, **kw)  # warm-up (graph build)
+    ms, out = timed(**kw)
+    it, st, _ = P.component_results()
+    ms50, _ = timed(eps=0.0, max_iter=50, precision="fp32", use_graph=1, adaptive_rho=1)
+    P.solve("primal", outputs=False, eps=0.0, max_iter=20, precision="fp32", profile=1, adaptive_rho=1)
+    proj_ms, launches, iter_ms = P.profile()
+    ms64, _ = timed(eps=0.0, max_iter=10, precision="fp64", use_graph=0, check_every=10, warm_start=0, adaptive_rho=1)
+    sizes = np.diff(P.cliques()[0]).astype(np.float64)
+    flops = float(np.sum(10.0 * sizes ** 3))
+    gflops = flops / (proj_ms / launches / 1e3) / 1e9
+    return {"workload": "256 block-arrow SDPs, direct sum", "n": int(info["n"]), "m": int(info["m"]),
+            "cliques": int(info["p"]), "clique_order_max": int(info["max_clique"]), "components": int(info["ncomp"]),
+            "nnz_A": int(info["nnz_A"]), "generate_s": t1 - t0, "setup_s": t2 - t1,
+            "time_to_eps_ms": ms, "status": int(out["status"]), "iters_to_eps_max": int(out["iters"]),
+            "component_iters": {"min": int(it.min()), "median": int(np.median(it)), "max": int(it.max()),
+                                "sum": int(it.sum())},
+            "components_solved": int(np.sum(st == 0)),
+            "fp32_graph_ms_per_iter_all_active": ms50 / 50,
+            "fp64_plain_ms_per_iter_all_active": ms64 / 10,
+            "per_iter_speedup_fp32_graph_vs_fp64_plain": (ms64 / 10) / (ms50 / 50),
+            "clique_proj_gflops": gflops, "proj_ms_per_iter": proj_ms / launches,
+            "proj_flops_per_iter_nominal": flops}
 
 
 def main():
@@ -132,6 +189,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-SDP batched workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -184,10 +242,11 @@ def main():
             assert out["status"] == 0, out
         return ms, its
 
+    ADAPT = dict(adaptive_rho=1)
     # ---- FP32-projection form, graph (the headline value)
     barrier()
     clk = _clock_sampler(torch.cuda.current_device()) if rank == 0 else None
-    ms32, it32 = timed_solves(args.steps, args.warmup, precision="fp32", use_graph=1)
+    ms32, it32 = timed_solves(args.steps, args.warmup, precision="fp32", use_graph=1, **ADAPT)
     barrier()
     clocks = _clock_summary(clk) if rank == 0 else None
     tot_ms = torch.tensor([sum(ms32)], dtype=torch.float64, device="cuda")
@@ -199,10 +258,13 @@ def main():
     time_to_eps_ms = statistics.median(ms32)
 
     # ---- plain FP64 form (FP64 everywhere, one launch per phase, no graph)
-    ms64, it64 = timed_solves(1, 0, precision="fp64", use_graph=0, check_every=10, warm_start=0)
+    ms64, it64 = timed_solves(1, 0, precision="fp64", use_graph=0, check_every=10, warm_start=0, **ADAPT)
+    # ---- both forms with the penalty fixed at rho = 1
+    ms32f, it32f = timed_solves(1, 1, precision="fp32", use_graph=1)
+    ms64f, it64f = timed_solves(1, 0, precision="fp64", use_graph=0, check_every=10, warm_start=0)
 
     # ---- profiled FP32 solve: per-launch projection time from CUDA events
-    P.solve("primal", outputs=False, eps=1e-4, max_iter=max_iter, precision="fp32", profile=1, check_every=50)
+    P.solve("primal", outputs=False, eps=1e-4, max_iter=max_iter, precision="fp32", profile=1, check_every=50, **ADAPT)
     proj_ms, proj_launches, iter_ms = P.profile()
     sizes = np.diff(P.cliques()[0])
     flops_per_launch = float(np.sum(10.0 * sizes.astype(np.float64) ** 3))   # nominal 10 s^3 per clique
@@ -219,7 +281,7 @@ def main():
         t = time.perf_counter()
         Q = cdsdp.Problem(prob)
         Q.bind(max_iter=max_iter)
-        out = Q.solve("primal", eps=1e-4, max_iter=max_iter, precision="fp32", use_graph=1)
+        out = Q.solve("primal", eps=1e-4, max_iter=max_iter, precision="fp32", use_graph=1, **ADAPT)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
         if s > 0:  # the first call also builds the graph
@@ -230,6 +292,9 @@ def main():
         d2h = (2 * nz + int(info["m"])) * 8 + out["iters"] * 8 * 8
         del Q
     e2e_value = sum(e2e_it) / (sum(e2e_ms) / 1e3)
+    del P
+
+    batched = None if args.no_batched else _batched(cdsdp, workloads, torch, flush, stream)
 
     line = None
     if rank == 0:
@@ -257,6 +322,14 @@ def main():
                            "iters_to_eps": int(statistics.median(it64)),
                            "form": "float64 everywhere, cold Jacobi every iteration, one launch per phase, no graph"},
             "speedup_time_to_eps_fp32_graph_vs_fp64_plain": statistics.median(ms64) / time_to_eps_ms,
+            "rho": "adaptive (Section 7.1.2), every iteration, mu 2, nu 10, from rho = 1",
+            "fixed_rho": {"rho": 1.0,
+                          "fp32_graph": {"time_to_eps_ms": ms32f[0], "iters_to_eps": it32f[0],
+                                         "iters_per_s": it32f[0] / (ms32f[0] / 1e3)},
+                          "fp64_plain": {"time_to_eps_ms": ms64f[0], "iters_to_eps": it64f[0],
+                                         "iters_per_s": it64f[0] / (ms64f[0] / 1e3)},
+                          "speedup_time_to_eps": ms64f[0] / ms32f[0]},
+            "batched": batched,
             "clique_proj_gflops": gflops,
             "setup_ms": setup_s * 1e3,
             "roofline": {"bound": "alu", "achieved": gflops / 1e3, "peak": peak_fp32, "unit": "TFLOP/s",
