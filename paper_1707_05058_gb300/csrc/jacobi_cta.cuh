@@ -2,15 +2,24 @@
 // (CTA) per clique.  Same method as jacobi.cuh (two-sided Jacobi in the
 // Brent-Luk parallel ordering, 2x2 symmetric Schur step in Rutishauser's form,
 // warm start from the clique's previous eigenvectors, stagnation stop at the
-// rounding-noise floor), laid out for a CTA:
-//  * A lives in two shared-memory buffers (S x S+1); each round every thread
-//    takes pair-blocks (I, J), I >= J, applies J_I^T B J_J and stores them at
-//    their positions permuted by sigma in the other buffer;
-//  * V (S x S+1) lives in shared memory and is rotated in place at the
-//    round's logical column pair (L[2k], L[2k+1]); L, the logical index held by
-//    each storage position, follows sigma (two small buffers);
+// rounding-noise floor), laid out for a CTA.
+//
+// Orders up to 64 (CTAJacobiMid, padded orders in steps of 4):
+//  * A (lower triangle) and V live in shared memory, each double-buffered;
+//    V is kept in the same storage order as A, so a round is one uniform pass
+//    over pair-blocks: lower blocks (I, J) of A get J_I^T B J_J, blocks of V
+//    get the column rotation B J_J, and every result is stored at its
+//    position permuted by sigma in the other buffer;
+//  * each thread owns a fixed list of pair-blocks whose source and permuted
+//    destination offsets it computes once per launch (registers);
+//  * V^T W V (warm start) and V max(Lambda, 0) V^T are 4x4-tiled products;
 //  * two barriers per round (rotations ready; buffers swapped).
+// Orders 65..128 (CTAJacobi): A double-buffered as above, V single-buffered
+// and rotated in place at the round's logical column pair (L[2k], L[2k+1]),
+// L following sigma.
 #pragma once
+
+#include <type_traits>
 
 #include "jacobi.cuh"
 
@@ -217,6 +226,289 @@ struct CTAJacobi {
     }
 };
 
+// Vector views of shared memory (the dynamic buffer is only 16-byte aligned,
+// so a 4-vector of doubles is read as two 16-byte halves).
+template <typename T> struct alignas(2 * sizeof(T)) Vec2 { T x, y; };
+template <typename T> struct alignas(16) Vec4 { T x, y, z, w; };
+
+template <typename T, int S>
+struct CTAJacobiMid {
+    static_assert(S % 4 == 0 && S <= 64, "padded orders 36..64 in steps of 4");
+    using RR = RoundRobin<S>;
+    using T2 = Vec2<T>;
+    using T4 = Vec4<T>;
+    static constexpr int K = S / 2;
+    static constexpr int R = S - 1;
+    static constexpr int LDA = S + 4;          // rows stay 16-byte aligned
+    static constexpr int BUF = S * LDA;
+    static constexpr int NB = K * (K + 1) / 2; // lower pair-blocks of A
+    static constexpr int NBLK = NB + K * K;    // plus the pair-blocks of V
+    static constexpr int NPT = (NBLK + kCtaThreads - 1) / kCtaThreads;
+    static constexpr int S4 = S / 4;
+    static constexpr size_t bytes = ((4 * (size_t)BUF + 3 * K + 32 + S) * sizeof(T) + 15) & ~size_t(15);
+
+    T* X;    // A, current
+    T* Y;    // A, next
+    T* V;    // eigenvectors (storage order), current
+    T* Vn;   // next
+    T* cs;   // [K] (cos, sin) pairs
+    T* ta;   // [K] t * a_pq
+    T* red;  // [32] reduction scratch
+    T* lam;  // [S] max(lambda, 0)
+    // this thread's pair-blocks: source offset, four destination offsets, and
+    // kind | I << 2 | J << 10 (kind 1: diagonal block of A, 2: off-diagonal
+    // block of A, 3: block of V, 0: none)
+    int b_src[NPT], b_d0[NPT], b_d1[NPT], b_d2[NPT], b_d3[NPT], b_meta[NPT];
+
+    __device__ __forceinline__ static int lower(int r, int c) { return r >= c ? r * LDA + c : c * LDA + r; }
+
+    __device__ __forceinline__ void bind(unsigned char* base) {
+        X = reinterpret_cast<T*>(base);
+        Y = X + BUF;
+        V = Y + BUF;
+        Vn = V + BUF;
+        cs = Vn + BUF;
+        ta = cs + 2 * K;
+        red = ta + K;
+        lam = red + 32;
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const int b = threadIdx.x + j * kCtaThreads;
+            int kind = 0, I = 0, J = 0;
+            if (b < K) {
+                kind = 1;
+                I = J = b;
+            } else if (b < NB) {
+                int o = b - K;
+                I = 1;
+                while (o >= I) { o -= I; ++I; }
+                J = o;
+                kind = 2;
+            } else if (b < NBLK) {
+                const int v = b - NB;
+                I = v / K;
+                J = v - I * K;
+                kind = 3;
+            }
+            const int r0 = 2 * I, r1 = r0 + 1, c0 = 2 * J, c1 = c0 + 1;
+            b_src[j] = r0 * LDA + c0;
+            b_meta[j] = kind | (I << 2) | (J << 10);
+            if (kind == 3) {  // rows of V stay, columns move with sigma
+                b_d0[j] = r0 * LDA + RR::sigma(c0);
+                b_d1[j] = b_d0[j] + LDA;
+                b_d2[j] = r0 * LDA + RR::sigma(c1);
+                b_d3[j] = b_d2[j] + LDA;
+            } else {
+                const int sr0 = RR::sigma(r0), sr1 = RR::sigma(r1), sc0 = RR::sigma(c0), sc1 = RR::sigma(c1);
+                b_d0[j] = lower(sr0, sc0);
+                b_d1[j] = lower(sr1, sc0);
+                b_d2[j] = lower(sr0, sc1);
+                b_d3[j] = lower(sr1, sc1);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void clear() {
+        for (int i = threadIdx.x; i < BUF; i += blockDim.x) X[i] = T(0);
+        __syncthreads();
+    }
+    __device__ __forceinline__ void put(int a, int b, T w) {
+        X[a * LDA + b] = w;
+        X[b * LDA + a] = w;
+    }
+
+    // block-wide max of |off-diagonal| of the lower triangle of A
+    __device__ T off_max() {
+        T m = T(0);
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const int kind = b_meta[j] & 3, src = b_src[j];
+            if (kind == 1) {
+                m = fmax(m, fabs(X[src + LDA]));
+            } else if (kind == 2) {
+                m = fmax(fmax(m, fabs(X[src])), fabs(X[src + 1]));
+                m = fmax(fmax(m, fabs(X[src + LDA])), fabs(X[src + LDA + 1]));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        __syncthreads();
+        if (lane == 0) red[warp] = m;
+        __syncthreads();
+        T r = T(0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+        __syncthreads();
+        return r;
+    }
+
+    __device__ void round(T tol) {
+        const int tid = threadIdx.x;
+        if (tid < K) {  // rotation of pair tid (Rutishauser form)
+            const T app = X[(2 * tid) * LDA + 2 * tid], aqq = X[(2 * tid + 1) * LDA + 2 * tid + 1];
+            const T apq = X[(2 * tid + 1) * LDA + 2 * tid];
+            T c = T(1), sn = T(0), tq = T(0);
+            if (fabs(apq) > tol) {
+                const T zeta = T(0.5) * (aqq - app);
+                const T r2 = zeta * zeta + apq * apq;
+                const T r = r2 * rsqrt_t<T>(r2);
+                const T tt = copysign(T(1), zeta) * div_t<T>(apq, fabs(zeta) + r);
+                c = rsqrt_t<T>(T(1) + tt * tt);
+                sn = tt * c;
+                tq = tt * apq;
+            }
+            reinterpret_cast<T2*>(cs)[tid] = T2{c, sn};
+            ta[tid] = tq;
+        }
+        __syncthreads();
+        const T2* rot = reinterpret_cast<const T2*>(cs);
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const int meta = b_meta[j], kind = meta & 3;
+            if (kind == 0) continue;
+            const int I = (meta >> 2) & 255, J = meta >> 10, src = b_src[j];
+            if (kind == 3) {
+                const T2 v0 = *reinterpret_cast<const T2*>(V + src);
+                const T2 v1 = *reinterpret_cast<const T2*>(V + src + LDA);
+                const T2 r = rot[J];
+                Vn[b_d0[j]] = r.x * v0.x - r.y * v0.y;
+                Vn[b_d2[j]] = r.y * v0.x + r.x * v0.y;
+                Vn[b_d1[j]] = r.x * v1.x - r.y * v1.y;
+                Vn[b_d3[j]] = r.y * v1.x + r.x * v1.y;
+            } else if (kind == 1) {
+                const T t = ta[I];
+                const bool rotated = t != T(0) || rot[I].y != T(0);
+                const T b00 = X[src], b10 = X[src + LDA], b11 = X[src + LDA + 1];
+                Y[b_d0[j]] = b00 - t;
+                Y[b_d1[j]] = rotated ? T(0) : b10;
+                Y[b_d3[j]] = b11 + t;
+            } else {
+                const T2 ra = *reinterpret_cast<const T2*>(X + src);        // b00, b01
+                const T2 rb = *reinterpret_cast<const T2*>(X + src + LDA);  // b10, b11
+                const T2 ri = rot[I], rj = rot[J];
+                const T q00 = ri.x * ra.x - ri.y * rb.x, q10 = ri.y * ra.x + ri.x * rb.x;
+                const T q01 = ri.x * ra.y - ri.y * rb.y, q11 = ri.y * ra.y + ri.x * rb.y;
+                Y[b_d0[j]] = rj.x * q00 - rj.y * q01;
+                Y[b_d2[j]] = rj.y * q00 + rj.x * q01;
+                Y[b_d1[j]] = rj.x * q10 - rj.y * q11;
+                Y[b_d3[j]] = rj.y * q10 + rj.x * q11;
+            }
+        }
+        __syncthreads();
+        T* t = X; X = Y; Y = t;
+        t = V; V = Vn; Vn = t;
+    }
+
+    // V <- identity (cold) or keep the loaded basis (warm), then sweep; each
+    // sweep returns the storage order to the identity.
+    __device__ int run(T tol, int max_sweeps, bool v_preset) {
+        if (!v_preset)
+            for (int i = threadIdx.x; i < BUF; i += blockDim.x) V[i] = ((i / LDA) == (i % LDA)) ? T(1) : T(0);
+        __syncthreads();
+        const T noise = tol * T(2 * S);
+        T prev = T(3.0e38);
+        int sw = 0;
+        while (sw < max_sweeps) {
+            const T off = off_max();
+            if (off <= tol) break;
+            if (off <= noise && off > T(0.5) * prev) break;
+            prev = off;
+            ++sw;
+            for (int r = 0; r < R; ++r) round(tol);
+        }
+        return sw;
+    }
+
+    // C = A^T B over 4x4 output tiles (A, B, C: S x S with leading dimension LDA).
+    __device__ void atb(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C) const {
+        for (int tile = threadIdx.x; tile < S4 * S4; tile += blockDim.x) {
+            const int tr = tile / S4, tc = tile - tr * S4;
+            T acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+#pragma unroll 4
+            for (int i = 0; i < S; ++i) {
+                const T4 a = *reinterpret_cast<const T4*>(A + i * LDA + 4 * tr);
+                const T4 b = *reinterpret_cast<const T4*>(B + i * LDA + 4 * tc);
+                const T av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                *reinterpret_cast<T4*>(C + (4 * tr + u) * LDA + 4 * tc) = T4{acc[u][0], acc[u][1], acc[u][2], acc[u][3]};
+        }
+    }
+
+    // A <- V^T W V (X holds the symmetric W in both triangles, V the basis).
+    __device__ void rotate_into_basis() {
+        atb(X, V, Y);  // Y = W V (W symmetric)
+        __syncthreads();
+        atb(V, Y, X);  // X = V^T Y
+        __syncthreads();
+    }
+
+    __device__ void load_basis(const T* __restrict__ Vc, int s) {
+        for (int i = threadIdx.x; i < BUF; i += blockDim.x) {
+            const int r = i / LDA, c = i - r * LDA;
+            V[i] = (r < s && c < s) ? Vc[r * s + c] : (r == c ? T(1) : T(0));
+        }
+        __syncthreads();
+    }
+    __device__ void store_basis(T* __restrict__ Vc, int s) const {
+        for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+            const int r = i / s, c = i - r * s;
+            Vc[i] = V[r * LDA + c];
+        }
+    }
+
+    // X <- V max(Lambda, 0) V^T (lower 4x4 tiles), Lambda on X's diagonal.
+    __device__ void prepare_rebuild() {
+        for (int i = threadIdx.x; i < S; i += blockDim.x) {
+            const T l = X[i * LDA + i];
+            lam[i] = l > T(0) ? l : T(0);
+        }
+        for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {  // Y = V^T
+            const int r = idx / S, c = idx - r * S;
+            Y[c * LDA + r] = V[r * LDA + c];
+        }
+        __syncthreads();
+        for (int tile = threadIdx.x; tile < S4 * (S4 + 1) / 2; tile += blockDim.x) {
+            int tr = 0, o = tile;
+            while (o > tr) { o -= tr + 1; ++tr; }
+            const int tc = o;  // tr >= tc
+            T acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+#pragma unroll 4
+            for (int c = 0; c < S; ++c) {
+                const T l = lam[c];
+                const T4 a = *reinterpret_cast<const T4*>(Y + c * LDA + 4 * tr);
+                const T4 b = *reinterpret_cast<const T4*>(Y + c * LDA + 4 * tc);
+                const T av[4] = {l * a.x, l * a.y, l * a.z, l * a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                *reinterpret_cast<T4*>(X + (4 * tr + u) * LDA + 4 * tc) = T4{acc[u][0], acc[u][1], acc[u][2], acc[u][3]};
+        }
+        __syncthreads();
+    }
+    __device__ __forceinline__ T rebuild(int a, int b, int) const { return X[a * LDA + b]; }
+};
+
+template <typename T, int S>
+using CTASolver = typename std::conditional<(S <= 64), CTAJacobiMid<T, S>, CTAJacobi<T, S>>::type;
+
 template <int NV>
 __device__ __forceinline__ void cta_sum(double (&v)[NV], double* sh) {
     block_sum<NV>(v, sh);  // valid in thread 0
@@ -229,7 +521,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* _
                                                               FinishArgs fa, const int* __restrict__ off_arr,
                                                               const int* __restrict__ size_arr,
                                                               const T* __restrict__ Win, T* Xout) {
-    using J = CTAJacobi<T, S>;
+    using J = CTASolver<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double shr[32 * 6];
     if (FORM != 3 && stopped(d)) return;

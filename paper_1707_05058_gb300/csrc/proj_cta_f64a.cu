@@ -1,0 +1,5 @@
+// double thread-block-per-clique projection kernels, padded orders 36, 40, 44, 48.
+#define CTA_T double
+#define CTA_SUFFIX(name) name##_f64a
+#define CTA_SIZES(X) X(36) X(40) X(44) X(48)
+#include "proj_cta_impl.cuh"

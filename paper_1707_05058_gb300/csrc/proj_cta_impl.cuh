@@ -1,0 +1,71 @@
+// CTA-per-clique projection kernels (orders 33..128 in float32, 33..64 in
+// float64): instantiations and launchers.  Included once per translation unit
+// with CTA_T (element type), CTA_SUFFIX (name suffix) and CTA_SIZES (X-macro
+// list of the padded orders instantiated there) defined.
+#include <algorithm>
+
+#include "jacobi_cta.cuh"
+#include "proj_launch.h"
+
+namespace cdsdp_dev {
+namespace {
+
+template <typename T, int S, int FORM>
+cudaError_t launch_cta(const Dev& d, const int* list, int nlist, const ProjArgs& pa_in, const FinishArgs& fa,
+                       const int* off, const int* size, const void* W, void* X, int max_sweeps, cudaStream_t st) {
+    if (nlist <= 0) return cudaSuccess;
+    const size_t smem = CTASolver<T, S>::bytes;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_project_cta<T, S, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    ProjArgs pa = pa_in;
+    pa.tolrel = jacobi_tolrel(S, sizeof(T) == 4);
+    if (FORM == 3) pa.max_sweeps = max_sweeps;
+    k_project_cta<T, S, FORM><<<proj_cta_grid(nlist), kCtaThreads, smem, st>>>(d, list, nlist, pa, fa, off, size,
+                                                                               (const T*)W, (T*)X);
+    return cudaGetLastError();
+}
+
+template <typename T, int S>
+cudaError_t launch_cta_form(int form, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
+                            const FinishArgs& fa, cudaStream_t st) {
+    switch (form) {
+        case 0: return launch_cta<T, S, 0>(d, list, nlist, pa, fa, nullptr, nullptr, nullptr, nullptr, 0, st);
+        case 1: return launch_cta<T, S, 1>(d, list, nlist, pa, fa, nullptr, nullptr, nullptr, nullptr, 0, st);
+        default: return launch_cta<T, S, 2>(d, list, nlist, pa, fa, nullptr, nullptr, nullptr, nullptr, 0, st);
+    }
+}
+
+}  // namespace
+
+cudaError_t CTA_SUFFIX(launch_proj_cta)(int S, int form, const Dev& d, const int* list, int nlist,
+                                        const ProjArgs& pa, const FinishArgs& fa, cudaStream_t st) {
+    switch (S) {
+#define CTA_CASE(N) \
+    case N: return launch_cta_form<CTA_T, N>(form, d, list, nlist, pa, fa, st);
+        CTA_SIZES(CTA_CASE)
+#undef CTA_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t CTA_SUFFIX(launch_proj_cta_standalone)(int S, int p, const int* off, const int* size, const void* W,
+                                                   void* X, int max_sweeps, cudaStream_t st) {
+    Dev d{};
+    ProjArgs pa{};
+    FinishArgs fa{};
+    pa.restart = 1;
+    switch (S) {
+#define CTA_CASE(N) \
+    case N: return launch_cta<CTA_T, N, 3>(d, nullptr, p, pa, fa, off, size, W, X, max_sweeps, st);
+        CTA_SIZES(CTA_CASE)
+#undef CTA_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cdsdp_dev

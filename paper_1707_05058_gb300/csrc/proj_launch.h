@@ -1,5 +1,5 @@
-// Launchers of the batched projection kernels, one translation unit per
-// precision (proj_f32.cu, proj_f64.cu) so the two compile in parallel.
+// Launchers of the batched projection kernels, spread over several
+// translation units (by precision and order) so that they compile in parallel.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,8 +10,8 @@ namespace cdsdp_dev {
 
 // Padded orders of the projection kernels: one warp per clique up to 32, one
 // thread block per clique above (float32 up to 128, float64 up to 64).
-constexpr int kProjClasses[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32, 48, 64, 96, 128};
-constexpr int kNumProjClasses = 16;
+constexpr int kProjClasses[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32, 36, 40, 44, 48, 52, 56, 60, 64, 96, 128};
+constexpr int kNumProjClasses = 22;
 constexpr int kMaxWarpOrder = 32;
 constexpr int kMaxOrderF32 = 128;
 constexpr int kMaxOrderF64 = 64;
@@ -57,10 +57,40 @@ CDSDP_DECLARE_PROJ(f64_small)
 CDSDP_DECLARE_PROJ(f64_large)
 #undef CDSDP_DECLARE_PROJ
 
-cudaError_t launch_proj_cta(bool fp32, int form, int cls, const Dev& d, const int* list, int nlist,
-                            const ProjArgs& pa, const FinishArgs& fa, cudaStream_t st);
-cudaError_t launch_proj_cta_standalone(bool fp32, int cls, int p, const int* off, const int* size, const void* W,
-                                       void* X, int max_sweeps, cudaStream_t st);
+// Thread-block-per-clique kernels, instantiated in proj_cta_{f32a,f32b,f32c,f64a,f64b}.cu
+// (padded orders 36..48, 52..64, 96..128 in float; 36..48, 52..64 in double).
+#define CDSDP_DECLARE_CTA(SUF)                                                                                  \
+    cudaError_t launch_proj_cta_##SUF(int S, int form, const Dev& d, const int* list, int nlist,               \
+                                      const ProjArgs& pa, const FinishArgs& fa, cudaStream_t st);                \
+    cudaError_t launch_proj_cta_standalone_##SUF(int S, int p, const int* off, const int* size, const void* W, \
+                                                 void* X, int max_sweeps, cudaStream_t st);
+CDSDP_DECLARE_CTA(f32a)
+CDSDP_DECLARE_CTA(f32b)
+CDSDP_DECLARE_CTA(f32c)
+CDSDP_DECLARE_CTA(f64a)
+CDSDP_DECLARE_CTA(f64b)
+#undef CDSDP_DECLARE_CTA
+
+inline cudaError_t launch_proj_cta(bool fp32, int form, int cls, const Dev& d, const int* list, int nlist,
+                                   const ProjArgs& pa, const FinishArgs& fa, cudaStream_t st) {
+    const int S = kProjClasses[cls];
+    if (fp32)
+        return S <= 48 ? launch_proj_cta_f32a(S, form, d, list, nlist, pa, fa, st)
+                       : (S <= 64 ? launch_proj_cta_f32b(S, form, d, list, nlist, pa, fa, st)
+                                  : launch_proj_cta_f32c(S, form, d, list, nlist, pa, fa, st));
+    return S <= 48 ? launch_proj_cta_f64a(S, form, d, list, nlist, pa, fa, st)
+                   : launch_proj_cta_f64b(S, form, d, list, nlist, pa, fa, st);
+}
+inline cudaError_t launch_proj_cta_standalone(bool fp32, int cls, int p, const int* off, const int* size,
+                                              const void* W, void* X, int max_sweeps, cudaStream_t st) {
+    const int S = kProjClasses[cls];
+    if (fp32)
+        return S <= 48 ? launch_proj_cta_standalone_f32a(S, p, off, size, W, X, max_sweeps, st)
+                       : (S <= 64 ? launch_proj_cta_standalone_f32b(S, p, off, size, W, X, max_sweeps, st)
+                                  : launch_proj_cta_standalone_f32c(S, p, off, size, W, X, max_sweeps, st));
+    return S <= 48 ? launch_proj_cta_standalone_f64a(S, p, off, size, W, X, max_sweeps, st)
+                   : launch_proj_cta_standalone_f64b(S, p, off, size, W, X, max_sweeps, st);
+}
 
 inline cudaError_t launch_proj_f32(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,
                                    const FinishArgs& fa, cudaStream_t st) {
