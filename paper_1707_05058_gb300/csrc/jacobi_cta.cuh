@@ -255,10 +255,12 @@ struct CTAJacobiMid {
     T* ta;   // [K] t * a_pq
     T* red;  // [32] reduction scratch
     T* lam;  // [S] max(lambda, 0)
-    // this thread's pair-blocks: source offset, four destination offsets, and
-    // kind | I << 2 | J << 10 (kind 1: diagonal block of A, 2: off-diagonal
-    // block of A, 3: block of V, 0: none)
-    int b_src[NPT], b_d0[NPT], b_d1[NPT], b_d2[NPT], b_d3[NPT], b_meta[NPT];
+    static_assert(BUF < 65536, "offsets fit 16 bits");
+    // The pair-blocks a thread owns during the sweeps, three 16-bit pairs each:
+    // (source offset, destination 0), (destination 1, destination 2),
+    // (destination 3, meta) with meta = kind | I << 2 | J << 7 (kind 1:
+    // diagonal block of A, 2: off-diagonal block of A, 3: block of V, 0: none).
+    struct Plan { unsigned w0[NPT], w1[NPT], w2[NPT]; };
 
     __device__ __forceinline__ static int lower(int r, int c) { return r >= c ? r * LDA + c : c * LDA + r; }
 
@@ -271,6 +273,9 @@ struct CTAJacobiMid {
         ta = cs + 2 * K;
         red = ta + K;
         lam = red + 32;
+    }
+
+    __device__ __forceinline__ static void plan(Plan& P) {
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             const int b = threadIdx.x + j * kCtaThreads;
@@ -291,20 +296,23 @@ struct CTAJacobiMid {
                 kind = 3;
             }
             const int r0 = 2 * I, r1 = r0 + 1, c0 = 2 * J, c1 = c0 + 1;
-            b_src[j] = r0 * LDA + c0;
-            b_meta[j] = kind | (I << 2) | (J << 10);
+            int d0, d1, d2, d3;
             if (kind == 3) {  // rows of V stay, columns move with sigma
-                b_d0[j] = r0 * LDA + RR::sigma(c0);
-                b_d1[j] = b_d0[j] + LDA;
-                b_d2[j] = r0 * LDA + RR::sigma(c1);
-                b_d3[j] = b_d2[j] + LDA;
+                d0 = r0 * LDA + RR::sigma(c0);
+                d1 = d0 + LDA;
+                d2 = r0 * LDA + RR::sigma(c1);
+                d3 = d2 + LDA;
             } else {
                 const int sr0 = RR::sigma(r0), sr1 = RR::sigma(r1), sc0 = RR::sigma(c0), sc1 = RR::sigma(c1);
-                b_d0[j] = lower(sr0, sc0);
-                b_d1[j] = lower(sr1, sc0);
-                b_d2[j] = lower(sr0, sc1);
-                b_d3[j] = lower(sr1, sc1);
+                d0 = lower(sr0, sc0);
+                d1 = lower(sr1, sc0);
+                d2 = lower(sr0, sc1);
+                d3 = lower(sr1, sc1);
             }
+            const unsigned meta = unsigned(kind | (I << 2) | (J << 7));
+            P.w0[j] = unsigned(r0 * LDA + c0) | (unsigned(d0) << 16);
+            P.w1[j] = unsigned(d1) | (unsigned(d2) << 16);
+            P.w2[j] = unsigned(d3) | (meta << 16);
         }
     }
 
@@ -318,11 +326,11 @@ struct CTAJacobiMid {
     }
 
     // block-wide max of |off-diagonal| of the lower triangle of A
-    __device__ T off_max() {
+    __device__ T off_max(const Plan& P) {
         T m = T(0);
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
-            const int kind = b_meta[j] & 3, src = b_src[j];
+            const int kind = (P.w2[j] >> 16) & 3, src = P.w0[j] & 0xffff;
             if (kind == 1) {
                 m = fmax(m, fabs(X[src + LDA]));
             } else if (kind == 2) {
@@ -342,7 +350,7 @@ struct CTAJacobiMid {
         return r;
     }
 
-    __device__ void round(T tol) {
+    __device__ void round(T tol, const Plan& P) {
         const int tid = threadIdx.x;
         if (tid < K) {  // rotation of pair tid (Rutishauser form)
             const T app = X[(2 * tid) * LDA + 2 * tid], aqq = X[(2 * tid + 1) * LDA + 2 * tid + 1];
@@ -364,34 +372,36 @@ struct CTAJacobiMid {
         const T2* rot = reinterpret_cast<const T2*>(cs);
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
-            const int meta = b_meta[j], kind = meta & 3;
+            const unsigned meta = P.w2[j] >> 16;
+            const int kind = meta & 3;
             if (kind == 0) continue;
-            const int I = (meta >> 2) & 255, J = meta >> 10, src = b_src[j];
+            const int I = (meta >> 2) & 31, J = meta >> 7, src = P.w0[j] & 0xffff;
+            const int d0 = P.w0[j] >> 16, d1 = P.w1[j] & 0xffff, d2 = P.w1[j] >> 16, d3 = P.w2[j] & 0xffff;
             if (kind == 3) {
                 const T2 v0 = *reinterpret_cast<const T2*>(V + src);
                 const T2 v1 = *reinterpret_cast<const T2*>(V + src + LDA);
                 const T2 r = rot[J];
-                Vn[b_d0[j]] = r.x * v0.x - r.y * v0.y;
-                Vn[b_d2[j]] = r.y * v0.x + r.x * v0.y;
-                Vn[b_d1[j]] = r.x * v1.x - r.y * v1.y;
-                Vn[b_d3[j]] = r.y * v1.x + r.x * v1.y;
+                Vn[d0] = r.x * v0.x - r.y * v0.y;
+                Vn[d2] = r.y * v0.x + r.x * v0.y;
+                Vn[d1] = r.x * v1.x - r.y * v1.y;
+                Vn[d3] = r.y * v1.x + r.x * v1.y;
             } else if (kind == 1) {
                 const T t = ta[I];
                 const bool rotated = t != T(0) || rot[I].y != T(0);
                 const T b00 = X[src], b10 = X[src + LDA], b11 = X[src + LDA + 1];
-                Y[b_d0[j]] = b00 - t;
-                Y[b_d1[j]] = rotated ? T(0) : b10;
-                Y[b_d3[j]] = b11 + t;
+                Y[d0] = b00 - t;
+                Y[d1] = rotated ? T(0) : b10;
+                Y[d3] = b11 + t;
             } else {
                 const T2 ra = *reinterpret_cast<const T2*>(X + src);        // b00, b01
                 const T2 rb = *reinterpret_cast<const T2*>(X + src + LDA);  // b10, b11
                 const T2 ri = rot[I], rj = rot[J];
                 const T q00 = ri.x * ra.x - ri.y * rb.x, q10 = ri.y * ra.x + ri.x * rb.x;
                 const T q01 = ri.x * ra.y - ri.y * rb.y, q11 = ri.y * ra.y + ri.x * rb.y;
-                Y[b_d0[j]] = rj.x * q00 - rj.y * q01;
-                Y[b_d2[j]] = rj.y * q00 + rj.x * q01;
-                Y[b_d1[j]] = rj.x * q10 - rj.y * q11;
-                Y[b_d3[j]] = rj.y * q10 + rj.x * q11;
+                Y[d0] = rj.x * q00 - rj.y * q01;
+                Y[d2] = rj.y * q00 + rj.x * q01;
+                Y[d1] = rj.x * q10 - rj.y * q11;
+                Y[d3] = rj.y * q10 + rj.x * q11;
             }
         }
         __syncthreads();
@@ -405,16 +415,18 @@ struct CTAJacobiMid {
         if (!v_preset)
             for (int i = threadIdx.x; i < BUF; i += blockDim.x) V[i] = ((i / LDA) == (i % LDA)) ? T(1) : T(0);
         __syncthreads();
+        Plan P;
+        plan(P);
         const T noise = tol * T(2 * S);
         T prev = T(3.0e38);
         int sw = 0;
         while (sw < max_sweeps) {
-            const T off = off_max();
+            const T off = off_max(P);
             if (off <= tol) break;
             if (off <= noise && off > T(0.5) * prev) break;
             prev = off;
             ++sw;
-            for (int r = 0; r < R; ++r) round(tol);
+            for (int r = 0; r < R; ++r) round(tol, P);
         }
         return sw;
     }
@@ -517,7 +529,7 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double* sh) {
 // One kernel for every form: FORM 0/1/2 = Algorithm 1/2/3 step (as the warp
 // kernels of jacobi.cuh), FORM 3 = standalone projection.
 template <typename T, int S, int FORM>
-__global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
+__global__ void __launch_bounds__(kCtaThreads, (sizeof(T) == 4 && S <= 64) ? 3 : 1) k_project_cta(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
                                                               FinishArgs fa, const int* __restrict__ off_arr,
                                                               const int* __restrict__ size_arr,
                                                               const T* __restrict__ Win, T* Xout) {
@@ -534,7 +546,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_project_cta(Dev d, const int* _
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = FORM != 3 && pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     const double gamma = FORM == 2 ? d.scal[SC_GAMMA] : 0.0;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    __shared__ double acc[6];  // block partial sums, kept by thread 0
+    if (tid < 6) acc[tid] = 0.0;
     for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
         const int k = FORM == 3 ? li : list[li];
         const int s = FORM == 3 ? size_arr[k] : d.csize[k];
