@@ -86,6 +86,10 @@ typedef struct {
                               component_stop).  The cached factor does not involve rho. */
     double rho_mu;         /* >= 1; the paper's default 2                              */
     double rho_nu;         /* >= 1; the paper's default 10                             */
+    int x_update;          /* Algorithm 1, where x = D^-1 (bhat - A^T y) is formed:
+                              0 = automatic (inside the projection's gather while A is
+                              small enough to stay in L2, else 2); 1 = inside the
+                              gather; 2 = a separate kernel over the A^T rows     */
 } cdsdp_opts;
 
 typedef struct {
@@ -105,7 +109,8 @@ typedef struct {
 /* Fill `o` with defaults: eps 1e-4, max_iter 2000, rho 1, FP32 projection,
  * graph on, check_every 50, 30 Jacobi sweeps, warm start with a cold start every
  * 16 iterations, no profiling, per-component stopping, fixed rho (adaptive
- * rule off; rho_mu 2, rho_nu 10 when switched on). */
+ * rule off; rho_mu 2, rho_nu 10 when switched on), automatic x-update
+ * placement. */
 void cdsdp_default_opts(cdsdp_opts* o);
 
 /* Data preprocessing of Algorithms 1-3 (host only, no GPU call):

@@ -430,15 +430,18 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
             if (f < npk) {
                 const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
                 const int ent = d.gmap[off + f];
-                double aty = 0.0;
-                const int q1 = d.at_ptr[ent + 1];
+                double xe;
+                if (pa.x_ready) {
+                    xe = d.x[ent];
+                } else {
+                    double aty = 0.0;
+                    const int q1 = d.at_ptr[ent + 1];
 #pragma unroll 4
-                for (int q = d.at_ptr[ent]; q < q1; ++q) aty += d.at_val[q] * d.y[d.at_col[q]];
-                const double xe = d.t[ent] - d.dinv[ent] * aty;
-                if (d.owner[off + f]) {
-                    d.x[ent] = xe;
-                    cx += d.wgt[ent] * d.c[ent] * xe;
+                    for (int q = d.at_ptr[ent]; q < q1; ++q) aty += d.at_val[q] * d.y[d.at_col[q]];
+                    xe = d.t[ent] - d.dinv[ent] * aty;
+                    if (d.owner[off + f]) d.x[ent] = xe;
                 }
+                if (d.owner[off + f]) cx += d.wgt[ent] * d.c[ent] * xe;
                 hx[e] = T(xe);
                 const T w = hx[e] - lam[off + f] * irho;
                 if (d.wstore) {

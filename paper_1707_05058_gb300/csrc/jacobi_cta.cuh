@@ -563,14 +563,17 @@ __global__ void __launch_bounds__(kCtaThreads, (sizeof(T) == 4 && S <= 64) ? 3 :
             double w;
             if (FORM == 0) {
                 const int ent = d.gmap[off + f];
-                double aty = 0.0;
-                for (int q = d.at_ptr[ent]; q < d.at_ptr[ent + 1]; ++q) aty += d.at_val[q] * d.y[d.at_col[q]];
-                const double xe = d.t[ent] - d.dinv[ent] * aty;
-                if (d.owner[off + f]) {
-                    d.x[ent] = xe;
-                    cx += d.wgt[ent] * d.c[ent] * xe;
+                double xe;
+                if (pa.x_ready) {
+                    xe = d.x[ent];
+                } else {
+                    double aty = 0.0;
+                    for (int q = d.at_ptr[ent]; q < d.at_ptr[ent + 1]; ++q) aty += d.at_val[q] * d.y[d.at_col[q]];
+                    xe = d.t[ent] - d.dinv[ent] * aty;
+                    if (d.owner[off + f]) d.x[ent] = xe;
+                    d.q[ent] = xe;  // H_k x for the epilogue (scratch, same value from every clique)
                 }
-                d.q[ent] = xe;  // H_k x for the epilogue (scratch, same value from every clique)
+                if (d.owner[off + f]) cx += d.wgt[ent] * d.c[ent] * xe;
                 w = xe - double(c1[off + f]) * irho;
                 if (d.wstore) {
                     const int slot = d.ctl[CTL_ITER];
@@ -609,7 +612,7 @@ __global__ void __launch_bounds__(kCtaThreads, (sizeof(T) == 4 && S <= 64) ? 3 :
             const T xn = jac.rebuild(a, b, s);
             const double w = (a == b) ? 1.0 : 2.0;
             if (FORM == 0) {
-                const double hx = d.q[d.gmap[off + f]];
+                const double hx = pa.x_ready ? d.x[d.gmap[off + f]] : d.q[d.gmap[off + f]];
                 const double lm = c1[off + f];
                 const double xo = c0[off + f];
                 const double ln = lm + rho * (double(xn) - hx);

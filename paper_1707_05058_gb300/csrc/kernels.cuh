@@ -118,6 +118,8 @@ struct ProjArgs {
     int warm_start;      // reuse the previous iteration's eigenvectors
     int restart;         // cold start every `restart` iterations
     int row_off;         // first row of this launch in the per-block partial table
+    int x_ready;         // Algorithm 1: x was computed by a separate kernel this
+                         // iteration (read it) instead of inside the gather
 };
 
 __device__ __forceinline__ bool stopped(const Dev& d) {

@@ -55,6 +55,11 @@ struct cdsdp {
     // per entry for scatters (Gs) and A^T rows (Ga), threads per A row (TPR)
     // and per row of the cached inverse (TPRM)
     int GE = 1, GR = 1, Gs = 1, Ga = 1, TPR = 32, TPRM = 32;
+    // Algorithm 1: compute x = t - D^-1 A^T y in its own kernel (coalesced
+    // A^T rows) rather than inside the projection's gather; the automatic
+    // choice when A is too large to stay in L2 between iterations
+    bool x_split_auto = false;
+    bool x_split = false;  // choice of the current solve
     // cached graph of a whole solve
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -229,6 +234,8 @@ void make_dev(cdsdp* h) {
     h->Gs = pow2_clamp(avg_sc / 2.0, 1, 32);
     h->Ga = pow2_clamp(std::max(avg_at, avg_sc) / 3.0, 1, 32);
     h->TPR = pow2_clamp(avg_a / 4.0, 32, RTHREADS);
+    h->x_split_auto = (double)hp.a_col.size() * 12.0 > 48.0 * (1 << 20);
+    h->x_split = h->x_split_auto;
     int max_mc = 0;
     for (int c = 0; c < hp.ncomp; ++c) max_mc = std::max(max_mc, hp.crow_ptr[c + 1] - hp.crow_ptr[c]);
     h->TPRM = hp.diag_factor ? 32 : pow2_clamp(max_mc / 4.0, 32, RTHREADS);
@@ -253,6 +260,7 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
         if (h->cls_off[c + 1] > h->cls_off[c]) last = c;
     cudaError_t e = cudaSuccess;
     pa.row_off = 0;
+    pa.x_ready = (form == 0 && h->x_split) ? 1 : 0;
     for (int c = 0; c < kNumClasses && e == cudaSuccess; ++c) {
         const int* list = bl + h->cls_off[c];
         const int nl = h->cls_off[c + 1] - h->cls_off[c];
@@ -292,6 +300,7 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0, 1.0, 1.0, 1, 1, d.dinv, d.t, 1, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, 0, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
+        if (h->x_split) k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
         if ((e = launch_projection<T>(h, 0, o, fin, st)) != cudaSuccess) return e;
@@ -338,7 +347,7 @@ bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
     return a.eps == b.eps && a.max_iter == b.max_iter && a.rho == b.rho && a.precision == b.precision &&
            a.jacobi_max_sweeps == b.jacobi_max_sweeps && a.warm_start == b.warm_start &&
            a.component_stop == b.component_stop && a.adaptive_rho == b.adaptive_rho && a.rho_mu == b.rho_mu &&
-           a.rho_nu == b.rho_nu;
+           a.rho_nu == b.rho_nu && a.x_update == b.x_update;
 }
 
 void drop_graph(cdsdp* h) {
@@ -388,6 +397,7 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     if (o.warm_start < 0) return CDSDP_ERR_ARG;
     if (o.component_stop != 0 && o.component_stop != 1) return CDSDP_ERR_ARG;
     if (o.adaptive_rho < 0 || !(o.rho_mu >= 1.0) || !(o.rho_nu >= 1.0)) return CDSDP_ERR_ARG;
+    if (o.x_update < 0 || o.x_update > 2) return CDSDP_ERR_ARG;
     if (o.precision == CDSDP_FP64 && h->hp.max_clique > kMaxOrderF64) return CDSDP_ERR_UNSUPPORTED;
     return CDSDP_SOLVED;
 }
@@ -524,6 +534,7 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->adaptive_rho = 0;
     o->rho_mu = 2.0;
     o->rho_nu = 10.0;
+    o->x_update = 0;
 }
 
 int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
@@ -655,6 +666,7 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     Dev& d = h->dev;
     d.max_iter = o.max_iter;
     d.comp_mode = (h->hp.ncomp > 1 && form != 2 && o.component_stop) ? 1 : 0;
+    h->x_split = o.x_update == 0 ? h->x_split_auto : o.x_update == 2;
     // zero the state (clique vectors, iterates, partials, history)
     CK(cudaMemsetAsync(h->ws + h->L.const_end, 0, h->L.total - h->L.const_end, st));
     k_init<<<1, 256, 0, st>>>(d, form, o.rho);
@@ -803,6 +815,7 @@ int cdsdp_unrolled_forward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckpt
                            const double* d_b, void* d_gws, size_t gws_bytes, double* d_x, void* stream) {
     if (!h || !d_c || !d_b || !d_gws || !d_x) return CDSDP_ERR_ARG;
     const cdsdp_opts o = unrolled_opts(opts);
+    h->x_split = o.x_update == 0 ? h->x_split_auto : o.x_update == 2;
     int rc = check_unrolled(h, o, iters, ckpt_every);
     if (rc != CDSDP_SOLVED) return rc;
     const bool fp32 = o.precision != CDSDP_FP64;
@@ -835,6 +848,7 @@ int cdsdp_unrolled_backward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckp
                             double* d_bbar, void* stream) {
     if (!h || !d_c || !d_b || !d_gws || !d_xbar || !d_cbar || !d_bbar) return CDSDP_ERR_ARG;
     const cdsdp_opts o = unrolled_opts(opts);
+    h->x_split = o.x_update == 0 ? h->x_split_auto : o.x_update == 2;
     int rc = check_unrolled(h, o, iters, ckpt_every);
     if (rc != CDSDP_SOLVED) return rc;
     const bool fp32 = o.precision != CDSDP_FP64;

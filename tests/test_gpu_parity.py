@@ -384,3 +384,20 @@ def test_banded_full_size_adaptive_rho(lib, torch_cuda):
         assert rp <= 5e-4 and rd <= 5e-4
         res[prec] = float(dp.c @ _full(dp, out["X"]))
     assert abs(res["fp32"] - res["fp64"]) <= 1e-4 * abs(res["fp64"])
+
+
+@pytest.mark.parametrize("x_update", [1, 2])
+@pytest.mark.parametrize("clique", ["warp", "block"])
+def test_x_update_placement_fp64(lib, torch_cuda, x_update, clique):
+    """Algorithm 1 with x formed inside the projection's gather (1) or by a
+    separate kernel over the A^T rows (2): both follow the oracle (cliques of
+    order 15, one warp each; order 36, one thread block each)."""
+    prob = W.workload(0) if clique == "warp" else W.block_arrow(2, 30, 6, 10, seed=77)
+    dp = admm.decompose(prob)
+    ref = admm.primal_admm(dp, eps=0.0, max_iter=25)
+    P = lib.Problem(prob).bind(max_iter=25)
+    out = P.solve("primal", eps=0.0, max_iter=25, precision="fp64", x_update=x_update)
+    assert out["iters"] == 25
+    np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-8, atol=1e-10)
+    Xr = dp.lower_values(ref.X)
+    assert np.abs(out["X"] - Xr).max() <= 1e-8 * max(1.0, np.abs(Xr).max())
