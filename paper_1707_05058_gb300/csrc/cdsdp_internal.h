@@ -46,10 +46,12 @@ struct HostProblem {
     std::vector<int> crow_ptr, crow_idx;  // constraints of each component (ascending)
     std::vector<int> ccl_ptr, ccl_idx;    // cliques of each component (ascending)
     std::vector<long long> minv_off;   // [ncomp] offset of each dense block in minv / kinv
+    long long factor_size = 0;         // doubles in minv (and kinv)
     // cached inverses: per component a dense row-major m_c x m_c block (or, when
     // diag_factor, one value per constraint)
     std::vector<double> minv;         // (A W D^-1 A^T)^-1, Algorithms 1-2
     std::vector<double> kinv;         // (I + A W P^-1 A^T)^-1, P = I + D/2, Algorithm 3
+    bool hsde_ready = false;          // kinv and the HSDE constants below are built
     // HSDE constants (Proposition 2): zeta_hat = M^-1 zeta / (1 + zeta^T M^-1 zeta);
     // its s/t parts equal +-H zhat_x / 2 and are formed on the fly.
     std::vector<double> zhat_x, zhat_y;
@@ -66,6 +68,13 @@ int build_host_problem(int n, int m,
                        long long nnzC, const int* C_row, const int* C_col, const double* C_val,
                        long long nnzP, const int* P_row, const int* P_col,
                        HostProblem& hp);
+
+// Cached inverse for Algorithms 1-2 (hsde = false) or 3 (hsde = true).
+int build_factor(const HostProblem& hp, bool hsde, std::vector<double>& inv);
+
+// kinv, zeta_hat and the other constants of Algorithm 3 (built on the first
+// HSDE solve; primal and dual solves do not need them).
+int build_hsde_constants(HostProblem& hp);
 
 inline int packed_size(int s) { return s * (s + 1) / 2; }
 

@@ -26,6 +26,15 @@
 namespace cdsdp_dev {
 
 constexpr int kCtaThreads = 256;
+// Threads per clique block: float32 orders up to 48 use 128 threads, so that
+// six independent cliques share an SM (more latency hidden per round);
+// larger orders and float64 use 256.
+template <typename T, int S>
+__host__ __device__ constexpr int cta_threads() { return (sizeof(T) == 4 && S <= 48) ? 128 : kCtaThreads; }
+template <typename T, int S>
+__host__ __device__ constexpr int cta_min_blocks() {
+    return (sizeof(T) == 4 && S <= 48) ? 6 : ((sizeof(T) == 4 && S <= 64) ? 3 : 1);
+}
 
 template <typename T, int S>
 struct CTAJacobi {
@@ -243,26 +252,37 @@ struct CTAJacobiMid {
     static constexpr int BUF = S * LDA;
     static constexpr int NB = K * (K + 1) / 2; // lower pair-blocks of A
     static constexpr int NBLK = NB + K * K;    // plus the pair-blocks of V
-    static constexpr int NPT = (NBLK + kCtaThreads - 1) / kCtaThreads;
+    static constexpr int NT = cta_threads<T, S>();
+    static constexpr int NPT = (NBLK + NT - 1) / NT;
     static constexpr int S4 = S / 4;
     static constexpr size_t bytes = ((4 * (size_t)BUF + 3 * K + 32 + S) * sizeof(T) + 15) & ~size_t(15);
+    static_assert(BUF < 65536, "offsets fit 16 bits");
+
+    // Physical layout: storage index i lives at phys(i) (even indices first,
+    // then odd ones) in both dimensions, so the entries a warp writes to
+    // their sigma-permuted positions (even -> next even, odd -> previous odd)
+    // are consecutive words.  Products and the rebuild work directly on the
+    // physical arrays (the same permutation on every index).
+    __host__ __device__ static constexpr int phys(int i) { return (i & 1) ? K + (i >> 1) : (i >> 1); }
+    __host__ __device__ static constexpr int logical(int q) { return q < K ? 2 * q : 2 * (q - K) + 1; }
+    __device__ __forceinline__ static int at(int r, int c) { return phys(r) * LDA + phys(c); }
+    __device__ __forceinline__ static int lower(int r, int c) { return r >= c ? at(r, c) : at(c, r); }
 
     T* X;    // A, current
     T* Y;    // A, next
-    T* V;    // eigenvectors (storage order), current
+    T* V;    // eigenvectors, current (column = storage index)
     T* Vn;   // next
     T* cs;   // [K] (cos, sin) pairs
     T* ta;   // [K] t * a_pq
     T* red;  // [32] reduction scratch
-    T* lam;  // [S] max(lambda, 0)
-    static_assert(BUF < 65536, "offsets fit 16 bits");
-    // The pair-blocks a thread owns during the sweeps, three 16-bit pairs each:
-    // (source offset, destination 0), (destination 1, destination 2),
-    // (destination 3, meta) with meta = kind | I << 2 | J << 7 (kind 1:
-    // diagonal block of A, 2: off-diagonal block of A, 3: block of V, 0: none).
-    struct Plan { unsigned w0[NPT], w1[NPT], w2[NPT]; };
+    T* lam;  // [S] max(lambda, 0), physical order
 
-    __device__ __forceinline__ static int lower(int r, int c) { return r >= c ? r * LDA + c : c * LDA + r; }
+    // The pair-blocks a thread owns during the sweeps, three 16-bit pairs each:
+    // (source, destination 0), (destination 1, destination 2), (destination 3,
+    // meta) with meta = kind | I << 2 | J << 7 (kind 1: diagonal block of A,
+    // 2: off-diagonal block of A, 3: block of V, 0: none).  The four source
+    // entries of a block sit at source + {0, K, K LDA, K LDA + K}.
+    struct Plan { unsigned w0[NPT], w1[NPT], w2[NPT]; };
 
     __device__ __forceinline__ void bind(unsigned char* base) {
         X = reinterpret_cast<T*>(base);
@@ -278,7 +298,7 @@ struct CTAJacobiMid {
     __device__ __forceinline__ static void plan(Plan& P) {
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
-            const int b = threadIdx.x + j * kCtaThreads;
+            const int b = threadIdx.x + j * NT;
             int kind = 0, I = 0, J = 0;
             if (b < K) {
                 kind = 1;
@@ -296,21 +316,22 @@ struct CTAJacobiMid {
                 kind = 3;
             }
             const int r0 = 2 * I, r1 = r0 + 1, c0 = 2 * J, c1 = c0 + 1;
+            const int sc0 = RR::sigma(c0), sc1 = RR::sigma(c1);
             int d0, d1, d2, d3;
             if (kind == 3) {  // rows of V stay, columns move with sigma
-                d0 = r0 * LDA + RR::sigma(c0);
-                d1 = d0 + LDA;
-                d2 = r0 * LDA + RR::sigma(c1);
-                d3 = d2 + LDA;
+                d0 = at(r0, sc0);
+                d1 = at(r1, sc0);
+                d2 = at(r0, sc1);
+                d3 = at(r1, sc1);
             } else {
-                const int sr0 = RR::sigma(r0), sr1 = RR::sigma(r1), sc0 = RR::sigma(c0), sc1 = RR::sigma(c1);
+                const int sr0 = RR::sigma(r0), sr1 = RR::sigma(r1);
                 d0 = lower(sr0, sc0);
                 d1 = lower(sr1, sc0);
                 d2 = lower(sr0, sc1);
                 d3 = lower(sr1, sc1);
             }
             const unsigned meta = unsigned(kind | (I << 2) | (J << 7));
-            P.w0[j] = unsigned(r0 * LDA + c0) | (unsigned(d0) << 16);
+            P.w0[j] = unsigned(I * LDA + J) | (unsigned(d0) << 16);  // = at(r0, c0)
             P.w1[j] = unsigned(d1) | (unsigned(d2) << 16);
             P.w2[j] = unsigned(d3) | (meta << 16);
         }
@@ -321,8 +342,8 @@ struct CTAJacobiMid {
         __syncthreads();
     }
     __device__ __forceinline__ void put(int a, int b, T w) {
-        X[a * LDA + b] = w;
-        X[b * LDA + a] = w;
+        X[at(a, b)] = w;
+        X[at(b, a)] = w;
     }
 
     // block-wide max of |off-diagonal| of the lower triangle of A
@@ -332,10 +353,10 @@ struct CTAJacobiMid {
         for (int j = 0; j < NPT; ++j) {
             const int kind = (P.w2[j] >> 16) & 3, src = P.w0[j] & 0xffff;
             if (kind == 1) {
-                m = fmax(m, fabs(X[src + LDA]));
+                m = fmax(m, fabs(X[src + K * LDA]));
             } else if (kind == 2) {
-                m = fmax(fmax(m, fabs(X[src])), fabs(X[src + 1]));
-                m = fmax(fmax(m, fabs(X[src + LDA])), fabs(X[src + LDA + 1]));
+                m = fmax(fmax(m, fabs(X[src])), fabs(X[src + K]));
+                m = fmax(fmax(m, fabs(X[src + K * LDA])), fabs(X[src + K * LDA + K]));
             }
         }
 #pragma unroll
@@ -353,8 +374,8 @@ struct CTAJacobiMid {
     __device__ void round(T tol, const Plan& P) {
         const int tid = threadIdx.x;
         if (tid < K) {  // rotation of pair tid (Rutishauser form)
-            const T app = X[(2 * tid) * LDA + 2 * tid], aqq = X[(2 * tid + 1) * LDA + 2 * tid + 1];
-            const T apq = X[(2 * tid + 1) * LDA + 2 * tid];
+            const T app = X[tid * LDA + tid], aqq = X[(K + tid) * LDA + K + tid];
+            const T apq = X[(K + tid) * LDA + tid];
             T c = T(1), sn = T(0), tq = T(0);
             if (fabs(apq) > tol) {
                 const T zeta = T(0.5) * (aqq - app);
@@ -378,26 +399,24 @@ struct CTAJacobiMid {
             const int I = (meta >> 2) & 31, J = meta >> 7, src = P.w0[j] & 0xffff;
             const int d0 = P.w0[j] >> 16, d1 = P.w1[j] & 0xffff, d2 = P.w1[j] >> 16, d3 = P.w2[j] & 0xffff;
             if (kind == 3) {
-                const T2 v0 = *reinterpret_cast<const T2*>(V + src);
-                const T2 v1 = *reinterpret_cast<const T2*>(V + src + LDA);
+                const T v00 = V[src], v01 = V[src + K], v10 = V[src + K * LDA], v11 = V[src + K * LDA + K];
                 const T2 r = rot[J];
-                Vn[d0] = r.x * v0.x - r.y * v0.y;
-                Vn[d2] = r.y * v0.x + r.x * v0.y;
-                Vn[d1] = r.x * v1.x - r.y * v1.y;
-                Vn[d3] = r.y * v1.x + r.x * v1.y;
+                Vn[d0] = r.x * v00 - r.y * v01;
+                Vn[d2] = r.y * v00 + r.x * v01;
+                Vn[d1] = r.x * v10 - r.y * v11;
+                Vn[d3] = r.y * v10 + r.x * v11;
             } else if (kind == 1) {
                 const T t = ta[I];
                 const bool rotated = t != T(0) || rot[I].y != T(0);
-                const T b00 = X[src], b10 = X[src + LDA], b11 = X[src + LDA + 1];
+                const T b00 = X[src], b10 = X[src + K * LDA], b11 = X[src + K * LDA + K];
                 Y[d0] = b00 - t;
                 Y[d1] = rotated ? T(0) : b10;
                 Y[d3] = b11 + t;
             } else {
-                const T2 ra = *reinterpret_cast<const T2*>(X + src);        // b00, b01
-                const T2 rb = *reinterpret_cast<const T2*>(X + src + LDA);  // b10, b11
+                const T b00 = X[src], b01 = X[src + K], b10 = X[src + K * LDA], b11 = X[src + K * LDA + K];
                 const T2 ri = rot[I], rj = rot[J];
-                const T q00 = ri.x * ra.x - ri.y * rb.x, q10 = ri.y * ra.x + ri.x * rb.x;
-                const T q01 = ri.x * ra.y - ri.y * rb.y, q11 = ri.y * ra.y + ri.x * rb.y;
+                const T q00 = ri.x * b00 - ri.y * b10, q10 = ri.y * b00 + ri.x * b10;
+                const T q01 = ri.x * b01 - ri.y * b11, q11 = ri.y * b01 + ri.x * b11;
                 Y[d0] = rj.x * q00 - rj.y * q01;
                 Y[d2] = rj.y * q00 + rj.x * q01;
                 Y[d1] = rj.x * q10 - rj.y * q11;
@@ -431,7 +450,7 @@ struct CTAJacobiMid {
         return sw;
     }
 
-    // C = A^T B over 4x4 output tiles (A, B, C: S x S with leading dimension LDA).
+    // C = A^T B over 4x4 output tiles (physical S x S arrays, leading dimension LDA).
     __device__ void atb(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C) const {
         for (int tile = threadIdx.x; tile < S4 * S4; tile += blockDim.x) {
             const int tr = tile / S4, tc = tile - tr * S4;
@@ -466,19 +485,21 @@ struct CTAJacobiMid {
 
     __device__ void load_basis(const T* __restrict__ Vc, int s) {
         for (int i = threadIdx.x; i < BUF; i += blockDim.x) {
-            const int r = i / LDA, c = i - r * LDA;
-            V[i] = (r < s && c < s) ? Vc[r * s + c] : (r == c ? T(1) : T(0));
+            const int qr = i / LDA, qc = i - qr * LDA;
+            const int r = logical(qr), c = logical(qc);
+            V[i] = (r < s && c < s && qc < S) ? Vc[r * s + c] : (r == c ? T(1) : T(0));
         }
         __syncthreads();
     }
     __device__ void store_basis(T* __restrict__ Vc, int s) const {
         for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
             const int r = i / s, c = i - r * s;
-            Vc[i] = V[r * LDA + c];
+            Vc[i] = V[at(r, c)];
         }
     }
 
-    // X <- V max(Lambda, 0) V^T (lower 4x4 tiles), Lambda on X's diagonal.
+    // X <- V max(Lambda, 0) V^T over the lower physical 4x4 tiles, Lambda on
+    // X's diagonal.
     __device__ void prepare_rebuild() {
         for (int i = threadIdx.x; i < S; i += blockDim.x) {
             const T l = X[i * LDA + i];
@@ -515,7 +536,11 @@ struct CTAJacobiMid {
         }
         __syncthreads();
     }
-    __device__ __forceinline__ T rebuild(int a, int b, int) const { return X[a * LDA + b]; }
+    // entry (a, b) of the rebuilt block (symmetric: read its lower physical half)
+    __device__ __forceinline__ T rebuild(int a, int b, int) const {
+        const int pa = phys(a), pb = phys(b);
+        return pa >= pb ? X[pa * LDA + pb] : X[pb * LDA + pa];
+    }
 };
 
 template <typename T, int S>
@@ -529,7 +554,7 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double* sh) {
 // One kernel for every form: FORM 0/1/2 = Algorithm 1/2/3 step (as the warp
 // kernels of jacobi.cuh), FORM 3 = standalone projection.
 template <typename T, int S, int FORM>
-__global__ void __launch_bounds__(kCtaThreads, (sizeof(T) == 4 && S <= 64) ? 3 : 1) k_project_cta(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
+__global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k_project_cta(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
                                                               FinishArgs fa, const int* __restrict__ off_arr,
                                                               const int* __restrict__ size_arr,
                                                               const T* __restrict__ Win, T* Xout) {

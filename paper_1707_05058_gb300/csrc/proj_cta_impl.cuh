@@ -25,7 +25,7 @@ cudaError_t launch_cta(const Dev& d, const int* list, int nlist, const ProjArgs&
     ProjArgs pa = pa_in;
     pa.tolrel = jacobi_tolrel(S, sizeof(T) == 4);
     if (FORM == 3) pa.max_sweeps = max_sweeps;
-    k_project_cta<T, S, FORM><<<proj_cta_grid(nlist), kCtaThreads, smem, st>>>(d, list, nlist, pa, fa, off, size,
+    k_project_cta<T, S, FORM><<<proj_cta_grid(nlist), cta_threads<T, S>(), smem, st>>>(d, list, nlist, pa, fa, off, size,
                                                                                (const T*)W, (T*)X);
     return cudaGetLastError();
 }

@@ -14,10 +14,12 @@
 //    with parent(u) = v has |later(u)| = |later(v)| + 1 (parent = first later
 //    neighbour); cliques sorted ascending, list sorted lexicographically.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <new>
 #include <set>
+#include <thread>
 #include <utility>
 
 #include "cdsdp_internal.h"
@@ -25,43 +27,68 @@
 namespace cdsdp_impl {
 namespace {
 
+// Run body(t) for t = 0 .. T-1 on T host threads (T = hardware threads, at
+// most `cap`); plain loop when one thread is enough.
+template <typename F>
+void parallel_threads(int cap, F&& body) {
+    int T = (int)std::thread::hardware_concurrency();
+    T = std::max(1, std::min(T, cap));
+    if (T == 1) { body(0, 1); return; }
+    std::vector<std::thread> th;
+    th.reserve(T - 1);
+    for (int t = 1; t < T; ++t) th.emplace_back([&body, t, T]() { body(t, T); });
+    body(0, T);
+    for (auto& x : th) x.join();
+}
+
 // Dense Cholesky (lower, row-major, in place) followed by the explicit
-// inverse inv = L^-T L^-1.  Returns false on a non-positive pivot.
-bool spd_inverse(std::vector<double>& a, int m, std::vector<double>& inv) {
+// inverse inv = L^-T L^-1: the columns of L^-1 by forward substitution, then
+// inv_ij = <column i, column j>, both in parallel over columns; every inner
+// loop runs along contiguous memory.  Returns false on a non-positive pivot.
+bool spd_inverse(std::vector<double>& a, int m, std::vector<double>& inv, int threads) {
     double maxdiag = 0.0;
     for (int i = 0; i < m; ++i) maxdiag = std::max(maxdiag, std::fabs(a[(size_t)i * m + i]));
     for (int j = 0; j < m; ++j) {
-        double d = a[(size_t)j * m + j];
-        for (int k = 0; k < j; ++k) d -= a[(size_t)j * m + k] * a[(size_t)j * m + k];
+        const double* rj = &a[(size_t)j * m];
+        double d = rj[j];
+        for (int k = 0; k < j; ++k) d -= rj[k] * rj[k];
         if (!(d > 1e-14 * maxdiag)) return false;
-        double ljj = std::sqrt(d);
+        const double ljj = std::sqrt(d);
         a[(size_t)j * m + j] = ljj;
         for (int i = j + 1; i < m; ++i) {
-            double s = a[(size_t)i * m + j];
-            const double* ri = &a[(size_t)i * m];
-            const double* rj = &a[(size_t)j * m];
+            double* ri = &a[(size_t)i * m];
+            double s = ri[j];
             for (int k = 0; k < j; ++k) s -= ri[k] * rj[k];
-            a[(size_t)i * m + j] = s / ljj;
+            ri[j] = s / ljj;
         }
     }
-    // W = L^-1 (lower), by forward substitution column by column of I
-    std::vector<double> w((size_t)m * m, 0.0);
-    for (int j = 0; j < m; ++j) {
-        for (int i = j; i < m; ++i) {
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int k = j; k < i; ++k) s -= a[(size_t)i * m + k] * w[(size_t)k * m + j];
-            w[(size_t)i * m + j] = s / a[(size_t)i * m + i];
+    // xt row j = column j of L^-1 (entries j..m-1): L x = e_j
+    std::vector<double> xt((size_t)m * m, 0.0);
+    const int cap = m >= 128 ? threads : 1;
+    parallel_threads(cap, [&](int t, int T) {
+        for (int j = t; j < m; j += T) {
+            double* x = &xt[(size_t)j * m];
+            for (int i = j; i < m; ++i) {
+                const double* li = &a[(size_t)i * m];
+                double s = (i == j) ? 1.0 : 0.0;
+                for (int k = j; k < i; ++k) s -= li[k] * x[k];
+                x[i] = s / li[i];
+            }
         }
-    }
-    // inv = W^T W
+    });
     inv.assign((size_t)m * m, 0.0);
-    for (int i = 0; i < m; ++i)
-        for (int j = 0; j <= i; ++j) {
-            double s = 0.0;
-            for (int k = i; k < m; ++k) s += w[(size_t)k * m + i] * w[(size_t)k * m + j];
-            inv[(size_t)i * m + j] = s;
-            inv[(size_t)j * m + i] = s;
+    parallel_threads(cap, [&](int t, int T) {
+        for (int i = t; i < m; i += T) {
+            const double* xi = &xt[(size_t)i * m];
+            for (int j = 0; j <= i; ++j) {
+                const double* xj = &xt[(size_t)j * m];
+                double s = 0.0;
+                for (int k = i; k < m; ++k) s += xi[k] * xj[k];  // k >= max(i, j) = i
+                inv[(size_t)i * m + j] = s;
+                inv[(size_t)j * m + i] = s;
+            }
         }
+    });
     return true;
 }
 
@@ -74,6 +101,136 @@ int entry_of(const HostProblem& hp, int i, int j) {  // i >= j
 }
 
 }  // namespace
+
+// Cached inverse of A W diag(d)^-1 A^T (+ I for the HSDE system, d = 1 + D/2),
+// block diagonal over the independent components (Eqs.
+// ADMMprimalFatorization, HSDEFactorizationFinal).
+int build_factor(const HostProblem& hp, bool hsde, std::vector<double>& inv) {
+    const int NE = (int)hp.prow.size(), m = hp.m;
+    auto wgt = [&](int e) { return hp.prow[e] == hp.pcol[e] ? 1.0 : 2.0; };
+    if (hp.diag_factor) {
+        inv.assign(m, hsde ? 1.0 : 0.0);
+        for (int e = 0; e < NE; ++e)
+            for (int q = hp.at_ptr[e]; q < hp.at_ptr[e + 1]; ++q) {
+                const double dd = hsde ? 1.0 + 0.5 * hp.D[e] : hp.D[e];
+                inv[hp.at_col[q]] += wgt(e) * hp.at_val[q] * hp.at_val[q] / dd;
+            }
+        for (int i = 0; i < m; ++i) {
+            if (!(inv[i] > 0.0)) return CDSDP_ERR_RANK;
+            inv[i] = 1.0 / inv[i];
+        }
+        return CDSDP_SOLVED;
+    }
+    inv.assign((size_t)hp.factor_size, 0.0);
+    std::vector<std::vector<double>> blocks(hp.ncomp);
+    for (int c = 0; c < hp.ncomp; ++c) {
+        const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+        blocks[c].assign((size_t)mc * mc, 0.0);
+        for (int i = 0; hsde && i < mc; ++i) blocks[c][(size_t)i * mc + i] = 1.0;
+    }
+    // lower triangle of each block (the constraints of an A^T row are in
+    // ascending order, hence so are their positions in the block), then mirror
+    std::vector<int> lr;
+    for (int e = 0; e < NE; ++e) {
+        const int c = hp.comp_of_entry[e];
+        const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+        double* S = blocks[c].data();
+        const double f = wgt(e) / (hsde ? 1.0 + 0.5 * hp.D[e] : hp.D[e]);
+        const int q0 = hp.at_ptr[e], nq = hp.at_ptr[e + 1] - q0;
+        lr.resize(nq);
+        for (int u = 0; u < nq; ++u) lr[u] = hp.lrow[hp.at_col[q0 + u]];
+        const double* av = &hp.at_val[q0];
+        for (int u = 0; u < nq; ++u) {
+            const double v1 = f * av[u];
+            double* row = S + (size_t)lr[u] * mc;
+            for (int w = 0; w <= u; ++w) row[lr[w]] += v1 * av[w];
+        }
+    }
+    for (int c = 0; c < hp.ncomp; ++c) {
+        const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+        double* S = blocks[c].data();
+        for (int i = 0; i < mc; ++i)
+            for (int j = 0; j < i; ++j) S[(size_t)j * mc + i] = S[(size_t)i * mc + j];
+    }
+    // one component: threads inside the inverse; several: one component per thread
+    std::atomic<int> bad(0);
+    if (hp.ncomp == 1) {
+        std::vector<double> bi;
+        if (!spd_inverse(blocks[0], hp.m, bi, 16)) return CDSDP_ERR_RANK;
+        std::copy(bi.begin(), bi.end(), inv.begin());
+    } else {
+        std::atomic<int> next(0);
+        parallel_threads(16, [&](int, int) {
+            for (int c = next++; c < hp.ncomp; c = next++) {
+                const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+                std::vector<double> bi;
+                if (!spd_inverse(blocks[c], mc, bi, 1)) { bad = 1; continue; }
+                std::copy(bi.begin(), bi.end(), inv.begin() + hp.minv_off[c]);
+            }
+        });
+    }
+    return bad ? CDSDP_ERR_RANK : CDSDP_SOLVED;
+}
+
+int build_hsde_constants(HostProblem& hp) {
+    if (hp.hsde_ready) return CDSDP_SOLVED;
+    const int NE = (int)hp.prow.size(), m = hp.m;
+    auto wgt = [&](int e) { return hp.prow[e] == hp.pcol[e] ? 1.0 : 2.0; };
+    int st = build_factor(hp, true, hp.kinv);
+    if (st != CDSDP_SOLVED) return st;
+    // ---- HSDE: zeta_hat from one inner solve with nu = zeta = (c, 0, -b, 0)
+    {
+        auto kinv_apply = [&](const std::vector<double>& r, std::vector<double>& out) {
+            out.assign(m, 0.0);
+            if (hp.diag_factor) { for (int i = 0; i < m; ++i) out[i] = hp.kinv[i] * r[i]; return; }
+            for (int i = 0; i < m; ++i) {
+                const int c = hp.comp_of_row[i], mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
+                const double* row = hp.kinv.data() + hp.minv_off[c] + (size_t)hp.lrow[i] * mc;
+                double s = 0.0;
+                for (int j = 0; j < mc; ++j) s += row[j] * r[hp.crow_idx[hp.crow_ptr[c] + j]];
+                out[i] = s;
+            }
+        };
+        auto A_w = [&](const std::vector<double>& x, std::vector<double>& out) {  // A W x
+            out.assign(m, 0.0);
+            for (int i = 0; i < m; ++i) {
+                double s = 0.0;
+                for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) s += hp.a_val[q] * wgt(hp.a_col[q]) * x[hp.a_col[q]];
+                out[i] = s;
+            }
+        };
+        auto A_T = [&](const std::vector<double>& y, std::vector<double>& out) {
+            out.assign(NE, 0.0);
+            for (int e = 0; e < NE; ++e) {
+                double s = 0.0;
+                for (int q = hp.at_ptr[e]; q < hp.at_ptr[e + 1]; ++q) s += hp.at_val[q] * y[hp.at_col[q]];
+                out[e] = s;
+            }
+        };
+        A_T(hp.b, hp.atb);
+        std::vector<double> pe(NE), r, hh, athh, s11(NE), as11;
+        for (int e = 0; e < NE; ++e) pe[e] = (hp.c[e] - hp.atb[e]) / (1.0 + 0.5 * hp.D[e]);
+        A_w(pe, r);
+        kinv_apply(r, hh);
+        A_T(hh, athh);
+        for (int e = 0; e < NE; ++e) s11[e] = pe[e] - athh[e] / (1.0 + 0.5 * hp.D[e]);
+        A_w(s11, as11);
+        std::vector<double> s21(m);
+        for (int i = 0; i < m; ++i) s21[i] = -hp.b[i] - as11[i];
+        double zMz = 0.0;
+        for (int e = 0; e < NE; ++e) zMz += wgt(e) * hp.c[e] * s11[e];
+        for (int i = 0; i < m; ++i) zMz -= hp.b[i] * s21[i];
+        double denom = 1.0 + zMz;
+        hp.zhat_x.resize(NE);
+        hp.zhat_y.resize(m);
+        for (int e = 0; e < NE; ++e) hp.zhat_x[e] = s11[e] / denom;
+        for (int i = 0; i < m; ++i) hp.zhat_y[i] = s21[i] / denom;
+        hp.zeta_dot_zhat = zMz / denom;
+        A_w(hp.zhat_x, hp.a_zhat_x);
+    }
+    hp.hsde_ready = true;
+    return CDSDP_SOLVED;
+}
 
 int build_host_problem(int n, int m,
                        long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
@@ -102,18 +259,33 @@ int build_host_problem(int n, int m,
     hp.n = n;
     hp.m = m;
 
-    // ---- aggregate pattern (off-diagonal adjacency, sorted, unique)
+    // ---- aggregate pattern (off-diagonal adjacency, sorted, unique): C and
+    // the extra edges first, then the entries of A that are not there yet
+    // (usually none: C tends to cover the pattern of the A_i)
     std::vector<std::vector<int>> adj(n);
     auto add_edge = [&](int r, int c) {
         if (r != c) { adj[r].push_back(c); adj[c].push_back(r); }
     };
+    auto tidy = [&]() {
+        for (auto& a : adj) {
+            std::sort(a.begin(), a.end());
+            a.erase(std::unique(a.begin(), a.end()), a.end());
+        }
+    };
     for (long long k = 0; k < nnzC; ++k) add_edge(C_row[k], C_col[k]);
-    for (long long k = 0; k < nnzA; ++k) add_edge(A_row[k], A_col[k]);
     for (long long k = 0; k < nnzP; ++k) add_edge(P_row[k], P_col[k]);
+    tidy();
+    {
+        std::vector<std::pair<int, int>> extra;
+        for (long long k = 0; k < nnzA; ++k) {
+            const int r = A_row[k], c = A_col[k];
+            if (r != c && !std::binary_search(adj[r].begin(), adj[r].end(), c)) extra.push_back({r, c});
+        }
+        for (auto& e : extra) add_edge(e.first, e.second);
+        if (!extra.empty()) tidy();
+    }
     long long nedges = 0;
     for (auto& a : adj) {
-        std::sort(a.begin(), a.end());
-        a.erase(std::unique(a.begin(), a.end()), a.end());
         nedges += (long long)a.size();
     }
     nedges /= 2;
@@ -268,22 +440,31 @@ int build_host_problem(int n, int m,
     hp.c.assign(NE, 0.0);
     for (long long k = 0; k < nnzC; ++k) hp.c[entry_of(hp, C_row[k], C_col[k])] += C_val[k];
     {
-        std::vector<std::pair<long long, double>> t;
-        t.reserve(nnzA);
-        for (long long k = 0; k < nnzA; ++k)
-            t.push_back({(long long)A_con[k] * NE + entry_of(hp, A_row[k], A_col[k]), A_val[k]});
-        std::sort(t.begin(), t.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-        hp.a_ptr.assign(m + 1, 0);
-        long long last = -1;
-        for (auto& kv : t) {
-            if (kv.first == last) { hp.a_val.back() += kv.second; continue; }
-            last = kv.first;
-            int con = (int)(kv.first / NE), e = (int)(kv.first % NE);
-            hp.a_col.push_back(e);
-            hp.a_val.push_back(kv.second);
-            ++hp.a_ptr[con + 1];
+        // bucket the triplets by constraint, sort each row by entry, merge duplicates
+        std::vector<long long> rp(m + 1, 0);
+        for (long long k = 0; k < nnzA; ++k) ++rp[A_con[k] + 1];
+        for (int i = 0; i < m; ++i) rp[i + 1] += rp[i];
+        std::vector<std::pair<int, double>> t((size_t)nnzA);
+        {
+            std::vector<long long> fill(rp.begin(), rp.end() - 1);
+            for (long long k = 0; k < nnzA; ++k)
+                t[(size_t)fill[A_con[k]]++] = {entry_of(hp, A_row[k], A_col[k]), A_val[k]};
         }
-        for (int i = 0; i < m; ++i) hp.a_ptr[i + 1] += hp.a_ptr[i];
+        hp.a_ptr.assign(m + 1, 0);
+        hp.a_col.reserve((size_t)nnzA);
+        hp.a_val.reserve((size_t)nnzA);
+        for (int i = 0; i < m; ++i) {
+            auto b0 = t.begin() + rp[i], b1 = t.begin() + rp[i + 1];
+            std::sort(b0, b1, [](const auto& x, const auto& y) { return x.first < y.first; });
+            int last = -1;
+            for (auto it = b0; it != b1; ++it) {
+                if (it->first == last) { hp.a_val.back() += it->second; continue; }
+                last = it->first;
+                hp.a_col.push_back(it->first);
+                hp.a_val.push_back(it->second);
+            }
+            hp.a_ptr[i + 1] = (int)hp.a_col.size();
+        }
         hp.at_ptr.assign(NE + 1, 0);
         for (int e : hp.a_col) ++hp.at_ptr[e + 1];
         for (int e = 0; e < NE; ++e) hp.at_ptr[e + 1] += hp.at_ptr[e];
@@ -371,107 +552,15 @@ int build_host_problem(int n, int m,
         hp.minv_off[c] = tot;
         tot += mc * mc;
     }
-    auto build = [&](bool hsde, std::vector<double>& inv) -> int {
-        if (structurally_diag) {
-            inv.assign(m, hsde ? 1.0 : 0.0);
-            for (int e = 0; e < NE; ++e)
-                for (int q = hp.at_ptr[e]; q < hp.at_ptr[e + 1]; ++q) {
-                    double dd = hsde ? 1.0 + 0.5 * hp.D[e] : hp.D[e];
-                    inv[hp.at_col[q]] += wgt(e) * hp.at_val[q] * hp.at_val[q] / dd;
-                }
-            for (int i = 0; i < m; ++i) {
-                if (!(inv[i] > 0.0)) return CDSDP_ERR_RANK;
-                inv[i] = 1.0 / inv[i];
-            }
-            return CDSDP_SOLVED;
-        }
-        inv.assign((size_t)tot, 0.0);
-        std::vector<std::vector<double>> blocks(hp.ncomp);
-        for (int c = 0; c < hp.ncomp; ++c) {
-            const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
-            blocks[c].assign((size_t)mc * mc, 0.0);
-            for (int i = 0; hsde && i < mc; ++i) blocks[c][(size_t)i * mc + i] = 1.0;
-        }
-        for (int e = 0; e < NE; ++e) {
-            const int c = hp.comp_of_entry[e];
-            const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
-            double* S = blocks[c].data();
-            const double f = wgt(e) / (hsde ? 1.0 + 0.5 * hp.D[e] : hp.D[e]);
-            for (int q1 = hp.at_ptr[e]; q1 < hp.at_ptr[e + 1]; ++q1) {
-                const double v1 = f * hp.at_val[q1];
-                double* row = S + (size_t)hp.lrow[hp.at_col[q1]] * mc;
-                for (int q2 = hp.at_ptr[e]; q2 < hp.at_ptr[e + 1]; ++q2) row[hp.lrow[hp.at_col[q2]]] += v1 * hp.at_val[q2];
-            }
-        }
-        for (int c = 0; c < hp.ncomp; ++c) {
-            const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
-            std::vector<double> bi;
-            if (!spd_inverse(blocks[c], mc, bi)) return CDSDP_ERR_RANK;
-            std::copy(bi.begin(), bi.end(), inv.begin() + hp.minv_off[c]);
-        }
-        return CDSDP_SOLVED;
-    };
     hp.diag_factor = structurally_diag;
-    int st = build(false, hp.minv);
+    hp.factor_size = tot;
+    int st = build_factor(hp, false, hp.minv);
     if (st != CDSDP_SOLVED) return st;
-    st = build(true, hp.kinv);
-    if (st != CDSDP_SOLVED) return st;
-
-    // ---- HSDE: zeta_hat from one inner solve with nu = zeta = (c, 0, -b, 0)
-    {
-        auto kinv_apply = [&](const std::vector<double>& r, std::vector<double>& out) {
-            out.assign(m, 0.0);
-            if (hp.diag_factor) { for (int i = 0; i < m; ++i) out[i] = hp.kinv[i] * r[i]; return; }
-            for (int i = 0; i < m; ++i) {
-                const int c = hp.comp_of_row[i], mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
-                const double* row = hp.kinv.data() + hp.minv_off[c] + (size_t)hp.lrow[i] * mc;
-                double s = 0.0;
-                for (int j = 0; j < mc; ++j) s += row[j] * r[hp.crow_idx[hp.crow_ptr[c] + j]];
-                out[i] = s;
-            }
-        };
-        auto A_w = [&](const std::vector<double>& x, std::vector<double>& out) {  // A W x
-            out.assign(m, 0.0);
-            for (int i = 0; i < m; ++i) {
-                double s = 0.0;
-                for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) s += hp.a_val[q] * wgt(hp.a_col[q]) * x[hp.a_col[q]];
-                out[i] = s;
-            }
-        };
-        auto A_T = [&](const std::vector<double>& y, std::vector<double>& out) {
-            out.assign(NE, 0.0);
-            for (int e = 0; e < NE; ++e) {
-                double s = 0.0;
-                for (int q = hp.at_ptr[e]; q < hp.at_ptr[e + 1]; ++q) s += hp.at_val[q] * y[hp.at_col[q]];
-                out[e] = s;
-            }
-        };
-        A_T(hp.b, hp.atb);
-        std::vector<double> pe(NE), r, hh, athh, s11(NE), as11;
-        for (int e = 0; e < NE; ++e) pe[e] = (hp.c[e] - hp.atb[e]) / (1.0 + 0.5 * hp.D[e]);
-        A_w(pe, r);
-        kinv_apply(r, hh);
-        A_T(hh, athh);
-        for (int e = 0; e < NE; ++e) s11[e] = pe[e] - athh[e] / (1.0 + 0.5 * hp.D[e]);
-        A_w(s11, as11);
-        std::vector<double> s21(m);
-        for (int i = 0; i < m; ++i) s21[i] = -hp.b[i] - as11[i];
-        double zMz = 0.0;
-        for (int e = 0; e < NE; ++e) zMz += wgt(e) * hp.c[e] * s11[e];
-        for (int i = 0; i < m; ++i) zMz -= hp.b[i] * s21[i];
-        double denom = 1.0 + zMz;
-        hp.zhat_x.resize(NE);
-        hp.zhat_y.resize(m);
-        for (int e = 0; e < NE; ++e) hp.zhat_x[e] = s11[e] / denom;
-        for (int i = 0; i < m; ++i) hp.zhat_y[i] = s21[i] / denom;
-        hp.zeta_dot_zhat = zMz / denom;
-        A_w(hp.zhat_x, hp.a_zhat_x);
-        double nb = 0.0, nc = 0.0;
-        for (int i = 0; i < m; ++i) nb += hp.b[i] * hp.b[i];
-        for (int e = 0; e < NE; ++e) nc += wgt(e) * hp.c[e] * hp.c[e];
-        hp.norm_b = std::sqrt(nb);
-        hp.norm_c = std::sqrt(nc);
-    }
+    double nb = 0.0, nc = 0.0;
+    for (int i = 0; i < m; ++i) nb += hp.b[i] * hp.b[i];
+    for (int e = 0; e < NE; ++e) nc += wgt(e) * hp.c[e] * hp.c[e];
+    hp.norm_b = std::sqrt(nb);
+    hp.norm_c = std::sqrt(nc);
     return CDSDP_SOLVED;
 }
 

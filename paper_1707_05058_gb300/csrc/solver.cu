@@ -402,6 +402,34 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     return CDSDP_SOLVED;
 }
 
+// Algorithm 3's cached inverse and constants are built on the first HSDE solve
+// (host) and copied into their slots of the bound workspace.
+int ensure_hsde(cdsdp* h, cudaStream_t st) {
+    if (h->hp.hsde_ready) return CDSDP_SOLVED;
+    int rc;
+    try {
+        rc = cdsdp_impl::build_hsde_constants(h->hp);
+    } catch (const std::bad_alloc&) {
+        rc = CDSDP_ERR_NOMEM;
+    }
+    if (rc != CDSDP_SOLVED) return rc;
+    const HostProblem& hp = h->hp;
+    const Layout& L = h->L;
+    put(h->image, L.kinv, hp.kinv);
+    put(h->image, L.zhx, hp.zhat_x);
+    put(h->image, L.zhy, hp.zhat_y);
+    put(h->image, L.atb, hp.atb);
+    put(h->image, L.azhx, hp.a_zhat_x);
+    const size_t sections[5][2] = {{L.kinv, hp.kinv.size() * 8}, {L.zhx, hp.zhat_x.size() * 8},
+                                   {L.zhy, hp.zhat_y.size() * 8}, {L.atb, hp.atb.size() * 8},
+                                   {L.azhx, hp.a_zhat_x.size() * 8}};
+    for (const auto& sec : sections)
+        if (sec[1]) CK(cudaMemcpyAsync(h->ws + sec[0], h->image.data() + sec[0], sec[1], cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    h->dev.zeta_dot_zhat = hp.zeta_dot_zhat;
+    return CDSDP_SOLVED;
+}
+
 int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, double* hist, double* cert) {
     Dev& d = h->dev;
     const int form = h->last_form;
@@ -663,6 +691,7 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     int rc = check_opts(h, o);
     if (rc != CDSDP_SOLVED) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    if (form == 2 && (rc = ensure_hsde(h, st)) != CDSDP_SOLVED) return rc;
     Dev& d = h->dev;
     d.max_iter = o.max_iter;
     d.comp_mode = (h->hp.ncomp > 1 && form != 2 && o.component_stop) ? 1 : 0;
