@@ -116,7 +116,7 @@ void cdsdp_default_opts(cdsdp_opts* o);
 /* Data preprocessing of Algorithms 1-3 (host only, no GPU call):
  * aggregate sparsity pattern E* of C, every A_i and the optional extra
  * edges P (Section 2.1, Eq. AggregateSparsity), chordal extension and maximal
- * cliques (Section 6.1.1; maximum cardinality search when already chordal,
+ * cliques (Section 7.1.1; maximum cardinality search when already chordal,
  * minimum-degree elimination otherwise; cliques sorted lexicographically),
  * the entry selectors H_k (Section 4), D = sum_k H_k^T H_k, and the cached
  * inverses of A D^-1 A^T (Eq. ADMMprimalFatorization) and of
@@ -260,7 +260,7 @@ int cdsdp_unrolled_backward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckp
                             const double* d_b, void* d_gws, size_t gws_bytes, const double* d_xbar, double* d_cbar,
                             double* d_bbar, void* stream);
 
-/* PSD-violation measure of Section 6.1.3 (Eq. PSD-violation):
+/* PSD-violation measure of Section 7.2 (Eq. PSD-violation):
  *   alpha = -min{0, lambda_min(W_0), ..., lambda_min(W_{p-1})}
  * over p lower-packed symmetric blocks (layout and orders as in
  * cdsdp_psd_project; order <= 32).  With W_k = mat(H_k x) this is the bound

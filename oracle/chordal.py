@@ -4,7 +4,7 @@ Test infrastructure only.  Nothing in the product path (the CUDA library, its
 binding, or bench.py's timed arms) may import this module.
 
 Follows Section 2.1 (chordal graphs, maximal cliques, chordal extension) and
-the data-preprocessing step of Algorithms 1-3 (Section 6.1.1: chordal
+the data-preprocessing step of Algorithms 1-3 (Section 7.1.1: chordal
 extension from a minimum-degree elimination, maximal cliques read off it).
 
 Canonical rules (the paper does not fix them; the CUDA library's host setup

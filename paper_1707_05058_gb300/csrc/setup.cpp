@@ -1,5 +1,5 @@
 // Host data preprocessing of Algorithms 1-3 (arXiv 1707.05058): aggregate
-// pattern (Section 2.1), chordal extension and maximal cliques (Section 6.1.1),
+// pattern (Section 2.1), chordal extension and maximal cliques (Section 7.1.1),
 // entry selectors H_k and D = sum_k H_k^T H_k (Section 4), the cached
 // inverses of A D^-1 A^T (Eq. ADMMprimalFatorization) and of
 // I + A (I + D/2)^-1 A^T (Eq. HSDEFactorizationFinal), and zeta_hat

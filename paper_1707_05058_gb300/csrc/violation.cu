@@ -1,4 +1,4 @@
-// PSD-violation measure of Section 6.1.3 (Eq. PSD-violation) of arXiv 1707.05058:
+// PSD-violation measure of Section 7.2 (Eq. PSD-violation) of arXiv 1707.05058:
 //   alpha = -min{0, lambda_min[mat(H_1 x)], ..., lambda_min[mat(H_p x)]}
 // over a batch of lower-packed blocks, in one kernel: one warp per block runs
 // the Jacobi eigensolver of jacobi.cuh, each thread block writes its minimum

@@ -8,7 +8,7 @@ given as 0-based lower-triangle triplets (row >= col).  A_i is the symmetric
 matrix whose lower triangle holds the listed values.  Off-diagonal entries
 count twice in <A_i, X>.
 
-The random families follow the block-arrow recipe of Section 6.3 (a strictly
+The random families follow the block-arrow recipe of Section 7.4 (a strictly
 feasible X0 gives b, a strictly feasible (y0, Z0) gives C) with N(0,1) draws
 instead of the paper's U(0,1).  Every random value is rounded to float32 and
 stored as float64, so float32 and float64 consumers read identical numbers.
@@ -126,7 +126,7 @@ def _bernoulli_positions(rng, total, density):
 
 
 def block_arrow(l, d, h, m, seed, name=None, density=None):
-    """Random block-arrow SDP (Section 6.3 recipe, N(0,1) draws): every A_i is
+    """Random block-arrow SDP (Section 7.4 recipe, N(0,1) draws): every A_i is
     dense on the lower block-arrow pattern, or, with `density`, each lower
     pattern entry of each A_i is nonzero with that probability."""
     rng = np.random.default_rng(seed)

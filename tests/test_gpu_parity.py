@@ -135,7 +135,7 @@ def test_psd_projection_eigenpairs(lib, torch_cuda):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_psd_violation_kernel(lib, torch_cuda, prec):
-    """alpha = -min(0, min_k lambda_min(W_k)) (Section 6.1.3, Eq. PSD-violation)
+    """alpha = -min(0, min_k lambda_min(W_k)) (Section 7.2, Eq. PSD-violation)
     against LAPACK eigenvalues, over 2000 blocks of mixed order (many thread
     blocks, so the last-block reduction is exercised), and for all-PSD input."""
     torch = torch_cuda

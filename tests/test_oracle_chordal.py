@@ -73,7 +73,7 @@ def test_selector_example_section_2_2():
 
 @pytest.mark.parametrize("l,d,h", [(5, 10, 5), (3, 4, 2), (7, 3, 6)])
 def test_block_arrow_closed_form(l, d, h):
-    """Section 6.3: the block-arrow pattern is chordal with l maximal cliques
+    """Section 7.4: the block-arrow pattern is chordal with l maximal cliques
     of size d + h (block k plus the arrow head)."""
     rows, cols = W._lower_pairs_block_arrow(l, d, h)
     cl, lower, nfill, is_chordal = chordal.chordal_decomposition(l * d + h, [(rows, cols)])
