@@ -39,6 +39,10 @@ sys.path.insert(0, ROOT)
 METRIC = "ADMM iters/s & time-to-1e-4 (FP32 batched vs FP64 plain, 1 GB300); clique-proj GFLOP/s"
 WORKLOAD = "banded_n2000_w10_m500"
 SM_COUNT = 152
+# DRAM bytes of one launch of the dominant kernel (k_project_primal<float,12> on the
+# banded workload) from the ncu capture summarised under profiles/ (10.333184 MB
+# read + 2.304 KB written); to be re-taken whenever that kernel changes.
+KERNEL_TRAFFIC_BYTES = 10333184 + 2304
 FP32_LANES_PER_SM = 128
 
 
@@ -380,7 +384,9 @@ def main():
             "clique_proj_gflops": gflops,
             "setup_ms": setup_s * 1e3,
             "roofline": {"bound": "alu", "achieved": gflops / 1e3, "peak": peak_fp32, "unit": "TFLOP/s",
-                         "frac": gflops / 1e3 / peak_fp32, "traffic": None,
+                         "frac": gflops / 1e3 / peak_fp32, "traffic": KERNEL_TRAFFIC_BYTES,
+                         "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one warm-started launch, "
+                                           "ncu full capture (cold caches), profiles/k_project_primal_banded_n2000_fp32.md",
                          "kernel": "k_project_primal<float,12>",
                          "peak_note": f"FP32 FMA peak derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x sampled SM clock",
                          "flops_per_launch": flops_per_launch, "launch_ms": proj_s_per_launch * 1e3},
