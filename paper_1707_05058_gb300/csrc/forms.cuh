@@ -65,7 +65,7 @@ __device__ void finish_dual_block(const Dev& d, const FinishArgs& fa) {
     __shared__ double sh[32 * 5];
     const int cols[5] = {0, 1, 2, 3, 5};
     double s[5];
-    sum_cols<5>(d.part, d.p, cols, s, sh);
+    sum_cols<5>(d.part, fa.npart, cols, s, sh);
     const double cx = sum_col(d.parte, fa.nbe, 0, sh);
     const double by = sum_col(d.partr, fa.nbr, 0, sh);
     if (threadIdx.x == 0) {
@@ -381,7 +381,7 @@ __device__ void finish_hsde_block(const Dev& d, const FinishArgs& fa) {
     const int nbe = fa.nbe, nbr = fa.nbr;
     const int cols6[6] = {0, 1, 2, 3, 4, 5}, cols2[2] = {0, 1};
     double s[6], pe[2], pr[2];
-    sum_cols<6>(d.part, d.p, cols6, s, sh);
+    sum_cols<6>(d.part, fa.npart, cols6, s, sh);
     sum_cols<2>(d.parte, nbe, cols2, pe, sh);
     sum_cols<2>(d.partr, nbr, cols2, pr, sh);
     const double rd2 = pe[0], cux = pe[1], rp2 = pr[0], buy = pr[1];

@@ -106,6 +106,7 @@ struct FinishArgs {
     double mu, nu;       // adaptive penalty (Section 7.1.2): factor and balance ratio
     int adapt_every;     // 0: fixed rho; N: apply the rule after every N-th iteration
     int nbe, nbr;        // rows of the per-block partial tables to reduce
+    int npart;           // rows of the clique partial table written this iteration
     int enabled;         // 0: this launch does not finish the iteration
     int use_cond;        // 1: inside the graph while loop (set its condition)
     cudaGraphConditionalHandle hnd;

@@ -82,7 +82,7 @@ __device__ __forceinline__ void finish_primal_block(const Dev& d, const FinishAr
     __shared__ double sh[32 * 6];
     const int cols[6] = {0, 1, 2, 3, 4, 5};
     double s[6];
-    sum_cols<6>(d.part, d.p, cols, s, sh);
+    sum_cols<6>(d.part, fa.npart, cols, s, sh);
     const double cx = s[5];
     const double by = sum_col(d.partr, fa.nbr, 0, sh);
     if (threadIdx.x == 0) {

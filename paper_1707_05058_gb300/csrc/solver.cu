@@ -288,6 +288,14 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
     fa.adapt_every = o.adaptive_rho;
     fa.nbe = GE;
     fa.nbr = GR;
+    // rows of the clique partial table written this iteration: one per block of
+    // every projection launch (and, for Algorithm 2, of the v/lambda kernel)
+    int prow = 0;
+    for (int c = 0; c < kNumClasses; ++c) {
+        const int nl = h->cls_off[c + 1] - h->cls_off[c];
+        if (nl > 0) prow += proj_launch_grid(c, nl, sizeof(T) == 4);
+    }
+    fa.npart = std::min(d.p, form == 1 ? std::max(prow, PG) : prow);
     fa.enabled = 1;
     fa.use_cond = use_cond;
     fa.hnd = hnd;
