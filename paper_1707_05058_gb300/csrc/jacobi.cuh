@@ -429,19 +429,21 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
             hx[e] = T(0);
             if (f < npk) {
                 const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
-                const int ent = d.gmap[off + f];
+                // read-only loads (__ldg): free to move past this kernel's stores
+                const int ent = __ldg(d.gmap + off + f);
+                const bool own = __ldg(d.owner + off + f) != 0;
                 double xe;
                 if (pa.x_ready) {
                     xe = d.x[ent];
                 } else {
                     double aty = 0.0;
-                    const int q1 = d.at_ptr[ent + 1];
-#pragma unroll 4
-                    for (int q = d.at_ptr[ent]; q < q1; ++q) aty += d.at_val[q] * d.y[d.at_col[q]];
-                    xe = d.t[ent] - d.dinv[ent] * aty;
-                    if (d.owner[off + f]) d.x[ent] = xe;
+                    const int q0 = __ldg(d.at_ptr + ent), q1 = __ldg(d.at_ptr + ent + 1);
+#pragma unroll 8
+                    for (int q = q0; q < q1; ++q) aty += __ldg(d.at_val + q) * __ldg(d.y + __ldg(d.at_col + q));
+                    xe = __ldg(d.t + ent) - __ldg(d.dinv + ent) * aty;
+                    if (own) d.x[ent] = xe;
                 }
-                if (d.owner[off + f]) cx += d.wgt[ent] * d.c[ent] * xe;
+                if (own) cx += __ldg(d.wgt + ent) * __ldg(d.c + ent) * xe;
                 hx[e] = T(xe);
                 const T w = hx[e] - lam[off + f] * irho;
                 if (d.wstore) {
