@@ -268,6 +268,7 @@ struct CTAJacobiMid {
     __device__ __forceinline__ static int at(int r, int c) { return phys(r) * LDA + phys(c); }
     __device__ __forceinline__ static int lower(int r, int c) { return r >= c ? at(r, c) : at(c, r); }
 
+    T* base; // four S x LDA buffers: A (two), V (two)
     T* X;    // A, current
     T* Y;    // A, next
     T* V;    // eigenvectors, current (column = storage index)
@@ -284,8 +285,9 @@ struct CTAJacobiMid {
     // entries of a block sit at source + {0, K, K LDA, K LDA + K}.
     struct Plan { unsigned w0[NPT], w1[NPT], w2[NPT]; };
 
-    __device__ __forceinline__ void bind(unsigned char* base) {
-        X = reinterpret_cast<T*>(base);
+    __device__ __forceinline__ void bind(unsigned char* smem_base) {
+        base = reinterpret_cast<T*>(smem_base);
+        X = base;
         Y = X + BUF;
         V = Y + BUF;
         Vn = V + BUF;
@@ -371,11 +373,19 @@ struct CTAJacobiMid {
         return r;
     }
 
-    __device__ void round(T tol, const Plan& P) {
+    // One round from buffer B into buffer 1 - B.  The buffers sit at fixed
+    // offsets from the block's shared memory, so every access is a register
+    // offset plus a constant.
+    template <int B>
+    __device__ __forceinline__ void round_b(T tol, const Plan& P) {
         const int tid = threadIdx.x;
+        const T* Xc = base + B * BUF;
+        T* Yn = base + (1 - B) * BUF;
+        const T* Vc = base + (2 + B) * BUF;
+        T* Vw = base + (3 - B) * BUF;
         if (tid < K) {  // rotation of pair tid (Rutishauser form)
-            const T app = X[tid * LDA + tid], aqq = X[(K + tid) * LDA + K + tid];
-            const T apq = X[(K + tid) * LDA + tid];
+            const T app = Xc[tid * LDA + tid], aqq = Xc[(K + tid) * LDA + K + tid];
+            const T apq = Xc[(K + tid) * LDA + tid];
             T c = T(1), sn = T(0), tq = T(0);
             if (fabs(apq) > tol) {
                 const T zeta = T(0.5) * (aqq - app);
@@ -399,33 +409,40 @@ struct CTAJacobiMid {
             const int I = (meta >> 2) & 31, J = meta >> 7, src = P.w0[j] & 0xffff;
             const int d0 = P.w0[j] >> 16, d1 = P.w1[j] & 0xffff, d2 = P.w1[j] >> 16, d3 = P.w2[j] & 0xffff;
             if (kind == 3) {
-                const T v00 = V[src], v01 = V[src + K], v10 = V[src + K * LDA], v11 = V[src + K * LDA + K];
+                const T v00 = Vc[src], v01 = Vc[src + K], v10 = Vc[src + K * LDA], v11 = Vc[src + K * LDA + K];
                 const T2 r = rot[J];
-                Vn[d0] = r.x * v00 - r.y * v01;
-                Vn[d2] = r.y * v00 + r.x * v01;
-                Vn[d1] = r.x * v10 - r.y * v11;
-                Vn[d3] = r.y * v10 + r.x * v11;
+                Vw[d0] = r.x * v00 - r.y * v01;
+                Vw[d2] = r.y * v00 + r.x * v01;
+                Vw[d1] = r.x * v10 - r.y * v11;
+                Vw[d3] = r.y * v10 + r.x * v11;
             } else if (kind == 1) {
                 const T t = ta[I];
                 const bool rotated = t != T(0) || rot[I].y != T(0);
-                const T b00 = X[src], b10 = X[src + K * LDA], b11 = X[src + K * LDA + K];
-                Y[d0] = b00 - t;
-                Y[d1] = rotated ? T(0) : b10;
-                Y[d3] = b11 + t;
+                const T b00 = Xc[src], b10 = Xc[src + K * LDA], b11 = Xc[src + K * LDA + K];
+                Yn[d0] = b00 - t;
+                Yn[d1] = rotated ? T(0) : b10;
+                Yn[d3] = b11 + t;
             } else {
-                const T b00 = X[src], b01 = X[src + K], b10 = X[src + K * LDA], b11 = X[src + K * LDA + K];
+                const T b00 = Xc[src], b01 = Xc[src + K], b10 = Xc[src + K * LDA], b11 = Xc[src + K * LDA + K];
                 const T2 ri = rot[I], rj = rot[J];
                 const T q00 = ri.x * b00 - ri.y * b10, q10 = ri.y * b00 + ri.x * b10;
                 const T q01 = ri.x * b01 - ri.y * b11, q11 = ri.y * b01 + ri.x * b11;
-                Y[d0] = rj.x * q00 - rj.y * q01;
-                Y[d2] = rj.y * q00 + rj.x * q01;
-                Y[d1] = rj.x * q10 - rj.y * q11;
-                Y[d3] = rj.y * q10 + rj.x * q11;
+                Yn[d0] = rj.x * q00 - rj.y * q01;
+                Yn[d2] = rj.y * q00 + rj.x * q01;
+                Yn[d1] = rj.x * q10 - rj.y * q11;
+                Yn[d3] = rj.y * q10 + rj.x * q11;
             }
         }
         __syncthreads();
-        T* t = X; X = Y; Y = t;
-        t = V; V = Vn; Vn = t;
+    }
+    // one sweep (R rounds, R odd) starting in buffer B; it ends in 1 - B
+    template <int B>
+    __device__ void sweep(T tol, const Plan& P) {
+        for (int r = 0; r + 1 < R; r += 2) {
+            round_b<B>(tol, P);
+            round_b<1 - B>(tol, P);
+        }
+        round_b<B>(tol, P);
     }
 
     // V <- identity (cold) or keep the loaded basis (warm), then sweep; each
@@ -434,19 +451,26 @@ struct CTAJacobiMid {
         if (!v_preset)
             for (int i = threadIdx.x; i < BUF; i += blockDim.x) V[i] = ((i / LDA) == (i % LDA)) ? T(1) : T(0);
         __syncthreads();
+        // buffers 0/1 hold A and 2/3 V; X and V are buffers cur and 2 + cur
         Plan P;
         plan(P);
         const T noise = tol * T(2 * S);
         T prev = T(3.0e38);
-        int sw = 0;
+        int sw = 0, cur = (X == base) ? 0 : 1;
         while (sw < max_sweeps) {
+            X = base + cur * BUF;
             const T off = off_max(P);
             if (off <= tol) break;
             if (off <= noise && off > T(0.5) * prev) break;
             prev = off;
             ++sw;
-            for (int r = 0; r < R; ++r) round(tol, P);
+            if (cur == 0) sweep<0>(tol, P); else sweep<1>(tol, P);
+            cur ^= 1;
         }
+        X = base + cur * BUF;
+        Y = base + (1 - cur) * BUF;
+        V = base + (2 + cur) * BUF;
+        Vn = base + (3 - cur) * BUF;
         return sw;
     }
 

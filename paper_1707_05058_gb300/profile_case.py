@@ -29,6 +29,8 @@ def main(argv=None):
     ap.add_argument("--form", default="primal", choices=["primal", "dual", "hsde"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--x-update", type=int, default=0, choices=[0, 1, 2],
+                    help="Algorithm 1: 0 automatic, 1 inside the projection gather, 2 separate kernel")
     args = ap.parse_args(argv)
 
     import torch
@@ -43,7 +45,7 @@ def main(argv=None):
         prob = workloads.workload(1 if args.workload == "banded" else 0)
     P = cdsdp.Problem(prob).bind(max_iter=args.iters)
     out = P.solve(args.form, eps=0.0, max_iter=args.iters, precision=args.precision, use_graph=0,
-                  check_every=args.iters, outputs=False)
+                  check_every=args.iters, outputs=False, x_update=args.x_update)
     torch.cuda.synchronize()
     print(f"{args.workload} {args.form} {args.precision}: {out['iters']} iterations, status {out['status']}")
 
