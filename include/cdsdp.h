@@ -87,9 +87,9 @@ typedef struct {
     double rho_mu;         /* >= 1; the paper's default 2                              */
     double rho_nu;         /* >= 1; the paper's default 10                             */
     int x_update;          /* Algorithm 1, where x = D^-1 (bhat - A^T y) is formed:
-                              0 = automatic (inside the projection's gather while A is
-                              small enough to stay in L2, else 2); 1 = inside the
-                              gather; 2 = a separate kernel over the A^T rows     */
+                              0 = default (2); 1 = inside the projection's gather,
+                              once per clique holding the entry; 2 = a separate
+                              kernel over the A^T rows, once per entry             */
 } cdsdp_opts;
 
 typedef struct {
@@ -109,8 +109,8 @@ typedef struct {
 /* Fill `o` with defaults: eps 1e-4, max_iter 2000, rho 1, FP32 projection,
  * graph on, check_every 50, 30 Jacobi sweeps, warm start with a cold start every
  * 16 iterations, no profiling, per-component stopping, fixed rho (adaptive
- * rule off; rho_mu 2, rho_nu 10 when switched on), automatic x-update
- * placement. */
+ * rule off; rho_mu 2, rho_nu 10 when switched on), x formed by its own
+ * kernel. */
 void cdsdp_default_opts(cdsdp_opts* o);
 
 /* Data preprocessing of Algorithms 1-3 (host only, no GPU call):

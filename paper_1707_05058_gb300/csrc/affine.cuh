@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(ETHREADS) k_scatter(Dev d, const T* __restrict
 // x_e = t_e - dinv_e (A^T y)_e  (Appendix A, Eq. KKTflops_s1), with the
 // per-block partial sum of <c, x> (weighted) in parte[block][0].
 __global__ void __launch_bounds__(ETHREADS) k_xupd(Dev d, const double* __restrict__ t, const double* __restrict__ y,
-                                                   double* __restrict__ x, int G) {
+                                                   double* __restrict__ x, int G, int want_cx) {
     __shared__ double sh[32];
     if (stopped(d)) return;
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G, lig = threadIdx.x & (G - 1);
@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(ETHREADS) k_xupd(Dev d, const double* __restri
             cx[0] += d.wgt[e] * d.c[e] * xe;
         }
     }
+    if (!want_cx) return;  // block-uniform
     block_sum<1>(cx, sh);
     if (threadIdx.x == 0) d.parte[blockIdx.x * PART_COLS + 0] = cx[0];
 }

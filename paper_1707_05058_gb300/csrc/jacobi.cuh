@@ -464,7 +464,9 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
         jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm);
         if (pa.warm_start) jac.store_basis(vc + d.vv_off[k], s, lane);
         jac.prepare_rebuild(lane);
-        double p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0;
+        // per-clique sums of the stopping test in the clique state's precision
+        // (float32 values; the sums over cliques are float64)
+        T p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0;
 #pragma unroll
         for (int e = 0; e < J::MAXE; ++e) {
             const int f = lane + 32 * e;
@@ -476,16 +478,17 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
                 const T ln = lm + rho_t * (xn - hx[e]);
                 xk[off + f] = xn;
                 lam[off + f] = ln;
-                const double w = (a == b) ? 1.0 : 2.0;
-                const double dc = double(xn) - double(hx[e]), dx = double(xn) - double(xo);
+                const T w = (a == b) ? T(1) : T(2);
+                const T dc = xn - hx[e], dx = xn - xo;
                 p0 += w * dc * dc;
-                p1 += w * double(xn) * double(xn);
-                p2 += w * double(hx[e]) * double(hx[e]);
+                p1 += w * xn * xn;
+                p2 += w * hx[e] * hx[e];
                 p3 += w * dx * dx;
-                p4 += w * double(ln) * double(ln);
+                p4 += w * ln * ln;
             }
         }
-        const double q[6] = {warp_sum(p0), warp_sum(p1), warp_sum(p2), warp_sum(p3), warp_sum(p4), cxk};
+        const double q[6] = {double(warp_sum(p0)), double(warp_sum(p1)), double(warp_sum(p2)),
+                             double(warp_sum(p3)), double(warp_sum(p4)), cxk};
         if (d.comp_mode) {  // per-clique row, reduced per component
             if (lane == 0)
 #pragma unroll

@@ -656,20 +656,31 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
         if (FORM != 3 && pa.warm_start) jac.store_basis(vc + d.vv_off[k], s);
         jac.prepare_rebuild();
         double p[6] = {0, 0, 0, 0, 0, 0};
+        T pf[5] = {0, 0, 0, 0, 0};  // float32 form of Algorithm 1: per-thread sums in float
         for (int f = tid; f < npk; f += blockDim.x) {
             const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
             const T xn = jac.rebuild(a, b, s);
             const double w = (a == b) ? 1.0 : 2.0;
             if (FORM == 0) {
                 const double hx = pa.x_ready ? d.x[d.gmap[off + f]] : d.q[d.gmap[off + f]];
-                const double lm = c1[off + f];
-                const double xo = c0[off + f];
-                const double ln = lm + rho * (double(xn) - hx);
-                c0[off + f] = xn;
-                c1[off + f] = T(ln);
-                const double dc = double(xn) - hx, dx = double(xn) - xo;
-                p[0] += w * dc * dc; p[1] += w * double(xn) * double(xn); p[2] += w * hx * hx;
-                p[3] += w * dx * dx; p[4] += w * ln * ln;
+                if constexpr (sizeof(T) == 4) {  // clique state in float32: its sums too
+                    const T hxt = T(hx), lm = c1[off + f], xo = c0[off + f];
+                    const T ln = lm + T(rho) * (xn - hxt);
+                    c0[off + f] = xn;
+                    c1[off + f] = ln;
+                    const T wt = T(w), dc = xn - hxt, dx = xn - xo;
+                    pf[0] += wt * dc * dc; pf[1] += wt * xn * xn; pf[2] += wt * hxt * hxt;
+                    pf[3] += wt * dx * dx; pf[4] += wt * ln * ln;
+                } else {
+                    const double lm = c1[off + f];
+                    const double xo = c0[off + f];
+                    const double ln = lm + rho * (double(xn) - hx);
+                    c0[off + f] = xn;
+                    c1[off + f] = T(ln);
+                    const double dc = double(xn) - hx, dx = double(xn) - xo;
+                    p[0] += w * dc * dc; p[1] += w * double(xn) * double(xn); p[2] += w * hx * hx;
+                    p[3] += w * dx * dx; p[4] += w * ln * ln;
+                }
             } else if (FORM == 1) {
                 const double dz = double(xn) - double(c0[off + f]);
                 c0[off + f] = xn;
@@ -694,6 +705,8 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
             }
         }
         if (FORM != 3) {
+            if (FORM == 0 && sizeof(T) == 4)
+                for (int c = 0; c < 5; ++c) p[c] = double(pf[c]);
             cta_sum<6>(p, shr);
             if (FORM != 2) p[5] = cxk;
             if (tid == 0 && d.comp_mode) {  // per-clique row, reduced per component

@@ -54,10 +54,9 @@ struct cdsdp {
     // launch shapes: grids of the pattern-entry / constraint-row kernels, lanes
     // per entry for scatters (Gs) and A^T rows (Ga), threads per A row (TPR)
     // and per row of the cached inverse (TPRM)
-    int GE = 1, GR = 1, Gs = 1, Ga = 1, TPR = 32, TPRM = 32;
+    int GE = 1, GR = 1, Gs = 1, Ga = 1, Gx = 1, TPR = 32, TPRM = 32;
     // Algorithm 1: compute x = t - D^-1 A^T y in its own kernel (coalesced
-    // A^T rows) rather than inside the projection's gather; the automatic
-    // choice when A is too large to stay in L2 between iterations
+    // A^T rows) rather than inside the projection's gather (the default)
     bool x_split_auto = false;
     bool x_split = false;  // choice of the current solve
     // cached graph of a whole solve
@@ -233,8 +232,11 @@ void make_dev(cdsdp* h) {
     const double avg_a = d.m ? double(hp.a_col.size()) / d.m : 1.0;
     h->Gs = pow2_clamp(avg_sc / 2.0, 1, 32);
     h->Ga = pow2_clamp(std::max(avg_at, avg_sc) / 3.0, 1, 32);
+    h->Gx = pow2_clamp(avg_at / 6.0, 1, 32);  // lanes per A^T row in the separate x-update
     h->TPR = pow2_clamp(avg_a / 4.0, 32, RTHREADS);
-    h->x_split_auto = (double)hp.a_col.size() * 12.0 > 48.0 * (1 << 20);
+    // The separate kernel forms each x_e once (in float64, whose throughput is
+    // low on this GPU); inside the gather it is formed once per clique holding e.
+    h->x_split_auto = true;
     h->x_split = h->x_split_auto;
     int max_mc = 0;
     for (int c = 0; c < hp.ncomp; ++c) max_mc = std::max(max_mc, hp.crow_ptr[c + 1] - hp.crow_ptr[c]);
@@ -308,7 +310,7 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0, 1.0, 1.0, 1, 1, d.dinv, d.t, 1, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, 0, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
-        if (h->x_split) k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
+        if (h->x_split) k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Gx, 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
         if ((e = launch_projection<T>(h, 0, o, fin, st)) != cudaSuccess) return e;
@@ -323,7 +325,7 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0, 0, 1, d.dinv, d.t, 1, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0, 1, d.g, h->TPR);
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
-        k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga);
+        k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga, 1);
         k_vlam_dual<T><<<PG, 128, 0, st>>>(d, fin);
         if (d.comp_mode) k_finish_components<<<d.ncomp, 256, 0, st>>>(d, 1, fa);
     } else {  // Algorithm 3; gamma/tau/kappa in sigma21's last block, stopping test in row_update's
