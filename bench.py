@@ -40,9 +40,10 @@ METRIC = "ADMM iters/s & time-to-1e-4 (FP32 batched vs FP64 plain, 1 GB300); cli
 WORKLOAD = "banded_n2000_w10_m500"
 SM_COUNT = 152
 # DRAM bytes of one launch of the dominant kernel (k_project_primal<float,12> on the
-# banded workload) from the ncu capture summarised under profiles/ (10.333184 MB
-# read + 2.304 KB written); to be re-taken whenever that kernel changes.
-KERNEL_TRAFFIC_BYTES = 10333184 + 2304
+# banded workload, x formed by its own kernel) from the ncu capture summarised
+# under profiles/ (3.359488 MB read, 0 written); to be re-taken whenever that
+# kernel changes.
+KERNEL_TRAFFIC_BYTES = 3359488
 FP32_LANES_PER_SM = 128
 
 
