@@ -180,12 +180,13 @@ def _batched(cdsdp, workloads, torch, flush, stream, rank=0, world=1):
         e1.synchronize()
         return e0.elapsed_time(e1), out
 
-    kw = dict(eps=1e-4, max_iter=10000, precision="fp32", use_graph=1, adaptive_rho=1)
+    tuned, cand_ms = P.autotune("primal", iters=20, precision="fp32", adaptive_rho=1)
+    kw = dict(eps=1e-4, max_iter=10000, precision="fp32", use_graph=1, adaptive_rho=1, **tuned)
     P.solve("primal", outputs=False, **kw)  # warm-up (graph build)
     ms, out = timed(**kw)
     it, st, _ = P.component_results()
-    ms50, _ = timed(eps=0.0, max_iter=50, precision="fp32", use_graph=1, adaptive_rho=1)
-    P.solve("primal", outputs=False, eps=0.0, max_iter=20, precision="fp32", profile=1, adaptive_rho=1)
+    ms50, _ = timed(eps=0.0, max_iter=50, precision="fp32", use_graph=1, adaptive_rho=1, **tuned)
+    P.solve("primal", outputs=False, eps=0.0, max_iter=20, precision="fp32", profile=1, adaptive_rho=1, **tuned)
     proj_ms, launches, iter_ms = P.profile()
     ms64, _ = timed(eps=0.0, max_iter=10, precision="fp64", use_graph=0, check_every=10, warm_start=0, adaptive_rho=1)
     sizes = np.diff(P.cliques()[0]).astype(np.float64)
@@ -201,6 +202,7 @@ def _batched(cdsdp, workloads, torch, flush, stream, rank=0, world=1):
             "fp32_graph_ms_per_iter_all_active": ms50 / 50,
             "fp64_plain_ms_per_iter_all_active": ms64 / 10,
             "per_iter_speedup_fp32_graph_vs_fp64_plain": (ms64 / 10) / (ms50 / 50),
+            "schedule": tuned, "autotune_ms_per_iter": cand_ms,
             "clique_proj_gflops": gflops, "proj_ms_per_iter": proj_ms / launches,
             "proj_flops_per_iter_nominal": flops}
 

@@ -90,6 +90,8 @@ typedef struct {
                               0 = default (2); 1 = inside the projection's gather,
                               once per clique holding the entry; 2 = a separate
                               kernel over the A^T rows, once per entry             */
+    int proj_warps_div;    /* warp-per-clique projections (orders <= 32): warps per
+                              block = the kernel's maximum / this (1, 2 or 4)       */
 } cdsdp_opts;
 
 typedef struct {
@@ -208,6 +210,19 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream,
  *   iter_ms       summed duration of whole iterations
  * Errors: CDSDP_ERR_STATE when the last solve was not profiled. */
 int cdsdp_profile(const cdsdp* h, double* proj_ms, int* proj_launches, double* iter_ms);
+
+/* Schedule autotuner (not in the paper; the launch schedule is a GPU choice):
+ * times `iters` iterations (no early stop; graph or not as in opts) of `form`
+ * for each candidate schedule and writes into *tuned a copy of *opts (the
+ * defaults when opts is NULL) with the fastest candidate's fields:
+ *   x_update        1 or 2 (Algorithm 1 only)
+ *   proj_warps_div  1, 2 or 4
+ *   warm_start      16 or 64 (only when opts->warm_start > 0)
+ * ms_per_iter[] receives each candidate's device time per iteration in
+ * candidate order (at most 12 entries; may be NULL), *n_cand their number (may
+ * be NULL).  Overwrites the last solve's state.  Errors as cdsdp_solve. */
+int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* stream, cdsdp_opts* tuned,
+                   double* ms_per_iter, int* n_cand);
 
 /* Copy the last solve's results again (same meaning as in cdsdp_solve). */
 int cdsdp_results(cdsdp* h, void* stream, double* X, double* y, double* Z, double* hist, double* cert);

@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("jacobi_max_sweeps", ctypes.c_int), ("warm_start", ctypes.c_int), ("profile", ctypes.c_int),
                 ("component_stop", ctypes.c_int), ("adaptive_rho", ctypes.c_int), ("rho_mu", ctypes.c_double),
-                ("rho_nu", ctypes.c_double), ("x_update", ctypes.c_int)]
+                ("rho_nu", ctypes.c_double), ("x_update", ctypes.c_int), ("proj_warps_div", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -56,6 +56,8 @@ _lib.cdsdp_cliques.argtypes = [_vp, _i32p, _i32p]
 _lib.cdsdp_pattern.argtypes = [_vp, _i32p, _i32p]
 _lib.cdsdp_components.argtypes = [_vp, _i32p, _i32p]
 _lib.cdsdp_component_results.argtypes = [_vp, _vp, _i32p, _i32p, _f64p]
+_lib.cdsdp_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_int, _vp, ctypes.POINTER(Opts),
+                               _f64p, _i32p]
 _lib.cdsdp_workspace_bytes.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
 _lib.cdsdp_bind.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.c_int, _vp]
 _lib.cdsdp_solve.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, _f64p, _f64p, _f64p, _f64p, _i32p, _f64p]
@@ -84,7 +86,7 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile", "cdsdp_psd_violation_scratch_bytes",
             "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc", "cdsdp_grad_workspace_bytes",
             "cdsdp_unrolled_forward", "cdsdp_unrolled_backward", "cdsdp_components",
-            "cdsdp_component_results"]
+            "cdsdp_component_results", "cdsdp_autotune"]
 
 
 class CdsdpError(RuntimeError):
@@ -229,6 +231,22 @@ class Problem:
             elif st == DUAL_INFEASIBLE:
                 out["cert"] = cert[:nz]
         return out
+
+    def autotune(self, form="primal", iters=50, stream=None, **opts):
+        """Fastest launch schedule for this problem: returns (options dict to
+        pass to solve, list of ms per iteration of every candidate)."""
+        o = default_opts(**opts)
+        if self.workspace is None or self.max_iter < iters:
+            self.bind(max(iters, self.max_iter or 0))
+        tuned = Opts()
+        ms = np.zeros(12)
+        n = ctypes.c_int(0)
+        st = _lib.cdsdp_autotune(self._h, FORMS.get(form, form), ctypes.byref(o), int(iters), _stream_ptr(stream),
+                                 ctypes.byref(tuned), _ptr(ms, ctypes.c_double), ctypes.byref(n))
+        if st < 0:
+            raise CdsdpError(st, "cdsdp_autotune")
+        return ({"x_update": tuned.x_update, "proj_warps_div": tuned.proj_warps_div, "warm_start": tuned.warm_start},
+                ms[:n.value].tolist())
 
     def profile(self):
         """(projection ms summed, projection launches, iteration ms summed) of

@@ -119,6 +119,7 @@ struct ProjArgs {
     int warm_start;      // reuse the previous iteration's eigenvectors
     int restart;         // cold start every `restart` iterations
     int row_off;         // first row of this launch in the per-block partial table
+    int warps_div;       // warp-per-clique launches: warps per block = the maximum / warps_div
     int x_ready;         // Algorithm 1: x was computed by a separate kernel this
                          // iteration (read it) instead of inside the gather
 };

@@ -13,7 +13,7 @@ cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, cons
                         const FinishArgs& fa, cudaStream_t st) {
     if (nlist <= 0) return cudaSuccess;
     constexpr int MW = proj_max_warps(S, sizeof(T) == 4);
-    const ProjShape sh = proj_shape(nlist, MW);
+    const ProjShape sh = proj_shape(nlist, std::max(1, MW / std::max(1, pa_in.warps_div)));
     const size_t smem = (size_t)sh.wpb * BLJacobi<T, S>::bytes;
     const size_t smem_max = (size_t)MW * BLJacobi<T, S>::bytes;
     ProjArgs pa = pa_in;

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace cdsdp_dev {
@@ -105,10 +107,10 @@ inline cudaError_t launch_proj_f64(int form, int cls, const Dev& d, const int* l
                                    : launch_proj_f64_large(form, cls, d, list, nlist, pa, fa, st);
 }
 // grid of one projection launch (rows it writes in the partial table)
-inline int proj_launch_grid(int cls, int nlist, bool fp32) {
+inline int proj_launch_grid(int cls, int nlist, bool fp32, int warps_div = 1) {
     const int S = kProjClasses[cls];
     if (S > kMaxWarpOrder) return proj_cta_grid(nlist);
-    return proj_shape(nlist, proj_max_warps(S, fp32)).grid;
+    return proj_shape(nlist, std::max(1, proj_max_warps(S, fp32) / std::max(1, warps_div))).grid;
 }
 inline cudaError_t launch_proj_standalone_f32(int cls, int p, const int* off, const int* size, const void* W, void* X,
                                               void* eig, const int* voff, void* V, const int* vvoff, double tolrel,

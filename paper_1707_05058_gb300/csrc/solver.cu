@@ -262,6 +262,7 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
         if (h->cls_off[c + 1] > h->cls_off[c]) last = c;
     cudaError_t e = cudaSuccess;
     pa.row_off = 0;
+    pa.warps_div = o.proj_warps_div;
     pa.x_ready = (form == 0 && h->x_split) ? 1 : 0;
     for (int c = 0; c < kNumClasses && e == cudaSuccess; ++c) {
         const int* list = bl + h->cls_off[c];
@@ -271,7 +272,7 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
         f.enabled = (c == last) ? fa.enabled : 0;  // the last launch finishes the iteration
         e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, pa, f, st)
                            : launch_proj_f64(form, c, h->dev, list, nl, pa, f, st);
-        pa.row_off += proj_launch_grid(c, nl, sizeof(T) == 4);  // rows of this launch
+        pa.row_off += proj_launch_grid(c, nl, sizeof(T) == 4, pa.warps_div);  // rows of this launch
     }
     return e;
 }
@@ -295,7 +296,7 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
     int prow = 0;
     for (int c = 0; c < kNumClasses; ++c) {
         const int nl = h->cls_off[c + 1] - h->cls_off[c];
-        if (nl > 0) prow += proj_launch_grid(c, nl, sizeof(T) == 4);
+        if (nl > 0) prow += proj_launch_grid(c, nl, sizeof(T) == 4, o.proj_warps_div);
     }
     fa.npart = std::min(d.p, form == 1 ? std::max(prow, PG) : prow);
     fa.enabled = 1;
@@ -357,7 +358,7 @@ bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
     return a.eps == b.eps && a.max_iter == b.max_iter && a.rho == b.rho && a.precision == b.precision &&
            a.jacobi_max_sweeps == b.jacobi_max_sweeps && a.warm_start == b.warm_start &&
            a.component_stop == b.component_stop && a.adaptive_rho == b.adaptive_rho && a.rho_mu == b.rho_mu &&
-           a.rho_nu == b.rho_nu && a.x_update == b.x_update;
+           a.rho_nu == b.rho_nu && a.x_update == b.x_update && a.proj_warps_div == b.proj_warps_div;
 }
 
 void drop_graph(cdsdp* h) {
@@ -408,6 +409,7 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     if (o.component_stop != 0 && o.component_stop != 1) return CDSDP_ERR_ARG;
     if (o.adaptive_rho < 0 || !(o.rho_mu >= 1.0) || !(o.rho_nu >= 1.0)) return CDSDP_ERR_ARG;
     if (o.x_update < 0 || o.x_update > 2) return CDSDP_ERR_ARG;
+    if (o.proj_warps_div != 1 && o.proj_warps_div != 2 && o.proj_warps_div != 4) return CDSDP_ERR_ARG;
     if (o.precision == CDSDP_FP64 && h->hp.max_clique > kMaxOrderF64) return CDSDP_ERR_UNSUPPORTED;
     return CDSDP_SOLVED;
 }
@@ -573,6 +575,7 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->rho_mu = 2.0;
     o->rho_nu = 10.0;
     o->x_update = 0;
+    o->proj_warps_div = 1;
 }
 
 int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
@@ -782,6 +785,61 @@ int cdsdp_results(cdsdp* h, void* stream, double* X, double* y, double* Z, doubl
     if (!h) return CDSDP_ERR_ARG;
     if (!h->ws || h->last_form < 0) return CDSDP_ERR_STATE;
     return copy_results(h, (cudaStream_t)stream, X, y, Z, hist, cert);
+}
+
+int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* stream, cdsdp_opts* tuned,
+                   double* ms_per_iter, int* n_cand) {
+    if (!h || !tuned || iters < 1) return CDSDP_ERR_ARG;
+    if (!h->ws) return CDSDP_ERR_STATE;
+    if (form < 0 || form > 2) return CDSDP_ERR_ARG;
+    cdsdp_opts base;
+    if (opts) base = *opts; else cdsdp_default_opts(&base);
+    base.eps = 0.0;  // fixed number of iterations
+    base.max_iter = std::min(iters, h->ws_max_iter);
+    base.profile = 0;
+    // candidate schedules: x-update placement (Algorithm 1), warps per block of
+    // the warp-per-clique projections, cold-restart interval of the eigensolver
+    std::vector<cdsdp_opts> cand;
+    const int xs[2] = {2, 1}, wd[3] = {1, 2, 4}, rs[2] = {16, 64};
+    for (int xi = 0; xi < (form == 0 ? 2 : 1); ++xi)
+        for (int wi = 0; wi < 3; ++wi)
+            for (int ri = 0; ri < (base.warm_start > 0 ? 2 : 1); ++ri) {
+                cdsdp_opts o = base;
+                o.x_update = xs[xi];
+                o.proj_warps_div = wd[wi];
+                if (base.warm_start > 0) o.warm_start = rs[ri];
+                cand.push_back(o);
+            }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int ibest = 0, rc = CDSDP_SOLVED;
+    for (size_t i = 0; i < cand.size() && rc >= 0; ++i) {
+        rc = cdsdp_solve(h, form, &cand[i], stream, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);  // warm-up
+        if (rc < 0) break;
+        cudaEventRecord(e0, st);
+        rc = cdsdp_solve(h, form, &cand[i], stream, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+        cudaEventRecord(e1, st);
+        if (rc < 0) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / std::max(1, h->last_iters);
+        if (ms_per_iter) ms_per_iter[i] = per;
+        if (per < best) { best = per; ibest = (int)i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc < 0) return rc;
+    *tuned = opts ? *opts : cand[0];
+    if (!opts) cdsdp_default_opts(tuned);
+    tuned->x_update = cand[ibest].x_update;
+    tuned->proj_warps_div = cand[ibest].proj_warps_div;
+    tuned->warm_start = cand[ibest].warm_start;
+    if (n_cand) *n_cand = (int)cand.size();
+    return CDSDP_SOLVED;
 }
 
 int cdsdp_profile(const cdsdp* h, double* proj_ms, int* proj_launches, double* iter_ms) {

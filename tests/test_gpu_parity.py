@@ -401,3 +401,29 @@ def test_x_update_placement_fp64(lib, torch_cuda, x_update, clique):
     np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-8, atol=1e-10)
     Xr = dp.lower_values(ref.X)
     assert np.abs(out["X"] - Xr).max() <= 1e-8 * max(1.0, np.abs(Xr).max())
+
+
+@pytest.mark.parametrize("div", [2, 4])
+def test_projection_warps_per_block_fp64(lib, torch_cuda, div):
+    """Fewer warps per block in the warp-per-clique projection (a schedule
+    choice): the FP64 trajectory still equals the oracle's."""
+    prob = W.banded(120, 6, 30, seed=7, density=0.3)
+    dp = admm.decompose(prob)
+    ref = admm.primal_admm(dp, eps=0.0, max_iter=30)
+    P = lib.Problem(prob).bind(max_iter=30)
+    out = P.solve("primal", eps=0.0, max_iter=30, precision="fp64", proj_warps_div=div)
+    np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("form", ["primal", "dual"])
+def test_autotune_picks_a_candidate_and_keeps_parity(lib, torch_cuda, form):
+    """The schedule autotuner times its candidates and returns one of them;
+    a solve with the tuned schedule still follows the oracle (FP64)."""
+    prob = W.workload(0)
+    dp, ref = _oracle(prob, form, 1e-4, 2000)
+    P = lib.Problem(prob).bind(max_iter=2000)
+    tuned, ms = P.autotune(form, iters=20, precision="fp64")
+    assert len(ms) == (12 if form == "primal" else 6) and all(m > 0 for m in ms)
+    assert tuned["x_update"] in (1, 2) and tuned["proj_warps_div"] in (1, 2, 4) and tuned["warm_start"] in (16, 64)
+    out = P.solve(form, eps=1e-4, max_iter=2000, precision="fp64", **tuned)
+    _assert_trajectory(dp, ref, out)
