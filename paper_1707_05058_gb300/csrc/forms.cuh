@@ -25,23 +25,27 @@ __global__ void __launch_bounds__(128) k_vlam_dual(Dev d, FinishArgs fa) {
         if (frozen_clique(d, k)) continue;  // warp-uniform
         const double rho = rho_clique(d, k);
         const int off = d.pk_off[k], s = d.csize[k], npk = s * (s + 1) / 2;
-        double p0 = 0, p1 = 0, p2 = 0, p3 = 0, cx = 0;
+        // v and lambda are formed in float64 (z + lambda/rho + x cancels) and
+        // stored in T; the per-clique sums of the stopping test are in T
+        T p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+        double cx = 0;
         for (int f = lane; f < npk; f += 32) {
             const int ent = d.gmap[off + f];
             if (d.comp_mode && d.owner[off + f]) cx += d.wgt[ent] * d.c[ent] * d.x[ent];
-            const double zz = z[off + f], ll = lam[off + f];
+            const T zt = z[off + f];
+            const double zz = zt, ll = lam[off + f];
             const T vn = T(zz + ll / rho + d.x[ent]);
             const T ln = T(ll + rho * (zz - double(vn)));
             v[off + f] = vn;
             lam[off + f] = ln;
-            const double w = d.wgt[ent];
-            const double dv = zz - double(vn);
-            p0 += w * dv * dv;
-            p1 += w * zz * zz;
-            p2 += w * double(vn) * double(vn);
-            p3 += w * double(ln) * double(ln);
+            const T wt = T(d.wgt[ent]);
+            const T dv = zt - vn;
+            p0 += wt * dv * dv;
+            p1 += wt * zt * zt;
+            p2 += wt * vn * vn;
+            p3 += wt * ln * ln;
         }
-        const double q[4] = {warp_sum(p0), warp_sum(p1), warp_sum(p2), warp_sum(p3)};
+        const double q[4] = {double(warp_sum(p0)), double(warp_sum(p1)), double(warp_sum(p2)), double(warp_sum(p3))};
         if (d.comp_mode) {  // per-clique row (column 6: <c, x> over the entries the clique owns)
             const double cxk = warp_sum(cx);
             if (lane == 0) {

@@ -543,15 +543,15 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
         jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm);
         if (pa.warm_start) jac.store_basis(vc + d.vv_off[k], s, lane);
         jac.prepare_rebuild(lane);
-        double p0 = 0;
+        T p0 = 0;  // in the clique state's precision; float64 across cliques
         for (int f = lane; f < npk; f += 32) {
             const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
             const T zn = jac.rebuild(a, b, s);
-            const double dz = double(zn) - double(z[off + f]);
+            const T dz = zn - z[off + f];
             z[off + f] = zn;
-            p0 += (a == b ? 1.0 : 2.0) * dz * dz;
+            p0 += (a == b ? T(1) : T(2)) * dz * dz;
         }
-        const double q0 = warp_sum(p0);
+        const double q0 = double(warp_sum(p0));
         if (d.comp_mode) {
             if (lane == 0) d.part[(size_t)k * PART_COLS + 5] = q0;
         } else {

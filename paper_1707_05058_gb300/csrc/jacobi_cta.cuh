@@ -682,9 +682,10 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
                     p[3] += w * dx * dx; p[4] += w * ln * ln;
                 }
             } else if (FORM == 1) {
-                const double dz = double(xn) - double(c0[off + f]);
+                const T dz = xn - c0[off + f];
                 c0[off + f] = xn;
-                p[0] += w * dz * dz;
+                if constexpr (sizeof(T) == 4) pf[0] += T(w) * dz * dz;
+                else p[0] += w * double(dz) * double(dz);
             } else if (FORM == 2) {
                 const int ent = d.gmap[off + f];
                 const double hs = d.s11[ent], zs = 0.5 * d.zhx[ent];
@@ -707,6 +708,7 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
         if (FORM != 3) {
             if (FORM == 0 && sizeof(T) == 4)
                 for (int c = 0; c < 5; ++c) p[c] = double(pf[c]);
+            if (FORM == 1 && sizeof(T) == 4) p[0] = double(pf[0]);
             cta_sum<6>(p, shr);
             if (FORM != 2) p[5] = cxk;
             if (tid == 0 && d.comp_mode) {  // per-clique row, reduced per component
