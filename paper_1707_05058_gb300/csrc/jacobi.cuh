@@ -391,12 +391,13 @@ struct BLJacobi {
 };
 
 // ---------------------------------------------------------------------------
-// Algorithm 1, affine x-update, projection and multiplier step for every
-// clique in `list`:
-//   x_e = t_e - (A^T y)_e / D_e on the clique's entries (Appendix A, Eq. KKTflops_s1),
+// Algorithm 1, projection and multiplier step for every clique in `list`:
 //   W = H_k x - lambda_k / rho,  x_k <- P(W),  lambda_k <- lambda_k + rho (x_k - H_k x)
-// (Eqs. XkUpdate, LambdakUpdate).  The first clique covering an entry stores
-// x_e and its term of <c, x>.  Per-block sums of the stopping test (Eq.
+// (Eqs. XkUpdate, LambdakUpdate).  x comes from k_xupd (pa.x_ready, the
+// default) or is formed here on the clique's entries,
+//   x_e = t_e - (A^T y)_e / D_e (Appendix A, Eq. KKTflops_s1),
+// the first clique covering an entry storing it.  That clique also adds the
+// entry's term of <c, x>.  Per-block sums of the stopping test (Eq.
 // PrimalConsensusResidual and eps_lambda) go to the partial table:
 //   |x_k - H_k x|^2, |x_k|^2, |H_k x|^2, |x_k - x_k_old|^2, |lambda_k|^2, <c, x>.
 template <typename T, int S>
