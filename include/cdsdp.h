@@ -139,6 +139,36 @@ int cdsdp_setup(int n, int m,
                 long long nnzP, const int* P_row, const int* P_col,
                 cdsdp** out);
 
+/* Same as cdsdp_setup, on data scaled as Section 7.1.3 describes (host only,
+ * no GPU call).  The paper scales the decomposed problem by positive diagonal
+ * matrices and two scalars and maps the scaled solution back; the reading used
+ * here is a diagonal congruence, which keeps the PSD cone and every clique
+ * block:  Abar_i = e_i D A_i D,  bbar = tau E b,  Cbar = sigma D C D,
+ * D = diag(d), E = diag(e).  d and e come from scale_passes rounds of symmetric
+ * Ruiz equilibration of the A triplets (e_i <- e_i / sqrt(||Abar_i||_F), then
+ * d_j <- d_j / sqrt(max |Abar_i(j,k)|), each clipped to [1e-4, 1e4]; both
+ * triangles of an off-diagonal entry counted), then tau = 1 / ||E b||_2 and
+ * sigma = 1 / ||D C D||_F (1 where the norm is 0).  scale_passes = 0 keeps
+ * d = e = 1 and only normalises b and C.
+ * Solves on the handle run on the scaled data; cdsdp_solve / cdsdp_results
+ * map X, y, Z back on the host (X = D Xbar D / tau, y_i = e_i ybar_i / sigma,
+ * Z = D^-1 Zbar D^-1 / sigma) and certificates to the normalisation of an
+ * unscaled solve (b^T y = 1, C . X = -1).  The residual history, the
+ * per-component residuals and the stopping test are those of the scaled
+ * problem.  cdsdp_unrolled_* return CDSDP_ERR_UNSUPPORTED on such a handle.
+ * Errors: as cdsdp_setup, and CDSDP_ERR_ARG for scale_passes < 0. */
+int cdsdp_setup_scaled(int n, int m,
+                       long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
+                       const double* b,
+                       long long nnzC, const int* C_row, const int* C_col, const double* C_val,
+                       long long nnzP, const int* P_row, const int* P_col,
+                       int scale_passes, cdsdp** out);
+
+/* Scaling factors of a handle (Section 7.1.3): d [n], e [m] (host buffers the
+ * caller owns; any may be NULL), tau and sigma.  A handle made by cdsdp_setup
+ * reports d = e = 1, tau = sigma = 1.  Errors: CDSDP_ERR_ARG (NULL handle). */
+int cdsdp_scaling(const cdsdp* h, double* d, double* e, double* tau, double* sigma);
+
 int cdsdp_info(const cdsdp* h, cdsdp_info_t* info);
 
 /* Maximal cliques in canonical order: offsets[p+1], vertices[offsets[p]],

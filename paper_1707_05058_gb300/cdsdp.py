@@ -51,6 +51,9 @@ _lib.cdsdp_default_opts.argtypes = [ctypes.POINTER(Opts)]
 _lib.cdsdp_default_opts.restype = None
 _lib.cdsdp_setup.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32p, _f64p, _f64p,
                              _ll, _i32p, _i32p, _f64p, _ll, _i32p, _i32p, ctypes.POINTER(_vp)]
+_lib.cdsdp_setup_scaled.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32p, _f64p, _f64p,
+                                    _ll, _i32p, _i32p, _f64p, _ll, _i32p, _i32p, ctypes.c_int, ctypes.POINTER(_vp)]
+_lib.cdsdp_scaling.argtypes = [_vp, _f64p, _f64p, _f64p, _f64p]
 _lib.cdsdp_info.argtypes = [_vp, ctypes.POINTER(Info)]
 _lib.cdsdp_cliques.argtypes = [_vp, _i32p, _i32p]
 _lib.cdsdp_pattern.argtypes = [_vp, _i32p, _i32p]
@@ -86,7 +89,7 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile", "cdsdp_psd_violation_scratch_bytes",
             "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc", "cdsdp_grad_workspace_bytes",
             "cdsdp_unrolled_forward", "cdsdp_unrolled_backward", "cdsdp_components",
-            "cdsdp_component_results", "cdsdp_autotune"]
+            "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling"]
 
 
 class CdsdpError(RuntimeError):
@@ -121,19 +124,28 @@ def _stream_ptr(stream):
 
 
 class Problem:
-    """One SDP after the data preprocessing of Algorithms 1-3 (host only)."""
+    """One SDP after the data preprocessing of Algorithms 1-3 (host only).
 
-    def __init__(self, prob):
+    scale_passes=None sets the data up as given (cdsdp_setup); an integer k >= 0
+    scales it first as Section 7.1.3 describes, with k equilibration passes
+    (cdsdp_setup_scaled); solutions come back in the original units."""
+
+    def __init__(self, prob, scale_passes=None):
         (A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col) = prob.arrays()
         self._keep = (A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col)
         h = _vp()
-        st = _lib.cdsdp_setup(int(prob.n), int(prob.m), A_con.size, _ptr(A_con, ctypes.c_int), _ptr(A_row, ctypes.c_int),
-                              _ptr(A_col, ctypes.c_int), _ptr(A_val, ctypes.c_double), _ptr(b, ctypes.c_double),
-                              C_row.size, _ptr(C_row, ctypes.c_int), _ptr(C_col, ctypes.c_int),
-                              _ptr(C_val, ctypes.c_double), P_row.size, _ptr(P_row, ctypes.c_int),
-                              _ptr(P_col, ctypes.c_int), ctypes.byref(h))
+        args = (int(prob.n), int(prob.m), A_con.size, _ptr(A_con, ctypes.c_int), _ptr(A_row, ctypes.c_int),
+                _ptr(A_col, ctypes.c_int), _ptr(A_val, ctypes.c_double), _ptr(b, ctypes.c_double),
+                C_row.size, _ptr(C_row, ctypes.c_int), _ptr(C_col, ctypes.c_int),
+                _ptr(C_val, ctypes.c_double), P_row.size, _ptr(P_row, ctypes.c_int), _ptr(P_col, ctypes.c_int))
+        if scale_passes is None:
+            st = _lib.cdsdp_setup(*args, ctypes.byref(h))
+            what = "cdsdp_setup"
+        else:
+            st = _lib.cdsdp_setup_scaled(*args, int(scale_passes), ctypes.byref(h))
+            what = "cdsdp_setup_scaled"
         if st != 0:
-            raise CdsdpError(st, "cdsdp_setup")
+            raise CdsdpError(st, what)
         self._h = h
         self.workspace = None
         self.max_iter = 0
@@ -165,6 +177,18 @@ class Problem:
         c = np.zeros(nz, np.int32)
         _lib.cdsdp_pattern(self._h, _ptr(r, ctypes.c_int), _ptr(c, ctypes.c_int))
         return r, c
+
+    def scaling(self):
+        """(d [n], e [m], tau, sigma) of Section 7.1.3; ones for an unscaled handle."""
+        d = np.zeros(int(self.info["n"]))
+        e = np.zeros(int(self.info["m"]))
+        tau = ctypes.c_double()
+        sigma = ctypes.c_double()
+        st = _lib.cdsdp_scaling(self._h, _ptr(d, ctypes.c_double), _ptr(e, ctypes.c_double), ctypes.byref(tau),
+                                ctypes.byref(sigma))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_scaling")
+        return d, e, tau.value, sigma.value
 
     def components(self):
         """(component of each vertex [n], component of each constraint [m])."""

@@ -59,6 +59,11 @@ struct HostProblem {
     std::vector<double> atb;          // A^T b per pattern entry
     std::vector<double> a_zhat_x;     // A W zhat_x per constraint
     double norm_b = 0.0, norm_c = 0.0;
+    // data scaling (Section 7.1.3), when the problem was set up scaled:
+    // Abar_i = e_i D A_i D, bbar = tau E b, Cbar = sigma D C D (D = diag(d))
+    bool scaled = false;
+    std::vector<double> sc_d, sc_e;   // [n], [m]
+    double sc_tau = 1.0, sc_sigma = 1.0;
 };
 
 // Build everything above.  Returns a cdsdp_status.
@@ -75,6 +80,13 @@ int build_factor(const HostProblem& hp, bool hsde, std::vector<double>& inv);
 // kinv, zeta_hat and the other constants of Algorithm 3 (built on the first
 // HSDE solve; primal and dual solves do not need them).
 int build_hsde_constants(HostProblem& hp);
+
+// Scaling factors of Section 7.1.3 (symmetric Ruiz equilibration of the
+// constraint triplets, then b and C normalised); see cdsdp_setup_scaled.
+void scaling_factors(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col,
+                     const double* A_val, const double* b, long long nnzC, const int* C_row, const int* C_col,
+                     const double* C_val, int passes, std::vector<double>& d, std::vector<double>& e, double& tau,
+                     double& sigma);
 
 inline int packed_size(int s) { return s * (s + 1) / 2; }
 

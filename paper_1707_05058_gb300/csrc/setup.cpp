@@ -564,4 +564,43 @@ int build_host_problem(int n, int m,
     return CDSDP_SOLVED;
 }
 
+void scaling_factors(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col,
+                     const double* A_val, const double* b, long long nnzC, const int* C_row, const int* C_col,
+                     const double* C_val, int passes, std::vector<double>& d, std::vector<double>& e, double& tau,
+                     double& sigma) {
+    d.assign(n, 1.0);
+    e.assign(m, 1.0);
+    std::vector<double> rown(m), mj(n);
+    auto clip = [](double x) { return std::min(1e4, std::max(1e-4, x)); };
+    for (int pass = 0; pass < passes; ++pass) {
+        std::fill(rown.begin(), rown.end(), 0.0);
+        for (long long k = 0; k < nnzA; ++k) {
+            const double a = e[A_con[k]] * d[A_row[k]] * d[A_col[k]] * A_val[k];
+            rown[A_con[k]] += (A_row[k] == A_col[k] ? 1.0 : 2.0) * a * a;
+        }
+        for (int i = 0; i < m; ++i) {
+            const double r = std::sqrt(rown[i]);
+            e[i] = clip(e[i] / std::sqrt(r > 0.0 ? r : 1.0));
+        }
+        std::fill(mj.begin(), mj.end(), 0.0);
+        for (long long k = 0; k < nnzA; ++k) {
+            const double a = std::fabs(e[A_con[k]] * d[A_row[k]] * d[A_col[k]] * A_val[k]);
+            mj[A_row[k]] = std::max(mj[A_row[k]], a);
+            mj[A_col[k]] = std::max(mj[A_col[k]], a);
+        }
+        for (int j = 0; j < n; ++j) d[j] = clip(d[j] / std::sqrt(mj[j] > 0.0 ? mj[j] : 1.0));
+    }
+    double nb = 0.0;
+    for (int i = 0; i < m; ++i) nb += (e[i] * b[i]) * (e[i] * b[i]);
+    nb = std::sqrt(nb);
+    tau = nb > 0.0 ? 1.0 / nb : 1.0;
+    double nc = 0.0;
+    for (long long k = 0; k < nnzC; ++k) {
+        const double v = d[C_row[k]] * d[C_col[k]] * C_val[k];
+        nc += (C_row[k] == C_col[k] ? 1.0 : 2.0) * v * v;
+    }
+    nc = std::sqrt(nc);
+    sigma = nc > 0.0 ? 1.0 / nc : 1.0;
+}
+
 }  // namespace cdsdp_impl

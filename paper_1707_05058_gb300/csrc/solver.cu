@@ -442,6 +442,33 @@ int ensure_hsde(cdsdp* h, cudaStream_t st) {
     return CDSDP_SOLVED;
 }
 
+// Map a solution of the scaled problem (Section 7.1.3) back on the host:
+// X = D Xbar D / tau, y_i = e_i ybar_i / sigma, Z = D^-1 Zbar D^-1 / sigma,
+// entrywise on the lower pattern.
+void unscale_results(const HostProblem& hp, double* X, double* y, double* Z) {
+    const size_t NE = hp.prow.size();
+    for (size_t k = 0; k < NE; ++k) {
+        const double dd = hp.sc_d[hp.prow[k]] * hp.sc_d[hp.pcol[k]];
+        if (X) X[k] *= dd / hp.sc_tau;
+        if (Z) Z[k] /= dd * hp.sc_sigma;
+    }
+    if (y)
+        for (int i = 0; i < hp.m; ++i) y[i] *= hp.sc_e[i] / hp.sc_sigma;
+}
+
+// Certificates of the scaled problem mapped back.  A primal infeasibility
+// certificate ybar with bbar^T ybar = 1 gives y_i = tau e_i ybar_i with
+// b^T y = 1; a dual one Xbar with Cbar . Xbar = -1 gives X = sigma D Xbar D
+// with C . X = -1, the normalisations of an unscaled solve.
+void unscale_cert(const HostProblem& hp, int status, double* cert) {
+    if (status == CDSDP_PRIMAL_INFEASIBLE) {
+        for (int i = 0; i < hp.m; ++i) cert[i] *= hp.sc_tau * hp.sc_e[i];
+    } else if (status == CDSDP_DUAL_INFEASIBLE) {
+        const size_t NE = hp.prow.size();
+        for (size_t k = 0; k < NE; ++k) cert[k] *= hp.sc_sigma * hp.sc_d[hp.prow[k]] * hp.sc_d[hp.pcol[k]];
+    }
+}
+
 int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, double* hist, double* cert) {
     Dev& d = h->dev;
     const int form = h->last_form;
@@ -475,6 +502,7 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
         CK(cudaMemcpyAsync(Z, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
+    if (h->hp.scaled) unscale_results(h->hp, X, y, Z);
     if (hist && h->last_iters > 0) {
         CK(cudaMemcpyAsync(hist, d.hist, (size_t)h->last_iters * HIST_COLS * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -494,6 +522,7 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
             CK(cudaMemcpyAsync(cert, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
         }
         CK(cudaStreamSynchronize(st));
+        if (h->hp.scaled) unscale_cert(h->hp, h->last_status, cert);
     }
     return CDSDP_SOLVED;
 }
@@ -527,6 +556,7 @@ int check_unrolled(cdsdp* h, const cdsdp_opts& o, int iters, int ckpt_every) {
     if (iters < 1 || ckpt_every < 1 || !(o.rho > 0) || o.jacobi_max_sweeps < 1) return CDSDP_ERR_ARG;
     if (o.precision != CDSDP_FP32_PROJECTION && o.precision != CDSDP_FP64) return CDSDP_ERR_ARG;
     if (h->hp.max_clique > kMaxWarpOrder) return CDSDP_ERR_UNSUPPORTED;
+    if (h->hp.scaled) return CDSDP_ERR_UNSUPPORTED;  // c and b would be in scaled units
     if (ckpt_every > h->ws_max_iter) return CDSDP_ERR_ARG;
     return CDSDP_SOLVED;
 }
@@ -594,6 +624,66 @@ int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row
     }
     if (st != CDSDP_SOLVED) { delete h; return st; }
     *out = h;
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_setup_scaled(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col,
+                       const double* A_val, const double* b, long long nnzC, const int* C_row, const int* C_col,
+                       const double* C_val, long long nnzP, const int* P_row, const int* P_col, int scale_passes,
+                       cdsdp** out) {
+    if (!out) return CDSDP_ERR_ARG;
+    *out = nullptr;
+    if (scale_passes < 0 || n < 1 || m < 0 || nnzA < 0 || nnzC < 0) return CDSDP_ERR_ARG;
+    if ((nnzA > 0 && (!A_con || !A_row || !A_col || !A_val)) || (m > 0 && !b) ||
+        (nnzC > 0 && (!C_row || !C_col || !C_val)))
+        return CDSDP_ERR_ARG;
+    for (long long k = 0; k < nnzA; ++k)
+        if (A_con[k] < 0 || A_con[k] >= m || A_row[k] < 0 || A_row[k] >= n || A_col[k] < 0 || A_col[k] >= n)
+            return CDSDP_ERR_ARG;
+    for (long long k = 0; k < nnzC; ++k)
+        if (C_row[k] < 0 || C_row[k] >= n || C_col[k] < 0 || C_col[k] >= n) return CDSDP_ERR_ARG;
+    cdsdp* h = new (std::nothrow) cdsdp();
+    if (!h) return CDSDP_ERR_NOMEM;
+    int st;
+    try {
+        std::vector<double> d, e;
+        double tau = 1.0, sigma = 1.0;
+        cdsdp_impl::scaling_factors(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val,
+                                    scale_passes, d, e, tau, sigma);
+        std::vector<double> av(nnzA), bv(m), cv(nnzC);
+        for (long long k = 0; k < nnzA; ++k) av[k] = e[A_con[k]] * d[A_row[k]] * d[A_col[k]] * A_val[k];
+        for (int i = 0; i < m; ++i) bv[i] = tau * e[i] * b[i];
+        for (long long k = 0; k < nnzC; ++k) cv[k] = sigma * d[C_row[k]] * d[C_col[k]] * C_val[k];
+        st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, av.data(), bv.data(), nnzC, C_row,
+                                            C_col, cv.data(), nnzP, P_row, P_col, h->hp);
+        if (st == CDSDP_SOLVED) {
+            h->hp.scaled = true;
+            h->hp.sc_d = std::move(d);
+            h->hp.sc_e = std::move(e);
+            h->hp.sc_tau = tau;
+            h->hp.sc_sigma = sigma;
+        }
+    } catch (const std::bad_alloc&) {
+        st = CDSDP_ERR_NOMEM;
+    }
+    if (st != CDSDP_SOLVED) { delete h; return st; }
+    *out = h;
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_scaling(const cdsdp* h, double* d, double* e, double* tau, double* sigma) {
+    if (!h) return CDSDP_ERR_ARG;
+    const HostProblem& hp = h->hp;
+    if (d) {
+        if (hp.scaled) std::copy(hp.sc_d.begin(), hp.sc_d.end(), d);
+        else std::fill(d, d + hp.n, 1.0);
+    }
+    if (e) {
+        if (hp.scaled) std::copy(hp.sc_e.begin(), hp.sc_e.end(), e);
+        else std::fill(e, e + hp.m, 1.0);
+    }
+    if (tau) *tau = hp.sc_tau;
+    if (sigma) *sigma = hp.sc_sigma;
     return CDSDP_SOLVED;
 }
 

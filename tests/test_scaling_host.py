@@ -1,0 +1,55 @@
+"""Data scaling of Section 7.1.3 in the library's host setup: the factors
+cdsdp_setup_scaled computes equal the oracle's, the scaled handle keeps the
+pattern and cliques of the unscaled one, and bad arguments are rejected.
+Host only: no GPU call."""
+import numpy as np
+import pytest
+
+from oracle import scaling
+from paper_1707_05058_gb300 import workloads as W
+
+CASES = [W.workload(0), W.block_arrow(3, 4, 2, 6, seed=5), W.maxcut_cycle(7),
+         W.lambda_max_tridiagonal(8, 1.0, 0.5), W.direct_sum([W.block_arrow(2, 3, 2, 4, seed=1),
+                                                              W.maxcut_cycle(5)])]
+
+
+@pytest.mark.parametrize("passes", [0, 1, 5])
+@pytest.mark.parametrize("prob", CASES, ids=lambda p: p.name)
+def test_scaling_factors_match_oracle(lib, prob, passes):
+    P = lib.Problem(prob, scale_passes=passes)
+    d, e, tau, sigma = P.scaling()
+    rd, re, rtau, rsigma = scaling.scaling_factors(prob, passes)
+    np.testing.assert_allclose(d, rd, rtol=1e-14)
+    np.testing.assert_allclose(e, re, rtol=1e-14)
+    assert abs(tau - rtau) <= 1e-13 * rtau
+    assert abs(sigma - rsigma) <= 1e-13 * rsigma
+
+
+def test_unscaled_handle_reports_unit_factors(lib):
+    prob = W.workload(0)
+    d, e, tau, sigma = lib.Problem(prob).scaling()
+    assert np.all(d == 1.0) and np.all(e == 1.0) and tau == 1.0 and sigma == 1.0
+
+
+@pytest.mark.parametrize("prob", CASES[:3], ids=lambda p: p.name)
+def test_scaled_setup_keeps_pattern_and_cliques(lib, prob):
+    P0 = lib.Problem(prob)
+    P1 = lib.Problem(prob, scale_passes=4)
+    for k in ("n", "m", "p", "max_clique", "nnz_pattern", "n_d_lower", "nnz_A", "n_fill", "ncomp"):
+        assert P0.info[k] == P1.info[k], k
+    assert P0.clique_list() == P1.clique_list()
+    for a, b in zip(P0.pattern(), P1.pattern()):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_scaled_setup_rejects_bad_arguments(lib):
+    prob = W.workload(0)
+    with pytest.raises(lib.CdsdpError) as ex:
+        lib.Problem(prob, scale_passes=-1)
+    assert ex.value.status == -1  # CDSDP_ERR_ARG
+    import dataclasses
+    bad = dataclasses.replace(prob, A_row=prob.A_row.copy())
+    bad.A_row[3] = prob.n  # out of range
+    with pytest.raises(lib.CdsdpError) as ex:
+        lib.Problem(bad, scale_passes=2)
+    assert ex.value.status == -1  # CDSDP_ERR_ARG
