@@ -236,6 +236,42 @@ def _grad_batch(cdsdp, workloads, torch, stream):
             "forward_ms": fwd, "backward_ms": bwd, "grad_finite": bool(torch.isfinite(cbar).all().item())}
 
 
+def _completion(cdsdp, workloads, torch, stream):
+    """Maximum-determinant completion (Section 7.1.1) of a positive definite
+    partial matrix on the pattern of (a) the banded n=2000 workload and (b)
+    the 64-SDP direct sum (n=500 each): factor only (t_k, s_k, log det) and
+    with the dense blocks.  Device time over the whole call (the call waits
+    once on the stream for its positive-definiteness flag)."""
+    import numpy as np
+    res = {}
+    for key, prob in (("banded_n2000", workloads.workload(1)),
+                      ("direct_sum_64x_n500", workloads.direct_sum(workloads.workload(4)))):
+        P = cdsdp.Problem(prob)
+        r, c = P.pattern()
+        X = torch.tensor(workloads.pd_on_pattern(prob.n, r, c, 5), device="cuda")
+        sb, we, _ = P.completion_sizes()
+        scratch = torch.empty(sb, dtype=torch.uint8, device="cuda")
+        Wd = torch.empty(we, dtype=torch.float64, device="cuda")
+        out = {}
+        for dense in (False, True):
+            ms = []
+            for rep in range(4):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.complete(X, dense=dense, stream=stream, scratch=scratch, out=Wd)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            out["dense_ms" if dense else "factor_ms"] = statistics.median(ms[1:])
+        vc, _ = P.components()
+        sizes = np.bincount(vc)
+        out.update({"n": int(prob.n), "components": int(P.info["ncomp"]), "dense_doubles": int(we),
+                    "step_launches": int(sizes.max()) - 1})
+        res[key] = out
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,6 +385,7 @@ def main():
 
     batched = None if args.no_batched else _batched(cdsdp, workloads, torch, flush, stream, rank, world)
     grad = None if args.no_batched else _grad_batch(cdsdp, workloads, torch, stream)
+    compl = None if args.no_batched else _completion(cdsdp, workloads, torch, stream)
     if batched is not None and world > 1:  # each rank solved its share of the 256 SDPs
         _, tmax, _ = aggregate_over_ranks(torch, dist, world, batched["time_to_eps_ms"], 0, "cuda")
         batched["time_to_eps_ms"] = tmax
@@ -390,6 +427,7 @@ def main():
                           "speedup_time_to_eps": ms64f[0] / ms32f[0]},
             "batched": batched,
             "grad": grad,
+            "completion": compl,
             "clique_proj_gflops": gflops,
             "setup_ms": setup_s * 1e3,
             "roofline": {"bound": "alu", "achieved": gflops / 1e3, "peak": peak_fp32, "unit": "TFLOP/s",

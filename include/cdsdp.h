@@ -42,6 +42,8 @@ typedef enum {
     CDSDP_MAX_ITER = 1,
     CDSDP_PRIMAL_INFEASIBLE = 2, /* HSDE only: certificate u_y / (b^T u_y)        */
     CDSDP_DUAL_INFEASIBLE = 3,   /* HSDE only: certificate -u_x / (c^T u_x)       */
+    CDSDP_NOT_PD = 4,            /* completion: a clique block is not positive
+                                    definite, so no max-det completion exists     */
     CDSDP_ERR_ARG = -1,          /* malformed argument                            */
     CDSDP_ERR_RANK = -2,         /* A not full row rank: Cholesky pivot <= 0      */
     CDSDP_ERR_CUDA = -3,         /* a CUDA runtime call failed                    */
@@ -168,6 +170,36 @@ int cdsdp_setup_scaled(int n, int m,
  * caller owns; any may be NULL), tau and sigma.  A handle made by cdsdp_setup
  * reports d = e = 1, tau = sigma = 1.  Errors: CDSDP_ERR_ARG (NULL handle). */
 int cdsdp_scaling(const cdsdp* h, double* d, double* e, double* tau, double* sigma);
+
+/* Maximum-determinant positive definite completion (Section 7.1.1) of a
+ * partial matrix X on the handle's extended pattern E* (the X that
+ * cdsdp_solve returns).  The completion W is the unique positive definite
+ * matrix with W = X on E* and (W^-1)_ij = 0 off E*; it exists exactly when
+ * every clique block of X is positive definite.  It is computed along a
+ * perfect elimination order of E* (Vandenberghe and Andersen, Chapter 10.2).
+ * The output holds one dense row-major n_c x n_c block per independent
+ * component c of the handle (cdsdp_components), rows and columns in
+ * ascending vertex order, block c at element offset w_offsets[c]; entries
+ * between components are zero and not stored.
+ *
+ * cdsdp_completion_sizes (host only):
+ *   scratch_bytes  device scratch that cdsdp_complete needs
+ *   w_elems        doubles of the dense output (sum of n_c^2)
+ *   w_offsets      [ncomp + 1] element offsets of the blocks (may be NULL)
+ * cdsdp_complete:
+ *   d_X        device, nnz_pattern doubles in cdsdp_pattern order
+ *   d_scratch  device, scratch_bytes, 256-byte aligned, caller-owned
+ *   d_W        device, w_elems doubles (may be NULL: factor and log det only)
+ *   logdet     host [ncomp], log det of each block (may be NULL)
+ *   stream     CUDA stream; the call synchronises it once (to read the
+ *              positive-definiteness flag) and returns with the dense
+ *              blocks queued on it.
+ * Returns CDSDP_SOLVED, CDSDP_NOT_PD (d_W and logdet untouched),
+ * CDSDP_ERR_ARG (NULL or misaligned pointer), CDSDP_ERR_NOMEM (scratch too
+ * small), CDSDP_ERR_UNSUPPORTED (largest clique above order 160), CDSDP_ERR_CUDA. */
+int cdsdp_completion_sizes(const cdsdp* h, size_t* scratch_bytes, long long* w_elems, long long* w_offsets);
+int cdsdp_complete(cdsdp* h, const double* d_X, void* d_scratch, size_t scratch_bytes, double* d_W, double* logdet,
+                   void* stream);
 
 int cdsdp_info(const cdsdp* h, cdsdp_info_t* info);
 

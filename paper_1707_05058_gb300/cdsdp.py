@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 PRIMAL, DUAL, HSDE = 0, 1, 2
 FORMS = {"primal": PRIMAL, "dual": DUAL, "hsde": HSDE}
 FP32, FP64 = 0, 1
-SOLVED, MAX_ITER, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE = 0, 1, 2, 3
+SOLVED, MAX_ITER, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, NOT_PD = 0, 1, 2, 3, 4
 
 _i32p = ctypes.POINTER(ctypes.c_int)
 _f64p = ctypes.POINTER(ctypes.c_double)
@@ -54,6 +54,8 @@ _lib.cdsdp_setup.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32
 _lib.cdsdp_setup_scaled.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32p, _f64p, _f64p,
                                     _ll, _i32p, _i32p, _f64p, _ll, _i32p, _i32p, ctypes.c_int, ctypes.POINTER(_vp)]
 _lib.cdsdp_scaling.argtypes = [_vp, _f64p, _f64p, _f64p, _f64p]
+_lib.cdsdp_completion_sizes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_ll), _vp]
+_lib.cdsdp_complete.argtypes = [_vp, _vp, _vp, ctypes.c_size_t, _vp, _f64p, _vp]
 _lib.cdsdp_info.argtypes = [_vp, ctypes.POINTER(Info)]
 _lib.cdsdp_cliques.argtypes = [_vp, _i32p, _i32p]
 _lib.cdsdp_pattern.argtypes = [_vp, _i32p, _i32p]
@@ -89,7 +91,8 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile", "cdsdp_psd_violation_scratch_bytes",
             "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc", "cdsdp_grad_workspace_bytes",
             "cdsdp_unrolled_forward", "cdsdp_unrolled_backward", "cdsdp_components",
-            "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling"]
+            "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling",
+            "cdsdp_completion_sizes", "cdsdp_complete"]
 
 
 class CdsdpError(RuntimeError):
@@ -189,6 +192,42 @@ class Problem:
         if st != 0:
             raise CdsdpError(st, "cdsdp_scaling")
         return d, e, tau.value, sigma.value
+
+    def completion_sizes(self):
+        """(device scratch bytes, doubles of the dense blocks, block offsets [ncomp + 1])."""
+        sb = ctypes.c_size_t()
+        we = _ll()
+        offs = np.zeros(int(self.info["ncomp"]) + 1, np.int64)
+        st = _lib.cdsdp_completion_sizes(self._h, ctypes.byref(sb), ctypes.byref(we),
+                                         ctypes.c_void_p(offs.ctypes.data))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_completion_sizes")
+        return sb.value, we.value, offs
+
+    def complete(self, X, dense=True, stream=None, scratch=None, out=None):
+        """Maximum-determinant completion (Section 7.1.1) of X (pattern values,
+        host array or CUDA tensor).  Returns (W, logdet): W a CUDA float64
+        tensor holding the dense blocks of the components back to back (None
+        when dense=False), logdet a numpy array per component.  Raises
+        CdsdpError with status NOT_PD when a clique block of X is not positive
+        definite."""
+        import torch
+        sb, we, _ = self.completion_sizes()
+        if not torch.is_tensor(X):
+            X = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float64)).cuda()
+        X = X.contiguous()
+        if scratch is None:
+            scratch = torch.empty(sb, dtype=torch.uint8, device=X.device)
+        W = None
+        if dense:
+            W = out if out is not None else torch.empty(we, dtype=torch.float64, device=X.device)
+        ld = np.zeros(int(self.info["ncomp"]))
+        st = _lib.cdsdp_complete(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(scratch.data_ptr()),
+                                 scratch.numel(), ctypes.c_void_p(W.data_ptr()) if W is not None else None,
+                                 _ptr(ld, ctypes.c_double), _stream_ptr(stream))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_complete")
+        return W, ld
 
     def components(self):
         """(component of each vertex [n], component of each constraint [m])."""

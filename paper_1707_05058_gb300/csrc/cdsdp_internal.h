@@ -16,6 +16,10 @@ struct HostProblem {
     int n = 0, m = 0;
     // extended pattern E*, lower entries (row >= col), column-major order
     std::vector<int> prow, pcol, colptr;  // colptr[n+1] indexes prow/pcol
+    // perfect elimination order of the extended pattern (vertex eliminated at
+    // step k) and, per vertex, its neighbours eliminated after it (a clique),
+    // ascending: lt_idx[lt_ptr[v] .. lt_ptr[v+1])
+    std::vector<int> peo, lt_ptr, lt_idx;
     // maximal cliques, each ascending, list in lexicographic order
     std::vector<int> cl_off, cl_vert;
     int max_clique = 0;
@@ -87,6 +91,11 @@ void scaling_factors(int n, int m, long long nnzA, const int* A_con, const int* 
                      const double* A_val, const double* b, long long nnzC, const int* C_row, const int* C_col,
                      const double* C_val, int passes, std::vector<double>& d, std::vector<double>& e, double& tau,
                      double& sigma);
+
+// Maximum-determinant completion (Section 7.1.1), completion.cu.
+int completion_sizes(const HostProblem& hp, size_t* scratch_bytes, long long* w_elems, long long* w_offsets);
+int completion_run(const HostProblem& hp, const double* d_X, void* d_scratch, size_t scratch_bytes, double* d_W,
+                   double* logdet, void* stream, std::string* err);
 
 inline int packed_size(int s) { return s * (s + 1) / 2; }
 

@@ -361,6 +361,12 @@ int build_host_problem(int n, int m,
         }
     }
     for (auto& l : later) std::sort(l.begin(), l.end());
+    hp.peo = elim;
+    hp.lt_ptr.assign(n + 1, 0);
+    for (int v = 0; v < n; ++v) hp.lt_ptr[v + 1] = hp.lt_ptr[v] + (int)later[v].size();
+    hp.lt_idx.clear();
+    hp.lt_idx.reserve(hp.lt_ptr[n]);
+    for (int v = 0; v < n; ++v) hp.lt_idx.insert(hp.lt_idx.end(), later[v].begin(), later[v].end());
 
     // ---- maximal cliques (parent rule on the PEO)
     std::vector<char> maximal(n, 1);

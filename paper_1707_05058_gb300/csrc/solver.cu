@@ -687,6 +687,25 @@ int cdsdp_scaling(const cdsdp* h, double* d, double* e, double* tau, double* sig
     return CDSDP_SOLVED;
 }
 
+int cdsdp_completion_sizes(const cdsdp* h, size_t* scratch_bytes, long long* w_elems, long long* w_offsets) {
+    if (!h) return CDSDP_ERR_ARG;
+    try {
+        return cdsdp_impl::completion_sizes(h->hp, scratch_bytes, w_elems, w_offsets);
+    } catch (const std::bad_alloc&) {
+        return CDSDP_ERR_NOMEM;
+    }
+}
+
+int cdsdp_complete(cdsdp* h, const double* d_X, void* d_scratch, size_t scratch_bytes, double* d_W, double* logdet,
+                   void* stream) {
+    if (!h) return CDSDP_ERR_ARG;
+    try {
+        return cdsdp_impl::completion_run(h->hp, d_X, d_scratch, scratch_bytes, d_W, logdet, stream, &h->err);
+    } catch (const std::bad_alloc&) {
+        return CDSDP_ERR_NOMEM;
+    }
+}
+
 int cdsdp_info(const cdsdp* h, cdsdp_info_t* info) {
     if (!h || !info) return CDSDP_ERR_ARG;
     const HostProblem& hp = h->hp;
@@ -955,6 +974,7 @@ const char* cdsdp_strerror(int s) {
         case CDSDP_MAX_ITER: return "maximum number of iterations reached";
         case CDSDP_PRIMAL_INFEASIBLE: return "primal infeasible (certificate returned)";
         case CDSDP_DUAL_INFEASIBLE: return "dual infeasible (certificate returned)";
+        case CDSDP_NOT_PD: return "a clique block is not positive definite (no completion)";
         case CDSDP_ERR_ARG: return "invalid argument";
         case CDSDP_ERR_RANK: return "A is not full row rank (factorisation failed)";
         case CDSDP_ERR_CUDA: return "CUDA runtime error";

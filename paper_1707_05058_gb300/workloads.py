@@ -230,6 +230,18 @@ def direct_sum(problems, name=None):
                       name or "direct_sum_" + "+".join(p.name for p in problems), opt)
 
 
+def pd_on_pattern(n, rows, cols, seed, rank=16, shift=0.5):
+    """Entries (rows[k], cols[k]) of the positive definite matrix
+    shift I + U U^T, U an n x rank matrix of N(0, 1/rank) draws: a partial
+    matrix every clique block of which is positive definite (input of the
+    maximum-determinant completion)."""
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((n, rank)) / math.sqrt(rank)
+    rows = np.asarray(rows, np.int64)
+    cols = np.asarray(cols, np.int64)
+    return np.einsum("kr,kr->k", U[rows], U[cols]) + np.where(rows == cols, shift, 0.0)
+
+
 def banded_batch(count, n, w, m, seed):
     return [banded(n, w, m, seed + 1 + i) for i in range(count)]
 
