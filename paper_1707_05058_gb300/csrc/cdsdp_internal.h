@@ -92,10 +92,18 @@ void scaling_factors(int n, int m, long long nnzA, const int* A_con, const int* 
                      const double* C_val, int passes, std::vector<double>& d, std::vector<double>& e, double& tau,
                      double& sigma);
 
-// Maximum-determinant completion (Section 7.1.1), completion.cu.
+// Maximum-determinant completion (Section 7.1.1), completion.cu.  The step
+// launches of the dense recurrence are replayed from a CUDA graph cached per
+// (scratch, output) pair.
+struct CmpGraph {
+    void* exec = nullptr;  // cudaGraphExec_t
+    const void* scratch = nullptr;
+    const void* W = nullptr;
+};
 int completion_sizes(const HostProblem& hp, size_t* scratch_bytes, long long* w_elems, long long* w_offsets);
 int completion_run(const HostProblem& hp, const double* d_X, void* d_scratch, size_t scratch_bytes, double* d_W,
-                   double* logdet, void* stream, std::string* err);
+                   double* logdet, void* stream, std::string* err, CmpGraph* cache);
+void completion_release(CmpGraph& g);
 
 inline int packed_size(int s) { return s * (s + 1) / 2; }
 

@@ -19,7 +19,8 @@
 //   k_cmp_logdet   one thread block per component: sum of log s_k in a fixed
 //                  order.
 //   k_cmp_scatter  the given entries into the dense blocks.
-//   k_cmp_step     one launch per step of the recurrence; within a step each
+//   k_cmp_step     one launch per step of the recurrence (the launches are
+//                  captured once into a CUDA graph and replayed); within a step each
 //                  thread owns one later vertex j of one component (all
 //                  components advance together, aligned at their last
 //                  vertex), reads rows N_k of the block at column j
@@ -283,6 +284,13 @@ int cuda_fail(std::string* err, cudaError_t e, const char* what) {
 
 }  // namespace
 
+void completion_release(CmpGraph& g) {
+    if (g.exec) cudaGraphExecDestroy((cudaGraphExec_t)g.exec);
+    g.exec = nullptr;
+    g.scratch = nullptr;
+    g.W = nullptr;
+}
+
 int completion_sizes(const HostProblem& hp, size_t* scratch_bytes, long long* w_elems, long long* w_offsets) {
     const CmpLayout L = cmp_layout(hp);
     std::vector<unsigned char> img;
@@ -296,7 +304,7 @@ int completion_sizes(const HostProblem& hp, size_t* scratch_bytes, long long* w_
 }
 
 int completion_run(const HostProblem& hp, const double* d_X, void* d_scratch, size_t scratch_bytes, double* d_W,
-                   double* logdet, void* stream, std::string* err) {
+                   double* logdet, void* stream, std::string* err, CmpGraph* cache) {
     if (!d_X || !d_scratch) return CDSDP_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(d_scratch) % kCmpAlign) return CDSDP_ERR_ARG;
     const CmpLayout L = cmp_layout(hp);
@@ -355,11 +363,37 @@ int completion_run(const HostProblem& hp, const double* d_X, void* d_scratch, si
         k_cmp_scatter<<<gs, 256, 0, st>>>(NE, prow, pcol, comp, loc, peo_off, dwoff, d_X, d_W);
         CMP_CK(cudaGetLastError());
         const int gn = (n + kStepThreads - 1) / kStepThreads;
-        for (int r = 1; r < maxnc; ++r) {
-            k_cmp_step<<<gn, kStepThreads, 0, st>>>(n, r, lt_ptr, lt_idx, comp, loc, posl, peo_cat, peo_off, dwoff,
-                                                    T, d_W);
+        auto steps = [&](cudaStream_t s2) {
+            for (int r = 1; r < maxnc; ++r)
+                k_cmp_step<<<gn, kStepThreads, 0, s2>>>(n, r, lt_ptr, lt_idx, comp, loc, posl, peo_cat, peo_off,
+                                                        dwoff, T, d_W);
+            return cudaGetLastError();
+        };
+        if (!cache || maxnc < 2) {
+            CMP_CK(steps(st));
+        } else {
+            if (!cache->exec || cache->scratch != d_scratch || cache->W != d_W) {
+                completion_release(*cache);
+                cudaStream_t cs;
+                CMP_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+                cudaGraph_t graph = nullptr;
+                e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    const cudaError_t e2 = steps(cs);
+                    e = cudaStreamEndCapture(cs, &graph);
+                    if (e2 != cudaSuccess) e = e2;
+                }
+                cudaStreamDestroy(cs);
+                cudaGraphExec_t exec = nullptr;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e != cudaSuccess) return cuda_fail(err, e, "completion graph");
+                cache->exec = exec;
+                cache->scratch = d_scratch;
+                cache->W = d_W;
+            }
+            CMP_CK(cudaGraphLaunch((cudaGraphExec_t)cache->exec, st));
         }
-        CMP_CK(cudaGetLastError());
     }
     if (logdet) {
         CMP_CK(cudaMemcpyAsync(logdet, dlog, C * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -72,6 +72,7 @@ struct cdsdp {
     bool last_profiled = false;
     double prof_proj_ms = 0.0, prof_iter_ms = 0.0;
     int prof_launches = 0;
+    cdsdp_impl::CmpGraph cmp_graph;  // cached step graph of the completion
 };
 
 namespace {
@@ -700,7 +701,8 @@ int cdsdp_complete(cdsdp* h, const double* d_X, void* d_scratch, size_t scratch_
                    void* stream) {
     if (!h) return CDSDP_ERR_ARG;
     try {
-        return cdsdp_impl::completion_run(h->hp, d_X, d_scratch, scratch_bytes, d_W, logdet, stream, &h->err);
+        return cdsdp_impl::completion_run(h->hp, d_X, d_scratch, scratch_bytes, d_W, logdet, stream, &h->err,
+                                          &h->cmp_graph);
     } catch (const std::bad_alloc&) {
         return CDSDP_ERR_NOMEM;
     }
@@ -963,6 +965,7 @@ int cdsdp_profile(const cdsdp* h, double* proj_ms, int* proj_launches, double* i
 int cdsdp_free(cdsdp* h) {
     if (!h) return CDSDP_ERR_ARG;
     drop_graph(h);
+    cdsdp_impl::completion_release(h->cmp_graph);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     delete h;
     return CDSDP_SOLVED;
