@@ -152,7 +152,50 @@ def adapt_rho(rho, eps_p, eps_d, mu, nu):
     return rho
 
 
-def primal_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None, adapt_every=0, mu=2.0, nu=10.0):
+def conjugate_gradient(matvec, r, y0, tol, max_iter):
+    """Conjugate gradient method (Hestenes and Stiefel 1952; the textbook form
+    in Saad 2003, Section 6.7) for S y = r with S symmetric positive definite
+    given as a product v -> S v.  Starts from y0 and stops once
+    ||r - S y|| <= tol ||r|| or after max_iter steps.  Returns (y, steps)."""
+    y = np.array(y0, dtype=float)
+    res = r - matvec(y)
+    p = res.copy()
+    rr = float(res @ res)
+    target = tol * float(np.linalg.norm(r))
+    k = 0
+    while k < max_iter and np.sqrt(rr) > target:
+        q = matvec(p)
+        alpha = rr / float(p @ q)
+        y = y + alpha * p
+        res = res - alpha * q
+        rr_new = float(res @ res)
+        p = res + (rr_new / rr) * p
+        rr = rr_new
+        k += 1
+    return y, k
+
+
+def _kkt_solver(A, AT, D, linear_solver):
+    """Solver of (A D^-1 A^T) y = r, the only system of Eqs. OptCondMinYPrimal
+    and OptCondMinYDual after eliminating x (Section 4.1.1).  linear_solver
+    None: the cached Cholesky factor (Eq. ADMMprimalFatorization).  ("cg", tol,
+    max_iter): the conjugate gradient method the same section names for when
+    the factorisation is too expensive, warm-started from the previous
+    iteration's y.  Returns solve(r, y_prev) -> (y, cg_steps)."""
+    if linear_solver is None:
+        fac = _cholesky((A @ scipy.sparse.diags(1.0 / D) @ A.T).toarray())
+        return lambda r, y_prev: (scipy.linalg.cho_solve(fac, r), 0)
+    kind, tol, max_steps = linear_solver
+    if kind != "cg":
+        raise ValueError(f"unknown linear solver {kind!r}")
+
+    def matvec(v):
+        return A @ ((AT @ v) / D)
+    return lambda r, y_prev: conjugate_gradient(matvec, r, y_prev, tol, max_steps)
+
+
+def primal_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None, adapt_every=0, mu=2.0, nu=10.0,
+                linear_solver=None):
     """Algorithm 1 (ADMM for the domain-space decomposition).
     x-step: KKT system Eq. OptCondMinYPrimal by block elimination with the
     cached Cholesky factor of A D^-1 A^T (Eq. ADMMprimalFatorization, and
@@ -162,17 +205,22 @@ def primal_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None,
     adapt_every = N > 0 applies the adaptive penalty rule (Section 7.1.2,
     `adapt_rho`) after every N-th iteration whose stopping test failed; the
     multipliers are unscaled, so nothing else changes with rho.  History
-    column 2 holds the rho of each iteration."""
+    column 2 holds the rho of each iteration.  linear_solver: see
+    `_kkt_solver` (None: cached Cholesky factor; ("cg", tol, steps): conjugate
+    gradient, steps per iteration kept in state["cg_steps"])."""
     A, b, c, D = dp.A, dp.b, dp.c, dp.D
     AT = A.T.tocsr()
-    fac = _cholesky((A @ scipy.sparse.diags(1.0 / D) @ A.T).toarray())
+    kkt = _kkt_solver(A, AT, D, linear_solver)
     xk = np.zeros(dp.nd)
     lam = np.zeros(dp.nd)
+    y = np.zeros(dp.m)
+    cg_steps = []
     hist = []
     status = MAX_ITER
     for it in range(1, max_iter + 1):
         bhat = dp.HT(xk + lam / rho) - c / rho
-        y = scipy.linalg.cho_solve(fac, A @ (bhat / D) - b)
+        y, steps = kkt(A @ (bhat / D) - b, y)
+        cg_steps.append(steps)
         x = (bhat - AT @ y) / D
         Hx = dp.H(x)
         xk_new = dp.project_cliques(Hx - lam / rho)
@@ -190,28 +238,32 @@ def primal_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None,
         if adapt_every > 0 and it % adapt_every == 0:
             rho = adapt_rho(rho, eps_c, eps_l, mu, nu)
     return Result(status, it, x, -rho_it * y, dp.HT(lam), np.array(hist),
-                  state=dict(x=x, y_kkt=y, xk=xk, lam=lam, rho=rho_it))
+                  state=dict(x=x, y_kkt=y, xk=xk, lam=lam, rho=rho_it, cg_steps=cg_steps))
 
 
-def dual_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None, adapt_every=0, mu=2.0, nu=10.0):
+def dual_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None, adapt_every=0, mu=2.0, nu=10.0,
+              linear_solver=None):
     """Algorithm 2 (ADMM for the range-space decomposition).
     z-step Eq. zkUpdate; (y, x) from the KKT system Eq. OptCondMinYDual with the
     same cached factor of A D^-1 A^T; v_k from Eq. vkEqn; lambda_k from the
     generic rule Eq. MultUpdateDualSDP; stopping Section 4.2.4.  Adaptive
-    penalty and history column 2 as in `primal_admm`."""
+    penalty, history column 2 and linear_solver as in `primal_admm`."""
     A, b, c, D = dp.A, dp.b, dp.c, dp.D
     AT = A.T.tocsr()
-    fac = _cholesky((A @ scipy.sparse.diags(1.0 / D) @ A.T).toarray())
+    kkt = _kkt_solver(A, AT, D, linear_solver)
     z = np.zeros(dp.nd)
     v = np.zeros(dp.nd)
     lam = np.zeros(dp.nd)
+    y = np.zeros(dp.m)
+    cg_steps = []
     hist = []
     status = MAX_ITER
     for it in range(1, max_iter + 1):
         z_new = dp.project_cliques(v - lam / rho)
         rhs1 = c - dp.HT(z_new + lam / rho)
         rhs2 = -b / rho
-        y = scipy.linalg.cho_solve(fac, A @ (rhs1 / D) - rhs2)
+        y, steps = kkt(A @ (rhs1 / D) - rhs2, y)
+        cg_steps.append(steps)
         x = (rhs1 - AT @ y) / D
         Hx = dp.H(x)
         v = z_new + lam / rho + Hx
@@ -229,7 +281,7 @@ def dual_admm(dp: Decomposed, rho=1.0, eps=1e-4, max_iter=2000, callback=None, a
         if adapt_every > 0 and it % adapt_every == 0:
             rho = adapt_rho(rho, eps_c, eps_l, mu, nu)
     return Result(status, it, -rho_it * x, y, dp.HT(z), np.array(hist),
-                  state=dict(x=x, y=y, z=z, v=v, lam=lam, rho=rho_it))
+                  state=dict(x=x, y=y, z=z, v=v, lam=lam, rho=rho_it, cg_steps=cg_steps))
 
 
 class HSDEOperator:
