@@ -29,6 +29,29 @@ namespace {
 
 // Run body(t) for t = 0 .. T-1 on T host threads (T = hardware threads, at
 // most `cap`); plain loop when one thread is enough.
+constexpr int kSetupThreads = 16;  // cap on threads of the triplet loops
+
+// Barrier for the threads of one parallel_threads call (all of them run at
+// once); spins briefly, then yields.
+class SpinBarrier {
+  public:
+    explicit SpinBarrier(int n) : n_(n) {}
+    void wait() {
+        const int g = gen_.load(std::memory_order_acquire);
+        if (count_.fetch_add(1, std::memory_order_acq_rel) + 1 == n_) {
+            count_.store(0, std::memory_order_relaxed);
+            gen_.fetch_add(1, std::memory_order_release);
+            return;
+        }
+        for (int spins = 0; gen_.load(std::memory_order_acquire) == g; ++spins)
+            if (spins > 256) std::this_thread::yield();
+    }
+
+  private:
+    std::atomic<int> count_{0}, gen_{0};
+    const int n_;
+};
+
 template <typename F>
 void parallel_threads(int cap, F&& body) {
     int T = (int)std::thread::hardware_concurrency();
@@ -48,20 +71,34 @@ void parallel_threads(int cap, F&& body) {
 bool spd_inverse(std::vector<double>& a, int m, std::vector<double>& inv, int threads) {
     double maxdiag = 0.0;
     for (int i = 0; i < m; ++i) maxdiag = std::max(maxdiag, std::fabs(a[(size_t)i * m + i]));
-    for (int j = 0; j < m; ++j) {
-        const double* rj = &a[(size_t)j * m];
-        double d = rj[j];
-        for (int k = 0; k < j; ++k) d -= rj[k] * rj[k];
-        if (!(d > 1e-14 * maxdiag)) return false;
-        const double ljj = std::sqrt(d);
-        a[(size_t)j * m + j] = ljj;
-        for (int i = j + 1; i < m; ++i) {
-            double* ri = &a[(size_t)i * m];
-            double s = ri[j];
-            for (int k = 0; k < j; ++k) s -= ri[k] * rj[k];
-            ri[j] = s / ljj;
+    // Cholesky by columns; the rows below the pivot are shared out, row i to
+    // thread i mod T, which also owns the pivot of column i; one barrier per
+    // column.  Every element sees the same operations in the same order for
+    // any T.
+    const int TC = m >= 256 ? std::max(1, std::min(threads, (int)std::thread::hardware_concurrency())) : 1;
+    SpinBarrier bar(TC);
+    std::atomic<int> bad(0);
+    parallel_threads(TC, [&](int t, int T) {
+        for (int j = 0; j < m; ++j) {
+            double* rj = &a[(size_t)j * m];
+            if (j % T == t) {
+                double d = rj[j];
+                for (int k = 0; k < j; ++k) d -= rj[k] * rj[k];
+                if (!(d > 1e-14 * maxdiag)) bad.store(1, std::memory_order_relaxed);
+                else rj[j] = std::sqrt(d);
+            }
+            if (T > 1) bar.wait();
+            if (bad.load(std::memory_order_relaxed)) return;
+            const double ljj = rj[j];
+            for (int i = j + 1 + ((t - j - 1) % T + T) % T; i < m; i += T) {
+                double* ri = &a[(size_t)i * m];
+                double s = ri[j];
+                for (int k = 0; k < j; ++k) s -= ri[k] * rj[k];
+                ri[j] = s / ljj;
+            }
         }
-    }
+    });
+    if (bad) return false;
     // xt row j = column j of L^-1 (entries j..m-1): L x = e_j
     std::vector<double> xt((size_t)m * m, 0.0);
     const int cap = m >= 128 ? threads : 1;
@@ -130,8 +167,10 @@ int build_factor(const HostProblem& hp, bool hsde, std::vector<double>& inv) {
     }
     // lower triangle of each block (the constraints of an A^T row are in
     // ascending order, hence so are their positions in the block), then mirror
-    std::vector<int> lr;
-    for (int e = 0; e < NE; ++e) {
+    // (every element gets its terms in entry order whatever the threading:
+    // one component -> threads own the block rows r with r mod T = t and each
+    // scans every entry; several -> threads take whole components)
+    auto accumulate = [&](int e, std::vector<int>& lr, int th, int T) {
         const int c = hp.comp_of_entry[e];
         const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
         double* S = blocks[c].data();
@@ -141,10 +180,32 @@ int build_factor(const HostProblem& hp, bool hsde, std::vector<double>& inv) {
         for (int u = 0; u < nq; ++u) lr[u] = hp.lrow[hp.at_col[q0 + u]];
         const double* av = &hp.at_val[q0];
         for (int u = 0; u < nq; ++u) {
+            if (lr[u] % T != th) continue;
             const double v1 = f * av[u];
             double* row = S + (size_t)lr[u] * mc;
             for (int w = 0; w <= u; ++w) row[lr[w]] += v1 * av[w];
         }
+    };
+    const int TS = hp.at_ptr[NE] >= (1 << 16) ? kSetupThreads : 1;
+    if (hp.ncomp == 1) {
+        parallel_threads(TS, [&](int th, int T) {
+            std::vector<int> lr;
+            for (int e = 0; e < NE; ++e) accumulate(e, lr, th, T);
+        });
+    } else {
+        std::vector<int> eptr(hp.ncomp + 1, 0), eidx(NE);
+        for (int e = 0; e < NE; ++e) ++eptr[hp.comp_of_entry[e] + 1];
+        for (int c = 0; c < hp.ncomp; ++c) eptr[c + 1] += eptr[c];
+        {
+            std::vector<int> fill(eptr.begin(), eptr.end() - 1);
+            for (int e = 0; e < NE; ++e) eidx[fill[hp.comp_of_entry[e]]++] = e;
+        }
+        std::atomic<int> next(0);
+        parallel_threads(TS, [&](int, int) {
+            std::vector<int> lr;
+            for (int c = next++; c < hp.ncomp; c = next++)
+                for (int q = eptr[c]; q < eptr[c + 1]; ++q) accumulate(eidx[q], lr, 0, 1);
+        });
     }
     for (int c = 0; c < hp.ncomp; ++c) {
         const int mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
@@ -276,13 +337,24 @@ int build_host_problem(int n, int m,
     for (long long k = 0; k < nnzP; ++k) add_edge(P_row[k], P_col[k]);
     tidy();
     {
-        std::vector<std::pair<int, int>> extra;
-        for (long long k = 0; k < nnzA; ++k) {
-            const int r = A_row[k], c = A_col[k];
-            if (r != c && !std::binary_search(adj[r].begin(), adj[r].end(), c)) extra.push_back({r, c});
+        // entries of A not yet in the pattern: threads over chunks of the
+        // triplets, results concatenated in triplet order
+        const int TA = nnzA >= (1 << 16) ? kSetupThreads : 1;
+        std::vector<std::vector<std::pair<int, int>>> extra_t(std::max(1, TA));
+        parallel_threads(TA, [&](int t, int T) {
+            const long long k0 = nnzA * t / T, k1 = nnzA * (t + 1) / T;
+            auto& ex = extra_t[t];
+            for (long long k = k0; k < k1; ++k) {
+                const int r = A_row[k], c = A_col[k];
+                if (r != c && !std::binary_search(adj[r].begin(), adj[r].end(), c)) ex.push_back({r, c});
+            }
+        });
+        bool any = false;
+        for (auto& ex : extra_t) {
+            for (auto& e : ex) add_edge(e.first, e.second);
+            any = any || !ex.empty();
         }
-        for (auto& e : extra) add_edge(e.first, e.second);
-        if (!extra.empty()) tidy();
+        if (any) tidy();
     }
     long long nedges = 0;
     for (auto& a : adj) {
@@ -446,43 +518,95 @@ int build_host_problem(int n, int m,
     hp.c.assign(NE, 0.0);
     for (long long k = 0; k < nnzC; ++k) hp.c[entry_of(hp, C_row[k], C_col[k])] += C_val[k];
     {
-        // bucket the triplets by constraint, sort each row by entry, merge duplicates
+        // bucket the triplets by constraint (triplet order kept within a row),
+        // sort each row by entry, merge duplicates; threads over chunks of the
+        // triplets, then over rows; the result does not depend on the thread count
+        const int TA = nnzA >= (1 << 16) ? kSetupThreads : 1;
+        const int T = std::max(1, std::min(TA, (int)std::thread::hardware_concurrency()));
+        std::vector<long long> cnt((size_t)T * m, 0);  // per chunk, per row
+        parallel_threads(T, [&](int t, int TT) {
+            const long long k0 = nnzA * t / TT, k1 = nnzA * (t + 1) / TT;
+            long long* ct = &cnt[(size_t)t * m];
+            for (long long k = k0; k < k1; ++k) ++ct[A_con[k]];
+        });
         std::vector<long long> rp(m + 1, 0);
-        for (long long k = 0; k < nnzA; ++k) ++rp[A_con[k] + 1];
-        for (int i = 0; i < m; ++i) rp[i + 1] += rp[i];
-        std::vector<std::pair<int, double>> t((size_t)nnzA);
-        {
-            std::vector<long long> fill(rp.begin(), rp.end() - 1);
-            for (long long k = 0; k < nnzA; ++k)
-                t[(size_t)fill[A_con[k]]++] = {entry_of(hp, A_row[k], A_col[k]), A_val[k]};
-        }
-        hp.a_ptr.assign(m + 1, 0);
-        hp.a_col.reserve((size_t)nnzA);
-        hp.a_val.reserve((size_t)nnzA);
         for (int i = 0; i < m; ++i) {
-            auto b0 = t.begin() + rp[i], b1 = t.begin() + rp[i + 1];
-            std::sort(b0, b1, [](const auto& x, const auto& y) { return x.first < y.first; });
-            int last = -1;
-            for (auto it = b0; it != b1; ++it) {
-                if (it->first == last) { hp.a_val.back() += it->second; continue; }
-                last = it->first;
-                hp.a_col.push_back(it->first);
-                hp.a_val.push_back(it->second);
+            long long o = rp[i];
+            for (int t = 0; t < T; ++t) {
+                const long long c = cnt[(size_t)t * m + i];
+                cnt[(size_t)t * m + i] = o;  // now the chunk's first slot in row i
+                o += c;
             }
-            hp.a_ptr[i + 1] = (int)hp.a_col.size();
+            rp[i + 1] = o;
         }
-        hp.at_ptr.assign(NE + 1, 0);
-        for (int e : hp.a_col) ++hp.at_ptr[e + 1];
-        for (int e = 0; e < NE; ++e) hp.at_ptr[e + 1] += hp.at_ptr[e];
-        hp.at_col.resize(hp.a_col.size());
-        hp.at_val.resize(hp.a_col.size());
-        std::vector<int> fill(hp.at_ptr.begin(), hp.at_ptr.end() - 1);
-        for (int i = 0; i < m; ++i)
-            for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) {
-                int dst = fill[hp.a_col[q]]++;
-                hp.at_col[dst] = i;
-                hp.at_val[dst] = hp.a_val[q];
+        std::vector<std::pair<int, double>> t((size_t)nnzA);
+        parallel_threads(T, [&](int th, int TT) {
+            const long long k0 = nnzA * th / TT, k1 = nnzA * (th + 1) / TT;
+            long long* fill = &cnt[(size_t)th * m];
+            for (long long k = k0; k < k1; ++k)
+                t[(size_t)fill[A_con[k]]++] = {entry_of(hp, A_row[k], A_col[k]), A_val[k]};
+        });
+        std::vector<int> merged(m, 0);
+        parallel_threads(T, [&](int th, int TT) {
+            for (int i = th; i < m; i += TT) {
+                auto b0 = t.begin() + rp[i], b1 = t.begin() + rp[i + 1];
+                std::sort(b0, b1, [](const auto& x, const auto& y) { return x.first < y.first; });
+                auto out = b0;
+                for (auto it = b0; it != b1; ++it) {
+                    if (out != b0 && (out - 1)->first == it->first) { (out - 1)->second += it->second; continue; }
+                    *out++ = *it;
+                }
+                merged[i] = (int)(out - b0);
             }
+        });
+        hp.a_ptr.assign(m + 1, 0);
+        for (int i = 0; i < m; ++i) hp.a_ptr[i + 1] = hp.a_ptr[i] + merged[i];
+        hp.a_col.resize(hp.a_ptr[m]);
+        hp.a_val.resize(hp.a_ptr[m]);
+        parallel_threads(T, [&](int th, int TT) {
+            for (int i = th; i < m; i += TT)
+                for (int q = 0; q < merged[i]; ++q) {
+                    hp.a_col[hp.a_ptr[i] + q] = t[(size_t)rp[i] + q].first;
+                    hp.a_val[hp.a_ptr[i] + q] = t[(size_t)rp[i] + q].second;
+                }
+        });
+        // A^T: counting sort by entry, rows ascending within an entry; threads
+        // over contiguous row ranges when their per-entry counters fit
+        const int nnz = hp.a_ptr[m];
+        const int TT2 = ((size_t)T * (NE + 1) * sizeof(int) <= (64u << 20) && nnz >= (1 << 16)) ? T : 1;
+        std::vector<int> rb(TT2 + 1, m);  // row range of chunk t: [rb[t], rb[t+1]), about nnz / TT2 each
+        rb[0] = 0;
+        for (int th = 1, i = 0; th < TT2; ++th) {
+            const long long target = (long long)nnz * th / TT2;
+            while (i < m && hp.a_ptr[i] < target) ++i;
+            rb[th] = i;
+        }
+        std::vector<int> ecnt((size_t)TT2 * NE, 0);
+        parallel_threads(TT2, [&](int th, int) {
+            int* ec = &ecnt[(size_t)th * NE];
+            for (int q = hp.a_ptr[rb[th]]; q < hp.a_ptr[rb[th + 1]]; ++q) ++ec[hp.a_col[q]];
+        });
+        hp.at_ptr.assign(NE + 1, 0);
+        for (int e = 0; e < NE; ++e) {
+            int o = hp.at_ptr[e];
+            for (int th = 0; th < TT2; ++th) {
+                const int c = ecnt[(size_t)th * NE + e];
+                ecnt[(size_t)th * NE + e] = o;
+                o += c;
+            }
+            hp.at_ptr[e + 1] = o;
+        }
+        hp.at_col.resize(nnz);
+        hp.at_val.resize(nnz);
+        parallel_threads(TT2, [&](int th, int) {
+            int* fill = &ecnt[(size_t)th * NE];
+            for (int i = rb[th]; i < rb[th + 1]; ++i)
+                for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) {
+                    const int dst = fill[hp.a_col[q]]++;
+                    hp.at_col[dst] = i;
+                    hp.at_val[dst] = hp.a_val[q];
+                }
+        });
     }
     hp.b.assign(bvec, bvec + m);
 
