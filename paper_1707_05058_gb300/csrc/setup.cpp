@@ -17,6 +17,7 @@
 #include <atomic>
 #include <cmath>
 #include <map>
+#include <memory>
 #include <new>
 #include <set>
 #include <thread>
@@ -539,7 +540,12 @@ int build_host_problem(int n, int m,
             }
             rp[i + 1] = o;
         }
-        std::vector<std::pair<int, double>> t((size_t)nnzA);
+        // (entry, value) records, left uninitialised: the threads touch them first
+        struct Rec {
+            int first;
+            double second;
+        };
+        std::unique_ptr<Rec[]> t(new Rec[(size_t)std::max(1LL, nnzA)]);
         parallel_threads(T, [&](int th, int TT) {
             const long long k0 = nnzA * th / TT, k1 = nnzA * (th + 1) / TT;
             long long* fill = &cnt[(size_t)th * m];
@@ -549,10 +555,11 @@ int build_host_problem(int n, int m,
         std::vector<int> merged(m, 0);
         parallel_threads(T, [&](int th, int TT) {
             for (int i = th; i < m; i += TT) {
-                auto b0 = t.begin() + rp[i], b1 = t.begin() + rp[i + 1];
+                Rec* b0 = t.get() + rp[i];
+                Rec* b1 = t.get() + rp[i + 1];
                 std::sort(b0, b1, [](const auto& x, const auto& y) { return x.first < y.first; });
-                auto out = b0;
-                for (auto it = b0; it != b1; ++it) {
+                Rec* out = b0;
+                for (Rec* it = b0; it != b1; ++it) {
                     if (out != b0 && (out - 1)->first == it->first) { (out - 1)->second += it->second; continue; }
                     *out++ = *it;
                 }
