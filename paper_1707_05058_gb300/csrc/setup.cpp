@@ -31,6 +31,7 @@ namespace {
 // Run body(t) for t = 0 .. T-1 on T host threads (T = hardware threads, at
 // most `cap`); plain loop when one thread is enough.
 constexpr int kSetupThreads = 16;  // cap on threads of the triplet loops
+constexpr size_t kBitsetMaxOrder = 32768;  // bit-matrix elimination graph up to n^2/8 = 128 MB
 
 // Barrier for the threads of one parallel_threads call (all of them run at
 // once); spins briefly, then yields.
@@ -407,7 +408,47 @@ int build_host_problem(int n, int m,
         }
     }
     hp.chordal = chordal;
-    if (!chordal) {
+    if (!chordal && (size_t)n <= kBitsetMaxOrder) {
+        // exact minimum-degree elimination game (ties: smallest vertex) on a
+        // bit-matrix elimination graph: eliminating v ORs row v into the rows
+        // of its neighbours (the fill) and clears v; degrees are popcounts
+        const size_t W = ((size_t)n + 63) / 64;
+        std::vector<uint64_t> bits((size_t)n * W, 0);
+        auto row = [&](int v) { return bits.data() + (size_t)v * W; };
+        for (int v = 0; v < n; ++v)
+            for (int u : adj[v]) row(v)[u >> 6] |= 1ULL << (u & 63);
+        std::vector<int> deg(n);
+        std::set<std::pair<int, int>> order;
+        for (int v = 0; v < n; ++v) {
+            deg[v] = (int)adj[v].size();
+            order.insert({deg[v], v});
+        }
+        std::vector<int> nb;
+        for (int k = 0; k < n; ++k) {
+            const int v = order.begin()->second;
+            order.erase(order.begin());
+            elim[k] = v;
+            pos[v] = k;
+            const uint64_t* rv = row(v);
+            nb.clear();
+            for (size_t w = 0; w < W; ++w)
+                for (uint64_t x = rv[w]; x; x &= x - 1) nb.push_back((int)(w * 64 + __builtin_ctzll(x)));
+            later[v] = nb;
+            const uint64_t vbit = 1ULL << (v & 63);
+            for (int u : nb) {
+                uint64_t* ru = row(u);
+                for (size_t w = 0; w < W; ++w) ru[w] |= rv[w];
+                ru[u >> 6] &= ~(1ULL << (u & 63));
+                ru[v >> 6] &= ~vbit;
+                int d = 0;
+                for (size_t w = 0; w < W; ++w) d += __builtin_popcountll(ru[w]);
+                order.erase({deg[u], u});
+                deg[u] = d;
+                order.insert({d, u});
+            }
+            std::fill(bits.begin() + (size_t)v * W, bits.begin() + (size_t)(v + 1) * W, 0ULL);
+        }
+    } else if (!chordal) {
         // exact minimum-degree elimination game (ties: smallest vertex)
         std::vector<std::set<int>> g(n);
         for (int v = 0; v < n; ++v) g[v].insert(adj[v].begin(), adj[v].end());
@@ -494,23 +535,65 @@ int build_host_problem(int n, int m,
     hp.pk_off.assign(p + 1, 0);
     for (int k = 0; k < p; ++k) hp.pk_off[k + 1] = hp.pk_off[k] + packed_size((int)cliques[k].size());
     hp.gmap.resize(hp.pk_off[p]);
-    for (int k = 0; k < p; ++k) {
-        const auto& cl = cliques[k];
-        int s = (int)cl.size(), q = hp.pk_off[k];
-        for (int bb = 0; bb < s; ++bb)
-            for (int a = bb; a < s; ++a) {
-                int e = entry_of(hp, cl[a], cl[bb]);
-                if (e < 0) return CDSDP_ERR_ARG;  // cannot happen for a valid extension
-                hp.gmap[q++] = e;
+    {
+        // threads take whole cliques; within a clique column the rows ascend,
+        // so each search starts past the previous hit
+        std::atomic<int> next(0), missing(0);
+        const int TG = hp.pk_off[p] >= (1 << 16) ? kSetupThreads : 1;
+        parallel_threads(TG, [&](int, int) {
+            for (int k = next++; k < p; k = next++) {
+                const auto& cl = cliques[k];
+                const int s = (int)cl.size();
+                int q = hp.pk_off[k];
+                for (int bb = 0; bb < s; ++bb) {
+                    const int* beg = hp.prow.data() + hp.colptr[cl[bb]];
+                    const int* end = hp.prow.data() + hp.colptr[cl[bb] + 1];
+                    for (int a = bb; a < s; ++a) {
+                        const int* it = std::lower_bound(beg, end, cl[a]);
+                        if (it == end || *it != cl[a]) {  // cannot happen for a valid extension
+                            missing = 1;
+                            hp.gmap[q++] = 0;
+                            continue;
+                        }
+                        hp.gmap[q++] = (int)(it - hp.prow.data());
+                        beg = it + 1;
+                    }
+                }
             }
+        });
+        if (missing) return CDSDP_ERR_ARG;
     }
     hp.sc_ptr.assign(NE + 1, 0);
-    for (int e : hp.gmap) ++hp.sc_ptr[e + 1];
-    for (int e = 0; e < NE; ++e) hp.sc_ptr[e + 1] += hp.sc_ptr[e];
     hp.sc_idx.resize(hp.gmap.size());
-    {
+    const long long nq = (long long)hp.gmap.size();
+    if (nq < (1 << 20)) {
+        for (int e : hp.gmap) ++hp.sc_ptr[e + 1];
+        for (int e = 0; e < NE; ++e) hp.sc_ptr[e + 1] += hp.sc_ptr[e];
         std::vector<int> fill(hp.sc_ptr.begin(), hp.sc_ptr.end() - 1);
-        for (int q = 0; q < (int)hp.gmap.size(); ++q) hp.sc_idx[fill[hp.gmap[q]]++] = q;
+        for (int q = 0; q < (int)nq; ++q) hp.sc_idx[fill[hp.gmap[q]]++] = q;
+    } else {
+        // threads over chunks of packed positions with atomic counters and
+        // cursors, then each entry's (short) position list sorted: the same
+        // ascending lists as the sequential pass
+        std::unique_ptr<std::atomic<int>[]> cur(new std::atomic<int>[NE]);
+        for (int e = 0; e < NE; ++e) cur[e].store(0, std::memory_order_relaxed);
+        parallel_threads(kSetupThreads, [&](int t, int T) {
+            const long long q0 = nq * t / T, q1 = nq * (t + 1) / T;
+            for (long long q = q0; q < q1; ++q) cur[hp.gmap[q]].fetch_add(1, std::memory_order_relaxed);
+        });
+        for (int e = 0; e < NE; ++e) {
+            hp.sc_ptr[e + 1] = hp.sc_ptr[e] + cur[e].load(std::memory_order_relaxed);
+            cur[e].store(hp.sc_ptr[e], std::memory_order_relaxed);
+        }
+        parallel_threads(kSetupThreads, [&](int t, int T) {
+            const long long q0 = nq * t / T, q1 = nq * (t + 1) / T;
+            for (long long q = q0; q < q1; ++q)
+                hp.sc_idx[cur[hp.gmap[q]].fetch_add(1, std::memory_order_relaxed)] = (int)q;
+        });
+        parallel_threads(kSetupThreads, [&](int t, int T) {
+            const int e0 = (int)((long long)NE * t / T), e1 = (int)((long long)NE * (t + 1) / T);
+            for (int e = e0; e < e1; ++e) std::sort(hp.sc_idx.begin() + hp.sc_ptr[e], hp.sc_idx.begin() + hp.sc_ptr[e + 1]);
+        });
     }
     hp.D.resize(NE);
     for (int e = 0; e < NE; ++e) hp.D[e] = (double)(hp.sc_ptr[e + 1] - hp.sc_ptr[e]);
