@@ -423,31 +423,49 @@ int build_host_problem(int n, int m,
             deg[v] = (int)adj[v].size();
             order.insert({deg[v], v});
         }
-        std::vector<int> nb;
-        for (int k = 0; k < n; ++k) {
-            const int v = order.begin()->second;
-            order.erase(order.begin());
-            elim[k] = v;
-            pos[v] = k;
-            const uint64_t* rv = row(v);
-            nb.clear();
-            for (size_t w = 0; w < W; ++w)
-                for (uint64_t x = rv[w]; x; x &= x - 1) nb.push_back((int)(w * 64 + __builtin_ctzll(x)));
-            later[v] = nb;
-            const uint64_t vbit = 1ULL << (v & 63);
-            for (int u : nb) {
-                uint64_t* ru = row(u);
-                for (size_t w = 0; w < W; ++w) ru[w] |= rv[w];
-                ru[u >> 6] &= ~(1ULL << (u & 63));
-                ru[v >> 6] &= ~vbit;
-                int d = 0;
-                for (size_t w = 0; w < W; ++w) d += __builtin_popcountll(ru[w]);
-                order.erase({deg[u], u});
-                deg[u] = d;
-                order.insert({d, u});
+        // thread 0 picks each pivot and keeps the degree order; the row
+        // updates of the pivot's neighbours are shared out (two barriers a step)
+        std::vector<int> nb, newdeg(n);
+        const int TE = std::max(1, std::min(n >= 2048 ? kSetupThreads : 1, (int)std::thread::hardware_concurrency()));
+        SpinBarrier bar(TE);
+        parallel_threads(TE, [&](int t, int T) {
+            for (int k = 0; k < n; ++k) {
+                if (t == 0) {
+                    const int v = order.begin()->second;
+                    order.erase(order.begin());
+                    elim[k] = v;
+                    pos[v] = k;
+                    const uint64_t* rv = row(v);
+                    nb.clear();
+                    for (size_t w = 0; w < W; ++w)
+                        for (uint64_t x = rv[w]; x; x &= x - 1) nb.push_back((int)(w * 64 + __builtin_ctzll(x)));
+                    later[v] = nb;
+                }
+                bar.wait();
+                const int v = elim[k];
+                const uint64_t* rv = row(v);
+                const uint64_t vbit = 1ULL << (v & 63);
+                for (size_t a = t; a < nb.size(); a += T) {
+                    const int u = nb[a];
+                    uint64_t* ru = row(u);
+                    for (size_t w = 0; w < W; ++w) ru[w] |= rv[w];
+                    ru[u >> 6] &= ~(1ULL << (u & 63));
+                    ru[v >> 6] &= ~vbit;
+                    int d = 0;
+                    for (size_t w = 0; w < W; ++w) d += __builtin_popcountll(ru[w]);
+                    newdeg[u] = d;
+                }
+                bar.wait();
+                if (t == 0) {
+                    for (int u : nb) {
+                        order.erase({deg[u], u});
+                        deg[u] = newdeg[u];
+                        order.insert({deg[u], u});
+                    }
+                    std::fill(bits.begin() + (size_t)v * W, bits.begin() + (size_t)(v + 1) * W, 0ULL);
+                }
             }
-            std::fill(bits.begin() + (size_t)v * W, bits.begin() + (size_t)(v + 1) * W, 0ULL);
-        }
+        });
     } else if (!chordal) {
         // exact minimum-degree elimination game (ties: smallest vertex)
         std::vector<std::set<int>> g(n);
