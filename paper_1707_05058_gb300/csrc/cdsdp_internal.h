@@ -4,12 +4,40 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
+#include <new>
+#include <type_traits>
+#include <utility>
 #include <string>
 #include <vector>
 
 #include "../../include/cdsdp.h"
 
 namespace cdsdp_impl {
+
+// Allocator whose value-initialisation leaves trivially constructible
+// elements uninitialised, so that resizing the large host arrays does not
+// zero gigabytes on one thread before the threads fill them.
+template <typename T>
+struct DefaultInitAlloc : std::allocator<T> {
+    template <typename U>
+    struct rebind {
+        using other = DefaultInitAlloc<U>;
+    };
+    DefaultInitAlloc() noexcept = default;
+    template <typename U>
+    DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
+    template <typename U>
+    void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+        ::new (static_cast<void*>(p)) U;
+    }
+    template <typename U, typename... Args>
+    void construct(U* p, Args&&... args) {
+        ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+    }
+};
+template <typename T>
+using BigVec = std::vector<T, DefaultInitAlloc<T>>;
 
 // Everything the data-preprocessing step of Algorithms 1-3 produces, on the host.
 struct HostProblem {
@@ -27,15 +55,18 @@ struct HostProblem {
     // entry (a, b), a >= b, of the |C_k| x |C_k| block sits at
     // pk_off[k] + b*(2s - b + 1)/2 + (a - b)
     std::vector<int> pk_off;
-    std::vector<int> gmap;            // packed position -> pattern entry (H_k)
-    std::vector<int> sc_ptr, sc_idx;  // pattern entry -> packed positions (H^T)
+    BigVec<int> gmap;                 // packed position -> pattern entry (H_k)
+    std::vector<int> sc_ptr;          // pattern entry -> packed positions (H^T)
+    BigVec<int> sc_idx;
     std::vector<double> c, D;         // per pattern entry
     // A as CSR over (constraint, pattern entry), unweighted values
-    std::vector<int> a_ptr, a_col;
-    std::vector<double> a_val;
+    std::vector<int> a_ptr;
+    BigVec<int> a_col;
+    BigVec<double> a_val;
     // A^T as CSR over (pattern entry, constraint)
-    std::vector<int> at_ptr, at_col;
-    std::vector<double> at_val;
+    std::vector<int> at_ptr;
+    BigVec<int> at_col;
+    BigVec<double> at_val;
     std::vector<double> b;
     long long nfill = 0;
     bool chordal = false;

@@ -678,43 +678,6 @@ int build_host_problem(int n, int m,
                     hp.a_val[hp.a_ptr[i] + q] = t[(size_t)rp[i] + q].second;
                 }
         });
-        // A^T: counting sort by entry, rows ascending within an entry; threads
-        // over contiguous row ranges when their per-entry counters fit
-        const int nnz = hp.a_ptr[m];
-        const int TT2 = ((size_t)T * (NE + 1) * sizeof(int) <= (64u << 20) && nnz >= (1 << 16)) ? T : 1;
-        std::vector<int> rb(TT2 + 1, m);  // row range of chunk t: [rb[t], rb[t+1]), about nnz / TT2 each
-        rb[0] = 0;
-        for (int th = 1, i = 0; th < TT2; ++th) {
-            const long long target = (long long)nnz * th / TT2;
-            while (i < m && hp.a_ptr[i] < target) ++i;
-            rb[th] = i;
-        }
-        std::vector<int> ecnt((size_t)TT2 * NE, 0);
-        parallel_threads(TT2, [&](int th, int) {
-            int* ec = &ecnt[(size_t)th * NE];
-            for (int q = hp.a_ptr[rb[th]]; q < hp.a_ptr[rb[th + 1]]; ++q) ++ec[hp.a_col[q]];
-        });
-        hp.at_ptr.assign(NE + 1, 0);
-        for (int e = 0; e < NE; ++e) {
-            int o = hp.at_ptr[e];
-            for (int th = 0; th < TT2; ++th) {
-                const int c = ecnt[(size_t)th * NE + e];
-                ecnt[(size_t)th * NE + e] = o;
-                o += c;
-            }
-            hp.at_ptr[e + 1] = o;
-        }
-        hp.at_col.resize(nnz);
-        hp.at_val.resize(nnz);
-        parallel_threads(TT2, [&](int th, int) {
-            int* fill = &ecnt[(size_t)th * NE];
-            for (int i = rb[th]; i < rb[th + 1]; ++i)
-                for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) {
-                    const int dst = fill[hp.a_col[q]]++;
-                    hp.at_col[dst] = i;
-                    hp.at_val[dst] = hp.a_val[q];
-                }
-        });
     }
     hp.b.assign(bvec, bvec + m);
 
@@ -774,6 +737,77 @@ int build_host_problem(int n, int m,
         {
             std::vector<int> fill(hp.ccl_ptr.begin(), hp.ccl_ptr.end() - 1);
             for (int k = 0; k < p; ++k) hp.ccl_idx[fill[hp.comp_of_clique[k]]++] = k;
+        }
+    }
+
+    // ---- A^T: counting sort by entry, rows ascending within an entry
+    {
+        const int T = std::max(1, std::min(kSetupThreads, (int)std::thread::hardware_concurrency()));
+        const int nnz = hp.a_ptr[m];
+        if (hp.ncomp > 1 && nnz >= (1 << 16)) {
+            // the components own disjoint rows and entries: threads take whole
+            // components, each walking its rows in ascending order
+            hp.at_ptr.assign(NE + 1, 0);
+            std::atomic<int> next(0);
+            parallel_threads(T, [&](int, int) {
+                for (int c = next++; c < hp.ncomp; c = next++)
+                    for (int r = hp.crow_ptr[c]; r < hp.crow_ptr[c + 1]; ++r) {
+                        const int i = hp.crow_idx[r];
+                        for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) ++hp.at_ptr[hp.a_col[q] + 1];
+                    }
+            });
+            for (int e = 0; e < NE; ++e) hp.at_ptr[e + 1] += hp.at_ptr[e];
+            hp.at_col.resize(nnz);
+            hp.at_val.resize(nnz);
+            std::vector<int> fill(hp.at_ptr.begin(), hp.at_ptr.end() - 1);
+            next = 0;
+            parallel_threads(T, [&](int, int) {
+                for (int c = next++; c < hp.ncomp; c = next++)
+                    for (int r = hp.crow_ptr[c]; r < hp.crow_ptr[c + 1]; ++r) {
+                        const int i = hp.crow_idx[r];
+                        for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) {
+                            const int dst = fill[hp.a_col[q]]++;
+                            hp.at_col[dst] = i;
+                            hp.at_val[dst] = hp.a_val[q];
+                        }
+                    }
+            });
+        } else {
+            // threads over contiguous row ranges when their per-entry counters fit
+            const int TT2 = ((size_t)T * (NE + 1) * sizeof(int) <= (64u << 20) && nnz >= (1 << 16)) ? T : 1;
+            std::vector<int> rb(TT2 + 1, m);  // rows of chunk t: [rb[t], rb[t+1]), about nnz / TT2 each
+            rb[0] = 0;
+            for (int th = 1, i = 0; th < TT2; ++th) {
+                const long long target = (long long)nnz * th / TT2;
+                while (i < m && hp.a_ptr[i] < target) ++i;
+                rb[th] = i;
+            }
+            std::vector<int> ecnt((size_t)TT2 * NE, 0);
+            parallel_threads(TT2, [&](int th, int) {
+                int* ec = &ecnt[(size_t)th * NE];
+                for (int q = hp.a_ptr[rb[th]]; q < hp.a_ptr[rb[th + 1]]; ++q) ++ec[hp.a_col[q]];
+            });
+            hp.at_ptr.assign(NE + 1, 0);
+            for (int e = 0; e < NE; ++e) {
+                int o = hp.at_ptr[e];
+                for (int th = 0; th < TT2; ++th) {
+                    const int c = ecnt[(size_t)th * NE + e];
+                    ecnt[(size_t)th * NE + e] = o;
+                    o += c;
+                }
+                hp.at_ptr[e + 1] = o;
+            }
+            hp.at_col.resize(nnz);
+            hp.at_val.resize(nnz);
+            parallel_threads(TT2, [&](int th, int) {
+                int* fill = &ecnt[(size_t)th * NE];
+                for (int i = rb[th]; i < rb[th + 1]; ++i)
+                    for (int q = hp.a_ptr[i]; q < hp.a_ptr[i + 1]; ++q) {
+                        const int dst = fill[hp.a_col[q]]++;
+                        hp.at_col[dst] = i;
+                        hp.at_val[dst] = hp.a_val[q];
+                    }
+            });
         }
     }
 

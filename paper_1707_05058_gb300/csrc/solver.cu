@@ -132,8 +132,8 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     return L;
 }
 
-template <typename V>
-void put(std::vector<unsigned char>& img, size_t off, const std::vector<V>& v) {
+template <typename V, typename A>
+void put(std::vector<unsigned char>& img, size_t off, const std::vector<V, A>& v) {
     if (!v.empty()) std::memcpy(img.data() + off, v.data(), v.size() * sizeof(V));
 }
 
