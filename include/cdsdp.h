@@ -29,7 +29,7 @@
 extern "C" {
 #endif
 
-typedef struct cdsdp cdsdp; /* opaque; created by cdsdp_setup, released by cdsdp_free */
+typedef struct cdsdp cdsdp; /* opaque; created by cdsdp_setup or cdsdp_setup_scaled, released by cdsdp_free */
 
 typedef enum {
     CDSDP_PRIMAL = 0, /* Algorithm 1: domain-space decomposition (Section 4.1) */
