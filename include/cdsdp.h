@@ -94,6 +94,15 @@ typedef struct {
                               kernel over the A^T rows, once per entry             */
     int proj_warps_div;    /* warp-per-clique projections (orders <= 32): warps per
                               block = the kernel's maximum / this (1, 2 or 4)       */
+    int linear_solver;     /* Algorithms 1-2, the system (A D^-1 A^T) y = r of Eqs.
+                              OptCondMinYPrimal / OptCondMinYDual: 0 = the cached
+                              inverse; 1 = conjugate gradient (Section 4.1.1), warm-
+                              started from the previous y, stopped once
+                              ||r - S y|| <= cg_tol ||r|| or after cg_max_steps steps;
+                              runs one stopping test over the whole problem.  HSDE:
+                              CDSDP_ERR_UNSUPPORTED.                                  */
+    double cg_tol;         /* relative residual tolerance of the CG solve (>= 0)       */
+    int cg_max_steps;      /* CG steps per ADMM iteration (0..1024)                    */
 } cdsdp_opts;
 
 typedef struct {
@@ -114,7 +123,7 @@ typedef struct {
  * graph on, check_every 50, 30 Jacobi sweeps, warm start with a cold start every
  * 16 iterations, no profiling, per-component stopping, fixed rho (adaptive
  * rule off; rho_mu 2, rho_nu 10 when switched on), x formed by its own
- * kernel. */
+ * kernel, cached inverse (CG tolerance 1e-10 and 50 steps when switched on). */
 void cdsdp_default_opts(cdsdp_opts* o);
 
 /* Data preprocessing of Algorithms 1-3 (host only, no GPU call):

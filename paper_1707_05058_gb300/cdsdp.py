@@ -37,7 +37,8 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("jacobi_max_sweeps", ctypes.c_int), ("warm_start", ctypes.c_int), ("profile", ctypes.c_int),
                 ("component_stop", ctypes.c_int), ("adaptive_rho", ctypes.c_int), ("rho_mu", ctypes.c_double),
-                ("rho_nu", ctypes.c_double), ("x_update", ctypes.c_int), ("proj_warps_div", ctypes.c_int)]
+                ("rho_nu", ctypes.c_double), ("x_update", ctypes.c_int), ("proj_warps_div", ctypes.c_int),
+                ("linear_solver", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_max_steps", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

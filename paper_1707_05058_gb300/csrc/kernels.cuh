@@ -92,6 +92,12 @@ struct Dev {
     double* comp_res;           // [ncomp * HIST_COLS] last stopping-test row of the component
     double* rho;                // [ncomp] penalty of Algorithms 1-2: one per component when
                                 // components stop on their own, else entry 0 for the whole problem
+    // conjugate-gradient affine step (opts.linear_solver = 1)
+    double *cg_res, *cg_p, *cg_q;  // [m]
+    double* cg_u;                  // [NE]
+    double* cg_scal;               // [4]: ||res||^2, target, steps, done
+    double cg_tol;
+    int cg_max;
 };
 
 constexpr int NBLK_E = 1216;  // 152 SMs x 8

@@ -13,6 +13,7 @@
 
 #include "cdsdp_internal.h"
 #include "forms.cuh"
+#include "cg.cuh"
 #include "proj_launch.h"
 #include "grad.cuh"
 #include "grad_launch.h"
@@ -36,7 +37,7 @@ struct Layout {
     size_t const_end;
     // state
     size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, vcache, part, parte, partr, scal, ctl, hist,
-        comp_done, comp_iter, comp_status, comp_res, rho;
+        comp_done, comp_iter, comp_status, comp_res, rho, cg_res, cg_p, cg_q, cg_u, cg_scal;
     size_t total;
 };
 
@@ -128,6 +129,8 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     L.comp_done = take(nc * 4); L.comp_iter = take(nc * 4); L.comp_status = take(nc * 4);
     L.comp_res = take(nc * HIST_COLS * 8);
     L.rho = take(nc * 8);
+    L.cg_res = take(m * 8); L.cg_p = take(m * 8); L.cg_q = take(m * 8); L.cg_u = take(NE * 8);
+    L.cg_scal = take(4 * 8);
     L.total = o;
     return L;
 }
@@ -223,6 +226,9 @@ void make_dev(cdsdp* h) {
     d.comp_done = (int*)(w + L.comp_done); d.comp_iter = (int*)(w + L.comp_iter);
     d.comp_status = (int*)(w + L.comp_status); d.comp_res = (double*)(w + L.comp_res);
     d.rho = (double*)(w + L.rho);
+    d.cg_res = (double*)(w + L.cg_res); d.cg_p = (double*)(w + L.cg_p); d.cg_q = (double*)(w + L.cg_q);
+    d.cg_u = (double*)(w + L.cg_u); d.cg_scal = (double*)(w + L.cg_scal);
+    d.cg_tol = 0.0; d.cg_max = 0;
     auto pow2_clamp = [](double x, int lo, int hi) {
         int v = lo;
         while (v < hi && v < x) v <<= 1;
@@ -280,6 +286,21 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
 
 // ---- one ADMM iteration -----------------------------------------------------
 
+// y from (A W D^-1 A^T) y = d.g by conjugate gradient (Section 4.1.1), warm
+// start from the y in place; leaves the <b, y> partial of k_gemv.
+void launch_cg(cdsdp* h, const cdsdp_opts& o, cudaStream_t st) {
+    Dev& d = h->dev;
+    k_cg_atp<<<h->GE, ETHREADS, 0, st>>>(d, d.y, h->Gx, 0);
+    k_cg_aw<<<h->GR, RTHREADS, 0, st>>>(d, h->TPR, 0);
+    k_cg_init<<<1, CG_THREADS, 0, st>>>(d, d.g);
+    for (int s = 0; s < o.cg_max_steps; ++s) {
+        k_cg_atp<<<h->GE, ETHREADS, 0, st>>>(d, d.cg_p, h->Gx, 1);
+        k_cg_aw<<<h->GR, RTHREADS, 0, st>>>(d, h->TPR, 1);
+        k_cg_update<<<1, CG_THREADS, 0, st>>>(d);
+    }
+    k_cg_finish<<<1, CG_THREADS, 0, st>>>(d, 0, h->GR);
+}
+
 template <typename T>
 cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream_t st, int use_cond,
                              cudaGraphConditionalHandle hnd, cudaEvent_t ev0, cudaEvent_t ev1) {
@@ -311,7 +332,8 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
     if (form == 0) {  // Algorithm 1; the projection computes x on the fly and its last block the stopping test
         k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0, 1.0, 1.0, 1, 1, d.dinv, d.t, 1, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, 0, d.g, h->TPR);
-        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
+        if (o.linear_solver == 1) launch_cg(h, o, st);
+        else k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
         if (h->x_split) k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Gx, 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
@@ -326,7 +348,8 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         if (ev1) cudaEventRecord(ev1, st);
         k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0, 0, 1, d.dinv, d.t, 1, h->Gs);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0, 1, d.g, h->TPR);
-        k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
+        if (o.linear_solver == 1) launch_cg(h, o, st);
+        else k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
         k_xupd<<<GE, ETHREADS, 0, st>>>(d, d.t, d.y, d.x, h->Ga, 1);
         k_vlam_dual<T><<<PG, 128, 0, st>>>(d, fin);
         if (d.comp_mode) k_finish_components<<<d.ncomp, 256, 0, st>>>(d, 1, fa);
@@ -359,7 +382,8 @@ bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
     return a.eps == b.eps && a.max_iter == b.max_iter && a.rho == b.rho && a.precision == b.precision &&
            a.jacobi_max_sweeps == b.jacobi_max_sweeps && a.warm_start == b.warm_start &&
            a.component_stop == b.component_stop && a.adaptive_rho == b.adaptive_rho && a.rho_mu == b.rho_mu &&
-           a.rho_nu == b.rho_nu && a.x_update == b.x_update && a.proj_warps_div == b.proj_warps_div;
+           a.rho_nu == b.rho_nu && a.x_update == b.x_update && a.proj_warps_div == b.proj_warps_div &&
+           a.linear_solver == b.linear_solver && a.cg_tol == b.cg_tol && a.cg_max_steps == b.cg_max_steps;
 }
 
 void drop_graph(cdsdp* h) {
@@ -411,6 +435,9 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     if (o.adaptive_rho < 0 || !(o.rho_mu >= 1.0) || !(o.rho_nu >= 1.0)) return CDSDP_ERR_ARG;
     if (o.x_update < 0 || o.x_update > 2) return CDSDP_ERR_ARG;
     if (o.proj_warps_div != 1 && o.proj_warps_div != 2 && o.proj_warps_div != 4) return CDSDP_ERR_ARG;
+    if (o.linear_solver != 0 && o.linear_solver != 1) return CDSDP_ERR_ARG;
+    if (!(o.cg_tol >= 0.0) || !std::isfinite(o.cg_tol) || o.cg_max_steps < 0 || o.cg_max_steps > 1024)
+        return CDSDP_ERR_ARG;
     if (o.precision == CDSDP_FP64 && h->hp.max_clique > kMaxOrderF64) return CDSDP_ERR_UNSUPPORTED;
     return CDSDP_SOLVED;
 }
@@ -582,6 +609,7 @@ cdsdp_opts unrolled_opts(const cdsdp_opts* opts) {
     o.use_graph = 0;
     o.profile = 0;
     o.adaptive_rho = 0;  // the reverse pass assumes one fixed rho
+    o.linear_solver = 0;  // and the cached inverse
     return o;
 }
 
@@ -607,6 +635,9 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->rho_nu = 10.0;
     o->x_update = 0;
     o->proj_warps_div = 1;
+    o->linear_solver = 0;
+    o->cg_tol = 1e-10;
+    o->cg_max_steps = 5;
 }
 
 int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
@@ -815,10 +846,13 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     int rc = check_opts(h, o);
     if (rc != CDSDP_SOLVED) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    if (form == 2 && o.linear_solver == 1) return CDSDP_ERR_UNSUPPORTED;
     if (form == 2 && (rc = ensure_hsde(h, st)) != CDSDP_SOLVED) return rc;
     Dev& d = h->dev;
     d.max_iter = o.max_iter;
-    d.comp_mode = (h->hp.ncomp > 1 && form != 2 && o.component_stop) ? 1 : 0;
+    d.comp_mode = (h->hp.ncomp > 1 && form != 2 && o.component_stop && o.linear_solver == 0) ? 1 : 0;
+    d.cg_tol = o.cg_tol;
+    d.cg_max = o.cg_max_steps;
     h->x_split = o.x_update == 0 ? h->x_split_auto : o.x_update == 2;
     // zero the state (clique vectors, iterates, partials, history)
     CK(cudaMemsetAsync(h->ws + h->L.const_end, 0, h->L.total - h->L.const_end, st));
