@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <string>
 #include <vector>
@@ -449,7 +450,7 @@ int ensure_hsde(cdsdp* h, cudaStream_t st) {
     int rc;
     try {
         rc = cdsdp_impl::build_hsde_constants(h->hp);
-    } catch (const std::bad_alloc&) {
+    } catch (const std::exception&) {  // allocation or thread creation failed
         rc = CDSDP_ERR_NOMEM;
     }
     if (rc != CDSDP_SOLVED) return rc;
@@ -651,7 +652,7 @@ int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row
     try {
         st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val,
                                             nnzP, P_row, P_col, h->hp);
-    } catch (const std::bad_alloc&) {
+    } catch (const std::exception&) {  // allocation or thread creation failed
         st = CDSDP_ERR_NOMEM;
     }
     if (st != CDSDP_SOLVED) { delete h; return st; }
@@ -695,7 +696,7 @@ int cdsdp_setup_scaled(int n, int m, long long nnzA, const int* A_con, const int
             h->hp.sc_tau = tau;
             h->hp.sc_sigma = sigma;
         }
-    } catch (const std::bad_alloc&) {
+    } catch (const std::exception&) {  // allocation or thread creation failed
         st = CDSDP_ERR_NOMEM;
     }
     if (st != CDSDP_SOLVED) { delete h; return st; }
@@ -723,7 +724,7 @@ int cdsdp_completion_sizes(const cdsdp* h, size_t* scratch_bytes, long long* w_e
     if (!h) return CDSDP_ERR_ARG;
     try {
         return cdsdp_impl::completion_sizes(h->hp, scratch_bytes, w_elems, w_offsets);
-    } catch (const std::bad_alloc&) {
+    } catch (const std::exception&) {  // allocation or thread creation failed
         return CDSDP_ERR_NOMEM;
     }
 }
@@ -734,7 +735,7 @@ int cdsdp_complete(cdsdp* h, const double* d_X, void* d_scratch, size_t scratch_
     try {
         return cdsdp_impl::completion_run(h->hp, d_X, d_scratch, scratch_bytes, d_W, logdet, stream, &h->err,
                                           &h->cmp_graph);
-    } catch (const std::bad_alloc&) {
+    } catch (const std::exception&) {  // allocation or thread creation failed
         return CDSDP_ERR_NOMEM;
     }
 }
@@ -825,7 +826,7 @@ int cdsdp_bind(cdsdp* h, void* d_workspace, size_t bytes, int max_iter, void* st
     h->ws_max_iter = max_iter;
     try {
         build_image(h);
-    } catch (const std::bad_alloc&) {
+    } catch (const std::exception&) {  // allocation or thread creation failed
         h->ws = nullptr;
         return CDSDP_ERR_NOMEM;
     }
