@@ -29,7 +29,7 @@
 extern "C" {
 #endif
 
-typedef struct cdsdp cdsdp; /* opaque; created by cdsdp_setup or cdsdp_setup_scaled, released by cdsdp_free */
+typedef struct cdsdp cdsdp; /* opaque; created by a cdsdp_setup* call, released by cdsdp_free */
 
 typedef enum {
     CDSDP_PRIMAL = 0, /* Algorithm 1: domain-space decomposition (Section 4.1) */
@@ -117,6 +117,8 @@ typedef struct {
     int diag_factor;         /* 1 if A D^-1 A^T is diagonal (e.g. MaxCut, Section 4.1.2) */
     long long upload_bytes;  /* size of the one host-to-device copy cdsdp_bind makes   */
     int ncomp;               /* independent components (see cdsdp_components)        */
+    int cached_factor;       /* 1 if the inverse of A D^-1 A^T is cached (0 after
+                                CDSDP_SETUP_NO_FACTOR)                               */
 } cdsdp_info_t;
 
 /* Fill `o` with defaults: eps 1e-4, max_iter 2000, rho 1, FP32 projection,
@@ -174,6 +176,25 @@ int cdsdp_setup_scaled(int n, int m,
                        long long nnzC, const int* C_row, const int* C_col, const double* C_val,
                        long long nnzP, const int* P_row, const int* P_col,
                        int scale_passes, cdsdp** out);
+
+/* Setup flags (cdsdp_setup_flags). */
+enum { CDSDP_SETUP_NO_FACTOR = 1 };
+
+/* cdsdp_setup (scale_passes < 0) or cdsdp_setup_scaled (scale_passes >= 0)
+ * with flags.  CDSDP_SETUP_NO_FACTOR skips the cached inverses of Algorithms
+ * 1-3: the m x m blocks and their O(m^3) factorisation, which bound the
+ * problem sizes the other paths take (a dense block above 8192 constraints is
+ * CDSDP_ERR_UNSUPPORTED there).  Such a handle solves Algorithms 1-2 with
+ * opts.linear_solver = 1 (conjugate gradient, Section 4.1.1) only; other
+ * solves, the autotuner with the cached inverse and the unrolled passes return
+ * CDSDP_ERR_UNSUPPORTED.  Without the factor no rank test of A is made.
+ * Errors: as cdsdp_setup_scaled, and CDSDP_ERR_ARG for an unknown flag. */
+int cdsdp_setup_flags(int n, int m,
+                      long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
+                      const double* b,
+                      long long nnzC, const int* C_row, const int* C_col, const double* C_val,
+                      long long nnzP, const int* P_row, const int* P_col,
+                      int scale_passes, unsigned flags, cdsdp** out);
 
 /* Scaling factors of a handle (Section 7.1.3): d [n], e [m] (host buffers the
  * caller owns; any may be NULL), tau and sigma.  A handle made by cdsdp_setup

@@ -45,7 +45,7 @@ class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int), ("max_clique", ctypes.c_int),
                 ("nnz_pattern", _ll), ("n_d_lower", _ll), ("nnz_A", _ll), ("n_fill", _ll),
                 ("chordal", ctypes.c_int), ("diag_factor", ctypes.c_int), ("upload_bytes", _ll),
-                ("ncomp", ctypes.c_int)]
+                ("ncomp", ctypes.c_int), ("cached_factor", ctypes.c_int)]
 
 
 _lib.cdsdp_default_opts.argtypes = [ctypes.POINTER(Opts)]
@@ -55,6 +55,10 @@ _lib.cdsdp_setup.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32
 _lib.cdsdp_setup_scaled.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32p, _f64p, _f64p,
                                     _ll, _i32p, _i32p, _f64p, _ll, _i32p, _i32p, ctypes.c_int, ctypes.POINTER(_vp)]
 _lib.cdsdp_scaling.argtypes = [_vp, _f64p, _f64p, _f64p, _f64p]
+_lib.cdsdp_setup_flags.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32p, _f64p, _f64p,
+                                   _ll, _i32p, _i32p, _f64p, _ll, _i32p, _i32p, ctypes.c_int, ctypes.c_uint,
+                                   ctypes.POINTER(_vp)]
+SETUP_NO_FACTOR = 1
 _lib.cdsdp_completion_sizes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_ll), _vp]
 _lib.cdsdp_complete.argtypes = [_vp, _vp, _vp, ctypes.c_size_t, _vp, _f64p, _vp]
 _lib.cdsdp_info.argtypes = [_vp, ctypes.POINTER(Info)]
@@ -93,7 +97,7 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc", "cdsdp_grad_workspace_bytes",
             "cdsdp_unrolled_forward", "cdsdp_unrolled_backward", "cdsdp_components",
             "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling",
-            "cdsdp_completion_sizes", "cdsdp_complete"]
+            "cdsdp_completion_sizes", "cdsdp_complete", "cdsdp_setup_flags"]
 
 
 class CdsdpError(RuntimeError):
@@ -132,9 +136,11 @@ class Problem:
 
     scale_passes=None sets the data up as given (cdsdp_setup); an integer k >= 0
     scales it first as Section 7.1.3 describes, with k equilibration passes
-    (cdsdp_setup_scaled); solutions come back in the original units."""
+    (cdsdp_setup_scaled); solutions come back in the original units.
+    cache_factor=False skips the cached inverses (cdsdp_setup_flags with
+    CDSDP_SETUP_NO_FACTOR): such a problem solves with linear_solver=1 only."""
 
-    def __init__(self, prob, scale_passes=None):
+    def __init__(self, prob, scale_passes=None, cache_factor=True):
         (A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col) = prob.arrays()
         self._keep = (A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col)
         h = _vp()
@@ -142,7 +148,11 @@ class Problem:
                 _ptr(A_col, ctypes.c_int), _ptr(A_val, ctypes.c_double), _ptr(b, ctypes.c_double),
                 C_row.size, _ptr(C_row, ctypes.c_int), _ptr(C_col, ctypes.c_int),
                 _ptr(C_val, ctypes.c_double), P_row.size, _ptr(P_row, ctypes.c_int), _ptr(P_col, ctypes.c_int))
-        if scale_passes is None:
+        if not cache_factor:
+            st = _lib.cdsdp_setup_flags(*args, -1 if scale_passes is None else int(scale_passes), SETUP_NO_FACTOR,
+                                        ctypes.byref(h))
+            what = "cdsdp_setup_flags"
+        elif scale_passes is None:
             st = _lib.cdsdp_setup(*args, ctypes.byref(h))
             what = "cdsdp_setup"
         else:

@@ -82,6 +82,7 @@ struct HostProblem {
     std::vector<int> ccl_ptr, ccl_idx;    // cliques of each component (ascending)
     std::vector<long long> minv_off;   // [ncomp] offset of each dense block in minv / kinv
     long long factor_size = 0;         // doubles in minv (and kinv)
+    bool cached_factor = true;         // false: setup skipped the inverses (CG only)
     // cached inverses: per component a dense row-major m_c x m_c block (or, when
     // diag_factor, one value per constraint)
     std::vector<double> minv;         // (A W D^-1 A^T)^-1, Algorithms 1-2
@@ -107,7 +108,7 @@ int build_host_problem(int n, int m,
                        const double* b,
                        long long nnzC, const int* C_row, const int* C_col, const double* C_val,
                        long long nnzP, const int* P_row, const int* P_col,
-                       HostProblem& hp);
+                       HostProblem& hp, bool cache_factor = true);
 
 // Cached inverse for Algorithms 1-2 (hsde = false) or 3 (hsde = true).
 int build_factor(const HostProblem& hp, bool hsde, std::vector<double>& inv);

@@ -300,7 +300,7 @@ int build_host_problem(int n, int m,
                        const double* bvec,
                        long long nnzC, const int* C_row, const int* C_col, const double* C_val,
                        long long nnzP, const int* P_row, const int* P_col,
-                       HostProblem& hp) {
+                       HostProblem& hp, bool cache_factor) {
     if (n < 1 || m < 1 || nnzA < 0 || nnzC < 0 || nnzP < 0) return CDSDP_ERR_ARG;
     if (nnzA > 0 && (!A_con || !A_row || !A_col || !A_val)) return CDSDP_ERR_ARG;
     if (nnzC > 0 && (!C_row || !C_col || !C_val)) return CDSDP_ERR_ARG;
@@ -820,14 +820,17 @@ int build_host_problem(int n, int m,
     long long tot = 0;
     for (int c = 0; c < hp.ncomp; ++c) {
         const long long mc = hp.crow_ptr[c + 1] - hp.crow_ptr[c];
-        if (!structurally_diag && mc > 8192) return CDSDP_ERR_UNSUPPORTED;
+        if (cache_factor && !structurally_diag && mc > 8192) return CDSDP_ERR_UNSUPPORTED;
         hp.minv_off[c] = tot;
         tot += mc * mc;
     }
     hp.diag_factor = structurally_diag;
-    hp.factor_size = tot;
-    int st = build_factor(hp, false, hp.minv);
-    if (st != CDSDP_SOLVED) return st;
+    hp.cached_factor = cache_factor;
+    hp.factor_size = cache_factor ? tot : 0;
+    if (cache_factor) {
+        const int st = build_factor(hp, false, hp.minv);
+        if (st != CDSDP_SOLVED) return st;
+    }
     double nb = 0.0, nc = 0.0;
     for (int i = 0; i < m; ++i) nb += hp.b[i] * hp.b[i];
     for (int e = 0; e < NE; ++e) nc += wgt(e) * hp.c[e] * hp.c[e];

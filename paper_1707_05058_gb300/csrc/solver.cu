@@ -586,6 +586,7 @@ int check_unrolled(cdsdp* h, const cdsdp_opts& o, int iters, int ckpt_every) {
     if (o.precision != CDSDP_FP32_PROJECTION && o.precision != CDSDP_FP64) return CDSDP_ERR_ARG;
     if (h->hp.max_clique > kMaxWarpOrder) return CDSDP_ERR_UNSUPPORTED;
     if (h->hp.scaled) return CDSDP_ERR_UNSUPPORTED;  // c and b would be in scaled units
+    if (!h->hp.cached_factor) return CDSDP_ERR_UNSUPPORTED;  // the reverse pass applies the inverse
     if (ckpt_every > h->ws_max_iter) return CDSDP_ERR_ARG;
     return CDSDP_SOLVED;
 }
@@ -641,17 +642,55 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->cg_max_steps = 5;
 }
 
-int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
-                const double* b, long long nnzC, const int* C_row, const int* C_col, const double* C_val,
-                long long nnzP, const int* P_row, const int* P_col, cdsdp** out) {
+namespace {
+
+// Both setup entry points: scale_passes < 0 sets the data up as given;
+// flags as cdsdp_setup_flags.
+int setup_common(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col,
+                 const double* A_val, const double* b, long long nnzC, const int* C_row, const int* C_col,
+                 const double* C_val, long long nnzP, const int* P_row, const int* P_col, int scale_passes,
+                 unsigned flags, cdsdp** out) {
     if (!out) return CDSDP_ERR_ARG;
     *out = nullptr;
+    if (flags & ~(unsigned)CDSDP_SETUP_NO_FACTOR) return CDSDP_ERR_ARG;
+    const bool cache_factor = !(flags & CDSDP_SETUP_NO_FACTOR);
+    if (scale_passes >= 0) {  // the factors read the triplets before the setup validates them
+        if (n < 1 || m < 0 || nnzA < 0 || nnzC < 0) return CDSDP_ERR_ARG;
+        if ((nnzA > 0 && (!A_con || !A_row || !A_col || !A_val)) || (m > 0 && !b) ||
+            (nnzC > 0 && (!C_row || !C_col || !C_val)))
+            return CDSDP_ERR_ARG;
+        for (long long k = 0; k < nnzA; ++k)
+            if (A_con[k] < 0 || A_con[k] >= m || A_row[k] < 0 || A_row[k] >= n || A_col[k] < 0 || A_col[k] >= n)
+                return CDSDP_ERR_ARG;
+        for (long long k = 0; k < nnzC; ++k)
+            if (C_row[k] < 0 || C_row[k] >= n || C_col[k] < 0 || C_col[k] >= n) return CDSDP_ERR_ARG;
+    }
     cdsdp* h = new (std::nothrow) cdsdp();
     if (!h) return CDSDP_ERR_NOMEM;
     int st;
     try {
-        st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val,
-                                            nnzP, P_row, P_col, h->hp);
+        if (scale_passes < 0) {
+            st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col,
+                                                C_val, nnzP, P_row, P_col, h->hp, cache_factor);
+        } else {
+            std::vector<double> d, e;
+            double tau = 1.0, sigma = 1.0;
+            cdsdp_impl::scaling_factors(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val,
+                                        scale_passes, d, e, tau, sigma);
+            std::vector<double> av(nnzA), bv(m), cv(nnzC);
+            for (long long k = 0; k < nnzA; ++k) av[k] = e[A_con[k]] * d[A_row[k]] * d[A_col[k]] * A_val[k];
+            for (int i = 0; i < m; ++i) bv[i] = tau * e[i] * b[i];
+            for (long long k = 0; k < nnzC; ++k) cv[k] = sigma * d[C_row[k]] * d[C_col[k]] * C_val[k];
+            st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, av.data(), bv.data(), nnzC, C_row,
+                                                C_col, cv.data(), nnzP, P_row, P_col, h->hp, cache_factor);
+            if (st == CDSDP_SOLVED) {
+                h->hp.scaled = true;
+                h->hp.sc_d = std::move(d);
+                h->hp.sc_e = std::move(e);
+                h->hp.sc_tau = tau;
+                h->hp.sc_sigma = sigma;
+            }
+        }
     } catch (const std::exception&) {  // allocation or thread creation failed
         st = CDSDP_ERR_NOMEM;
     }
@@ -660,48 +699,31 @@ int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row
     return CDSDP_SOLVED;
 }
 
+}  // namespace
+
+int cdsdp_setup(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,
+                const double* b, long long nnzC, const int* C_row, const int* C_col, const double* C_val,
+                long long nnzP, const int* P_row, const int* P_col, cdsdp** out) {
+    return setup_common(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val, nnzP, P_row, P_col,
+                        -1, 0u, out);
+}
+
 int cdsdp_setup_scaled(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col,
                        const double* A_val, const double* b, long long nnzC, const int* C_row, const int* C_col,
                        const double* C_val, long long nnzP, const int* P_row, const int* P_col, int scale_passes,
                        cdsdp** out) {
-    if (!out) return CDSDP_ERR_ARG;
-    *out = nullptr;
-    if (scale_passes < 0 || n < 1 || m < 0 || nnzA < 0 || nnzC < 0) return CDSDP_ERR_ARG;
-    if ((nnzA > 0 && (!A_con || !A_row || !A_col || !A_val)) || (m > 0 && !b) ||
-        (nnzC > 0 && (!C_row || !C_col || !C_val)))
-        return CDSDP_ERR_ARG;
-    for (long long k = 0; k < nnzA; ++k)
-        if (A_con[k] < 0 || A_con[k] >= m || A_row[k] < 0 || A_row[k] >= n || A_col[k] < 0 || A_col[k] >= n)
-            return CDSDP_ERR_ARG;
-    for (long long k = 0; k < nnzC; ++k)
-        if (C_row[k] < 0 || C_row[k] >= n || C_col[k] < 0 || C_col[k] >= n) return CDSDP_ERR_ARG;
-    cdsdp* h = new (std::nothrow) cdsdp();
-    if (!h) return CDSDP_ERR_NOMEM;
-    int st;
-    try {
-        std::vector<double> d, e;
-        double tau = 1.0, sigma = 1.0;
-        cdsdp_impl::scaling_factors(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val,
-                                    scale_passes, d, e, tau, sigma);
-        std::vector<double> av(nnzA), bv(m), cv(nnzC);
-        for (long long k = 0; k < nnzA; ++k) av[k] = e[A_con[k]] * d[A_row[k]] * d[A_col[k]] * A_val[k];
-        for (int i = 0; i < m; ++i) bv[i] = tau * e[i] * b[i];
-        for (long long k = 0; k < nnzC; ++k) cv[k] = sigma * d[C_row[k]] * d[C_col[k]] * C_val[k];
-        st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, av.data(), bv.data(), nnzC, C_row,
-                                            C_col, cv.data(), nnzP, P_row, P_col, h->hp);
-        if (st == CDSDP_SOLVED) {
-            h->hp.scaled = true;
-            h->hp.sc_d = std::move(d);
-            h->hp.sc_e = std::move(e);
-            h->hp.sc_tau = tau;
-            h->hp.sc_sigma = sigma;
-        }
-    } catch (const std::exception&) {  // allocation or thread creation failed
-        st = CDSDP_ERR_NOMEM;
-    }
-    if (st != CDSDP_SOLVED) { delete h; return st; }
-    *out = h;
-    return CDSDP_SOLVED;
+    if (out) *out = nullptr;
+    if (scale_passes < 0) return CDSDP_ERR_ARG;
+    return setup_common(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val, nnzP, P_row, P_col,
+                        scale_passes, 0u, out);
+}
+
+int cdsdp_setup_flags(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col,
+                      const double* A_val, const double* b, long long nnzC, const int* C_row, const int* C_col,
+                      const double* C_val, long long nnzP, const int* P_row, const int* P_col, int scale_passes,
+                      unsigned flags, cdsdp** out) {
+    return setup_common(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val, nnzP, P_row, P_col,
+                        scale_passes, flags, out);
 }
 
 int cdsdp_scaling(const cdsdp* h, double* d, double* e, double* tau, double* sigma) {
@@ -755,6 +777,7 @@ int cdsdp_info(const cdsdp* h, cdsdp_info_t* info) {
     info->diag_factor = hp.diag_factor ? 1 : 0;
     info->upload_bytes = (long long)make_layout(hp, 1).const_end;
     info->ncomp = hp.ncomp;
+    info->cached_factor = hp.cached_factor ? 1 : 0;
     return CDSDP_SOLVED;
 }
 
@@ -848,6 +871,7 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     if (rc != CDSDP_SOLVED) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     if (form == 2 && o.linear_solver == 1) return CDSDP_ERR_UNSUPPORTED;
+    if (!h->hp.cached_factor && (form == 2 || o.linear_solver == 0)) return CDSDP_ERR_UNSUPPORTED;
     if (form == 2 && (rc = ensure_hsde(h, st)) != CDSDP_SOLVED) return rc;
     Dev& d = h->dev;
     d.max_iter = o.max_iter;
@@ -940,6 +964,7 @@ int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* 
     if (form < 0 || form > 2) return CDSDP_ERR_ARG;
     cdsdp_opts base;
     if (opts) base = *opts; else cdsdp_default_opts(&base);
+    if (!h->hp.cached_factor && (form == 2 || base.linear_solver == 0)) return CDSDP_ERR_UNSUPPORTED;
     base.eps = 0.0;  // fixed number of iterations
     base.max_iter = std::min(iters, h->ws_max_iter);
     base.profile = 0;

@@ -53,3 +53,37 @@ def test_scaled_setup_rejects_bad_arguments(lib):
     with pytest.raises(lib.CdsdpError) as ex:
         lib.Problem(bad, scale_passes=2)
     assert ex.value.status == -1  # CDSDP_ERR_ARG
+
+
+def test_setup_without_the_cached_factor(lib):
+    """CDSDP_SETUP_NO_FACTOR: same structure, no inverse blocks in the
+    workspace (about 2 x 8 m^2 bytes fewer for a one-component problem), and a
+    component above 8192 constraints, refused with the factor, is accepted."""
+    prob = W.workload(0)
+    P1 = lib.Problem(prob)
+    P0 = lib.Problem(prob, cache_factor=False)
+    assert P1.info["cached_factor"] == 1 and P0.info["cached_factor"] == 0
+    for k in ("n", "m", "p", "nnz_pattern", "nnz_A", "ncomp"):
+        assert P0.info[k] == P1.info[k]
+    m = prob.m
+    assert P1.workspace_bytes(10) - P0.workspace_bytes(10) >= 2 * (8 * m * m - 256)  # sections 256-byte aligned
+    big = W.banded(9000, 2, 9000, seed=12, density=0.01)
+    with pytest.raises(lib.CdsdpError) as ex:
+        lib.Problem(big)
+    assert ex.value.status == -8  # CDSDP_ERR_UNSUPPORTED: dense block above 8192
+    Pb = lib.Problem(big, cache_factor=False)
+    assert Pb.info["m"] == 9000 and Pb.info["ncomp"] == 1 and Pb.info["cached_factor"] == 0
+
+
+def test_unknown_setup_flag_is_rejected(lib):
+    import ctypes
+    prob = W.workload(0)
+    arrs = prob.arrays()
+    ptr = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t)) if a.size else None
+    A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col = arrs
+    h = ctypes.c_void_p()
+    st = lib._lib.cdsdp_setup_flags(prob.n, prob.m, A_con.size, ptr(A_con, ctypes.c_int), ptr(A_row, ctypes.c_int),
+                                    ptr(A_col, ctypes.c_int), ptr(A_val, ctypes.c_double), ptr(b, ctypes.c_double),
+                                    C_row.size, ptr(C_row, ctypes.c_int), ptr(C_col, ctypes.c_int),
+                                    ptr(C_val, ctypes.c_double), 0, None, None, -1, 6, ctypes.byref(h))
+    assert st == -1 and not h.value
