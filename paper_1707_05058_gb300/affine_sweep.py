@@ -25,12 +25,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-PAPER_M = [200, 239, 286, 342, 409, 489, 585, 699, 836, 1000]
+TABLE_M = [  # m values of the affine-projection table (Section 7.4)
+    200, 239, 286, 342, 409, 489, 585, 699, 836, 1000]
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--m", type=int, nargs="+", default=PAPER_M)
+    ap.add_argument("--m", type=int, nargs="+", default=TABLE_M)
     ap.add_argument("--iters", type=int, default=100)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--forms", nargs="+", default=["primal", "dual", "hsde"])
