@@ -196,6 +196,24 @@ int cdsdp_setup_flags(int n, int m,
                       long long nnzP, const int* P_row, const int* P_col,
                       int scale_passes, unsigned flags, cdsdp** out);
 
+/* A batch of `count` independent SDPs set up as their direct sum (one handle;
+ * each SDP is an independent component, so with opts.component_stop each
+ * stops on its own test).  n[j], m[j], nnzA[j], nnzC[j], nnzP[j] (nnzP may be
+ * NULL) describe problem j; its triplets follow those of problems 0..j-1 in
+ * the concatenated arrays, with indices local to the problem (0-based, lower
+ * triangle); b is the concatenation of the b vectors.  The sum numbers the
+ * vertices and constraints of problem j after those of problems 0..j-1, so X
+ * and Z (pattern order), y and cliques of problem j are contiguous in the
+ * results.  scale_passes and flags as cdsdp_setup_flags (scaling factors of the
+ * sum as a whole).  Errors: as cdsdp_setup_flags; CDSDP_ERR_ARG for a local
+ * index out of its problem's range. */
+int cdsdp_setup_batch(int count, const int* n, const int* m,
+                      const long long* nnzA, const int* A_con, const int* A_row, const int* A_col,
+                      const double* A_val, const double* b,
+                      const long long* nnzC, const int* C_row, const int* C_col, const double* C_val,
+                      const long long* nnzP, const int* P_row, const int* P_col,
+                      int scale_passes, unsigned flags, cdsdp** out);
+
 /* Scaling factors of a handle (Section 7.1.3): d [n], e [m] (host buffers the
  * caller owns; any may be NULL), tau and sigma.  A handle made by cdsdp_setup
  * reports d = e = 1, tau = sigma = 1.  Errors: CDSDP_ERR_ARG (NULL handle). */

@@ -61,6 +61,9 @@ _lib.cdsdp_setup_flags.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p
 SETUP_NO_FACTOR = 1
 _lib.cdsdp_completion_sizes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_ll), _vp]
 _lib.cdsdp_complete.argtypes = [_vp, _vp, _vp, ctypes.c_size_t, _vp, _f64p, _vp]
+_lib.cdsdp_setup_batch.argtypes = [ctypes.c_int, _i32p, _i32p, ctypes.POINTER(_ll), _i32p, _i32p, _i32p, _f64p,
+                                   _f64p, ctypes.POINTER(_ll), _i32p, _i32p, _f64p, ctypes.POINTER(_ll), _i32p, _i32p,
+                                   ctypes.c_int, ctypes.c_uint, ctypes.POINTER(_vp)]
 _lib.cdsdp_info.argtypes = [_vp, ctypes.POINTER(Info)]
 _lib.cdsdp_cliques.argtypes = [_vp, _i32p, _i32p]
 _lib.cdsdp_pattern.argtypes = [_vp, _i32p, _i32p]
@@ -97,7 +100,7 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc", "cdsdp_grad_workspace_bytes",
             "cdsdp_unrolled_forward", "cdsdp_unrolled_backward", "cdsdp_components",
             "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling",
-            "cdsdp_completion_sizes", "cdsdp_complete", "cdsdp_setup_flags"]
+            "cdsdp_completion_sizes", "cdsdp_complete", "cdsdp_setup_flags", "cdsdp_setup_batch"]
 
 
 class CdsdpError(RuntimeError):
@@ -160,12 +163,67 @@ class Problem:
             what = "cdsdp_setup_scaled"
         if st != 0:
             raise CdsdpError(st, what)
+        self._adopt(h)
+
+    def _adopt(self, h):
         self._h = h
         self.workspace = None
         self.max_iter = 0
+        self._summands = None
         inf = Info()
         _lib.cdsdp_info(self._h, ctypes.byref(inf))
         self.info = {f: getattr(inf, f) for f, _ in Info._fields_}
+
+    @classmethod
+    def batch(cls, problems, scale_passes=None, cache_factor=True):
+        """A batch of independent SDPs as one handle (cdsdp_setup_batch): their
+        direct sum, problem j numbered after problems 0..j-1.  `split` cuts a
+        solution back into the problems'."""
+        arrs = [p.arrays() for p in problems]
+        cat_i = lambda k: np.ascontiguousarray(np.concatenate([a[k] for a in arrs]), dtype=np.int32)
+        cat_f = lambda k: np.ascontiguousarray(np.concatenate([a[k] for a in arrs]), dtype=np.float64)
+        A_con, A_row, A_col, A_val, b = cat_i(0), cat_i(1), cat_i(2), cat_f(3), cat_f(4)
+        C_row, C_col, C_val, P_row, P_col = cat_i(5), cat_i(6), cat_f(7), cat_i(8), cat_i(9)
+        n = np.array([p.n for p in problems], np.int32)
+        m = np.array([p.m for p in problems], np.int32)
+        nA = np.array([a[0].size for a in arrs], np.int64)
+        nC = np.array([a[5].size for a in arrs], np.int64)
+        nP = np.array([a[8].size for a in arrs], np.int64)
+        self = cls.__new__(cls)
+        self._keep = (A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col, n, m, nA, nC, nP)
+        h = _vp()
+        i64p = lambda a: a.ctypes.data_as(ctypes.POINTER(_ll))
+        st = _lib.cdsdp_setup_batch(len(problems), _ptr(n, ctypes.c_int), _ptr(m, ctypes.c_int), i64p(nA),
+                                    _ptr(A_con, ctypes.c_int), _ptr(A_row, ctypes.c_int), _ptr(A_col, ctypes.c_int),
+                                    _ptr(A_val, ctypes.c_double), _ptr(b, ctypes.c_double), i64p(nC),
+                                    _ptr(C_row, ctypes.c_int), _ptr(C_col, ctypes.c_int), _ptr(C_val, ctypes.c_double),
+                                    i64p(nP), _ptr(P_row, ctypes.c_int), _ptr(P_col, ctypes.c_int),
+                                    -1 if scale_passes is None else int(scale_passes),
+                                    0 if cache_factor else SETUP_NO_FACTOR, ctypes.byref(h))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_setup_batch")
+        self._adopt(h)
+        self._summands = (n.astype(np.int64), m.astype(np.int64))
+        return self
+
+    def split(self, out):
+        """Per-problem X, y, Z (and their pattern entries, local indices) of a
+        solve of a handle made by `batch`."""
+        if self._summands is None:
+            raise ValueError("split() needs a handle made by Problem.batch")
+        n, m = self._summands
+        rows, cols = self.pattern()
+        vo = np.concatenate([[0], np.cumsum(n)])
+        mo = np.concatenate([[0], np.cumsum(m)])
+        eo = np.searchsorted(cols, vo)  # pattern entries are column-major, so each problem's are contiguous
+        res = []
+        for j in range(len(n)):
+            e0, e1 = eo[j], eo[j + 1]
+            res.append({"rows": rows[e0:e1] - vo[j], "cols": cols[e0:e1] - vo[j],
+                        "X": None if out.get("X") is None else out["X"][e0:e1],
+                        "Z": None if out.get("Z") is None else out["Z"][e0:e1],
+                        "y": None if out.get("y") is None else out["y"][mo[j]:mo[j + 1]]})
+        return res
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -726,6 +726,62 @@ int cdsdp_setup_flags(int n, int m, long long nnzA, const int* A_con, const int*
                         scale_passes, flags, out);
 }
 
+int cdsdp_setup_batch(int count, const int* n, const int* m, const long long* nnzA, const int* A_con,
+                      const int* A_row, const int* A_col, const double* A_val, const double* b,
+                      const long long* nnzC, const int* C_row, const int* C_col, const double* C_val,
+                      const long long* nnzP, const int* P_row, const int* P_col, int scale_passes, unsigned flags,
+                      cdsdp** out) {
+    if (!out) return CDSDP_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || !n || !m || !nnzA || !nnzC) return CDSDP_ERR_ARG;
+    long long N = 0, M = 0, tA = 0, tC = 0, tP = 0;
+    for (int j = 0; j < count; ++j) {
+        if (n[j] < 1 || m[j] < 1 || nnzA[j] < 0 || nnzC[j] < 0 || (nnzP && nnzP[j] < 0)) return CDSDP_ERR_ARG;
+        N += n[j];
+        M += m[j];
+        tA += nnzA[j];
+        tC += nnzC[j];
+        if (nnzP) tP += nnzP[j];
+    }
+    if (N > 2000000000LL || M > 2000000000LL) return CDSDP_ERR_UNSUPPORTED;
+    if ((tA > 0 && (!A_con || !A_row || !A_col || !A_val)) || !b || (tC > 0 && (!C_row || !C_col || !C_val)) ||
+        (tP > 0 && (!P_row || !P_col)))
+        return CDSDP_ERR_ARG;
+    try {
+        // the direct sum: problem j's vertices and constraints shifted past
+        // those of problems 0..j-1; local indices are checked against n_j, m_j
+        std::vector<int> ac(tA), ar(tA), acl(tA), cr(tC), cc(tC), pr(tP), pc(tP);
+        long long ka = 0, kc = 0, kp = 0;
+        int vo = 0, mo = 0;
+        for (int j = 0; j < count; ++j) {
+            for (long long q = 0; q < nnzA[j]; ++q, ++ka) {
+                if (A_con[ka] < 0 || A_con[ka] >= m[j] || A_row[ka] < 0 || A_row[ka] >= n[j] || A_col[ka] < 0 ||
+                    A_col[ka] >= n[j])
+                    return CDSDP_ERR_ARG;
+                ac[ka] = A_con[ka] + mo;
+                ar[ka] = A_row[ka] + vo;
+                acl[ka] = A_col[ka] + vo;
+            }
+            for (long long q = 0; q < nnzC[j]; ++q, ++kc) {
+                if (C_row[kc] < 0 || C_row[kc] >= n[j] || C_col[kc] < 0 || C_col[kc] >= n[j]) return CDSDP_ERR_ARG;
+                cr[kc] = C_row[kc] + vo;
+                cc[kc] = C_col[kc] + vo;
+            }
+            for (long long q = 0; nnzP && q < nnzP[j]; ++q, ++kp) {
+                if (P_row[kp] < 0 || P_row[kp] >= n[j] || P_col[kp] < 0 || P_col[kp] >= n[j]) return CDSDP_ERR_ARG;
+                pr[kp] = P_row[kp] + vo;
+                pc[kp] = P_col[kp] + vo;
+            }
+            vo += n[j];
+            mo += m[j];
+        }
+        return setup_common((int)N, (int)M, tA, ac.data(), ar.data(), acl.data(), A_val, b, tC, cr.data(), cc.data(),
+                            C_val, tP, pr.data(), pc.data(), scale_passes, flags, out);
+    } catch (const std::exception&) {  // allocation failed
+        return CDSDP_ERR_NOMEM;
+    }
+}
+
 int cdsdp_scaling(const cdsdp* h, double* d, double* e, double* tau, double* sigma) {
     if (!h) return CDSDP_ERR_ARG;
     const HostProblem& hp = h->hp;
