@@ -225,6 +225,22 @@ class Problem:
                         "y": None if out.get("y") is None else out["y"][mo[j]:mo[j + 1]]})
         return res
 
+    def split_components(self, out):
+        """Per independent component (cdsdp_components): its pattern entries
+        (global indices), X, Z on them, its constraints and y on them."""
+        vc, rc = self.components()
+        rows, cols = self.pattern()
+        ec = vc[cols]
+        res = []
+        for c in range(int(self.info["ncomp"])):
+            ent = np.flatnonzero(ec == c)
+            con = np.flatnonzero(rc == c)
+            res.append({"entries": ent, "rows": rows[ent], "cols": cols[ent], "constraints": con,
+                        "X": None if out.get("X") is None else out["X"][ent],
+                        "Z": None if out.get("Z") is None else out["Z"][ent],
+                        "y": None if out.get("y") is None else out["y"][con]})
+        return res
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:

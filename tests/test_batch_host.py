@@ -46,3 +46,18 @@ def test_batch_rejects_a_local_index_out_of_range(lib):
     with pytest.raises(lib.CdsdpError) as ex:
         lib.Problem.batch([PARTS[0], bad])
     assert ex.value.status == -1  # CDSDP_ERR_ARG
+
+
+def test_split_components_partitions_the_solution(lib):
+    P = lib.Problem(W.direct_sum(PARTS))
+    nz, m = int(P.info["nnz_pattern"]), int(P.info["m"])
+    fake = {"X": np.arange(nz, dtype=float), "Z": None, "y": np.arange(m, dtype=float)}
+    parts = P.split_components(fake)
+    assert len(parts) == P.info["ncomp"]
+    ents = np.sort(np.concatenate([p["entries"] for p in parts]))
+    cons = np.sort(np.concatenate([p["constraints"] for p in parts]))
+    np.testing.assert_array_equal(ents, np.arange(nz))
+    np.testing.assert_array_equal(cons, np.arange(m))
+    for p in parts:
+        np.testing.assert_array_equal(p["X"], p["entries"].astype(float))
+        assert p["Z"] is None
