@@ -3,6 +3,7 @@
 of width h=20; the m values of the paper's affine-projection table).
 
     python -m paper_1707_05058_gb300.affine_sweep --m 200 409 699 1000 --iters 100
+    python -m paper_1707_05058_gb300.affine_sweep --m 1000 --linear-solver cg --cg-steps 5
 
 For each m: one synthetic block-arrow SDP (A_i dense on the pattern, seeded),
 host setup, then for each form a warm-up solve and a profiled solve of
@@ -35,7 +36,14 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=100)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--forms", nargs="+", default=["primal", "dual", "hsde"])
+    ap.add_argument("--linear-solver", default="factor", choices=["factor", "cg"],
+                    help="affine step of Algorithms 1-2: cached inverse or conjugate gradient (HSDE: factor only)")
+    ap.add_argument("--cg-steps", type=int, default=5)
+    ap.add_argument("--cg-tol", type=float, default=1e-10)
     args = ap.parse_args(argv)
+    cg = args.linear_solver == "cg"
+    if cg:
+        args.forms = [f for f in args.forms if f != "hsde"]
 
     import torch
 
@@ -52,11 +60,13 @@ def main(argv=None):
         t2 = time.perf_counter()
         row = {"m": m, "n": prob.n, "cliques": int(P.info["p"]), "clique_order": int(P.info["max_clique"]),
                "nnz_A": int(P.info["nnz_A"]), "generate_s": t1 - t0, "setup_s": t2 - t1}
+        lin = dict(linear_solver=1, cg_max_steps=args.cg_steps, cg_tol=args.cg_tol) if cg else {}
+        row["linear_solver"] = "cg, {} steps, tol {:g}".format(args.cg_steps, args.cg_tol) if cg else "cached inverse"
         for form in args.forms:
             P.solve(form, eps=0.0, max_iter=20, precision=args.precision, use_graph=0, check_every=20,
-                    outputs=False)
+                    outputs=False, **lin)
             P.solve(form, eps=0.0, max_iter=args.iters, precision=args.precision, use_graph=0,
-                    check_every=args.iters, outputs=False, profile=1)
+                    check_every=args.iters, outputs=False, profile=1, **lin)
             torch.cuda.synchronize()
             proj_ms, launches, iter_ms = P.profile()
             row[form] = {"affine_ms_per_iter": (iter_ms - proj_ms) / args.iters,
