@@ -32,6 +32,7 @@ namespace {
 // most `cap`); plain loop when one thread is enough.
 constexpr int kSetupThreads = 16;  // cap on threads of the triplet loops
 constexpr size_t kBitsetMaxOrder = 32768;  // bit-matrix elimination graph up to n^2/8 = 128 MB
+constexpr size_t kBucketBitsBytes = 256u << 20;  // cap on the bit-set buckets of the cardinality search
 
 // Barrier for the threads of one parallel_threads call (all of them run at
 // once); spins briefly, then yields.
@@ -367,7 +368,51 @@ int build_host_problem(int n, int m,
     // ---- maximum cardinality search with buckets (ties: smallest vertex)
     std::vector<int> visit;
     visit.reserve(n);
-    {
+    size_t maxdeg = 0;
+    for (auto& a : adj) maxdeg = std::max(maxdeg, a.size());
+    const size_t W0 = ((size_t)n + 63) / 64, W1 = (W0 + 63) / 64;
+    if ((maxdeg + 1) * (W0 + W1) * sizeof(uint64_t) <= kBucketBitsBytes) {
+        // buckets as two-level bit sets (a word per 64 vertices, a summary bit
+        // per word): the smallest vertex of the top bucket by find-first-set
+        std::vector<uint64_t> lv0((maxdeg + 1) * W0, 0), lv1((maxdeg + 1) * W1, 0);
+        std::vector<int> cnt(maxdeg + 1, 0), weight(n, 0);
+        std::vector<char> done(n, 0);
+        auto ins = [&](size_t w, int v) {
+            lv0[w * W0 + (v >> 6)] |= 1ULL << (v & 63);
+            lv1[w * W1 + (v >> 12)] |= 1ULL << ((v >> 6) & 63);
+            ++cnt[w];
+        };
+        auto del = [&](size_t w, int v) {
+            uint64_t& x = lv0[w * W0 + (v >> 6)];
+            x &= ~(1ULL << (v & 63));
+            if (!x) lv1[w * W1 + (v >> 12)] &= ~(1ULL << ((v >> 6) & 63));
+            --cnt[w];
+        };
+        auto first = [&](size_t w) {
+            for (size_t i = 0; i < W1; ++i)
+                if (const uint64_t sm = lv1[w * W1 + i]) {
+                    const size_t j = i * 64 + (size_t)__builtin_ctzll(sm);
+                    return (int)(j * 64 + (size_t)__builtin_ctzll(lv0[w * W0 + j]));
+                }
+            return -1;
+        };
+        for (int v = 0; v < n; ++v) ins(0, v);
+        size_t top = 0;
+        for (int step = 0; step < n; ++step) {
+            while (top > 0 && cnt[top] == 0) --top;
+            const int v = first(top);
+            del(top, v);
+            done[v] = 1;
+            visit.push_back(v);
+            for (int u : adj[v]) {
+                if (done[u]) continue;
+                del((size_t)weight[u], u);
+                ++weight[u];
+                ins((size_t)weight[u], u);
+                if ((size_t)weight[u] > top) top = (size_t)weight[u];
+            }
+        }
+    } else {
         std::vector<int> weight(n, 0);
         std::vector<char> done(n, 0);
         std::vector<std::set<int>> bucket(n + 1);
