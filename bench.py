@@ -1,28 +1,43 @@
-"""Benchmark: decomposed ADMM (Algorithm 1) on the banded SDP workload
-(n=2000, half-bandwidth 10, m=500; 1990 cliques of order 11) on one GB300.
+"""Benchmark: the decomposed ADMM of arXiv 1707.05058 (Algorithm 1) on the
+batched block-arrow workload on one GB300: 256 independent block-arrow SDPs of
+uneven size (l in [10, 100], d in [10, 40], h in [10, 20], m in [50, 400];
+A_i with 5% density on the pattern), solved as one direct sum in one CUDA
+graph, each SDP stopping on its own test at eps = 1e-4 (adaptive penalty of
+Section 7.1.2 every iteration).  n = 362,087, m = 58,337, 14,371 cliques of
+order 20..60.
 
-A step is one full solve to eps = 1e-4 from a cold start (every step of the
-iteration: scatter, affine projection with the cached inverse, clique gather,
-batched PSD projection, multiplier update, stopping reductions), with the
-adaptive penalty of Section 7.1.2 applied every iteration (mu = 2, nu = 10,
-rho starting at 1).
+A step is one solve of the whole batch to eps = 1e-4 from a cold start (every
+step of the iteration: scatter, affine projection with the cached inverse,
+clique gather, batched PSD projection, multiplier update, stopping
+reductions).
 
-  value     ADMM iterations/s of the FP32-projection form (launch schedule from
-            the library autotuner, chosen before timing), whole solve as one
-            CUDA graph (device-side while loop), inputs resident in HBM,
-            L2 flushed (256 MiB write) before every timed step
+  value     SDP-iterations/s of the FP32-projection form: the iterations run by
+            the 256 SDPs (each its own count until it stops) per second of
+            device time (CUDA events on the solve's stream); launch schedule
+            from the library autotuner, chosen before timing; the workspace
+            (5.8 GB) is larger than L2, and L2 is also flushed (256 MiB write)
+            before every timed step
   e2e       the same metric through the public API from host arrays:
-            host preprocessing, one H2D upload, solve, D2H of X, y, Z
-  fp64_plain  FP64 everywhere, cold Jacobi, one launch per phase, no graph
-  fixed_rho   both forms again with rho = 1 throughout
-  batched   256 independent uneven block-arrow SDPs (cliques of order
-            20..60) solved as one direct sum, each stopping on its own test
-  roofline  the batched projection kernel (FP32 ALU bound), launch durations
-            from CUDA events in a profiled solve on the solve's stream
-  cpu_baseline  the FP64 oracle on a bounded sample (host cores, 1 thread)
+            cdsdp_setup_batch (host preprocessing), one H2D upload of the
+            workspace, solve, D2H of X, y, Z and the history
+  per_iteration  ms per iteration with every SDP active, for the FP32 graph,
+            FP32 plain launches, FP64 plain (cold Jacobi), FP64 plain (warm
+            Jacobi) and FP64 graph (warm) forms: precision, warm start and
+            graph separated
+  parity    objective gap of the timed solve's SDPs against stored oracle
+            solves of three summands (tests/golden/batch_oracle.json)
+  roofline  the projection size class with the largest device time (FP32 ALU
+            bound): nominal 10 s^3 flops per clique / its launch duration from
+            CUDA events in a profiled solve, against the FMA peak measured by
+            cdsdp_fma_peak on this GPU
+  banded    the banded workload (n=2000, w=10, m=500; 1990 cliques of order
+            11): time to 1e-4 in the FP32 graph and plain FP64 forms
+  cpu_baseline  the FP64 oracle on a bounded sample of the same batch: 8 of its
+            SDPs, 4 iterations each, on 1 host thread and on one process per
+            SDP
 
---impl reference runs the FP64 oracle (the CPU reference of this build) on the
-same workload and metric.
+--impl reference runs the FP64 oracle (the CPU reference of this build) on
+the same workload and metric (bounded samples; see run_reference).
 """
 from __future__ import annotations
 
@@ -38,22 +53,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ADMM iters/s & time-to-1e-4 (FP32 batched vs FP64 plain, 1 GB300); clique-proj GFLOP/s"
-WORKLOAD = "banded_n2000_w10_m500"
-SM_COUNT = 152
-# DRAM bytes of one launch of the dominant kernel (k_project_primal<float,12> on the
-# banded workload, x formed by its own kernel) from the ncu capture summarised
-# under profiles/ (3.359488 MB read, 0 written); to be re-taken whenever that
-# kernel changes.
-KERNEL_TRAFFIC_BYTES = 3359488
-FP32_LANES_PER_SM = 128
-
-
-def _peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
-    except OSError:
-        return {}
+WORKLOAD = "batch256_block_arrow_l10-100_d10-40_h10-20_m50-400_density0.05"
+BANDED = "banded_n2000_w10_m500"
+# SDPs of the batch in the CPU-baseline sample (every 32nd) and oracle iterations per SDP
+CPU_SAMPLE = list(range(0, 256, 32))
+CPU_ITERS = 4
+# DRAM bytes of one launch of the roofline's kernel from the ncu capture
+# summarised under profiles/ (None until a capture of the current kernel exists)
+KERNEL_TRAFFIC_BYTES = None
 
 
 def _clock_sampler(dev_index):
@@ -93,52 +100,92 @@ def _clock_summary(proc):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _cpu_baseline(iters, timeout=600):
-    """Time the FP64 oracle (as it stands) on `iters` iterations of the
-    workload in a fresh single-threaded process; returns (iters/s, seconds)."""
-    code = (
-        "import os,sys,time,json\n"
-        f"sys.path.insert(0,{ROOT!r})\n"
-        "from oracle import admm\n"
-        "from paper_1707_05058_gb300 import workloads as W\n"
-        "dp=admm.decompose(W.workload(1))\n"
-        "t=time.perf_counter()\n"
-        f"r=admm.primal_admm(dp,eps=0.0,max_iter={iters},adapt_every=1)\n"
-        "dt=time.perf_counter()-t\n"
-        "print(json.dumps({'iters':r.iters,'sec':dt}))\n")
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["iters"] / d["sec"], d["sec"], d["iters"]
+# ---- CPU baseline: the oracle as it stands -----------------------------------
+
+def _oracle_member(args):
+    """Oracle (Algorithm 1, FP64, adaptive penalty every iteration) on SDP
+    `member` of the batch for `iters` iterations in this process; returns
+    (iterations, seconds of the iteration loop)."""
+    member, iters = args
+    os.environ["OMP_NUM_THREADS"] = "1"
+    sys.path.insert(0, ROOT)
+    from oracle import admm
+    from paper_1707_05058_gb300 import workloads as W
+    dp = admm.decompose(W.workload_batch_member(2, member))
+    t = time.perf_counter()
+    r = admm.primal_admm(dp, eps=0.0, max_iter=iters, adapt_every=1)
+    return r.iters, time.perf_counter() - t
+
+
+def _oracle_sample(members, iters, processes):
+    """The oracle on `members` of the batch, `iters` iterations each, in a
+    spawned pool of `processes` single-threaded processes (1: one after the
+    other).  Returns (SDP-iterations/s over the wall time of the iteration
+    loops, seconds, iterations)."""
+    import multiprocessing as mp
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(processes) as pool:
+            if processes == 1:
+                res = [pool.apply(_oracle_member, ((m, iters),)) for m in members]
+                secs = sum(r[1] for r in res)
+            else:
+                res = pool.map(_oracle_member, [(m, iters) for m in members])
+                secs = max(r[1] for r in res)  # the loops run side by side
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    its = sum(r[0] for r in res)
+    return its / secs, secs, its
+
+
+def _cpu_baseline_block():
+    cores = min(len(CPU_SAMPLE), os.cpu_count() or 1)
+    v1, s1, n1 = _oracle_sample(CPU_SAMPLE, CPU_ITERS, 1)
+    vn, sn, nn = _oracle_sample(CPU_SAMPLE, CPU_ITERS, cores)
+    sample = (f"SDPs {CPU_SAMPLE[0]}, {CPU_SAMPLE[1]}, ..., {CPU_SAMPLE[-1]} of the batch (every 32nd), "
+              f"{CPU_ITERS} iterations of the FP64 oracle (Algorithm 1, adaptive rho) each; setup excluded")
+    return {"value": vn, "unit": "SDP-iters/s", "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds": sn, "single_thread": {"value": v1, "cores": 1, "seconds": s1},
+            "host_cores": os.cpu_count()}
 
 
 def run_reference(args):
+    """--impl reference: the FP64 oracle on the machine's host cores, each step one
+    bounded sample of the batch (8 of its SDPs, 4 iterations each, one
+    process per SDP); same metric and unit as the GPU arm."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    iters = 10
-    vals, secs = [], []
+    cores = min(len(CPU_SAMPLE), os.cpu_count() or 1)
+    vals, secs, its = [], [], []
     for s in range(args.warmup + args.steps):
-        v, sec, _ = _cpu_baseline(iters)
+        v, sec, n = _oracle_sample(CPU_SAMPLE, CPU_ITERS, cores)
         if s >= args.warmup:
-            vals.append(v); secs.append(sec)
-    value = sum(iters for _ in vals) / sum(secs)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+            vals.append(v); secs.append(sec); its.append(n)
+    value = sum(its) / sum(secs)
+    sample = (f"SDPs {CPU_SAMPLE[0]}, {CPU_SAMPLE[1]}, ..., {CPU_SAMPLE[-1]} of the batch, {CPU_ITERS} iterations "
+              f"of the FP64 oracle each per step, {cores} processes")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "SDP-iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "primal", "rho": "adaptive every iteration",
-                       "sample": f"{iters} ADMM iterations per step"},
-            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{iters} iterations of the FP64 oracle (Algorithm 1) on {WORKLOAD} per step, 1 thread"},
-            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOAD, "form": "primal", "rho": "adaptive every iteration", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "SDP-iters/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "SDP-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ---- multi-rank helpers ----------------------------------------------------------
+
 def aggregate_over_ranks(torch, dist, world, total_ms, total_iters, device):
-    """Whole-job rate of N replicas: iterations summed over ranks divided by the
+    """Whole-job rate of N ranks: iterations summed over ranks divided by the
     slowest rank's device time (max), as every rank's timed region is bracketed
     by the same barriers.  Returns (value, max_ms, summed_iters)."""
     t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
@@ -155,57 +202,84 @@ def batch_shard(problems, rank, world):
     return problems[rank::world]
 
 
-def _batched(cdsdp, workloads, torch, flush, stream, rank=0, world=1):
-    """256 uneven block-arrow SDPs (l in [10,100], d in [10,40], h in [10,20],
-    m in [50,400]; A_i with 5% density on the pattern) as one direct sum, each
-    component stopping and freezing on its own test; FP32 graph with the
-    adaptive penalty to eps = 1e-4, then per-iteration times of the first 50
-    iterations (every component active) for the FP32 graph form, the profiled
-    projection launches, and the plain FP64 form."""
+# ---- sub-blocks ----------------------------------------------------------------
+
+def _event_ms(torch, stream, fn):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def _parity_vs_oracle(P, parts, members):
+    """Objective of each stored oracle summand in the last solve against the
+    oracle's objective at the same iteration (tests/golden/batch_oracle.json)."""
     import numpy as np
-    t0 = time.perf_counter()
-    prob = workloads.direct_sum(batch_shard(workloads.workload(2), rank, world))
-    t1 = time.perf_counter()
-    P = cdsdp.Problem(prob)
-    t2 = time.perf_counter()
-    P.bind(max_iter=10000)
-    info = P.info
+    path = os.path.join(ROOT, "tests", "golden", "batch_oracle.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        gold = [g for g in json.load(f)["results"] if g["form"] == "primal"]
+    X, _, _ = P.results()
+    r, c = P.pattern()
+    it, st, res = P.component_results()
+    index = {}
+    vo = np.concatenate([[0], np.cumsum([q.n for q in parts])])
+    out = []
+    for g in gold:
+        j = g["summand"]
+        if j not in members:
+            continue
+        k = members.index(j)
+        q = parts[k]
+        mask = (c >= vo[k]) & (c < vo[k + 1])
+        rr, cc = r[mask] - vo[k], c[mask] - vo[k]
+        index = {(int(a), int(b)): e for e, (a, b) in enumerate(zip(rr, cc))}
+        cvec = np.zeros(len(rr))
+        for a, b, v in zip(q.C_row, q.C_col, q.C_val):
+            cvec[index[(int(a), int(b))]] += v
+        obj = float(np.sum(np.where(rr == cc, 1.0, 2.0) * cvec * X[mask]))
+        want = g["objective"][min(int(it[k]), len(g["objective"])) - 1]
+        out.append({"summand": j, "iters": int(it[k]), "oracle_iters": g["iters"],
+                    "rel_objective_gap": abs(obj - want) / abs(want), "residuals": [float(res[k, 0]), float(res[k, 1])]})
+    return out
 
-    def timed(**kw):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        out = P.solve("primal", outputs=False, **kw)
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1), out
 
-    tuned, cand_ms = P.autotune("primal", iters=20, precision="fp32", adaptive_rho=1)
-    kw = dict(eps=1e-4, max_iter=10000, precision="fp32", use_graph=1, adaptive_rho=1, **tuned)
-    P.solve("primal", outputs=False, **kw)  # warm-up (graph build)
-    ms, out = timed(**kw)
-    it, st, _ = P.component_results()
-    ms50, _ = timed(eps=0.0, max_iter=50, precision="fp32", use_graph=1, adaptive_rho=1, **tuned)
-    P.solve("primal", outputs=False, eps=0.0, max_iter=20, precision="fp32", profile=1, adaptive_rho=1, **tuned)
-    proj_ms, launches, iter_ms = P.profile()
-    ms64, _ = timed(eps=0.0, max_iter=10, precision="fp64", use_graph=0, check_every=10, warm_start=0, adaptive_rho=1)
-    sizes = np.diff(P.cliques()[0]).astype(np.float64)
-    flops = float(np.sum(10.0 * sizes ** 3))
-    gflops = flops / (proj_ms / launches / 1e3) / 1e9
-    return {"workload": "256 block-arrow SDPs, direct sum", "n": int(info["n"]), "m": int(info["m"]),
-            "cliques": int(info["p"]), "clique_order_max": int(info["max_clique"]), "components": int(info["ncomp"]),
-            "nnz_A": int(info["nnz_A"]), "generate_s": t1 - t0, "setup_s": t2 - t1,
-            "time_to_eps_ms": ms, "status": int(out["status"]), "iters_to_eps_max": int(out["iters"]),
-            "component_iters": {"min": int(it.min()), "median": int(np.median(it)), "max": int(it.max()),
-                                "sum": int(it.sum())},
-            "components_solved": int(np.sum(st == 0)),
-            "fp32_graph_ms_per_iter_all_active": ms50 / 50,
-            "fp64_plain_ms_per_iter_all_active": ms64 / 10,
-            "per_iter_speedup_fp32_graph_vs_fp64_plain": (ms64 / 10) / (ms50 / 50),
-            "schedule": tuned, "autotune_ms_per_iter": cand_ms,
-            "clique_proj_gflops": gflops, "proj_ms_per_iter": proj_ms / launches,
-            "proj_flops_per_iter_nominal": flops}
+def _banded(cdsdp, workloads, torch, flush, stream):
+    """Banded n=2000, w=10, m=500: time to eps = 1e-4 (adaptive penalty every
+    iteration) in the FP32 graph form (autotuned schedule) and the plain FP64
+    form, and ADMM iterations/s of both."""
+    prob = workloads.workload(1)
+    P = cdsdp.Problem(prob).bind(max_iter=40000)
+    tuned, _ = P.autotune("primal", iters=30, precision="fp32", adaptive_rho=1)
+
+    def run(n, **kw):
+        ms, its = [], []
+        for _ in range(n):
+            flush.fill_(1)
+            t, out = _event_ms(torch, stream, lambda: P.solve("primal", outputs=False, eps=1e-4, max_iter=40000,
+                                                              adaptive_rho=1, **kw))
+            assert out["status"] == 0, out
+            ms.append(t); its.append(out["iters"])
+        return ms, its
+    run(2, precision="fp32", use_graph=1, **tuned)
+    ms32, it32 = run(5, precision="fp32", use_graph=1, **tuned)
+    ms64, it64 = run(1, precision="fp64", use_graph=0, check_every=10, warm_start=0)
+    P.solve("primal", outputs=False, eps=1e-4, max_iter=40000, precision="fp32", profile=1, check_every=50,
+            adaptive_rho=1, **tuned)
+    cls = P.profile_orders()
+    top = max(cls, key=lambda c: c["ms"])
+    return {"workload": BANDED, "cliques": int(P.info["p"]), "clique_order": int(P.info["max_clique"]),
+            "fp32_graph": {"time_to_eps_ms": statistics.median(ms32), "iters": int(statistics.median(it32)),
+                           "iters_per_s": sum(it32) / (sum(ms32) / 1e3)},
+            "fp64_plain": {"time_to_eps_ms": ms64[0], "iters": it64[0], "iters_per_s": it64[0] / (ms64[0] / 1e3),
+                           "form": "float64 everywhere, cold Jacobi, one launch per phase, no graph"},
+            "speedup_time_to_eps": ms64[0] / statistics.median(ms32), "schedule": tuned,
+            "projection": {"order": top["order"], "ms_per_launch": top["ms"] / top["launches"],
+                           "nominal_gflops": top["nominal_flops"] / (top["ms"] / top["launches"] / 1e3) / 1e9}}
 
 
 def _grad_batch(cdsdp, workloads, torch, stream):
@@ -256,13 +330,9 @@ def _completion(cdsdp, workloads, torch, stream):
         for dense in (False, True):
             ms = []
             for rep in range(4):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                P.complete(X, dense=dense, stream=stream, scratch=scratch, out=Wd)
-                e1.record(stream)
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
+                t, _ = _event_ms(torch, stream, lambda: P.complete(X, dense=dense, stream=stream, scratch=scratch,
+                                                                   out=Wd))
+                ms.append(t)
             out["dense_ms" if dense else "factor_ms"] = statistics.median(ms[1:])
         vc, _ = P.components()
         sizes = np.bincount(vc)
@@ -279,7 +349,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 256-SDP batched workload")
+    ap.add_argument("--no-extras", action="store_true", help="skip the banded, gradient and completion blocks")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -300,159 +370,159 @@ def main():
     __graft_entry__.build_library()
     from paper_1707_05058_gb300 import cdsdp, workloads
 
-    prob = workloads.workload(1)
+    t0 = time.perf_counter()
+    allparts = workloads.workload(2)
+    members = batch_shard(list(range(len(allparts))), rank, world)
+    parts = [allparts[j] for j in members]
+    prob = workloads.direct_sum(parts)
+    gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     P = cdsdp.Problem(prob)
     setup_s = time.perf_counter() - t0
-    max_iter = 40000
+    max_iter = 10000
     P.bind(max_iter=max_iter)
     info = P.info
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peak32 = cdsdp.fma_peak("fp32")
+    peak64 = cdsdp.fma_peak("fp64")
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed_solves(nsteps, warm, **opts):
-        for _ in range(warm):
-            P.solve("primal", outputs=False, eps=1e-4, max_iter=max_iter, **opts)
-        ms, its = [], []
-        for _ in range(nsteps):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            out = P.solve("primal", outputs=False, eps=1e-4, max_iter=max_iter, **opts)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            its.append(out["iters"])
-            assert out["status"] == 0, out
-        return ms, its
-
     ADAPT = dict(adaptive_rho=1)
-    # launch schedule of the FP32 form chosen by the library's autotuner (before timing)
-    TUNED, tune_ms = P.autotune("primal", iters=30, precision="fp32", adaptive_rho=1)
-    # ---- FP32-projection form, graph (the headline value)
+    TUNED, tune_ms = P.autotune("primal", iters=20, precision="fp32", **ADAPT)
+    KW = dict(eps=1e-4, max_iter=max_iter, precision="fp32", use_graph=1, **ADAPT, **TUNED)
+
+    def solve_step():
+        flush.fill_(1)
+        ms, out = _event_ms(torch, stream, lambda: P.solve("primal", outputs=False, **KW))
+        it, st, _ = P.component_results()
+        assert out["status"] == 0 and np.all(st == 0), (out, int(np.sum(st != 0)))
+        return ms, int(it.sum()), int(out["iters"])
+
+    # ---- FP32-projection form, one graph per solve (the headline value)
+    for _ in range(args.warmup):
+        solve_step()
     barrier()
     clk = _clock_sampler(torch.cuda.current_device()) if rank == 0 else None
-    ms32, it32 = timed_solves(args.steps, args.warmup, precision="fp32", use_graph=1, **ADAPT, **TUNED)
+    steps = [solve_step() for _ in range(args.steps)]
     barrier()
     clocks = _clock_summary(clk) if rank == 0 else None
-    value, _, _ = aggregate_over_ranks(torch, dist, world, sum(ms32), sum(it32), "cuda")
-    time_to_eps_ms = statistics.median(ms32)
+    ms_steps = [s[0] for s in steps]
+    sdp_iters = [s[1] for s in steps]
+    value, _, _ = aggregate_over_ranks(torch, dist, world, sum(ms_steps), sum(sdp_iters), "cuda")
+    parity = _parity_vs_oracle(P, parts, members)
 
-    # ---- plain FP64 form (FP64 everywhere, one launch per phase, no graph)
-    ms64, it64 = timed_solves(1, 0, precision="fp64", use_graph=0, check_every=10, warm_start=0, **ADAPT)
-    # ---- both forms with the penalty fixed at rho = 1
-    ms32f, it32f = timed_solves(1, 1, precision="fp32", use_graph=1, **TUNED)
-    ms64f, it64f = timed_solves(1, 0, precision="fp64", use_graph=0, check_every=10, warm_start=0)
+    # ---- ms per iteration with every SDP active: precision, warm start and graph apart
+    def per_iter(n, **kw):
+        flush.fill_(1)
+        ms, out = _event_ms(torch, stream, lambda: P.solve("primal", outputs=False, eps=0.0, max_iter=n, **ADAPT,
+                                                           **kw))
+        return ms / out["iters"]
+    pit = {"fp32_graph": per_iter(50, precision="fp32", use_graph=1, **TUNED),
+           "fp32_plain": per_iter(20, precision="fp32", use_graph=0, check_every=20, **TUNED),
+           "fp64_plain_cold_jacobi": per_iter(10, precision="fp64", use_graph=0, check_every=10, warm_start=0),
+           "fp64_plain_warm_jacobi": per_iter(10, precision="fp64", use_graph=0, check_every=10, warm_start=16),
+           "fp64_graph_warm_jacobi": per_iter(20, precision="fp64", use_graph=1, warm_start=16)}
+    pit["ratio_fp64_plain_cold_vs_fp32_graph"] = pit["fp64_plain_cold_jacobi"] / pit["fp32_graph"]
+    pit["ratio_fp64_graph_warm_vs_fp32_graph"] = pit["fp64_graph_warm_jacobi"] / pit["fp32_graph"]
 
-    # ---- profiled FP32 solve: per-launch projection time from CUDA events
-    P.solve("primal", outputs=False, eps=1e-4, max_iter=max_iter, precision="fp32", profile=1, check_every=50, **ADAPT,
+    # ---- profiled FP32 solve: per size class, launch durations from CUDA events
+    P.solve("primal", outputs=False, eps=0.0, max_iter=20, precision="fp32", profile=1, check_every=20, **ADAPT,
             **TUNED)
     proj_ms, proj_launches, iter_ms = P.profile()
-    sizes = np.diff(P.cliques()[0])
-    flops_per_launch = float(np.sum(10.0 * sizes.astype(np.float64) ** 3))   # nominal 10 s^3 per clique
-    proj_s_per_launch = proj_ms / 1e3 / max(proj_launches, 1)
-    gflops = flops_per_launch / proj_s_per_launch / 1e9
-    sm_mhz = (clocks or {}).get("sm_mhz") or 1440.0
-    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
+    cls = P.profile_orders()
+    top = max(cls, key=lambda c: c["ms"])
+    top_launch_ms = top["ms"] / top["launches"]
+    top_tflops = top["nominal_flops"] / (top_launch_ms / 1e3) / 1e12
+    all_flops = sum(c["nominal_flops"] for c in cls)
+    proj_gflops = all_flops / (proj_ms / proj_launches / 1e3) / 1e9
 
     # ---- end to end through the public API from host arrays
-    e2e_ms, e2e_it = [], []
-    e2e_parts = {"setup": [], "bind_upload": [], "solve_download": []}
+    e2e_ms, e2e_it, parts_ms = [], [], {"setup": [], "bind_upload": [], "solve_download": []}
     h2d = d2h = 0
-    for s in range(6):
+    for s in range(2):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        Q = cdsdp.Problem(prob)
+        Q = cdsdp.Problem.batch(parts)
         t1 = time.perf_counter()
         Q.bind(max_iter=max_iter)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        out = Q.solve("primal", eps=1e-4, max_iter=max_iter, precision="fp32", use_graph=1, **ADAPT, **TUNED)
+        out = Q.solve("primal", **KW)
         torch.cuda.synchronize()
         t3 = time.perf_counter()
-        dt = t3 - t
-        if s > 0:  # the first call also loads the library's kernels
-            e2e_ms.append(dt * 1e3)
-            e2e_it.append(out["iters"])
-            e2e_parts["setup"].append((t1 - t) * 1e3)
-            e2e_parts["bind_upload"].append((t2 - t1) * 1e3)
-            e2e_parts["solve_download"].append((t3 - t2) * 1e3)
-        nz = int(info["nnz_pattern"])
+        it, st, _ = Q.component_results()
+        e2e_ms.append((t3 - t) * 1e3)
+        e2e_it.append(int(it.sum()))
+        parts_ms["setup"].append((t1 - t) * 1e3)
+        parts_ms["bind_upload"].append((t2 - t1) * 1e3)
+        parts_ms["solve_download"].append((t3 - t2) * 1e3)
+        nz = int(Q.info["nnz_pattern"])
         h2d = int(Q.info["upload_bytes"])
-        d2h = (2 * nz + int(info["m"])) * 8 + out["iters"] * 8 * 8
+        d2h = (2 * nz + int(Q.info["m"])) * 8 + int(out["iters"]) * 8 * 8
         del Q
-    e2e_med = statistics.median(e2e_ms)
-    e2e_value = statistics.median(e2e_it) / (e2e_med / 1e3)
+    e2e_value = sum(e2e_it) / (sum(e2e_ms) / 1e3)
     del P
 
-    batched = None if args.no_batched else _batched(cdsdp, workloads, torch, flush, stream, rank, world)
-    grad = None if args.no_batched else _grad_batch(cdsdp, workloads, torch, stream)
-    compl = None if args.no_batched else _completion(cdsdp, workloads, torch, stream)
-    if batched is not None and world > 1:  # each rank solved its share of the 256 SDPs
-        _, tmax, _ = aggregate_over_ranks(torch, dist, world, batched["time_to_eps_ms"], 0, "cuda")
-        batched["time_to_eps_ms"] = tmax
-        batched["workload"] += f", {world} shards (every {world}th SDP per rank), time = slowest rank"
+    extras = {}
+    if not args.no_extras:
+        extras["banded"] = _banded(cdsdp, workloads, torch, flush, stream)
+        extras["grad"] = _grad_batch(cdsdp, workloads, torch, stream)
+        extras["completion"] = _completion(cdsdp, workloads, torch, stream)
 
-    line = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
             try:
-                v, sec, n_it = _cpu_baseline(30)
-                cpu = {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
-                       "sample": f"{n_it} iterations of the FP64 oracle (Algorithm 1) on {WORKLOAD}, 1 thread, {sec:.1f} s"}
+                cpu = _cpu_baseline_block()
             except Exception as exc:  # report, do not hide
-                cpu = {"value": None, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
-        launches_per_iter = 4  # scatter, A W t, cached-inverse GEMV, projection (+ x update, stopping test)
-        gpu_launches = sum(it32) * launches_per_iter + len(it32)
+                cpu = {"value": None, "unit": "SDP-iters/s", "cores": None, "kind": "oracle",
+                       "sample": f"failed: {exc}"}
+        sm_mhz = (clocks or {}).get("sm_mhz")
+        iters_max = [s[2] for s in steps]
+        nclass = len(cls)
+        launches_per_iter = 3 + nclass + 1 + (1 if TUNED.get("x_update") == 2 else 0)
+        traffic = None
+        if KERNEL_TRAFFIC_BYTES is not None:
+            traffic = KERNEL_TRAFFIC_BYTES
         line = {
-            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": statistics.mean(ms32), "higher_is_better": True,
+            "metric": METRIC, "value": value, "unit": "SDP-iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ms_steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "primal", "eps": 1e-4, "cliques": int(info["p"]),
-                       "clique_order": int(info["max_clique"]), "m": int(info["m"]),
-                       "precision": "fp32 projection, fp64 affine step and reductions",
-                       "l2": "flushed (256 MiB write) before every timed step",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "time_to_eps_ms": time_to_eps_ms, "iters_to_eps": int(statistics.median(it32)),
-            "fp64_plain": {"iters_per_s": sum(it64) / (sum(ms64) / 1e3), "time_to_eps_ms": statistics.median(ms64),
-                           "iters_to_eps": int(statistics.median(it64)),
-                           "form": "float64 everywhere, cold Jacobi every iteration, one launch per phase, no graph"},
-            "speedup_time_to_eps_fp32_graph_vs_fp64_plain": statistics.median(ms64) / time_to_eps_ms,
-            "rho": "adaptive (Section 7.1.2), every iteration, mu 2, nu 10, from rho = 1",
+            "config": {"workload": WORKLOAD, "form": "primal (Algorithm 1)", "eps": 1e-4, "sdps": len(parts),
+                       "n": int(info["n"]), "m": int(info["m"]), "cliques": int(info["p"]),
+                       "clique_order_max": int(info["max_clique"]), "nnz_A": int(info["nnz_A"]),
+                       "rho": "adaptive (Section 7.1.2) every iteration, mu 2, nu 10, from rho = 1, per SDP",
+                       "precision": "fp32 eigensolve, rebuild and clique state; fp64 affine step, reductions",
+                       "l2": "workspace (5.8 GB) larger than L2; L2 also flushed (256 MiB write) before every step",
+                       "parallelism": f"{world} ranks, SDPs sharded (every {world}th)" if world > 1 else "single"},
+            "time_to_eps_ms": statistics.median(ms_steps), "iters_to_eps_max": int(statistics.median(iters_max)),
+            "sdp_iters_per_step": int(statistics.median(sdp_iters)),
+            "per_iteration_ms_all_active": pit,
             "schedule": TUNED, "autotune_ms_per_iter": tune_ms,
-            "fixed_rho": {"rho": 1.0,
-                          "fp32_graph": {"time_to_eps_ms": ms32f[0], "iters_to_eps": it32f[0],
-                                         "iters_per_s": it32f[0] / (ms32f[0] / 1e3)},
-                          "fp64_plain": {"time_to_eps_ms": ms64f[0], "iters_to_eps": it64f[0],
-                                         "iters_per_s": it64f[0] / (ms64f[0] / 1e3)},
-                          "speedup_time_to_eps": ms64f[0] / ms32f[0]},
-            "batched": batched,
-            "grad": grad,
-            "completion": compl,
-            "clique_proj_gflops": gflops,
-            "setup_ms": setup_s * 1e3,
-            "roofline": {"bound": "alu", "achieved": gflops / 1e3, "peak": peak_fp32, "unit": "TFLOP/s",
-                         "frac": gflops / 1e3 / peak_fp32, "traffic": KERNEL_TRAFFIC_BYTES,
-                         "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one warm-started launch, "
-                                           "ncu full capture (cold caches), profiles/k_project_primal_banded_n2000_fp32.md",
-                         "kernel": "k_project_primal<float,12>",
-                         "peak_note": f"FP32 FMA peak derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x sampled SM clock",
-                         "flops_per_launch": flops_per_launch, "launch_ms": proj_s_per_launch * 1e3},
+            "parity_vs_oracle": parity,
+            "clique_proj_gflops": proj_gflops, "proj_ms_per_iter": proj_ms / proj_launches,
+            "proj_share_of_iteration": proj_ms / iter_ms,
+            "projection_classes": cls,
+            "generate_s": gen_s, "setup_s": setup_s,
+            "roofline": {"bound": "alu", "achieved": top_tflops, "peak": peak32, "unit": "TFLOP/s",
+                         "frac": top_tflops / peak32, "traffic": traffic,
+                         "kernel": f"projection of padded order {top['order']} ({top['cliques']} cliques)",
+                         "peak_source": "measured on this GPU: cdsdp_fma_peak, float FMA chains on every SM",
+                         "flops_per_launch_nominal": top["nominal_flops"], "launch_ms": top_launch_ms,
+                         "fp64_fma_peak_tflops": peak64, "sm_mhz_during_steps": sm_mhz},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": e2e_med, "steps": len(e2e_ms), "statistic": "median",
-                    "breakdown_ms": {k: statistics.median(v) for k, v in e2e_parts.items()},
-                    "setup_ms": setup_s * 1e3},
-            "gpu_launches": gpu_launches,
+            "e2e": {"value": e2e_value, "unit": "SDP-iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.mean(e2e_ms), "steps": len(e2e_ms),
+                    "breakdown_ms": {k: statistics.median(v) for k, v in parts_ms.items()}},
+            "gpu_launches": sum(iters_max) * launches_per_iter + len(iters_max),
             "clocks": clocks,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

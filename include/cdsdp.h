@@ -321,6 +321,35 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream,
  * Errors: CDSDP_ERR_STATE when the last solve was not profiled. */
 int cdsdp_profile(const cdsdp* h, double* proj_ms, int* proj_launches, double* iter_ms);
 
+/* Per size class of the projection kernels, for the last solve run with
+ * opts.profile = 1 (not in the paper; measurement).  Cliques are bucketed by
+ * padded order, one launch per non-empty class and iteration; each launch is
+ * bracketed by CUDA events on the solve's stream.  Arrays of
+ * CDSDP_PROJ_CLASSES entries, any of them may be NULL:
+ *   orders         padded order of the class
+ *   ms             total device time of its launches over the profiled iterations
+ *   launches       its launches over the profiled iterations
+ *   cliques        cliques in the class
+ *   nominal_flops  sum over its cliques of 10 s^3 (9 s^3 for a symmetric
+ *                  eigendecomposition with vectors, s^3 for the rebuild;
+ *                  Golub and Van Loan, Section 8.3): the algorithmic work of
+ *                  one launch
+ * Errors: CDSDP_ERR_ARG, CDSDP_ERR_STATE when the last solve was not profiled. */
+#define CDSDP_PROJ_CLASSES 22
+int cdsdp_profile_orders(const cdsdp* h, int* orders, double* ms, int* launches, int* cliques, double* nominal_flops);
+
+/* Measured FMA throughput of the current GPU, the peak against which the
+ * projection kernels (bound by the FP32, or FP64, FMA pipe) are reported.  Not
+ * in the paper.  One launch of register-resident independent FMA chains over
+ * every SM (8 blocks of 256 threads each), timed with CUDA events on `stream`
+ * after a warm-up launch; flops = 2 x FMAs.
+ *   precision  CDSDP_FP32_PROJECTION (float FMA) or CDSDP_FP64 (double FMA)
+ *   iters      chain steps per thread (>= 1; about 10^5 for float and 2 x 10^4
+ *              for double give launches of a few milliseconds)
+ *   tflops     out: TFLOP/s
+ * Synchronises `stream`.  Errors: CDSDP_ERR_ARG, CDSDP_ERR_CUDA. */
+int cdsdp_fma_peak(int precision, int iters, void* stream, double* tflops);
+
 /* Schedule autotuner (not in the paper; the launch schedule is a GPU choice):
  * times `iters` iterations (no early stop; graph or not as in opts) of `form`
  * for each candidate schedule and writes into *tuned a copy of *opts (the
@@ -396,17 +425,22 @@ int cdsdp_unrolled_backward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckp
  *              cdsdp_psd_violation_scratch_bytes(p) bytes; its first word is
  *              cleared on `stream` before the launch
  *   d_alpha    device pointer receiving alpha (one double)
- * Asynchronous on `stream`.  Errors: CDSDP_ERR_ARG (p < 1, order out of range,
- * misaligned scratch), CDSDP_ERR_NOMEM (scratch too small), CDSDP_ERR_CUDA. */
+ * Asynchronous on `stream`.  Errors: CDSDP_ERR_ARG (p < 1, max_size outside
+ * 1..32, misaligned scratch), CDSDP_ERR_NOMEM (scratch too small),
+ * CDSDP_ERR_CUDA.  The orders in d_size are device data: if any lies outside
+ * 1..max_size, alpha is written as NaN (no error code, the call is
+ * asynchronous). */
 size_t cdsdp_psd_violation_scratch_bytes(int p);
 int cdsdp_psd_violation(int p, const int* d_off, const int* d_size, int max_size, const void* d_W, int precision,
                         int max_sweeps, void* d_scratch, size_t scratch_bytes, double* d_alpha, void* stream);
 
 /* cdsdp_psd_violation for callers that cannot allocate device memory.  The
  * paper has no counterpart; this exists for callers that cannot call
- * cudaMalloc when they need the measure: code recording a CUDA graph by stream
- * capture, code running inside a framework whose caching allocator owns the
- * device memory, or real-time loops that forbid allocation.  Same arguments,
+ * cudaMalloc when they need the measure: code running inside a framework whose
+ * caching allocator owns the device memory (a raw cudaMalloc there would
+ * fragment or overcommit the pool it manages), a plugin whose host hands it
+ * only input and output buffers, or a real-time loop that forbids the latency
+ * and possible failure of an allocation.  Same arguments,
  * result and errors as cdsdp_psd_violation, minus the scratch: the scratch is
  * a fixed 1 MiB array inside the library, present on every GPU that loads it
  * until the process exits.  Limit: p <= 524160 blocks (131040 thread blocks of
@@ -416,7 +450,10 @@ int cdsdp_psd_violation(int p, const int* d_off, const int* d_size, int max_size
  * and clears its counter word on `stream` before launching; calls whose work
  * overlaps on the GPU (different streams, or different host threads) race on
  * the array and must be serialised by the caller.  Allocates nothing: no
- * cudaMalloc, cudaFree or allocating library routine. */
+ * cudaMalloc, cudaFree or allocating library routine.  The array's device
+ * address is kept for the life of the process: do not call this entry point on
+ * a device after cudaDeviceReset (the library's module is loaded again there,
+ * at a new address). */
 int cdsdp_psd_violation_noalloc(int p, const int* d_off, const int* d_size, int max_size, const void* d_W,
                                 int precision, int max_sweeps, double* d_alpha, void* stream);
 

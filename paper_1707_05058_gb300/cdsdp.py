@@ -77,6 +77,9 @@ _lib.cdsdp_solve.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, _f64p
 _lib.cdsdp_results.argtypes = [_vp, _vp, _f64p, _f64p, _f64p, _f64p, _f64p]
 _lib.cdsdp_free.argtypes = [_vp]
 _lib.cdsdp_profile.argtypes = [_vp, _f64p, _i32p, _f64p]
+_lib.cdsdp_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _f64p]
+_lib.cdsdp_profile_orders.argtypes = [_vp, _i32p, _f64p, _i32p, _i32p, _f64p]
+PROJ_CLASSES = 22
 _lib.cdsdp_strerror.argtypes = [ctypes.c_int]
 _lib.cdsdp_strerror.restype = ctypes.c_char_p
 _lib.cdsdp_psd_project.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -100,7 +103,8 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc", "cdsdp_grad_workspace_bytes",
             "cdsdp_unrolled_forward", "cdsdp_unrolled_backward", "cdsdp_components",
             "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling",
-            "cdsdp_completion_sizes", "cdsdp_complete", "cdsdp_setup_flags", "cdsdp_setup_batch"]
+            "cdsdp_completion_sizes", "cdsdp_complete", "cdsdp_setup_flags", "cdsdp_setup_batch",
+            "cdsdp_fma_peak", "cdsdp_profile_orders"]
 
 
 class CdsdpError(RuntimeError):
@@ -406,6 +410,19 @@ class Problem:
             raise CdsdpError(st, "cdsdp_profile")
         return a.value, n.value, c.value
 
+    def profile_orders(self):
+        """Per size class of the projection kernels in the last profiled solve:
+        a list of dicts (order, ms, launches, cliques, nominal_flops) for the
+        non-empty classes (cdsdp_profile_orders)."""
+        n = PROJ_CLASSES
+        orders, launches, cliques = (ctypes.c_int * n)(), (ctypes.c_int * n)(), (ctypes.c_int * n)()
+        ms, flops = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        st = _lib.cdsdp_profile_orders(self._h, orders, ms, launches, cliques, flops)
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_profile_orders")
+        return [{"order": orders[c], "ms": ms[c], "launches": launches[c], "cliques": cliques[c],
+                 "nominal_flops": flops[c]} for c in range(n) if cliques[c] > 0]
+
     # ---- differentiation through unrolled Algorithm 1 ----
 
     def problem_data(self, device="cuda"):
@@ -497,13 +514,52 @@ def psd_project(W, offsets, sizes, eig_offsets=None, vec_offsets=None, want_eig=
     return (X, eig, vec) if want_eig else X
 
 
+def _check_violation_args(W, offsets, sizes, alpha=None):
+    """Refuse, with ValueError, arguments the kernel would read or write out
+    of bounds: W float32 or float64, offsets and sizes int32 with
+    len(offsets) == len(sizes) + 1, alpha float64 with one element or more;
+    all contiguous CUDA tensors on one device.  Returns the precision code."""
+    import torch
+    if W.dtype not in (torch.float32, torch.float64):
+        raise ValueError(f"W must be float32 or float64, not {W.dtype}")
+    for name, t in (("offsets", offsets), ("sizes", sizes)):
+        if t.dtype != torch.int32:
+            raise ValueError(f"{name} must be int32, not {t.dtype}")
+    if sizes.dim() != 1 or sizes.numel() < 1:
+        raise ValueError("sizes must be a non-empty 1-D tensor")
+    if offsets.dim() != 1 or offsets.numel() != sizes.numel() + 1:
+        raise ValueError("offsets must hold len(sizes) + 1 entries")
+    if alpha is not None and (alpha.dtype != torch.float64 or alpha.numel() < 1):
+        raise ValueError("alpha must be a float64 tensor with at least one element")
+    ts = [W, offsets, sizes] + ([alpha] if alpha is not None else [])
+    if any(not t.is_contiguous() for t in ts):
+        raise ValueError("W, offsets, sizes and alpha must be contiguous")
+    if any(t.device.type != "cuda" for t in ts) or len({t.device for t in ts}) != 1:
+        raise ValueError("W, offsets, sizes and alpha must be CUDA tensors on one device")
+    return FP64 if W.dtype == torch.float64 else FP32
+
+
+def fma_peak(precision="fp32", iters=None, stream=None):
+    """Measured FMA throughput of the current GPU in TFLOP/s (float or double
+    FMA chains over every SM; cdsdp_fma_peak)."""
+    prec = FP64 if precision == "fp64" else FP32
+    if iters is None:
+        iters = 20000 if prec == FP64 else 100000
+    out = ctypes.c_double()
+    st = _lib.cdsdp_fma_peak(prec, int(iters), _stream_ptr(stream), ctypes.byref(out))
+    if st != 0:
+        raise CdsdpError(st, "cdsdp_fma_peak")
+    return out.value
+
+
 def psd_violation(W, offsets, sizes, max_sweeps=30, stream=None):
     """alpha = -min(0, min_k lambda_min(W_k)) of lower-packed blocks (torch
     CUDA tensors, layout of psd_project); returns a 1-element float64 CUDA
-    tensor.  Scratch comes from a PyTorch allocation."""
+    tensor.  Scratch comes from a PyTorch allocation.  An order outside
+    1..max(sizes) cannot occur here; the library writes NaN for one."""
     import torch
+    prec = _check_violation_args(W, offsets, sizes)
     p = int(sizes.numel())
-    prec = FP64 if W.dtype == torch.float64 else FP32
     nbytes = _lib.cdsdp_psd_violation_scratch_bytes(p)
     scratch = torch.empty(nbytes, dtype=torch.uint8, device=W.device)
     alpha = torch.empty(1, dtype=torch.float64, device=W.device)
@@ -519,10 +575,10 @@ def psd_violation(W, offsets, sizes, max_sweeps=30, stream=None):
 
 def psd_violation_noalloc(W, offsets, sizes, alpha, max_sweeps=30, stream=None):
     """As psd_violation, through the entry point that allocates nothing: the
-    caller passes the output `alpha` (1-element float64 CUDA tensor) and the
-    scratch is the library's fixed device array."""
+    caller passes the output `alpha` (float64 CUDA tensor, first element
+    written) and the scratch is the library's fixed device array."""
+    prec = _check_violation_args(W, offsets, sizes, alpha)
     p = int(sizes.numel())
-    prec = FP64 if str(W.dtype) == "torch.float64" else FP32
     maxs = int(sizes.max().item())
     st = _lib.cdsdp_psd_violation_noalloc(p, ctypes.c_void_p(offsets.data_ptr()), ctypes.c_void_p(sizes.data_ptr()),
                                           maxs, ctypes.c_void_p(W.data_ptr()), prec, int(max_sweeps),

@@ -16,6 +16,14 @@
 // applies J_I^T B J_J and writes them to their permuted positions in the other
 // buffer (one warp barrier per round).  Row `lane` of V stays in registers
 // and its columns are re-indexed by the same sigma (static register moves).
+// Every rotation is applied in Rutishauser's form (Handbook for Automatic
+// Computation II, contribution II/1, 1971): with tau = s / (1 + c),
+//   x' = c x - s y = x - s (y + tau x),   y' = s x + c y = y + s (x - tau y).
+// For the small angles of the late sweeps c rounds to 1 while s = t does not,
+// so the plain (c, s) products grow every rotated row and column by a factor
+// 1 + t^2 (a bias, not noise); in float32 this bias, summed over a few hundred
+// rotations per eigenvector, dominated the error of the projection.  The tau
+// form carries 1 - c = s tau implicitly and has no such bias.
 // A rotation is skipped when |a_pq| <= tol = 2 u ||W||_F (u the unit
 // roundoff), and a sweep starts only while some off-diagonal entry exceeds tol
 // (or until max_sweeps).  Eigenvalues clustered within rounding noise of each
@@ -278,7 +286,7 @@ struct BLJacobi {
         // rotation of pair `lane` (lanes < K own the diagonal blocks in slot 0):
         // t = sign(zeta) a_pq / (|zeta| + sqrt(zeta^2 + a_pq^2)), zeta = (a_qq - a_pp)/2
         // (Rutishauser's form of the 2x2 Schur step), c = 1/sqrt(1+t^2), s = t c.
-        T c = T(1), sn = T(0), ta = T(0);
+        T sn = T(0), tau = T(0), ta = T(0);
         bool my = false;
         if (lane < K) {
             const T apq = bv[0][1];
@@ -287,8 +295,9 @@ struct BLJacobi {
                 const T r2 = zeta * zeta + apq * apq;
                 const T r = r2 * rsqrt_t<T>(r2);
                 const T tt = copysign(T(1), zeta) * div_t<T>(apq, fabs(zeta) + r);
-                c = rsqrt_t<T>(T(1) + tt * tt);
+                const T c = rsqrt_t<T>(T(1) + tt * tt);
                 sn = tt * c;
+                tau = div_t<T>(sn, T(1) + c);
                 ta = tt * apq;
                 my = true;
             }
@@ -296,29 +305,31 @@ struct BLJacobi {
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
             const int I = bI[t] >= 0 ? bI[t] : 0, J = bJ[t];
-            const T cI = __shfl_sync(0xffffffffu, c, I), sI = __shfl_sync(0xffffffffu, sn, I);
-            const T cJ = __shfl_sync(0xffffffffu, c, J), sJ = __shfl_sync(0xffffffffu, sn, J);
+            const T sI = __shfl_sync(0xffffffffu, sn, I), uI = __shfl_sync(0xffffffffu, tau, I);
+            const T sJ = __shfl_sync(0xffffffffu, sn, J), uJ = __shfl_sync(0xffffffffu, tau, J);
             if (bI[t] < 0) continue;
             if (t == 0 && lane < K) {  // diagonal block: the 2x2 Schur result
                 Y[dst[t][0]] = bv[t][0] - ta;
                 Y[dst[t][1]] = my ? T(0) : bv[t][1];
                 Y[dst[t][3]] = bv[t][3] + ta;
-            } else {
-                const T r00 = cI * bv[t][0] - sI * bv[t][1], r10 = sI * bv[t][0] + cI * bv[t][1];
-                const T r01 = cI * bv[t][2] - sI * bv[t][3], r11 = sI * bv[t][2] + cI * bv[t][3];
-                Y[dst[t][0]] = cJ * r00 - sJ * r01;
-                Y[dst[t][2]] = sJ * r00 + cJ * r01;
-                Y[dst[t][1]] = cJ * r10 - sJ * r11;
-                Y[dst[t][3]] = sJ * r10 + cJ * r11;
+            } else {  // J_I^T B J_J, rows then columns, in the tau form
+                const T r00 = bv[t][0] - sI * (bv[t][1] + uI * bv[t][0]);
+                const T r10 = bv[t][1] + sI * (bv[t][0] - uI * bv[t][1]);
+                const T r01 = bv[t][2] - sI * (bv[t][3] + uI * bv[t][2]);
+                const T r11 = bv[t][3] + sI * (bv[t][2] - uI * bv[t][3]);
+                Y[dst[t][0]] = r00 - sJ * (r01 + uJ * r00);
+                Y[dst[t][2]] = r01 + sJ * (r00 - uJ * r01);
+                Y[dst[t][1]] = r10 - sJ * (r11 + uJ * r10);
+                Y[dst[t][3]] = r11 + sJ * (r10 - uJ * r11);
             }
         }
         // V <- V J on this lane's row, then re-index its columns by sigma like A
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const T ck = __shfl_sync(0xffffffffu, c, k), sk = __shfl_sync(0xffffffffu, sn, k);
+            const T sk = __shfl_sync(0xffffffffu, sn, k), uk = __shfl_sync(0xffffffffu, tau, k);
             const T vp = vin[2 * k], vq = vin[2 * k + 1];
-            vout[RR::sigma(2 * k)] = ck * vp - sk * vq;
-            vout[RR::sigma(2 * k + 1)] = sk * vp + ck * vq;
+            vout[RR::sigma(2 * k)] = vp - sk * (vq + uk * vp);
+            vout[RR::sigma(2 * k + 1)] = vq + sk * (vp - uk * vq);
         }
         __syncwarp();
         T* tmp = X; X = Y; Y = tmp;

@@ -1,6 +1,7 @@
 // Batched PSD projection of clique blocks of order 33..128: one thread block
 // (CTA) per clique.  Same method as jacobi.cuh (two-sided Jacobi in the
-// Brent-Luk parallel ordering, 2x2 symmetric Schur step in Rutishauser's form,
+// Brent-Luk parallel ordering, 2x2 symmetric Schur step and rotations in
+// Rutishauser's form (tau = s / (1 + c), no norm bias at small angles),
 // warm start from the clique's previous eigenvectors, stagnation stop at the
 // rounding-noise floor), laid out for a CTA.
 //
@@ -50,7 +51,7 @@ struct CTAJacobi {
     T* X;    // current A
     T* Y;    // next A
     T* V;    // eigenvectors, row-major, logical columns
-    T* cs;   // [K] cos, [K] sin, [K] t * a_pq
+    T* cs;   // [K] tau = s / (1 + c), [K] sin, [K] t * a_pq
     int* L;  // logical index at each storage position (current)
     int* Ln; // next
     T* red;  // [32] reduction scratch
@@ -108,17 +109,18 @@ struct CTAJacobi {
         if (tid < K) {  // rotation of pair tid (Rutishauser form)
             const T app = X[(2 * tid) * LDA + 2 * tid], aqq = X[(2 * tid + 1) * LDA + 2 * tid + 1];
             const T apq = X[(2 * tid + 1) * LDA + 2 * tid];
-            T c = T(1), sn = T(0), ta = T(0);
+            T tau = T(0), sn = T(0), ta = T(0);
             if (fabs(apq) > tol) {
                 const T zeta = T(0.5) * (aqq - app);
                 const T r2 = zeta * zeta + apq * apq;
                 const T r = r2 * rsqrt_t<T>(r2);
                 const T tt = copysign(T(1), zeta) * div_t<T>(apq, fabs(zeta) + r);
-                c = rsqrt_t<T>(T(1) + tt * tt);
+                const T c = rsqrt_t<T>(T(1) + tt * tt);
                 sn = tt * c;
+                tau = div_t<T>(sn, T(1) + c);
                 ta = tt * apq;
             }
-            cs[tid] = c;
+            cs[tid] = tau;
             cs[K + tid] = sn;
             cs[2 * K + tid] = ta;
         }
@@ -136,25 +138,25 @@ struct CTAJacobi {
                 Y[max(sr1, sc0) * LDA + min(sr1, sc0)] = rot ? T(0) : X[r1 * LDA + c0];
                 Y[max(sr1, sc1) * LDA + min(sr1, sc1)] = X[r1 * LDA + c1] + ta;
             } else {
-                const T cI = cs[I], sI = cs[K + I], cJ = cs[J], sJ = cs[K + J];
+                const T uI = cs[I], sI = cs[K + I], uJ = cs[J], sJ = cs[K + J];
                 const T b00 = X[r0 * LDA + c0], b10 = X[r1 * LDA + c0], b01 = X[r0 * LDA + c1], b11 = X[r1 * LDA + c1];
-                const T q00 = cI * b00 - sI * b10, q10 = sI * b00 + cI * b10;
-                const T q01 = cI * b01 - sI * b11, q11 = sI * b01 + cI * b11;
-                Y[max(sr0, sc0) * LDA + min(sr0, sc0)] = cJ * q00 - sJ * q01;
-                Y[max(sr0, sc1) * LDA + min(sr0, sc1)] = sJ * q00 + cJ * q01;
-                Y[max(sr1, sc0) * LDA + min(sr1, sc0)] = cJ * q10 - sJ * q11;
-                Y[max(sr1, sc1) * LDA + min(sr1, sc1)] = sJ * q10 + cJ * q11;
+                const T q00 = b00 - sI * (b10 + uI * b00), q10 = b10 + sI * (b00 - uI * b10);
+                const T q01 = b01 - sI * (b11 + uI * b01), q11 = b11 + sI * (b01 - uI * b11);
+                Y[max(sr0, sc0) * LDA + min(sr0, sc0)] = q00 - sJ * (q01 + uJ * q00);
+                Y[max(sr0, sc1) * LDA + min(sr0, sc1)] = q01 + sJ * (q00 - uJ * q01);
+                Y[max(sr1, sc0) * LDA + min(sr1, sc0)] = q10 - sJ * (q11 + uJ * q10);
+                Y[max(sr1, sc1) * LDA + min(sr1, sc1)] = q11 + sJ * (q10 - uJ * q11);
             }
         }
         for (int task = tid; task < S * K; task += nt) {  // V <- V J at the logical column pairs
             const int i = task / K, k = task - i * K;
-            const T c = cs[k], sn = cs[K + k];
+            const T u = cs[k], sn = cs[K + k];
             if (sn == T(0)) continue;
             const int p = L[2 * k], q = L[2 * k + 1];
             T* vr = V + i * LDA;
             const T vp = vr[p], vq = vr[q];
-            vr[p] = c * vp - sn * vq;
-            vr[q] = sn * vp + c * vq;
+            vr[p] = vp - sn * (vq + u * vp);
+            vr[q] = vq + sn * (vp - u * vq);
         }
         __syncthreads();
         T* t = X; X = Y; Y = t;
@@ -273,7 +275,7 @@ struct CTAJacobiMid {
     T* Y;    // A, next
     T* V;    // eigenvectors, current (column = storage index)
     T* Vn;   // next
-    T* cs;   // [K] (cos, sin) pairs
+    T* cs;   // [K] (tau, sin) pairs, tau = s / (1 + c)
     T* ta;   // [K] t * a_pq
     T* red;  // [32] reduction scratch
     T* lam;  // [S] max(lambda, 0), physical order
@@ -386,17 +388,18 @@ struct CTAJacobiMid {
         if (tid < K) {  // rotation of pair tid (Rutishauser form)
             const T app = Xc[tid * LDA + tid], aqq = Xc[(K + tid) * LDA + K + tid];
             const T apq = Xc[(K + tid) * LDA + tid];
-            T c = T(1), sn = T(0), tq = T(0);
+            T tau = T(0), sn = T(0), tq = T(0);
             if (fabs(apq) > tol) {
                 const T zeta = T(0.5) * (aqq - app);
                 const T r2 = zeta * zeta + apq * apq;
                 const T r = r2 * rsqrt_t<T>(r2);
                 const T tt = copysign(T(1), zeta) * div_t<T>(apq, fabs(zeta) + r);
-                c = rsqrt_t<T>(T(1) + tt * tt);
+                const T c = rsqrt_t<T>(T(1) + tt * tt);
                 sn = tt * c;
+                tau = div_t<T>(sn, T(1) + c);
                 tq = tt * apq;
             }
-            reinterpret_cast<T2*>(cs)[tid] = T2{c, sn};
+            reinterpret_cast<T2*>(cs)[tid] = T2{tau, sn};
             ta[tid] = tq;
         }
         __syncthreads();
@@ -410,11 +413,11 @@ struct CTAJacobiMid {
             const int d0 = P.w0[j] >> 16, d1 = P.w1[j] & 0xffff, d2 = P.w1[j] >> 16, d3 = P.w2[j] & 0xffff;
             if (kind == 3) {
                 const T v00 = Vc[src], v01 = Vc[src + K], v10 = Vc[src + K * LDA], v11 = Vc[src + K * LDA + K];
-                const T2 r = rot[J];
-                Vw[d0] = r.x * v00 - r.y * v01;
-                Vw[d2] = r.y * v00 + r.x * v01;
-                Vw[d1] = r.x * v10 - r.y * v11;
-                Vw[d3] = r.y * v10 + r.x * v11;
+                const T2 r = rot[J];  // (tau, s)
+                Vw[d0] = v00 - r.y * (v01 + r.x * v00);
+                Vw[d2] = v01 + r.y * (v00 - r.x * v01);
+                Vw[d1] = v10 - r.y * (v11 + r.x * v10);
+                Vw[d3] = v11 + r.y * (v10 - r.x * v11);
             } else if (kind == 1) {
                 const T t = ta[I];
                 const bool rotated = t != T(0) || rot[I].y != T(0);
@@ -424,13 +427,13 @@ struct CTAJacobiMid {
                 Yn[d3] = b11 + t;
             } else {
                 const T b00 = Xc[src], b01 = Xc[src + K], b10 = Xc[src + K * LDA], b11 = Xc[src + K * LDA + K];
-                const T2 ri = rot[I], rj = rot[J];
-                const T q00 = ri.x * b00 - ri.y * b10, q10 = ri.y * b00 + ri.x * b10;
-                const T q01 = ri.x * b01 - ri.y * b11, q11 = ri.y * b01 + ri.x * b11;
-                Yn[d0] = rj.x * q00 - rj.y * q01;
-                Yn[d2] = rj.y * q00 + rj.x * q01;
-                Yn[d1] = rj.x * q10 - rj.y * q11;
-                Yn[d3] = rj.y * q10 + rj.x * q11;
+                const T2 ri = rot[I], rj = rot[J];  // (tau, s)
+                const T q00 = b00 - ri.y * (b10 + ri.x * b00), q10 = b10 + ri.y * (b00 - ri.x * b10);
+                const T q01 = b01 - ri.y * (b11 + ri.x * b01), q11 = b11 + ri.y * (b01 - ri.x * b11);
+                Yn[d0] = q00 - rj.y * (q01 + rj.x * q00);
+                Yn[d2] = q01 + rj.y * (q00 - rj.x * q01);
+                Yn[d1] = q10 - rj.y * (q11 + rj.x * q10);
+                Yn[d3] = q11 + rj.y * (q10 - rj.x * q11);
             }
         }
         __syncthreads();

@@ -28,6 +28,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 constexpr int kNumClasses = kNumProjClasses;
+static_assert(kNumClasses == CDSDP_PROJ_CLASSES, "size classes of the C ABI");
 inline int class_of(int s) { return proj_class_of(s); }
 
 struct Layout {
@@ -74,6 +75,12 @@ struct cdsdp {
     bool last_profiled = false;
     double prof_proj_ms = 0.0, prof_iter_ms = 0.0;
     int prof_launches = 0;
+    // per size class: an event pair around each projection launch of every
+    // profiled iteration (cls_ev points at the current iteration's pairs)
+    std::vector<cudaEvent_t> cls_evs;
+    cudaEvent_t* cls_ev = nullptr;
+    double prof_cls_ms[kNumClasses] = {0};
+    int prof_cls_n[kNumClasses] = {0};
     cdsdp_impl::CmpGraph cmp_graph;  // cached step graph of the completion
 };
 
@@ -278,8 +285,10 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
         if (nl <= 0) continue;
         FinishArgs f = fa;
         f.enabled = (c == last) ? fa.enabled : 0;  // the last launch finishes the iteration
+        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * c], st);
         e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, pa, f, st)
                            : launch_proj_f64(form, c, h->dev, list, nl, pa, f, st);
+        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * c + 1], st);
         pa.row_off += proj_launch_grid(c, nl, sizeof(T) == 4, pa.warps_div);  // rows of this launch
     }
     return e;
@@ -948,11 +957,21 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
             CK(cudaEventCreate(&e));
             h->ev.push_back(e);
         }
+        const size_t need_cls = (size_t)2 * kNumClasses * o.max_iter;
+        while (h->cls_evs.size() < need_cls) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            h->cls_evs.push_back(e);
+        }
         int ctl[CTL_WORDS];
         int launched = 0;
         for (int it = 0; it < o.max_iter; ++it) {
             CK(cudaEventRecord(h->ev[4 * it], st));
-            CK(launch_iteration_any(h, form, o, st, 0, cudaGraphConditionalHandle{}, h->ev[4 * it + 1], h->ev[4 * it + 2]));
+            h->cls_ev = h->cls_evs.data() + (size_t)2 * kNumClasses * it;
+            const cudaError_t le =
+                launch_iteration_any(h, form, o, st, 0, cudaGraphConditionalHandle{}, h->ev[4 * it + 1], h->ev[4 * it + 2]);
+            h->cls_ev = nullptr;
+            CK(le);
             CK(cudaEventRecord(h->ev[4 * it + 3], st));
             ++launched;
             if ((it + 1) % o.check_every == 0 || it + 1 == o.max_iter) {
@@ -966,12 +985,24 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
         CK(cudaStreamSynchronize(st));
         const int ran = std::min(launched, ctl[CTL_ITER]);
         h->prof_proj_ms = h->prof_iter_ms = 0.0;
+        for (int c = 0; c < kNumClasses; ++c) {
+            h->prof_cls_ms[c] = 0.0;
+            h->prof_cls_n[c] = 0;
+        }
         for (int it = 0; it < ran; ++it) {
             float a = 0.f, b = 0.f;
             CK(cudaEventElapsedTime(&a, h->ev[4 * it + 1], h->ev[4 * it + 2]));
             CK(cudaEventElapsedTime(&b, h->ev[4 * it], h->ev[4 * it + 3]));
             h->prof_proj_ms += a;
             h->prof_iter_ms += b;
+            for (int c = 0; c < kNumClasses; ++c) {
+                if (h->cls_off[c + 1] <= h->cls_off[c]) continue;
+                const cudaEvent_t* pe = h->cls_evs.data() + (size_t)2 * kNumClasses * it + 2 * c;
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, pe[0], pe[1]));
+                h->prof_cls_ms[c] += t;
+                h->prof_cls_n[c] += 1;
+            }
         }
         h->prof_launches = ran;
         h->last_profiled = true;
@@ -1069,6 +1100,27 @@ int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* 
     return CDSDP_SOLVED;
 }
 
+int cdsdp_profile_orders(const cdsdp* h, int* orders, double* ms, int* launches, int* cliques, double* nominal_flops) {
+    if (!h) return CDSDP_ERR_ARG;
+    if (!h->last_profiled) return CDSDP_ERR_STATE;
+    for (int c = 0; c < kNumClasses; ++c) {
+        if (orders) orders[c] = kProjClasses[c];
+        if (ms) ms[c] = h->prof_cls_ms[c];
+        if (launches) launches[c] = h->prof_cls_n[c];
+        if (cliques) cliques[c] = h->cls_off[c + 1] - h->cls_off[c];
+        if (nominal_flops) nominal_flops[c] = 0.0;
+    }
+    if (nominal_flops) {
+        const size_t p = h->hp.cl_off.size() - 1;
+        for (size_t k = 0; k < p; ++k) {
+            const double s = double(h->hp.cl_off[k + 1] - h->hp.cl_off[k]);
+            const int c = class_of(int(s));
+            if (c >= 0) nominal_flops[c] += 10.0 * s * s * s;
+        }
+    }
+    return CDSDP_SOLVED;
+}
+
 int cdsdp_profile(const cdsdp* h, double* proj_ms, int* proj_launches, double* iter_ms) {
     if (!h) return CDSDP_ERR_ARG;
     if (!h->last_profiled) return CDSDP_ERR_STATE;
@@ -1083,6 +1135,7 @@ int cdsdp_free(cdsdp* h) {
     drop_graph(h);
     cdsdp_impl::completion_release(h->cmp_graph);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->cls_evs) cudaEventDestroy(e);
     delete h;
     return CDSDP_SOLVED;
 }

@@ -4,6 +4,8 @@
 // the Jacobi eigensolver of jacobi.cuh, each thread block writes its minimum
 // eigenvalue to scratch, and the last thread block to finish (an atomic
 // counter in scratch) reduces those partials in a fixed order and writes alpha.
+// A block whose order lies outside 1..max_size is not a valid input: its
+// thread block writes NaN as its partial, so alpha comes out NaN.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,8 +29,8 @@ inline size_t violation_scratch_bytes(int p) {
 template <typename T, int S>
 __global__ void __launch_bounds__(32 * kViolWarps) k_psd_violation(int p, const int* __restrict__ off_arr,
                                                                     const int* __restrict__ size_arr,
-                                                                    const T* __restrict__ W, double tolrel,
-                                                                    int max_sweeps, unsigned char* scratch,
+                                                                    const T* __restrict__ W, int max_size,
+                                                                    double tolrel, int max_sweeps, unsigned char* scratch,
                                                                     double* alpha_out) {
     using J = BLJacobi<T, S>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -40,10 +42,12 @@ __global__ void __launch_bounds__(32 * kViolWarps) k_psd_violation(int p, const 
     J jac;
     jac.bind(smem + warp * J::bytes, lane);
     double lmin = 0.0;  // min{0, ...}: start from 0
+    bool bad = false;   // an order outside 1..max_size (max_size <= S)
     const int k = blockIdx.x * kViolWarps + warp;
     if (k < p) {
         const int s = size_arr[k];
-        if (s >= 1 && s <= S) {  // warp-uniform
+        bad = s < 1 || s > max_size;
+        if (!bad) {  // warp-uniform
             const int off = off_arr[k], npk = s * (s + 1) / 2;
             jac.clear(lane);
             T nrm = T(0);
@@ -62,63 +66,79 @@ __global__ void __launch_bounds__(32 * kViolWarps) k_psd_violation(int p, const 
             lmin = fmin(0.0, l);
         }
     }
-    if (lane == 0) wmin[warp] = lmin;
+    if (lane == 0) wmin[warp] = bad ? __longlong_as_double(0x7ff8000000000000LL) : lmin;
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = 0.0;
-        for (int w = 0; w < kViolWarps; ++w) m = fmin(m, wmin[w]);
-        partial[blockIdx.x] = m;
+        bool nan = false;
+        for (int w = 0; w < kViolWarps; ++w) {
+            nan = nan || isnan(wmin[w]);
+            m = fmin(m, wmin[w]);
+        }
+        partial[blockIdx.x] = nan ? __longlong_as_double(0x7ff8000000000000LL) : m;
         __threadfence();
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last) {  // the final reduction, in a fixed order
+    if (last) {  // the final reduction, in a fixed order (fmin drops NaN, so it is counted apart)
         __threadfence();
         double m = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmin(m, ((volatile double*)partial)[b]);
+        int nan = 0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+            const double v = ((volatile double*)partial)[b];
+            nan |= isnan(v) ? 1 : 0;
+            m = fmin(m, v);
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) wmin[warp] = m;
+        for (int o = 16; o > 0; o >>= 1) {
+            m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+            nan |= __shfl_xor_sync(0xffffffffu, nan, o);
+        }
+        if (lane == 0) wmin[warp] = nan ? __longlong_as_double(0x7ff8000000000000LL) : m;
         __syncthreads();
         if (threadIdx.x == 0) {
             double mm = 0.0;
-            for (int w = 0; w < kViolWarps; ++w) mm = fmin(mm, wmin[w]);
-            *alpha_out = -mm;
+            bool any_nan = false;
+            for (int w = 0; w < kViolWarps; ++w) {
+                any_nan = any_nan || isnan(wmin[w]);
+                mm = fmin(mm, wmin[w]);
+            }
+            *alpha_out = any_nan ? __longlong_as_double(0x7ff8000000000000LL) : -mm;
             *counter = 0u;
         }
     }
 }
 
+// Jacobi threshold: jacobi_tolrel, the same as the projection kernels'.
 template <typename T, int S>
-cudaError_t launch_violation(int p, const int* off, const int* size, const void* W, double tolrel, int max_sweeps,
+cudaError_t launch_violation(int p, const int* off, const int* size, int max_size, const void* W, int max_sweeps,
                              unsigned char* scratch, double* alpha, cudaStream_t st) {
     const size_t smem = kViolWarps * BLJacobi<T, S>::bytes;
     cudaError_t e = cudaFuncSetAttribute(k_psd_violation<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, (p + kViolWarps - 1) / kViolWarps);
-    (void)tolrel;
-    k_psd_violation<T, S><<<grid, 32 * kViolWarps, smem, st>>>(p, off, size, (const T*)W,
+    k_psd_violation<T, S><<<grid, 32 * kViolWarps, smem, st>>>(p, off, size, (const T*)W, max_size,
                                                               jacobi_tolrel(S, sizeof(T) == 4), max_sweeps, scratch,
                                                               alpha);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t dispatch_violation(int cls, int p, const int* off, const int* size, const void* W, double tolrel,
+cudaError_t dispatch_violation(int cls, int p, const int* off, const int* size, int max_size, const void* W,
                                int max_sweeps, unsigned char* scratch, double* alpha, cudaStream_t st) {
     switch (kProjClasses[cls]) {
-        case 2: return launch_violation<T, 2>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 4: return launch_violation<T, 4>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 6: return launch_violation<T, 6>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 8: return launch_violation<T, 8>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 10: return launch_violation<T, 10>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 12: return launch_violation<T, 12>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 14: return launch_violation<T, 14>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 16: return launch_violation<T, 16>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 20: return launch_violation<T, 20>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 24: return launch_violation<T, 24>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 28: return launch_violation<T, 28>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
-        case 32: return launch_violation<T, 32>(p, off, size, W, tolrel, max_sweeps, scratch, alpha, st);
+        case 2: return launch_violation<T, 2>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 4: return launch_violation<T, 4>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 6: return launch_violation<T, 6>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 8: return launch_violation<T, 8>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 10: return launch_violation<T, 10>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 12: return launch_violation<T, 12>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 14: return launch_violation<T, 14>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 16: return launch_violation<T, 16>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 20: return launch_violation<T, 20>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 24: return launch_violation<T, 24>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 28: return launch_violation<T, 28>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
+        case 32: return launch_violation<T, 32>(p, off, size, max_size, W, max_sweeps, scratch, alpha, st);
         default: return cudaErrorInvalidValue;  // orders above 32 are not served by this entry point
     }
 }
@@ -130,9 +150,9 @@ int run_violation(int p, const int* d_off, const int* d_size, int max_size, cons
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) { cudaGetLastError(); return CDSDP_ERR_CUDA; }
     if (precision == CDSDP_FP64)
-        e = dispatch_violation<double>(cls, p, d_off, d_size, d_W, 2.3e-16, max_sweeps, scratch, d_alpha, st);
+        e = dispatch_violation<double>(cls, p, d_off, d_size, max_size, d_W, max_sweeps, scratch, d_alpha, st);
     else
-        e = dispatch_violation<float>(cls, p, d_off, d_size, d_W, 1.2e-7, max_sweeps, scratch, d_alpha, st);
+        e = dispatch_violation<float>(cls, p, d_off, d_size, max_size, d_W, max_sweeps, scratch, d_alpha, st);
     if (e != cudaSuccess) { cudaGetLastError(); return CDSDP_ERR_CUDA; }
     return CDSDP_SOLVED;
 }
@@ -167,11 +187,15 @@ int cdsdp_psd_violation(int p, const int* d_off, const int* d_size, int max_size
 // Variant for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the moment they need this measure:
-// code recording a CUDA graph by stream capture (allocation is not a
-// capturable operation), code inside a framework whose caching allocator owns
-// the device memory, or a real-time loop that forbids allocation latency.  For
-// them the scratch lives in a fixed array in the library's device image,
-// held on every GPU that loads the library until the process exits.
+// code running inside a framework whose caching allocator owns the device
+// memory (a raw cudaMalloc there fragments or overcommits the pool it
+// manages), a plugin whose host hands it only input and output buffers, or a
+// real-time loop that forbids the latency and possible failure of an
+// allocation.  For them the scratch lives in a fixed array in the library's
+// device image, held on every GPU that loads the library until the process
+// exits.  Its device address is looked up once per device and kept for the
+// life of the process, so the entry point must not be used on a device after
+// cudaDeviceReset (the module is loaded again there, at a new address).
 #include <mutex>
 
 namespace {

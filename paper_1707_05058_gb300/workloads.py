@@ -213,6 +213,25 @@ def block_arrow_batch(count, seed, density=0.05, l_range=(10, 100), d_range=(10,
     return [block_arrow(l, d, h, m, seed + 1 + i, density=density) for i, (l, d, h, m) in enumerate(shapes)]
 
 
+def block_arrow_batch_member(count, seed, index, density=0.05, l_range=(10, 100), d_range=(10, 40),
+                            h_range=(10, 20), m_range=(50, 400)):
+    """Problem `index` of block_arrow_batch(count, seed, ...) alone (the same
+    shape and seed), without generating the others."""
+    rng = np.random.default_rng(seed)
+    shapes = [(int(rng.integers(l_range[0], l_range[1] + 1)), int(rng.integers(d_range[0], d_range[1] + 1)),
+               int(rng.integers(h_range[0], h_range[1] + 1)), int(rng.integers(m_range[0], m_range[1] + 1)))
+              for _ in range(count)]
+    l, d, h, m = shapes[index]
+    return block_arrow(l, d, h, m, seed + 1 + index, density=density)
+
+
+def workload_batch_member(index: int, member: int):
+    """Member `member` of the batched workload `index` (2: 256 block-arrows)."""
+    if index == 2:
+        return block_arrow_batch_member(256, 3707, member)
+    raise ValueError(index)
+
+
 def direct_sum(problems, name=None):
     """The block-diagonal SDP whose summands are `problems`: vertices and
     constraints of problem j are shifted past those of problems 0..j-1.  Its

@@ -10,6 +10,9 @@ nonexpansive, so differences do not grow).  The FP32 path projects in float32
 ~1e-5 ||W||_F of the exact one, and solutions at eps = 1e-4 must match the
 oracle's to the stopping accuracy: relative objective gap <= 1e-4 and
 primal/dual residuals <= 1e-4 (the workload's stated tolerance)."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -367,23 +370,33 @@ def test_adaptive_rho_fp64_matches_oracle(lib, torch_cuda, form, use_graph):
 
 def test_banded_full_size_adaptive_rho(lib, torch_cuda):
     """Banded n=2000, w=10, m=500 with the adaptive penalty applied every
-    iteration: both precisions stop at eps=1e-4 with KKT residuals of
-    (X, y, Z) <= 5e-4 and objectives within 1e-4 of each other, and the FP64
-    run's first 40 iterates equal the oracle's."""
+    iteration (the benchmark's banded configuration), against the oracle's
+    full solve stored in tests/golden/banded_oracle.json (written by
+    tests/golden/make_batch_oracle.py --banded from oracle/ only): the FP64
+    run's first 40 iterates equal the oracle's; in both precisions the solve
+    stops within 5% of the oracle's iteration count, its objective is within
+    1e-4 of the oracle's at the same iteration, and the KKT residuals of its
+    (X, y, Z), computed here, are at most 1e-4 or, where the oracle's own
+    exceed that (Algorithms 1-2 stop on consensus, not on KKT residuals),
+    within 25% of the oracle's."""
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "banded_oracle.json")) as f:
+        gold = json.load(f)
     prob = W.workload(1)
     dp = admm.decompose(prob)
     ref = admm.primal_admm(dp, eps=0.0, max_iter=40, adapt_every=1)
     P = lib.Problem(prob).bind(max_iter=40000)
     out = P.solve("primal", eps=0.0, max_iter=40, precision="fp64", adaptive_rho=1)
     np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-9, atol=1e-12)
-    res = {}
     for prec in ("fp64", "fp32"):
         out = P.solve("primal", eps=1e-4, max_iter=40000, precision=prec, adaptive_rho=1)
         assert out["status"] == 0
+        assert abs(out["iters"] - gold["iters"]) <= max(3, 0.05 * gold["iters"]), (prec, out["iters"], gold["iters"])
+        obj = float(dp.c @ _full(dp, out["X"]))
+        want = gold["objective"][min(out["iters"], len(gold["objective"])) - 1]
+        assert abs(obj - want) <= 1e-4 * abs(want), (prec, obj, want)
         rp, rd, gap = _kkt(dp, out)
-        assert rp <= 5e-4 and rd <= 5e-4
-        res[prec] = float(dp.c @ _full(dp, out["X"]))
-    assert abs(res["fp32"] - res["fp64"]) <= 1e-4 * abs(res["fp64"])
+        assert rp <= max(1e-4, 1.25 * gold["kkt"]["primal"]), (prec, rp, gold["kkt"])
+        assert rd <= max(1e-4, 1.25 * gold["kkt"]["dual"]), (prec, rd, gold["kkt"])
 
 
 @pytest.mark.parametrize("x_update", [1, 2])

@@ -1,9 +1,10 @@
 """The PSD-violation entry point that allocates nothing.
 
-Some callers cannot call cudaMalloc when they need the measure (a CUDA graph
-being recorded by stream capture, a framework whose allocator owns device
-memory, a real-time loop).  cdsdp_psd_violation_noalloc serves them from a
-fixed device array inside the library.  This test calls it through the C ABI
+Some callers cannot call cudaMalloc when they need the measure: code inside
+a framework whose caching allocator owns the device memory, a plugin handed
+only its input and output buffers, or a real-time loop that forbids the
+latency and possible failure of an allocation.  cdsdp_psd_violation_noalloc
+serves them from a fixed device array inside the library.  This test calls it through the C ABI
 twice in a row, on two different batches, and checks each result against the
 entry point that takes caller scratch, within the tolerance of the other
 PSD-violation tests.  The file sorts last so that a run stopping at the first
@@ -63,3 +64,26 @@ def test_noalloc_rejects_oversize(lib):
     with pytest.raises(lib.CdsdpError) as e:
         lib.psd_violation_noalloc(Wd, off, sizes, alpha)
     assert e.value.status == -8
+
+
+@pytest.mark.parametrize("noalloc", [True, False])
+def test_order_out_of_range_gives_nan(lib, noalloc):
+    """An order outside 1..max_size (here 0) is not a valid block: alpha comes
+    out NaN instead of silently ignoring the block."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rng = np.random.default_rng(7)
+    blocks, sizes, packed, off = _batch(rng, 9, 0.5)
+    sizes = list(sizes)
+    sizes[4] = 0  # its packed entries are still read by nobody: offsets unchanged
+    Wd = torch.tensor(packed, dtype=torch.float64, device="cuda")
+    offd = torch.tensor(off, dtype=torch.int32, device="cuda")
+    szd = torch.tensor(sizes, dtype=torch.int32, device="cuda")
+    if noalloc:
+        alpha = torch.zeros(1, dtype=torch.float64, device="cuda")
+        lib.psd_violation_noalloc(Wd, offd, szd, alpha)
+    else:
+        alpha = lib.psd_violation(Wd, offd, szd)
+    torch.cuda.synchronize()
+    assert np.isnan(alpha.item())
