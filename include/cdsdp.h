@@ -414,6 +414,32 @@ int cdsdp_unrolled_backward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckp
                             const double* d_b, void* d_gws, size_t gws_bytes, const double* d_xbar, double* d_cbar,
                             double* d_bbar, void* stream);
 
+/* PSD projection of large blocks (order 129 .. 8192) on the tensor cores
+ * (Section 4.1.2, Eq. XkUpdate, for cliques too large for one thread block's
+ * Jacobi eigensolver).  P(W) = (W + W sign(W)) / 2 with sign(W) from an odd
+ * polynomial (Newton-Schulz) iteration on W / ||W||_F: 16 steps of
+ * X <- 3.30 X - 3.66 X^3 + 1.36 X^5, then 5 steps of X <- 1.5 X - 0.5 X^3,
+ * every product of two (commuting, symmetric) matrices as three TF32
+ * tcgen05 products (float32 accuracy), lower 128 x 128 tiles only.
+ * Eigenvalues with |lambda| < 1e-8 ||W||_F may stay unconverged; each adds at
+ * most |lambda| / 2 to the error of P.
+ *   p        number of blocks
+ *   h_size   [p] host: orders, 1 .. 8192
+ *   h_off    [p] host: offset (elements) of each block's packed lower values
+ *            (column-major lower packed, as in cdsdp_psd_project)
+ *   d_W      device float32: input blocks;  d_X  device float32: P(W_k), same layout
+ *   d_scratch  device scratch, 256-byte aligned, at least
+ *            cdsdp_psd_project_large_bytes(p, h_size) bytes: the tensor maps
+ *            of the iteration and ten dense float copies of every block
+ *            (order rounded up to a multiple of 128)
+ * Synchronises `stream`.  Errors: CDSDP_ERR_ARG, CDSDP_ERR_NOMEM (scratch too
+ * small), CDSDP_ERR_CUDA (also when the driver's tensor-map encoder is
+ * unavailable), CDSDP_ERR_TIMEOUT (a bounded wait inside the product kernel
+ * ran out; the results are then invalid). */
+int cdsdp_psd_project_large_bytes(int p, const int* h_size, size_t* bytes);
+int cdsdp_psd_project_large(int p, const int* h_size, const long long* h_off, const float* d_W, float* d_X,
+                            void* d_scratch, size_t scratch_bytes, void* stream);
+
 /* PSD-violation measure of Section 7.2 (Eq. PSD-violation):
  *   alpha = -min{0, lambda_min(W_0), ..., lambda_min(W_{p-1})}
  * over p lower-packed symmetric blocks (layout and orders as in

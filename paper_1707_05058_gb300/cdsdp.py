@@ -79,6 +79,9 @@ _lib.cdsdp_free.argtypes = [_vp]
 _lib.cdsdp_profile.argtypes = [_vp, _f64p, _i32p, _f64p]
 _lib.cdsdp_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _f64p]
 _lib.cdsdp_profile_orders.argtypes = [_vp, _i32p, _f64p, _i32p, _i32p, _f64p]
+_lib.cdsdp_psd_project_large_bytes.argtypes = [ctypes.c_int, _i32p, ctypes.POINTER(ctypes.c_size_t)]
+_lib.cdsdp_psd_project_large.argtypes = [ctypes.c_int, _i32p, ctypes.POINTER(_ll), _vp, _vp, _vp, ctypes.c_size_t,
+                                         _vp]
 PROJ_CLASSES = 22
 _lib.cdsdp_strerror.argtypes = [ctypes.c_int]
 _lib.cdsdp_strerror.restype = ctypes.c_char_p
@@ -104,7 +107,8 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_unrolled_forward", "cdsdp_unrolled_backward", "cdsdp_components",
             "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling",
             "cdsdp_completion_sizes", "cdsdp_complete", "cdsdp_setup_flags", "cdsdp_setup_batch",
-            "cdsdp_fma_peak", "cdsdp_profile_orders"]
+            "cdsdp_fma_peak", "cdsdp_profile_orders", "cdsdp_psd_project_large_bytes",
+            "cdsdp_psd_project_large"]
 
 
 class CdsdpError(RuntimeError):
@@ -512,6 +516,36 @@ def psd_project(W, offsets, sizes, eig_offsets=None, vec_offsets=None, want_eig=
     if st != 0:
         raise CdsdpError(st, "cdsdp_psd_project")
     return (X, eig, vec) if want_eig else X
+
+
+def psd_project_large(W, sizes, offsets=None, scratch=None, stream=None):
+    """P(W_k) of float32 lower-packed blocks of order 129..8192 on the tensor
+    cores (cdsdp_psd_project_large).  W: contiguous float32 CUDA tensor;
+    sizes, offsets: host integer sequences (offsets default to back-to-back
+    blocks).  Returns a new tensor like W."""
+    import torch
+    if W.dtype != torch.float32 or W.device.type != "cuda" or not W.is_contiguous():
+        raise ValueError("W must be a contiguous float32 CUDA tensor")
+    sz = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32))
+    if offsets is None:
+        offsets = np.concatenate([[0], np.cumsum(sz.astype(np.int64) * (sz + 1) // 2)[:-1]])
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    need = int(np.max(off + sz.astype(np.int64) * (sz + 1) // 2))
+    if off.size != sz.size or need > W.numel():
+        raise ValueError("offsets and sizes do not fit W")
+    nbytes = ctypes.c_size_t()
+    st = _lib.cdsdp_psd_project_large_bytes(int(sz.size), _ptr(sz, ctypes.c_int), ctypes.byref(nbytes))
+    if st != 0:
+        raise CdsdpError(st, "cdsdp_psd_project_large_bytes")
+    if scratch is None or scratch.numel() < nbytes.value:
+        scratch = torch.empty(nbytes.value, dtype=torch.uint8, device=W.device)
+    X = torch.empty_like(W)
+    st = _lib.cdsdp_psd_project_large(int(sz.size), _ptr(sz, ctypes.c_int), off.ctypes.data_as(ctypes.POINTER(_ll)),
+                                      ctypes.c_void_p(W.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                      ctypes.c_void_p(scratch.data_ptr()), nbytes.value, _stream_ptr(stream))
+    if st != 0:
+        raise CdsdpError(st, "cdsdp_psd_project_large")
+    return X
 
 
 def _check_violation_args(W, offsets, sizes, alpha=None):
