@@ -178,7 +178,7 @@ int cdsdp_setup_scaled(int n, int m,
                        int scale_passes, cdsdp** out);
 
 /* Setup flags (cdsdp_setup_flags). */
-enum { CDSDP_SETUP_NO_FACTOR = 1 };
+enum { CDSDP_SETUP_NO_FACTOR = 1, CDSDP_SETUP_MERGE_CLIQUES = 2 };
 
 /* cdsdp_setup (scale_passes < 0) or cdsdp_setup_scaled (scale_passes >= 0)
  * with flags.  CDSDP_SETUP_NO_FACTOR skips the cached inverses of Algorithms
@@ -188,6 +188,19 @@ enum { CDSDP_SETUP_NO_FACTOR = 1 };
  * opts.linear_solver = 1 (conjugate gradient, Section 4.1.1) only; other
  * solves, the autotuner with the cached inverse and the unrolled passes return
  * CDSDP_ERR_UNSUPPORTED.  Without the factor no rank test of A is made.
+ * CDSDP_SETUP_MERGE_CLIQUES replaces the maximal cliques of the extension by a
+ * coarser clique cover of a further chordal extension wherever that lowers the
+ * projection work sum_k |C_k|^3 (the paper decomposes along whatever chordal
+ * extension it is given; this picks a coarser one).  The clique tree is the
+ * maximum-weight spanning forest of the clique intersection graph (Kruskal,
+ * edges (i < j) in the order weight |C_i ^ C_j| descending, i, j ascending);
+ * the tree edge with the largest gain |C_i|^3 + |C_j|^3 - |C_i u C_j|^3 (ties:
+ * smaller min(i, j), then max(i, j)) is merged while that gain is positive,
+ * node min(i, j) keeping the union and the other node's tree edges; the
+ * extended pattern becomes every pair within a merged clique.  It pays where
+ * cliques overlap heavily (minimum-degree extensions of random graphs).  A
+ * merged handle does not serve cdsdp_completion_sizes / cdsdp_complete
+ * (CDSDP_ERR_UNSUPPORTED).
  * Errors: as cdsdp_setup_scaled, and CDSDP_ERR_ARG for an unknown flag. */
 int cdsdp_setup_flags(int n, int m,
                       long long nnzA, const int* A_con, const int* A_row, const int* A_col, const double* A_val,

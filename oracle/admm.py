@@ -82,13 +82,13 @@ class Decomposed:
         return out
 
 
-def decompose(prob) -> Decomposed:
+def decompose(prob, merge=False) -> Decomposed:
     """Data preprocessing of Algorithms 1-3: aggregate pattern, chordal
     extension and maximal cliques (Section 2.1), selectors H_k (Section 4) and
     D = sum_k H_k^T H_k."""
     n, m = prob.n, prob.m
     cliques, lower, nfill, is_chordal = chordal.chordal_decomposition(
-        n, [(prob.C_row, prob.C_col), (prob.A_row, prob.A_col), (prob.P_row, prob.P_col)])
+        n, [(prob.C_row, prob.C_col), (prob.A_row, prob.A_col), (prob.P_row, prob.P_col)], merge=merge)
     full = []
     for (i, j) in lower:
         full.append((i, j))

@@ -117,9 +117,70 @@ def cliques_from_elimination(elim, filled):
     return sorted(set(maximal))
 
 
-def chordal_decomposition(n, pairs_iterables):
+def merge_cliques(cliques):
+    """Coarser clique cover of a further chordal extension (an option, not in
+    the paper): merge cliques adjacent in a clique tree while that lowers the
+    projection work sum |C|^3.
+
+    Clique tree: the maximum-weight spanning forest of the clique intersection
+    graph (a clique tree of a chordal graph is exactly such a forest), built by
+    Kruskal's rule over the pairs i < j with |C_i & C_j| > 0 in the order
+    (weight descending, i ascending, j ascending).  Then, as long as some tree
+    edge has a positive gain |C_i|^3 + |C_j|^3 - |C_i | C_j|^3, the edge with
+    the largest gain (ties: smaller min(i, j), then smaller max(i, j)) is
+    contracted: node min(i, j) holds the union and takes over the other
+    node's tree edges.  Returns the cliques, each ascending, in lexicographic
+    order.  Plain search over all pairs and edges (small inputs only)."""
+    sets = [set(c) for c in cliques]
+    p = len(sets)
+    pairs = []
+    for i in range(p):
+        for j in range(i + 1, p):
+            w = len(sets[i] & sets[j])
+            if w > 0:
+                pairs.append((-w, i, j))
+    pairs.sort()
+    root = list(range(p))
+
+    def find(x):
+        while root[x] != x:
+            x = root[x]
+        return x
+
+    tree = set()
+    for _, i, j in pairs:
+        ri, rj = find(i), find(j)
+        if ri != rj:
+            root[ri] = rj
+            tree.add((i, j))
+    while True:
+        best = None
+        for i, j in tree:
+            g = len(sets[i]) ** 3 + len(sets[j]) ** 3 - len(sets[i] | sets[j]) ** 3
+            key = (-g, i, j)
+            if g > 0 and (best is None or key < best):
+                best = key
+        if best is None:
+            break
+        _, lo, hi = best
+        sets[lo] = sets[lo] | sets[hi]
+        sets[hi] = None
+        new_tree = set()
+        for i, j in tree:
+            if (i, j) == (lo, hi):
+                continue
+            i2 = lo if i == hi else i
+            j2 = lo if j == hi else j
+            new_tree.add((min(i2, j2), max(i2, j2)))
+        tree = new_tree
+    return sorted(tuple(sorted(c)) for c in sets if c is not None)
+
+
+def chordal_decomposition(n, pairs_iterables, merge=False):
     """Returns (cliques, lower edge list of the extended pattern incl. diagonal
-    in column-major order, number of fill edges, chordal flag)."""
+    in column-major order, number of fill edges, chordal flag).  With merge,
+    the cliques are those of merge_cliques and the extended pattern is every
+    pair within one of them."""
     edges = aggregate_edges(n, pairs_iterables)
     adj = adjacency(n, edges)
     elim = list(reversed(mcs_visit_order(n, adj)))
@@ -130,9 +191,16 @@ def chordal_decomposition(n, pairs_iterables):
         elim, filled = min_degree_elimination(n, adj)
     cliques = cliques_from_elimination(elim, filled)
     lower = set((i, i) for i in range(n))
-    for v in range(n):
-        for u in filled[v]:
-            lower.add((max(u, v), min(u, v)))
+    if merge:
+        cliques = merge_cliques(cliques)
+        for c in cliques:
+            for a in range(len(c)):
+                for bb in range(a + 1, len(c)):
+                    lower.add((c[bb], c[a]))
+    else:
+        for v in range(n):
+            for u in filled[v]:
+                lower.add((max(u, v), min(u, v)))
     lower = sorted(lower, key=lambda t: (t[1], t[0]))
-    nfill = sum(len(s) for s in filled) // 2 - len(edges)
+    nfill = len(lower) - n - len(edges)
     return cliques, lower, nfill, chordal

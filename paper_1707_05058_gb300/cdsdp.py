@@ -59,6 +59,7 @@ _lib.cdsdp_setup_flags.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p
                                    _ll, _i32p, _i32p, _f64p, _ll, _i32p, _i32p, ctypes.c_int, ctypes.c_uint,
                                    ctypes.POINTER(_vp)]
 SETUP_NO_FACTOR = 1
+SETUP_MERGE_CLIQUES = 2
 _lib.cdsdp_completion_sizes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_ll), _vp]
 _lib.cdsdp_complete.argtypes = [_vp, _vp, _vp, ctypes.c_size_t, _vp, _f64p, _vp]
 _lib.cdsdp_setup_batch.argtypes = [ctypes.c_int, _i32p, _i32p, ctypes.POINTER(_ll), _i32p, _i32p, _i32p, _f64p,
@@ -151,7 +152,7 @@ class Problem:
     cache_factor=False skips the cached inverses (cdsdp_setup_flags with
     CDSDP_SETUP_NO_FACTOR): such a problem solves with linear_solver=1 only."""
 
-    def __init__(self, prob, scale_passes=None, cache_factor=True):
+    def __init__(self, prob, scale_passes=None, cache_factor=True, merge_cliques=False):
         (A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col) = prob.arrays()
         self._keep = (A_con, A_row, A_col, A_val, b, C_row, C_col, C_val, P_row, P_col)
         h = _vp()
@@ -159,8 +160,9 @@ class Problem:
                 _ptr(A_col, ctypes.c_int), _ptr(A_val, ctypes.c_double), _ptr(b, ctypes.c_double),
                 C_row.size, _ptr(C_row, ctypes.c_int), _ptr(C_col, ctypes.c_int),
                 _ptr(C_val, ctypes.c_double), P_row.size, _ptr(P_row, ctypes.c_int), _ptr(P_col, ctypes.c_int))
-        if not cache_factor:
-            st = _lib.cdsdp_setup_flags(*args, -1 if scale_passes is None else int(scale_passes), SETUP_NO_FACTOR,
+        if not cache_factor or merge_cliques:
+            flags = (0 if cache_factor else SETUP_NO_FACTOR) | (SETUP_MERGE_CLIQUES if merge_cliques else 0)
+            st = _lib.cdsdp_setup_flags(*args, -1 if scale_passes is None else int(scale_passes), flags,
                                         ctypes.byref(h))
             what = "cdsdp_setup_flags"
         elif scale_passes is None:

@@ -70,6 +70,7 @@ struct HostProblem {
     std::vector<double> b;
     long long nfill = 0;
     bool chordal = false;
+    bool merged = false;              // cliques merged (CDSDP_SETUP_MERGE_CLIQUES); the PEO lists are not rebuilt
     bool diag_factor = false;
     // Independent components (connected components of the extended pattern with
     // every constraint joining the vertices of its entries): a direct sum of
@@ -108,7 +109,7 @@ int build_host_problem(int n, int m,
                        const double* b,
                        long long nnzC, const int* C_row, const int* C_col, const double* C_val,
                        long long nnzP, const int* P_row, const int* P_col,
-                       HostProblem& hp, bool cache_factor = true);
+                       HostProblem& hp, bool cache_factor = true, bool merge = false);
 
 // Cached inverse for Algorithms 1-2 (hsde = false) or 3 (hsde = true).
 int build_factor(const HostProblem& hp, bool hsde, std::vector<double>& inv);

@@ -16,10 +16,13 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <iterator>
 #include <map>
 #include <memory>
 #include <new>
+#include <queue>
 #include <set>
+#include <tuple>
 #include <thread>
 #include <utility>
 
@@ -130,6 +133,99 @@ bool spd_inverse(std::vector<double>& a, int m, std::vector<double>& inv, int th
         }
     });
     return true;
+}
+
+// Clique merging (an option, not in the paper): coarser cliques of a further
+// chordal extension when they cut the projection work sum |C|^3.  The rule is
+// fixed so that it can be restated independently:
+//  1. clique tree = maximum-weight spanning forest of the clique intersection
+//     graph (weight |C_i ^ C_j| > 0), Kruskal over edges (i < j) taken in the
+//     order (weight descending, i ascending, j ascending);
+//  2. repeatedly take the tree edge with the largest gain
+//     |C_i|^3 + |C_j|^3 - |C_i u C_j|^3 (ties: smaller min(i, j), then smaller
+//     max(i, j)) while that gain is positive; node min(i, j) becomes
+//     C_i u C_j and inherits the other node's tree edges;
+//  3. the surviving cliques, each ascending, sorted lexicographically.
+// Merging two cliques adjacent in a clique tree keeps the graph chordal and
+// the contracted tree a clique tree.
+std::vector<std::vector<int>> merge_cliques(const std::vector<std::vector<int>>& cl, int n) {
+    const int p = (int)cl.size();
+    std::vector<std::vector<int>> members(n);
+    for (int k = 0; k < p; ++k)
+        for (int v : cl[k]) members[v].push_back(k);
+    std::map<std::pair<int, int>, int> inter;
+    for (int v = 0; v < n; ++v) {
+        const auto& ks = members[v];
+        for (size_t a = 0; a < ks.size(); ++a)
+            for (size_t c = a + 1; c < ks.size(); ++c) ++inter[{ks[a], ks[c]}];
+    }
+    struct E { int w, i, j; };
+    std::vector<E> edges;
+    edges.reserve(inter.size());
+    for (const auto& kv : inter) edges.push_back({kv.second, kv.first.first, kv.first.second});
+    std::sort(edges.begin(), edges.end(), [](const E& x, const E& y) {
+        if (x.w != y.w) return x.w > y.w;
+        if (x.i != y.i) return x.i < y.i;
+        return x.j < y.j;
+    });
+    std::vector<int> uf(p);
+    for (int k = 0; k < p; ++k) uf[k] = k;
+    auto find = [&](int x) {
+        while (uf[x] != x) x = uf[x] = uf[uf[x]];
+        return x;
+    };
+    std::vector<std::set<int>> adj(p);
+    for (const E& e : edges) {
+        const int ri = find(e.i), rj = find(e.j);
+        if (ri == rj) continue;
+        uf[ri] = rj;
+        adj[e.i].insert(e.j);
+        adj[e.j].insert(e.i);
+    }
+    std::vector<std::vector<int>> sets(cl);
+    std::vector<char> alive(p, 1);
+    auto cube = [](long long x) { return x * x * x; };
+    auto gain = [&](int i, int j) {
+        std::vector<int> u;
+        std::set_union(sets[i].begin(), sets[i].end(), sets[j].begin(), sets[j].end(), std::back_inserter(u));
+        return cube((long long)sets[i].size()) + cube((long long)sets[j].size()) - cube((long long)u.size());
+    };
+    // max-heap on (gain, -lo, -hi): the largest gain, then the smallest ids
+    using H = std::tuple<long long, int, int>;
+    std::priority_queue<H> heap;
+    auto push = [&](int i, int j) {
+        const int lo = std::min(i, j), hi = std::max(i, j);
+        heap.push(H{gain(lo, hi), -lo, -hi});
+    };
+    for (int i = 0; i < p; ++i)
+        for (int j : adj[i])
+            if (i < j) push(i, j);
+    while (!heap.empty()) {
+        const auto [g, nlo, nhi] = heap.top();
+        heap.pop();
+        const int lo = -nlo, hi = -nhi;
+        if (!alive[lo] || !alive[hi] || !adj[lo].count(hi)) continue;
+        if (g != gain(lo, hi)) continue;  // stale: a fresh entry for this edge is in the heap
+        if (g <= 0) break;
+        std::vector<int> u;
+        std::set_union(sets[lo].begin(), sets[lo].end(), sets[hi].begin(), sets[hi].end(), std::back_inserter(u));
+        sets[lo] = std::move(u);
+        alive[hi] = 0;
+        adj[lo].erase(hi);
+        for (int c : adj[hi]) {
+            if (c == lo) continue;
+            adj[c].erase(hi);
+            adj[c].insert(lo);
+            adj[lo].insert(c);
+        }
+        adj[hi].clear();
+        for (int c : adj[lo]) push(lo, c);
+    }
+    std::vector<std::vector<int>> out;
+    for (int k = 0; k < p; ++k)
+        if (alive[k]) out.push_back(sets[k]);
+    std::sort(out.begin(), out.end());
+    return out;
 }
 
 int entry_of(const HostProblem& hp, int i, int j) {  // i >= j
@@ -301,7 +397,7 @@ int build_host_problem(int n, int m,
                        const double* bvec,
                        long long nnzC, const int* C_row, const int* C_col, const double* C_val,
                        long long nnzP, const int* P_row, const int* P_col,
-                       HostProblem& hp, bool cache_factor) {
+                       HostProblem& hp, bool cache_factor, bool merge) {
     if (n < 1 || m < 1 || nnzA < 0 || nnzC < 0 || nnzP < 0) return CDSDP_ERR_ARG;
     if (nnzA > 0 && (!A_con || !A_row || !A_col || !A_val)) return CDSDP_ERR_ARG;
     if (nnzC > 0 && (!C_row || !C_col || !C_val)) return CDSDP_ERR_ARG;
@@ -562,6 +658,10 @@ int build_host_problem(int n, int m,
         cliques.push_back(std::move(k));
     }
     std::sort(cliques.begin(), cliques.end());
+    if (merge) {
+        cliques = merge_cliques(cliques, n);
+        hp.merged = true;
+    }
     hp.cl_off.assign(1, 0);
     for (auto& k : cliques) {
         hp.cl_vert.insert(hp.cl_vert.end(), k.begin(), k.end());
@@ -573,11 +673,23 @@ int build_host_problem(int n, int m,
     {
         std::vector<std::vector<int>> col(n);
         long long off = 0;
-        for (int v = 0; v < n; ++v) {
-            col[v].push_back(v);
-            for (int u : later[v]) {
-                col[std::min(u, v)].push_back(std::max(u, v));
-                ++off;
+        if (!merge) {
+            for (int v = 0; v < n; ++v) {
+                col[v].push_back(v);
+                for (int u : later[v]) {
+                    col[std::min(u, v)].push_back(std::max(u, v));
+                    ++off;
+                }
+            }
+        } else {  // every pair within a merged clique
+            for (int v = 0; v < n; ++v) col[v].push_back(v);
+            for (const auto& k : cliques)
+                for (size_t bb = 0; bb < k.size(); ++bb)
+                    for (size_t a = bb + 1; a < k.size(); ++a) col[k[bb]].push_back(k[a]);
+            for (int v = 0; v < n; ++v) {
+                std::sort(col[v].begin() + 1, col[v].end());
+                col[v].erase(std::unique(col[v].begin() + 1, col[v].end()), col[v].end());
+                off += (long long)col[v].size() - 1;
             }
         }
         hp.nfill = off - nedges;

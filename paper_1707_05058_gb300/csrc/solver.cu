@@ -661,8 +661,9 @@ int setup_common(int n, int m, long long nnzA, const int* A_con, const int* A_ro
                  unsigned flags, cdsdp** out) {
     if (!out) return CDSDP_ERR_ARG;
     *out = nullptr;
-    if (flags & ~(unsigned)CDSDP_SETUP_NO_FACTOR) return CDSDP_ERR_ARG;
+    if (flags & ~(unsigned)(CDSDP_SETUP_NO_FACTOR | CDSDP_SETUP_MERGE_CLIQUES)) return CDSDP_ERR_ARG;
     const bool cache_factor = !(flags & CDSDP_SETUP_NO_FACTOR);
+    const bool merge = (flags & CDSDP_SETUP_MERGE_CLIQUES) != 0;
     if (scale_passes >= 0) {  // the factors read the triplets before the setup validates them
         if (n < 1 || m < 0 || nnzA < 0 || nnzC < 0) return CDSDP_ERR_ARG;
         if ((nnzA > 0 && (!A_con || !A_row || !A_col || !A_val)) || (m > 0 && !b) ||
@@ -680,7 +681,7 @@ int setup_common(int n, int m, long long nnzA, const int* A_con, const int* A_ro
     try {
         if (scale_passes < 0) {
             st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col,
-                                                C_val, nnzP, P_row, P_col, h->hp, cache_factor);
+                                                C_val, nnzP, P_row, P_col, h->hp, cache_factor, merge);
         } else {
             std::vector<double> d, e;
             double tau = 1.0, sigma = 1.0;
@@ -691,7 +692,7 @@ int setup_common(int n, int m, long long nnzA, const int* A_con, const int* A_ro
             for (int i = 0; i < m; ++i) bv[i] = tau * e[i] * b[i];
             for (long long k = 0; k < nnzC; ++k) cv[k] = sigma * d[C_row[k]] * d[C_col[k]] * C_val[k];
             st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, av.data(), bv.data(), nnzC, C_row,
-                                                C_col, cv.data(), nnzP, P_row, P_col, h->hp, cache_factor);
+                                                C_col, cv.data(), nnzP, P_row, P_col, h->hp, cache_factor, merge);
             if (st == CDSDP_SOLVED) {
                 h->hp.scaled = true;
                 h->hp.sc_d = std::move(d);
@@ -808,6 +809,7 @@ int cdsdp_scaling(const cdsdp* h, double* d, double* e, double* tau, double* sig
 }
 
 int cdsdp_completion_sizes(const cdsdp* h, size_t* scratch_bytes, long long* w_elems, long long* w_offsets) {
+    if (h && h->hp.merged) return CDSDP_ERR_UNSUPPORTED;
     if (!h) return CDSDP_ERR_ARG;
     try {
         return cdsdp_impl::completion_sizes(h->hp, scratch_bytes, w_elems, w_offsets);
@@ -818,6 +820,7 @@ int cdsdp_completion_sizes(const cdsdp* h, size_t* scratch_bytes, long long* w_e
 
 int cdsdp_complete(cdsdp* h, const double* d_X, void* d_scratch, size_t scratch_bytes, double* d_W, double* logdet,
                    void* stream) {
+    if (h && h->hp.merged) return CDSDP_ERR_UNSUPPORTED;
     if (!h) return CDSDP_ERR_ARG;
     try {
         return cdsdp_impl::completion_run(h->hp, d_X, d_scratch, scratch_bytes, d_W, logdet, stream, &h->err,
