@@ -351,6 +351,22 @@ int cdsdp_profile(const cdsdp* h, double* proj_ms, int* proj_launches, double* i
 #define CDSDP_PROJ_CLASSES 22
 int cdsdp_profile_orders(const cdsdp* h, int* orders, double* ms, int* launches, int* cliques, double* nominal_flops);
 
+/* The cliques of order > 128 in the last profiled solve (opts.profile = 1):
+ * their projection step (gather, sign iteration on the tensor cores, state
+ * update, sums) bracketed by CUDA events once per iteration.  Any pointer may
+ * be NULL.
+ *   ms             total device time over the profiled iterations
+ *   launches       iterations timed
+ *   cliques        cliques of order > 128
+ *   nominal_flops  sum of 10 s^3 over those cliques (the same nominal count as
+ *                  cdsdp_profile_orders)
+ *   tensor_flops   tensor-core work of one step: 59 products x 3 TF32 MMAs over
+ *                  the lower 128 x 128 tiles of each padded block (2 flops per
+ *                  multiply-add)
+ * Errors: CDSDP_ERR_ARG, CDSDP_ERR_STATE when the last solve was not profiled. */
+int cdsdp_profile_large(const cdsdp* h, double* ms, int* launches, int* cliques, double* nominal_flops,
+                        double* tensor_flops);
+
 /* Measured FMA throughput of the current GPU, the peak against which the
  * projection kernels (bound by the FP32, or FP64, FMA pipe) are reported.  Not
  * in the paper.  One launch of register-resident independent FMA chains over

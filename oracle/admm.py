@@ -53,6 +53,7 @@ class Decomposed:
     D: np.ndarray            # diag(sum_k H_k^T H_k), [N]
     nfill: int
     chordal: bool
+    eig: str = "jacobi"      # eigendecomposition step of the projection (oracle/psd.py)
 
     @property
     def nd(self):
@@ -76,13 +77,13 @@ class Decomposed:
             by_size.setdefault(len(cl), []).append(k)
         for s, ks in by_size.items():
             blocks = np.stack([w[self.offsets[k]:self.offsets[k + 1]].reshape(s, s, order="F") for k in ks])
-            proj = psd_project(blocks)
+            proj = psd_project(blocks, self.eig)
             for j, k in enumerate(ks):
                 out[self.offsets[k]:self.offsets[k + 1]] = proj[j].reshape(-1, order="F")
         return out
 
 
-def decompose(prob, merge=False) -> Decomposed:
+def decompose(prob, merge=False, eig="jacobi") -> Decomposed:
     """Data preprocessing of Algorithms 1-3: aggregate pattern, chordal
     extension and maximal cliques (Section 2.1), selectors H_k (Section 4) and
     D = sum_k H_k^T H_k."""
@@ -117,7 +118,7 @@ def decompose(prob, merge=False) -> Decomposed:
     offsets = np.concatenate([[0], np.cumsum([len(ix) for ix in clique_idx])]).astype(np.int64)
     D = np.bincount(hidx, minlength=N).astype(np.float64)
     return Decomposed(n, m, cliques, lower, full_index, N, c, A, np.asarray(prob.b, np.float64),
-                      clique_idx, hidx, offsets, D, nfill, is_chordal)
+                      clique_idx, hidx, offsets, D, nfill, is_chordal, eig)
 
 
 def _cholesky(M):

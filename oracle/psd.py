@@ -79,9 +79,19 @@ def jacobi_eigh(W):
     return lam.reshape(batch_shape + (s,)), V.reshape(batch_shape + (s, s))
 
 
-def psd_project(W):
-    """P(W) = V diag(max(lambda, 0)) V^T for a batch of symmetric matrices."""
-    lam, V = jacobi_eigh(W)
+def psd_project(W, eig="jacobi"):
+    """P(W) = V diag(max(lambda, 0)) V^T for a batch of symmetric matrices.
+
+    eig="jacobi" (the default) takes the eigendecomposition from jacobi_eigh
+    above; eig="lapack" takes it from LAPACK's symmetric eigensolver through
+    numpy.linalg.eigh, a library primitive serving as that one step, for the
+    problems whose cliques (orders in the hundreds, many sizes) put the
+    pure-Python Jacobi out of reach (seconds per block).  Both give P(W) to
+    rounding; tests/test_oracle_psd.py holds them equal."""
+    if eig == "lapack":
+        lam, V = np.linalg.eigh(np.asarray(W, dtype=np.float64))
+    else:
+        lam, V = jacobi_eigh(W)
     lp = np.maximum(lam, 0.0)
     return np.einsum("...ik,...k,...jk->...ij", V, lp, V)
 

@@ -80,6 +80,7 @@ _lib.cdsdp_free.argtypes = [_vp]
 _lib.cdsdp_profile.argtypes = [_vp, _f64p, _i32p, _f64p]
 _lib.cdsdp_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _f64p]
 _lib.cdsdp_profile_orders.argtypes = [_vp, _i32p, _f64p, _i32p, _i32p, _f64p]
+_lib.cdsdp_profile_large.argtypes = [_vp, _f64p, _i32p, _i32p, _f64p, _f64p]
 _lib.cdsdp_psd_project_large_bytes.argtypes = [ctypes.c_int, _i32p, ctypes.POINTER(ctypes.c_size_t)]
 _lib.cdsdp_psd_project_large.argtypes = [ctypes.c_int, _i32p, ctypes.POINTER(_ll), _vp, _vp, _vp, ctypes.c_size_t,
                                          _vp]
@@ -109,7 +110,7 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling",
             "cdsdp_completion_sizes", "cdsdp_complete", "cdsdp_setup_flags", "cdsdp_setup_batch",
             "cdsdp_fma_peak", "cdsdp_profile_orders", "cdsdp_psd_project_large_bytes",
-            "cdsdp_psd_project_large"]
+            "cdsdp_psd_project_large", "cdsdp_profile_large"]
 
 
 class CdsdpError(RuntimeError):
@@ -428,6 +429,18 @@ class Problem:
             raise CdsdpError(st, "cdsdp_profile_orders")
         return [{"order": orders[c], "ms": ms[c], "launches": launches[c], "cliques": cliques[c],
                  "nominal_flops": flops[c]} for c in range(n) if cliques[c] > 0]
+
+    def profile_large(self):
+        """The cliques of order > 128 in the last profiled solve: dict of ms,
+        launches, cliques, nominal_flops and tensor_flops (cdsdp_profile_large)."""
+        ms, nom, ten = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n, cl = ctypes.c_int(), ctypes.c_int()
+        st = _lib.cdsdp_profile_large(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(cl), ctypes.byref(nom),
+                                      ctypes.byref(ten))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_profile_large")
+        return {"ms": ms.value, "launches": n.value, "cliques": cl.value, "nominal_flops": nom.value,
+                "tensor_flops": ten.value}
 
     # ---- differentiation through unrolled Algorithm 1 ----
 

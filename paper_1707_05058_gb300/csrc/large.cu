@@ -434,7 +434,12 @@ NsLayout ns_layout(const std::vector<int>& sizes) {
         chunks += (b.S + kNormChunkRows - 1) / kNormChunkRows;
         L.chunk_off.push_back(chunks);
         L.max_S = std::max(L.max_S, b.S);
+        const int nu = (int)(((long long)s * (s + 1) / 2 + kUpdChunk - 1) / kUpdChunk);
+        if (L.upd_off.empty()) L.upd_off.push_back(0);
+        L.upd_off.push_back(L.upd_off.back() + nu);
+        L.max_upd = std::max(L.max_upd, nu);
     }
+    if (L.upd_off.empty()) L.upd_off.push_back(0);
     L.elems = off;
     size_t o = 0;
     L.o_err = o; o = up256(o + 16);
@@ -445,6 +450,9 @@ NsLayout ns_layout(const std::vector<int>& sizes) {
     L.o_partial = o; o = up256(o + sizeof(double) * std::max(1, chunks));
     L.o_scale = o; o = up256(o + sizeof(double) * std::max(1, L.nb));
     L.o_poff = o; o = up256(o + sizeof(long long) * std::max(1, L.nb));
+    L.o_list = o; o = up256(o + sizeof(int) * std::max(1, L.nb));
+    L.o_upd = o; o = up256(o + sizeof(int) * (L.nb + 1));
+    L.o_updpart = o; o = up256(o + sizeof(double) * 8 * std::max(1, L.upd_off.back()));
     for (int b = 0; b < 2 * NBUF; ++b) {
         L.o_buf[b] = o;
         o = up256(o + (size_t)off * sizeof(float));
@@ -457,7 +465,7 @@ NsLayout ns_layout(const std::vector<int>& sizes) {
 // offsets) for device memory at `base`; false when the tensor-map encoder is
 // unavailable or refuses a map.
 bool ns_tables(const NsLayout& L, unsigned char* base, const std::vector<long long>& poff,
-               std::vector<unsigned char>& img) {
+               const std::vector<int>& list, std::vector<unsigned char>& img) {
     if (!get_encode()) return false;
     img.assign(L.o_buf[0], 0);
     CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(img.data() + L.o_maps);
@@ -470,6 +478,8 @@ bool ns_tables(const NsLayout& L, unsigned char* base, const std::vector<long lo
     std::memcpy(img.data() + L.o_blocks, L.blocks.data(), sizeof(Block) * L.blocks.size());
     std::memcpy(img.data() + L.o_chunk, L.chunk_off.data(), sizeof(int) * L.chunk_off.size());
     std::memcpy(img.data() + L.o_poff, poff.data(), sizeof(long long) * poff.size());
+    std::memcpy(img.data() + L.o_list, list.data(), sizeof(int) * list.size());
+    std::memcpy(img.data() + L.o_upd, L.upd_off.data(), sizeof(int) * L.upd_off.size());
     return true;
 }
 
@@ -525,23 +535,33 @@ cudaError_t ns_iterate(const NsLayout& L, unsigned char* base, cudaStream_t st) 
     return e;
 }
 
-cudaError_t ns_from_packed(const NsLayout& L, unsigned char* base, const float* Wp, cudaStream_t st) {
+cudaError_t ns_scale_and_iterate(const NsLayout& L, unsigned char* base, cudaStream_t st) {
     const Block* blocks = reinterpret_cast<const Block*>(base + L.o_blocks);
-    const long long* poff = reinterpret_cast<const long long*>(base + L.o_poff);
     const int* chunk = reinterpret_cast<const int*>(base + L.o_chunk);
-    float* Wh = reinterpret_cast<float*>(base + L.o_buf[2 * BUF_W]);
-    float* Wl = reinterpret_cast<float*>(base + L.o_buf[2 * BUF_W + 1]);
+    const float* Wh = reinterpret_cast<const float*>(base + L.o_buf[2 * BUF_W]);
+    const float* Wl = reinterpret_cast<const float*>(base + L.o_buf[2 * BUF_W + 1]);
     float* Xh = reinterpret_cast<float*>(base + L.o_buf[2 * BUF_XA]);
     float* Xl = reinterpret_cast<float*>(base + L.o_buf[2 * BUF_XA + 1]);
-    cudaError_t e = cudaMemsetAsync(base + L.o_buf[2 * BUF_W], 0, 2 * (size_t)L.elems * sizeof(float), st);
-    if (e != cudaSuccess) return e;
     const int gx = std::min(1024, std::max(1, (int)(((long long)L.max_S * L.max_S / 2 + 255) / 256)));
-    k_dense_from_packed<<<dim3(gx, L.nb), 256, 0, st>>>(blocks, poff, Wp, Wh, Wl);
     const int maxchunk = (L.max_S + kNormChunkRows - 1) / kNormChunkRows;
     k_norm_partials<<<dim3(maxchunk, L.nb), 256, 0, st>>>(blocks, chunk, Wh, Wl,
                                                          reinterpret_cast<double*>(base + L.o_partial));
     k_scale_start<<<dim3(gx, L.nb), 256, 0, st>>>(blocks, chunk, reinterpret_cast<const double*>(base + L.o_partial),
                                                   Wh, Wl, Xh, Xl, reinterpret_cast<double*>(base + L.o_scale));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = ns_iterate(L, base, st);
+    return e;
+}
+
+cudaError_t ns_from_packed(const NsLayout& L, unsigned char* base, const float* Wp, cudaStream_t st) {
+    const Block* blocks = reinterpret_cast<const Block*>(base + L.o_blocks);
+    const long long* poff = reinterpret_cast<const long long*>(base + L.o_poff);
+    float* Wh = reinterpret_cast<float*>(base + L.o_buf[2 * BUF_W]);
+    float* Wl = reinterpret_cast<float*>(base + L.o_buf[2 * BUF_W + 1]);
+    cudaError_t e = cudaMemsetAsync(base + L.o_buf[2 * BUF_W], 0, 2 * (size_t)L.elems * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    const int gx = std::min(1024, std::max(1, (int)(((long long)L.max_S * L.max_S / 2 + 255) / 256)));
+    k_dense_from_packed<<<dim3(gx, L.nb), 256, 0, st>>>(blocks, poff, Wp, Wh, Wl);
     return cudaGetLastError();
 }
 
@@ -583,8 +603,10 @@ int cdsdp_psd_project_large(int p, const int* h_size, const long long* h_off, co
         if (scratch_bytes < L.bytes) return CDSDP_ERR_NOMEM;
         unsigned char* base = static_cast<unsigned char*>(d_scratch);
         std::vector<long long> poff(h_off, h_off + p);
+        std::vector<int> list(p);
+        for (int k = 0; k < p; ++k) list[k] = k;
         std::vector<unsigned char> img;
-        if (!ns_tables(L, base, poff, img)) return CDSDP_ERR_CUDA;
+        if (!ns_tables(L, base, poff, list, img)) return CDSDP_ERR_CUDA;
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         if (cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
@@ -592,7 +614,7 @@ int cdsdp_psd_project_large(int p, const int* h_size, const long long* h_off, co
             return CDSDP_ERR_CUDA;
         }
         cudaError_t e = ns_from_packed(L, base, d_W, st);
-        if (e == cudaSuccess) e = ns_iterate(L, base, st);
+        if (e == cudaSuccess) e = ns_scale_and_iterate(L, base, st);
         if (e == cudaSuccess) e = ns_to_packed(L, base, d_X, st);
         if (e != cudaSuccess) {
             cudaGetLastError();

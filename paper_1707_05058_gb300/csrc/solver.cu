@@ -18,6 +18,7 @@
 #include "proj_launch.h"
 #include "grad.cuh"
 #include "grad_launch.h"
+#include "large_launch.h"
 
 using namespace cdsdp_dev;
 using cdsdp_impl::HostProblem;
@@ -40,7 +41,9 @@ struct Layout {
     // state
     size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, vcache, part, parte, partr, scal, ctl, hist,
         comp_done, comp_iter, comp_status, comp_res, rho, cg_res, cg_p, cg_q, cg_u, cg_scal;
-    size_t total;
+    size_t total;   // end of the state section (zeroed at every solve)
+    size_t ns_off;  // dense buffers and tables of the large-clique projection (not zeroed per solve)
+    size_t ws_end;  // workspace bytes
 };
 
 }  // namespace
@@ -82,6 +85,10 @@ struct cdsdp {
     double prof_cls_ms[kNumClasses] = {0};
     int prof_cls_n[kNumClasses] = {0};
     cdsdp_impl::CmpGraph cmp_graph;  // cached step graph of the completion
+    // cliques of order > 128: sign iteration on the tensor cores (large.cu)
+    cdsdp_large::NsLayout ns;
+    double prof_large_ms = 0.0;
+    int prof_large_n = 0;
 };
 
 namespace {
@@ -96,6 +103,16 @@ int fail_cuda(cdsdp* h, cudaError_t e, const char* what) {
         cudaError_t _e = (call);                              \
         if (_e != cudaSuccess) return fail_cuda(h, _e, #call); \
     } while (0)
+
+// Orders of the cliques served by the sign iteration (order > 128), in clique order.
+std::vector<int> large_sizes(const HostProblem& hp) {
+    std::vector<int> s;
+    for (size_t k = 0; k + 1 < hp.cl_off.size(); ++k) {
+        const int sk = hp.cl_off[k + 1] - hp.cl_off[k];
+        if (sk >= cdsdp_large::kLargeFrom) s.push_back(sk);
+    }
+    return s;
+}
 
 Layout make_layout(const HostProblem& hp, int max_iter) {
     Layout L{};
@@ -140,6 +157,8 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     L.cg_res = take(m * 8); L.cg_p = take(m * 8); L.cg_q = take(m * 8); L.cg_u = take(NE * 8);
     L.cg_scal = take(4 * 8);
     L.total = o;
+    L.ns_off = o;
+    L.ws_end = o + cdsdp_large::ns_layout(large_sizes(hp)).bytes;
     return L;
 }
 
@@ -275,6 +294,8 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
     int last = -1;
     for (int c = 0; c < kNumClasses; ++c)
         if (h->cls_off[c + 1] > h->cls_off[c]) last = c;
+    const bool large = h->ns.nb > 0;
+    if (large) last = -1;  // the large cliques' reduction finishes the iteration
     cudaError_t e = cudaSuccess;
     pa.row_off = 0;
     pa.warps_div = o.proj_warps_div;
@@ -290,6 +311,11 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
                            : launch_proj_f64(form, c, h->dev, list, nl, pa, f, st);
         if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * c + 1], st);
         pa.row_off += proj_launch_grid(c, nl, sizeof(T) == 4, pa.warps_div);  // rows of this launch
+    }
+    if (large && e == cudaSuccess) {  // float clique state only (FP64 refuses these orders)
+        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * kNumClasses], st);
+        e = cdsdp_large::large_step(form, h->dev, h->ns, h->ws + h->L.ns_off, pa.row_off, fa, st);
+        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * kNumClasses + 1], st);
     }
     return e;
 }
@@ -330,6 +356,7 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         const int nl = h->cls_off[c + 1] - h->cls_off[c];
         if (nl > 0) prow += proj_launch_grid(c, nl, sizeof(T) == 4, o.proj_warps_div);
     }
+    prow += h->ns.nb;  // one row per large clique
     fa.npart = std::min(d.p, form == 1 ? std::max(prow, PG) : prow);
     fa.enabled = 1;
     fa.use_cond = use_cond;
@@ -900,16 +927,16 @@ int cdsdp_component_results(cdsdp* h, void* stream, int* iters, int* status, dou
 
 int cdsdp_workspace_bytes(const cdsdp* h, int max_iter, size_t* bytes) {
     if (!h || !bytes || max_iter < 1) return CDSDP_ERR_ARG;
-    *bytes = make_layout(h->hp, max_iter).total;
+    *bytes = make_layout(h->hp, max_iter).ws_end;
     return CDSDP_SOLVED;
 }
 
 int cdsdp_bind(cdsdp* h, void* d_workspace, size_t bytes, int max_iter, void* stream) {
     if (!h || !d_workspace || max_iter < 1) return CDSDP_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) return CDSDP_ERR_ARG;
-    if (h->hp.max_clique > kMaxOrderF32) return CDSDP_ERR_UNSUPPORTED;
+    if (h->hp.max_clique > cdsdp_large::kMaxLargeOrder) return CDSDP_ERR_UNSUPPORTED;
     Layout L = make_layout(h->hp, max_iter);
-    if (bytes < L.total) return CDSDP_ERR_NOMEM;
+    if (bytes < L.ws_end) return CDSDP_ERR_NOMEM;
     drop_graph(h);
     h->L = L;
     h->ws = (unsigned char*)d_workspace;
@@ -925,6 +952,29 @@ int cdsdp_bind(cdsdp* h, void* d_workspace, size_t bytes, int max_iter, void* st
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(h->ws, h->image.data(), h->image.size(), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
+    // large cliques: tensor maps of the dense buffers (they encode the
+    // workspace address), tables, and zero padding of the W buffers
+    std::vector<int> list;
+    std::vector<long long> poff;
+    for (size_t k = 0; k + 1 < h->hp.cl_off.size(); ++k)
+        if (h->hp.cl_off[k + 1] - h->hp.cl_off[k] >= cdsdp_large::kLargeFrom) {
+            list.push_back((int)k);
+            poff.push_back(h->hp.pk_off[k]);
+        }
+    h->ns = cdsdp_large::ns_layout(large_sizes(h->hp));
+    if (h->ns.nb > 0) {
+        std::vector<unsigned char> img;
+        unsigned char* base = h->ws + L.ns_off;
+        if (!cdsdp_large::ns_tables(h->ns, base, poff, list, img)) {
+            h->err = "tensor-map encoder unavailable or refused a map";
+            h->ws = nullptr;
+            return CDSDP_ERR_CUDA;
+        }
+        CK(cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(base + h->ns.o_buf[2 * cdsdp_large::BUF_W], 0,
+                           2 * (size_t)h->ns.elems * sizeof(float), st));
+        CK(cudaStreamSynchronize(st));
+    }
     return CDSDP_SOLVED;
 }
 
@@ -946,7 +996,7 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     d.comp_mode = (h->hp.ncomp > 1 && form != 2 && o.component_stop && o.linear_solver == 0) ? 1 : 0;
     d.cg_tol = o.cg_tol;
     d.cg_max = o.cg_max_steps;
-    h->x_split = o.x_update == 0 ? h->x_split_auto : o.x_update == 2;
+    h->x_split = h->ns.nb > 0 || (o.x_update == 0 ? h->x_split_auto : o.x_update == 2);
     // zero the state (clique vectors, iterates, partials, history)
     CK(cudaMemsetAsync(h->ws + h->L.const_end, 0, h->L.total - h->L.const_end, st));
     k_init<<<1, 256, 0, st>>>(d, form, o.rho);
@@ -960,7 +1010,7 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
             CK(cudaEventCreate(&e));
             h->ev.push_back(e);
         }
-        const size_t need_cls = (size_t)2 * kNumClasses * o.max_iter;
+        const size_t need_cls = (size_t)(2 * kNumClasses + 2) * o.max_iter;
         while (h->cls_evs.size() < need_cls) {
             cudaEvent_t e;
             CK(cudaEventCreate(&e));
@@ -970,7 +1020,7 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
         int launched = 0;
         for (int it = 0; it < o.max_iter; ++it) {
             CK(cudaEventRecord(h->ev[4 * it], st));
-            h->cls_ev = h->cls_evs.data() + (size_t)2 * kNumClasses * it;
+            h->cls_ev = h->cls_evs.data() + (size_t)(2 * kNumClasses + 2) * it;
             const cudaError_t le =
                 launch_iteration_any(h, form, o, st, 0, cudaGraphConditionalHandle{}, h->ev[4 * it + 1], h->ev[4 * it + 2]);
             h->cls_ev = nullptr;
@@ -992,6 +1042,8 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
             h->prof_cls_ms[c] = 0.0;
             h->prof_cls_n[c] = 0;
         }
+        h->prof_large_ms = 0.0;
+        h->prof_large_n = 0;
         for (int it = 0; it < ran; ++it) {
             float a = 0.f, b = 0.f;
             CK(cudaEventElapsedTime(&a, h->ev[4 * it + 1], h->ev[4 * it + 2]));
@@ -1000,11 +1052,18 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
             h->prof_iter_ms += b;
             for (int c = 0; c < kNumClasses; ++c) {
                 if (h->cls_off[c + 1] <= h->cls_off[c]) continue;
-                const cudaEvent_t* pe = h->cls_evs.data() + (size_t)2 * kNumClasses * it + 2 * c;
+                const cudaEvent_t* pe = h->cls_evs.data() + (size_t)(2 * kNumClasses + 2) * it + 2 * c;
                 float t = 0.f;
                 CK(cudaEventElapsedTime(&t, pe[0], pe[1]));
                 h->prof_cls_ms[c] += t;
                 h->prof_cls_n[c] += 1;
+            }
+            if (h->ns.nb > 0) {
+                const cudaEvent_t* pe = h->cls_evs.data() + (size_t)(2 * kNumClasses + 2) * it + 2 * kNumClasses;
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, pe[0], pe[1]));
+                h->prof_large_ms += t;
+                h->prof_large_n += 1;
             }
         }
         h->prof_launches = ran;
@@ -1036,6 +1095,17 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     h->last_status = ctl[CTL_STATUS];
     h->last_comp_mode = d.comp_mode;
     if (iters) *iters = h->last_iters;
+    if (h->ns.nb > 0) {  // a bounded wait inside the tensor-core products that ran out
+        int nerr = 0;
+        unsigned char* ep = h->ws + h->L.ns_off + h->ns.o_err;
+        CK(cudaMemcpyAsync(&nerr, ep, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (nerr) {
+            CK(cudaMemsetAsync(ep, 0, sizeof(int), st));
+            h->err = "a bounded wait in the tensor-core product kernel ran out";
+            return CDSDP_ERR_TIMEOUT;
+        }
+    }
     rc = copy_results(h, st, X, y, Z, hist, cert);
     if (rc != CDSDP_SOLVED) return rc;
     return h->last_status;
@@ -1124,6 +1194,25 @@ int cdsdp_profile_orders(const cdsdp* h, int* orders, double* ms, int* launches,
     return CDSDP_SOLVED;
 }
 
+int cdsdp_profile_large(const cdsdp* h, double* ms, int* launches, int* cliques, double* nominal_flops,
+                        double* tensor_flops) {
+    if (!h) return CDSDP_ERR_ARG;
+    if (!h->last_profiled) return CDSDP_ERR_STATE;
+    if (ms) *ms = h->prof_large_ms;
+    if (launches) *launches = h->prof_large_n;
+    if (cliques) *cliques = h->ns.nb;
+    double nom = 0.0, ten = 0.0;
+    const int products = 3 * cdsdp_large::kPhase1 + 2 * cdsdp_large::kPhase2 + 1;
+    for (const auto& b : h->ns.blocks) {
+        nom += 10.0 * double(b.s) * b.s * b.s;
+        const double T = b.S / cdsdp_large::kTile;
+        ten += products * (T * (T + 1) / 2) * 3.0 * 2.0 * cdsdp_large::kTile * cdsdp_large::kTile * double(b.S);
+    }
+    if (nominal_flops) *nominal_flops = nom;
+    if (tensor_flops) *tensor_flops = ten;
+    return CDSDP_SOLVED;
+}
+
 int cdsdp_profile(const cdsdp* h, double* proj_ms, int* proj_launches, double* iter_ms) {
     if (!h) return CDSDP_ERR_ARG;
     if (!h->last_profiled) return CDSDP_ERR_STATE;
@@ -1197,7 +1286,7 @@ int cdsdp_unrolled_forward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckpt
                            const double* d_b, void* d_gws, size_t gws_bytes, double* d_x, void* stream) {
     if (!h || !d_c || !d_b || !d_gws || !d_x) return CDSDP_ERR_ARG;
     const cdsdp_opts o = unrolled_opts(opts);
-    h->x_split = o.x_update == 0 ? h->x_split_auto : o.x_update == 2;
+    h->x_split = h->ns.nb > 0 || (o.x_update == 0 ? h->x_split_auto : o.x_update == 2);
     int rc = check_unrolled(h, o, iters, ckpt_every);
     if (rc != CDSDP_SOLVED) return rc;
     const bool fp32 = o.precision != CDSDP_FP64;
@@ -1230,7 +1319,7 @@ int cdsdp_unrolled_backward(cdsdp* h, const cdsdp_opts* opts, int iters, int ckp
                             double* d_bbar, void* stream) {
     if (!h || !d_c || !d_b || !d_gws || !d_xbar || !d_cbar || !d_bbar) return CDSDP_ERR_ARG;
     const cdsdp_opts o = unrolled_opts(opts);
-    h->x_split = o.x_update == 0 ? h->x_split_auto : o.x_update == 2;
+    h->x_split = h->ns.nb > 0 || (o.x_update == 0 ? h->x_split_auto : o.x_update == 2);
     int rc = check_unrolled(h, o, iters, ckpt_every);
     if (rc != CDSDP_SOLVED) return rc;
     const bool fp32 = o.precision != CDSDP_FP64;

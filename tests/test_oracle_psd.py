@@ -69,3 +69,16 @@ def test_daleckii_krein_matches_finite_differences(s):
         fd = (np.sum(G * psd.psd_project((Wm + h * dW)[None])[0]) -
               np.sum(G * psd.psd_project((Wm - h * dW)[None])[0])) / (2 * h)
         np.testing.assert_allclose(np.sum(g * dW), fd, rtol=1e-6, atol=1e-8)
+
+
+@pytest.mark.parametrize("s", [1, 2, 5, 17, 40])
+def test_lapack_step_equals_jacobi(s):
+    """The oracle's two eigendecomposition steps give the same projection
+    (the LAPACK step serves the problems with cliques of order in the
+    hundreds)."""
+    rng = np.random.default_rng(s)
+    G = rng.standard_normal((3, s, s))
+    W = G + np.swapaxes(G, 1, 2)
+    Pj = psd.psd_project(W)
+    Pl = psd.psd_project(W, eig="lapack")
+    assert np.abs(Pj - Pl).max() <= 1e-12 * max(1.0, np.abs(W).max())
