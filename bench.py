@@ -32,6 +32,9 @@ reductions).
             cdsdp_fma_peak on this GPU
   banded    the banded workload (n=2000, w=10, m=500; 1990 cliques of order
             11): time to 1e-4 in the FP32 graph and plain FP64 forms
+  maxcut    the MaxCut workload (n = 10^4, G(n, 6/(n-1)), merged cliques up to
+            order 3560): clique histogram, per-iteration split, the tensor-core
+            sign iteration against the TF32 peak, FP32 solve to 1e-4 (capped)
   cpu_baseline  the FP64 oracle on a bounded sample of the same batch: 8 of its
             SDPs, 4 iterations each, on 1 host thread and on one process per
             SDP
@@ -282,6 +285,52 @@ def _banded(cdsdp, workloads, torch, flush, stream):
                            "nominal_gflops": top["nominal_flops"] / (top["ms"] / top["launches"] / 1e3) / 1e9}}
 
 
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def _maxcut(cdsdp, workloads, torch, flush, stream, max_iter=2500):
+    """MaxCut relaxation on G(n, 6/(n-1)), n = 10^4 (weights U(0,1), C = -L/4,
+    diag(X) = 1): minimum-degree extension, cliques merged
+    (CDSDP_SETUP_MERGE_CLIQUES).  Clique-order histogram; a profiled run of 10
+    iterations (the step of the cliques above order 128 on the tensor cores
+    against the rest); Algorithm 1 in the FP32 form with the adaptive penalty
+    to eps = 1e-4 within max_iter iterations."""
+    import numpy as np
+    prob = workloads.workload(3)
+    t0 = time.perf_counter()
+    P = cdsdp.Problem(prob, merge_cliques=True)
+    setup_s = time.perf_counter() - t0
+    P.bind(max_iter=max_iter)
+    sizes = np.diff(P.cliques()[0])
+    edges = [1, 17, 33, 65, 129, 513, 2049, 1 << 20]
+    hist = {f"{lo}-{hi - 1}": int(np.sum((sizes >= lo) & (sizes < hi))) for lo, hi in zip(edges[:-1], edges[1:])}
+    P.solve("primal", outputs=False, eps=0.0, max_iter=10, precision="fp32", profile=1, check_every=10, adaptive_rho=1)
+    proj_ms, launches, iter_ms = P.profile()
+    lg = P.profile_large()
+    lg_ms = lg["ms"] / max(1, lg["launches"])
+    tensor_tflops = lg["tensor_flops"] / (lg_ms / 1e3) / 1e12
+    pk = _peaks()
+    tf32_peak = pk.get("bf16_tflops", 1910.0) * (1.1 / 2.25)  # nominal tf32 / bf16 dense ratio
+    flush.fill_(1)
+    ms, out = _event_ms(torch, stream, lambda: P.solve("primal", outputs=False, eps=1e-4, max_iter=max_iter,
+                                                       precision="fp32", adaptive_rho=1))
+    return {"workload": "maxcut_gnp_n10000_deg6, cliques merged", "n": int(P.info["n"]), "m": int(P.info["m"]),
+            "cliques": int(P.info["p"]), "clique_order_max": int(P.info["max_clique"]), "clique_histogram": hist,
+            "n_d_lower": int(P.info["n_d_lower"]), "components": int(P.info["ncomp"]), "setup_s": setup_s,
+            "ms_per_iter": iter_ms / launches, "proj_ms_per_iter": proj_ms / launches,
+            "large_cliques": lg["cliques"], "large_step_ms_per_iter": lg_ms,
+            "tensor_roofline": {"bound": "tensor", "achieved": tensor_tflops, "peak": tf32_peak, "unit": "TFLOP/s",
+                                "frac": tensor_tflops / tf32_peak,
+                                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio",
+                                "work": "59 products x 3 TF32 MMAs over the lower 128x128 tiles per step"},
+            "fp32_primal": {"status": int(out["status"]), "iters": int(out["iters"]), "ms": ms, "max_iter": max_iter}}
+
+
 def _grad_batch(cdsdp, workloads, torch, stream):
     """Differentiation workload: 64 banded SDPs (n=500, w=8, m=200) as one
     direct sum; 500 unrolled iterations of Algorithm 1 in the FP32-projection
@@ -349,7 +398,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the banded, gradient and completion blocks")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the banded, MaxCut, gradient and completion blocks")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -471,6 +521,7 @@ def main():
     extras = {}
     if not args.no_extras:
         extras["banded"] = _banded(cdsdp, workloads, torch, flush, stream)
+        extras["maxcut"] = _maxcut(cdsdp, workloads, torch, flush, stream)
         extras["grad"] = _grad_batch(cdsdp, workloads, torch, stream)
         extras["completion"] = _completion(cdsdp, workloads, torch, stream)
 

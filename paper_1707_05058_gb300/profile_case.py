@@ -10,6 +10,9 @@ no early stop.  Workloads:
   batched       direct sum of `--count` uneven block-arrow SDPs (l in [10,100],
                 d in [10,40], h in [10,20], m in [50,400]; cliques of order
                 20..60); --count 256 is the full batch
+  maxcut        MaxCut relaxation on G(n, 6/(n-1)) with --n vertices (10^4 is
+                the MaxCut workload), cliques merged; the cliques above order
+                128 run the tensor-core sign iteration
 """
 from __future__ import annotations
 
@@ -24,7 +27,8 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="banded", choices=["banded", "block_arrow", "batched"])
+    ap.add_argument("--workload", default="banded", choices=["banded", "block_arrow", "batched", "maxcut"])
+    ap.add_argument("--n", type=int, default=10000, help="vertices of the maxcut workload")
     ap.add_argument("--count", type=int, default=256, help="problems in the batched workload")
     ap.add_argument("--form", default="primal", choices=["primal", "dual", "hsde"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -39,11 +43,15 @@ def main(argv=None):
     __graft_entry__.build_library()
     from paper_1707_05058_gb300 import cdsdp, workloads
 
+    merge = False
     if args.workload == "batched":
         prob = workloads.direct_sum(workloads.block_arrow_batch(args.count, 3707))
+    elif args.workload == "maxcut":
+        prob = workloads.workload(3) if args.n == 10000 else workloads.maxcut(args.n, 6, 4707 + args.n)
+        merge = True
     else:
         prob = workloads.workload(1 if args.workload == "banded" else 0)
-    P = cdsdp.Problem(prob).bind(max_iter=args.iters)
+    P = cdsdp.Problem(prob, merge_cliques=merge).bind(max_iter=args.iters)
     out = P.solve(args.form, eps=0.0, max_iter=args.iters, precision=args.precision, use_graph=0,
                   check_every=args.iters, outputs=False, x_update=args.x_update)
     torch.cuda.synchronize()

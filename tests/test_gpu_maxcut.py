@@ -9,10 +9,13 @@ tests/golden/make_maxcut_oracle.py from oracle/ only).
     the tile kernels;
   * n = 800, cliques merged: one clique of order 296.
 
-Algorithm 1 (adaptive penalty every iteration) and Algorithm 3, eps = 1e-4.
-Checks: solved; iteration count within 5% (at least 3) of the oracle's; the
-objective <C, X> within 1e-4 (relative) of the oracle's at the same
-iteration (its last when the GPU runs longer)."""
+Algorithm 1 (adaptive penalty every iteration) to eps = 1e-4: solved,
+iteration count within 5% (at least 3) of the oracle's, the objective <C, X>
+within 1e-4 (relative) of the oracle's at the same iteration.  Algorithm 3:
+the first 300 iterations (one tau, kappa over these graphs' independent
+components keeps it from 1e-4 in 5000 iterations, on both sides); the
+objective c^T u_x / tau and b^T u_y / tau of iteration 300 within 1e-4 of the
+oracle's, and its residuals within 10% (at least 1e-6 absolute)."""
 import json
 import os
 
@@ -44,8 +47,16 @@ def test_maxcut_large_cliques_fp32(lib, gold, case, form):
     prob = W.maxcut(n, 6, 4707 + n, name=f"maxcut_n{n}")
     P = lib.Problem(prob, merge_cliques=merge).bind(max_iter=20000)
     assert P.info["max_clique"] == g["max_clique"] > 128
-    kw = dict(adaptive_rho=1) if form == "primal" else {}
-    out = P.solve(form, eps=1e-4, max_iter=20000, precision="fp32", **kw)
+    if form == "hsde":
+        out = P.solve("hsde", eps=0.0, max_iter=g["iters"], precision="fp32")
+        assert out["iters"] == g["iters"]
+        h, want = out["hist"][-1], g["hist"][-1]
+        for col in (4, 5):  # objective c^T x, b^T y
+            assert abs(h[col] - want[col]) <= 1e-4 * abs(want[col]), (col, h[col], want[col])
+        for col in (0, 1, 2, 3):  # eps_p, eps_d, eps_g, eps_c
+            assert abs(h[col] - want[col]) <= max(1e-6, 0.1 * abs(want[col])), (col, h[col], want[col])
+        return
+    out = P.solve(form, eps=1e-4, max_iter=20000, precision="fp32", adaptive_rho=1)
     assert out["status"] == 0 and g["status"] == 0
     assert abs(out["iters"] - g["iters"]) <= max(3, 0.05 * g["iters"]), (out["iters"], g["iters"])
     dp = admm.decompose(prob, merge=merge, eig="lapack")
