@@ -81,6 +81,8 @@ struct HostProblem {
     std::vector<int> lrow;             // [m] index of a constraint within its component
     std::vector<int> crow_ptr, crow_idx;  // constraints of each component (ascending)
     std::vector<int> ccl_ptr, ccl_idx;    // cliques of each component (ascending)
+    std::vector<int> cent_ptr, cent_idx;  // pattern entries of each component (ascending)
+    std::vector<double> comp_nb, comp_nc; // [ncomp] ||b_c||, ||c_c|| (weighted lower storage)
     std::vector<long long> minv_off;   // [ncomp] offset of each dense block in minv / kinv
     long long factor_size = 0;         // doubles in minv (and kinv)
     bool cached_factor = true;         // false: setup skipped the inverses (CG only)
@@ -93,6 +95,9 @@ struct HostProblem {
     // its s/t parts equal +-H zhat_x / 2 and are formed on the fly.
     std::vector<double> zhat_x, zhat_y;
     double zeta_dot_zhat = 0.0;
+    // The same constants for one embedding per component (each summand of a
+    // direct sum embedded on its own): zeta_hat_c = M_c^-1 zeta_c / (1 + zeta_c^T M_c^-1 zeta_c)
+    std::vector<double> zhat_x_c, zhat_y_c, a_zhat_x_c, zdz_c;
     std::vector<double> atb;          // A^T b per pattern entry
     std::vector<double> a_zhat_x;     // A W zhat_x per constraint
     double norm_b = 0.0, norm_c = 0.0;

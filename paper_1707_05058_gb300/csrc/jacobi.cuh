@@ -599,10 +599,11 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
     T* ut = reinterpret_cast<T*>(d.ck2);
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
-    const double gamma = d.scal[SC_GAMMA];
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
         const int k = list[li];
+        if (frozen_clique(d, k)) continue;  // warp-uniform
+        const double gamma = hs_gamma_c(d, comp_k(d, k));
         const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
         jac.clear(lane);
         T nrm = T(0);
@@ -654,10 +655,20 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
             p[4] += w * double(vn) * double(vn);
             p[5] += w * double(utn) * double(utn);
         }
+        double q[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += warp_sum(p[c]);
+        for (int c = 0; c < 6; ++c) q[c] = warp_sum(p[c]);
+        if (d.comp_mode) {  // per-clique row, reduced per component
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) d.part[(size_t)k * PART_COLS + c] = q[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[c] += q[c];
+        }
         __syncwarp();
     }
+    if (d.comp_mode) return;
     const int cols[6] = {0, 1, 2, 3, 4, 5};
     block_partial_row<6>(acc, d.part, pa.row_off + blockIdx.x, cols);
 }

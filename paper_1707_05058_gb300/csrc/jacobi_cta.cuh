@@ -597,7 +597,6 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
     T* c2 = reinterpret_cast<T*>(d.ck2);
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = FORM != 3 && pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
-    const double gamma = FORM == 2 ? d.scal[SC_GAMMA] : 0.0;
     __shared__ double acc[6];  // block partial sums, kept by thread 0
     if (tid < 6) acc[tid] = 0.0;
     for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
@@ -607,6 +606,7 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
         if (s > S || s < 1) continue;  // block-uniform
         if (FORM != 3 && frozen_clique(d, k)) continue;
         const double rho = (FORM == 0 || FORM == 1) ? rho_clique(d, k) : 1.0, irho = 1.0 / rho;
+        const double gamma = FORM == 2 ? hs_gamma_c(d, comp_k(d, k)) : 0.0;
         const int npk = s * (s + 1) / 2;
         jac.clear();
         double nrm = 0.0, cx = 0.0;
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
             if (FORM != 2) p[5] = cxk;
             if (tid == 0 && d.comp_mode) {  // per-clique row, reduced per component
                 double* pr = d.part + (size_t)k * PART_COLS;
-                if (FORM == 0) { for (int c = 0; c < 6; ++c) pr[c] = p[c]; }
+                if (FORM == 0 || FORM == 2) { for (int c = 0; c < 6; ++c) pr[c] = p[c]; }
                 else if (FORM == 1) { pr[5] = p[0]; }
             } else if (tid == 0) {
                 for (int c = 0; c < 5; ++c) acc[c] += p[c];

@@ -92,6 +92,17 @@ struct Dev {
     double* comp_res;           // [ncomp * HIST_COLS] last stopping-test row of the component
     double* rho;                // [ncomp] penalty of Algorithms 1-2: one per component when
                                 // components stop on their own, else entry 0 for the whole problem
+    // Algorithm 3 with one embedding per independent component (component
+    // mode): tau, kappa, gamma per component; zhx, zhy, azhx then point at the
+    // per-component zeta_hat of each component's own embedding
+    double* hs_tau;             // [ncomp]
+    double* hs_kappa;           // [ncomp]
+    double* hs_gamma;           // [ncomp]
+    const double* hs_zdz;       // [ncomp] zeta_c^T zeta_hat_c
+    const double* hs_nb;        // [ncomp] ||b_c||
+    const double* hs_nc;        // [ncomp] ||c_c|| (weighted lower storage)
+    const int* cent_ptr;        // [ncomp+1] pattern entries of each component
+    const int* cent_idx;        // [NE]
     // conjugate-gradient affine step (opts.linear_solver = 1)
     double *cg_res, *cg_p, *cg_q;  // [m]
     double* cg_u;                  // [NE]
@@ -150,6 +161,19 @@ __device__ __forceinline__ double adapt_rho(double rho, double ep, double ed, do
     if (ed >= nu * ep) return rho / mu;
     return rho;
 }
+
+// tau, kappa and gamma of Algorithm 3 seen by a pattern entry, constraint row
+// or clique: the component's own in component mode, else the single embedding's.
+__device__ __forceinline__ double hs_tau_c(const Dev& d, int c) { return d.comp_mode ? d.hs_tau[c] : d.scal[SC_TAU]; }
+__device__ __forceinline__ double hs_kappa_c(const Dev& d, int c) {
+    return d.comp_mode ? d.hs_kappa[c] : d.scal[SC_KAPPA];
+}
+__device__ __forceinline__ double hs_gamma_c(const Dev& d, int c) {
+    return d.comp_mode ? d.hs_gamma[c] : d.scal[SC_GAMMA];
+}
+__device__ __forceinline__ int comp_e(const Dev& d, int e) { return d.comp_mode ? d.comp_of_entry[e] : 0; }
+__device__ __forceinline__ int comp_r(const Dev& d, int i) { return d.comp_mode ? d.comp_of_row[i] : 0; }
+__device__ __forceinline__ int comp_k(const Dev& d, int k) { return d.comp_mode ? d.comp_of_clique[k] : 0; }
 
 // Component freeze: a stopped component's entries, rows and cliques are left alone.
 __device__ __forceinline__ bool frozen_clique(const Dev& d, int k) {

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) k_large_gather(Dev d, Step t) {
     const float* c1 = reinterpret_cast<const float*>(d.ck1);
     const float* c2 = reinterpret_cast<const float*>(d.ck2);
     const double irho = (FORM == 2) ? 1.0 : 1.0 / cdsdp_dev::rho_clique(d, k);
-    const double gamma = FORM == 2 ? d.scal[cdsdp_dev::SC_GAMMA] : 0.0;
+    const double gamma = FORM == 2 ? cdsdp_dev::hs_gamma_c(d, cdsdp_dev::comp_k(d, k)) : 0.0;
     for (long long f = f0 + threadIdx.x; f < f1; f += blockDim.x) {
         int a, b;
         packed_ab64(f, B.s, a, b);
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_large_update(Dev d, Step t) {
     float* c1 = reinterpret_cast<float*>(d.ck1);
     float* c2 = reinterpret_cast<float*>(d.ck2);
     const double rho = (FORM == 0 || FORM == 1) ? cdsdp_dev::rho_clique(d, k) : 1.0;
-    const double gamma = FORM == 2 ? d.scal[cdsdp_dev::SC_GAMMA] : 0.0;
+    const double gamma = FORM == 2 ? cdsdp_dev::hs_gamma_c(d, cdsdp_dev::comp_k(d, k)) : 0.0;
     double p[6] = {0, 0, 0, 0, 0, 0};
     for (long long f = f0 + threadIdx.x; f < f1; f += blockDim.x) {
         int a, b;

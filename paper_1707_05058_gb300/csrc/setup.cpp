@@ -387,6 +387,19 @@ int build_hsde_constants(HostProblem& hp) {
         for (int i = 0; i < m; ++i) hp.zhat_y[i] = s21[i] / denom;
         hp.zeta_dot_zhat = zMz / denom;
         A_w(hp.zhat_x, hp.a_zhat_x);
+        // one embedding per component: M is block diagonal over the components,
+        // so M^-1 zeta restricted to component c is M_c^-1 zeta_c (s11, s21 above),
+        // normalised by that component's own 1 + zeta_c^T M_c^-1 zeta_c
+        std::vector<double> zmz(hp.ncomp, 0.0);
+        for (int e = 0; e < NE; ++e) zmz[hp.comp_of_entry[e]] += wgt(e) * hp.c[e] * s11[e];
+        for (int i = 0; i < m; ++i) zmz[hp.comp_of_row[i]] -= hp.b[i] * s21[i];
+        hp.zhat_x_c.resize(NE);
+        hp.zhat_y_c.resize(m);
+        hp.zdz_c.resize(hp.ncomp);
+        for (int e = 0; e < NE; ++e) hp.zhat_x_c[e] = s11[e] / (1.0 + zmz[hp.comp_of_entry[e]]);
+        for (int i = 0; i < m; ++i) hp.zhat_y_c[i] = s21[i] / (1.0 + zmz[hp.comp_of_row[i]]);
+        for (int c = 0; c < hp.ncomp; ++c) hp.zdz_c[c] = zmz[c] / (1.0 + zmz[c]);
+        A_w(hp.zhat_x_c, hp.a_zhat_x_c);
     }
     hp.hsde_ready = true;
     return CDSDP_SOLVED;
@@ -993,6 +1006,23 @@ int build_host_problem(int n, int m,
     for (int e = 0; e < NE; ++e) nc += wgt(e) * hp.c[e] * hp.c[e];
     hp.norm_b = std::sqrt(nb);
     hp.norm_c = std::sqrt(nc);
+    // per component: its pattern entries and the norms of its b and c
+    hp.cent_ptr.assign(hp.ncomp + 1, 0);
+    for (int e = 0; e < NE; ++e) ++hp.cent_ptr[hp.comp_of_entry[e] + 1];
+    for (int c = 0; c < hp.ncomp; ++c) hp.cent_ptr[c + 1] += hp.cent_ptr[c];
+    hp.cent_idx.assign(NE, 0);
+    {
+        std::vector<int> fill(hp.cent_ptr.begin(), hp.cent_ptr.end() - 1);
+        for (int e = 0; e < NE; ++e) hp.cent_idx[fill[hp.comp_of_entry[e]]++] = e;
+    }
+    hp.comp_nb.assign(hp.ncomp, 0.0);
+    hp.comp_nc.assign(hp.ncomp, 0.0);
+    for (int i = 0; i < m; ++i) hp.comp_nb[hp.comp_of_row[i]] += hp.b[i] * hp.b[i];
+    for (int e = 0; e < NE; ++e) hp.comp_nc[hp.comp_of_entry[e]] += wgt(e) * hp.c[e] * hp.c[e];
+    for (int c = 0; c < hp.ncomp; ++c) {
+        hp.comp_nb[c] = std::sqrt(hp.comp_nb[c]);
+        hp.comp_nc[c] = std::sqrt(hp.comp_nc[c]);
+    }
     return CDSDP_SOLVED;
 }
 

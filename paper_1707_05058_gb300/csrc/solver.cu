@@ -36,11 +36,13 @@ struct Layout {
     // constants
     size_t c, dinv, pinv, wgt, a_ptr, a_col, a_valw, a_valu, at_ptr, at_col, at_val, b, minv, kinv, gmap, pk_off, csize,
         sc_ptr, sc_idx, zhx, zhy, atb, azhx, blist, vv_off, owner, comp_of_entry, comp_of_clique, comp_of_row, lrow,
-        crow_ptr, crow_idx, ccl_ptr, ccl_idx, minv_off;
+        crow_ptr, crow_idx, ccl_ptr, ccl_idx, minv_off, cent_ptr, cent_idx, hs_nb, hs_nc, zhx_c, zhy_c, azhx_c,
+        hs_zdz;
     size_t const_end;
     // state
     size_t x, t, q, s11, atuy, y, g, hh, s21, as11, ck0, ck1, ck2, vcache, part, parte, partr, scal, ctl, hist,
-        comp_done, comp_iter, comp_status, comp_res, rho, cg_res, cg_p, cg_q, cg_u, cg_scal;
+        comp_done, comp_iter, comp_status, comp_res, rho, cg_res, cg_p, cg_q, cg_u, cg_scal, hs_tau, hs_kappa,
+        hs_gamma;
     size_t total;   // end of the state section (zeroed at every solve)
     size_t ns_off;  // dense buffers and tables of the large-clique projection (not zeroed per solve)
     size_t ws_end;  // workspace bytes
@@ -135,6 +137,8 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     L.comp_of_entry = take(NE * 4); L.comp_of_clique = take(p * 4); L.comp_of_row = take(m * 4); L.lrow = take(m * 4);
     L.crow_ptr = take((nc + 1) * 4); L.crow_idx = take(m * 4); L.ccl_ptr = take((nc + 1) * 4); L.ccl_idx = take(p * 4);
     L.minv_off = take(nc * 8);
+    L.cent_ptr = take((nc + 1) * 4); L.cent_idx = take(NE * 4); L.hs_nb = take(nc * 8); L.hs_nc = take(nc * 8);
+    L.zhx_c = take(NE * 8); L.zhy_c = take(m * 8); L.azhx_c = take(m * 8); L.hs_zdz = take(nc * 8);
     L.const_end = o;
     L.x = take(NE * 8); L.t = take(NE * 8); L.q = take(NE * 8); L.s11 = take(NE * 8); L.atuy = take(NE * 8);
     L.y = take(m * 8); L.g = take(m * 8); L.hh = take(m * 8); L.s21 = take(m * 8); L.as11 = take(m * 8);
@@ -156,6 +160,7 @@ Layout make_layout(const HostProblem& hp, int max_iter) {
     L.rho = take(nc * 8);
     L.cg_res = take(m * 8); L.cg_p = take(m * 8); L.cg_q = take(m * 8); L.cg_u = take(NE * 8);
     L.cg_scal = take(4 * 8);
+    L.hs_tau = take(nc * 8); L.hs_kappa = take(nc * 8); L.hs_gamma = take(nc * 8);
     L.total = o;
     L.ns_off = o;
     L.ws_end = o + cdsdp_large::ns_layout(large_sizes(hp)).bytes;
@@ -211,6 +216,8 @@ void build_image(cdsdp* h) {
     put(img, L.comp_of_row, hp.comp_of_row); put(img, L.lrow, hp.lrow);
     put(img, L.crow_ptr, hp.crow_ptr); put(img, L.crow_idx, hp.crow_idx);
     put(img, L.ccl_ptr, hp.ccl_ptr); put(img, L.ccl_idx, hp.ccl_idx); put(img, L.minv_off, hp.minv_off);
+    put(img, L.cent_ptr, hp.cent_ptr); put(img, L.cent_idx, hp.cent_idx);
+    put(img, L.hs_nb, hp.comp_nb); put(img, L.hs_nc, hp.comp_nc);
 }
 
 void make_dev(cdsdp* h) {
@@ -256,6 +263,10 @@ void make_dev(cdsdp* h) {
     d.cg_res = (double*)(w + L.cg_res); d.cg_p = (double*)(w + L.cg_p); d.cg_q = (double*)(w + L.cg_q);
     d.cg_u = (double*)(w + L.cg_u); d.cg_scal = (double*)(w + L.cg_scal);
     d.cg_tol = 0.0; d.cg_max = 0;
+    d.hs_tau = (double*)(w + L.hs_tau); d.hs_kappa = (double*)(w + L.hs_kappa); d.hs_gamma = (double*)(w + L.hs_gamma);
+    d.hs_zdz = (const double*)(w + L.hs_zdz); d.hs_nb = (const double*)(w + L.hs_nb);
+    d.hs_nc = (const double*)(w + L.hs_nc);
+    d.cent_ptr = (const int*)(w + L.cent_ptr); d.cent_idx = (const int*)(w + L.cent_idx);
     auto pow2_clamp = [](double x, int lo, int hi) {
         int v = lo;
         while (v < hi && v < x) v <<= 1;
@@ -396,6 +407,7 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.kinv, d.g, d.hh, -1, h->TPRM);
         k_hsde_sigma11<<<GE, ETHREADS, 0, st>>>(d, h->Ga);
         k_hsde_sigma21<<<GR, RTHREADS, 0, st>>>(d, h->TPR, GE);
+        if (d.comp_mode) k_hsde_gamma_components<<<d.ncomp, 256, 0, st>>>(d);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (ev0) cudaEventRecord(ev0, st);
         FinishArgs none = fa;
@@ -404,6 +416,7 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         if (ev1) cudaEventRecord(ev1, st);
         k_hsde_entry_update<T><<<GE, ETHREADS, 0, st>>>(d, h->Ga);
         k_hsde_row_update<<<GR, RTHREADS, 0, st>>>(d, fa);
+        if (d.comp_mode) k_finish_hsde_components<<<d.ncomp, 256, 0, st>>>(d, fa);
     }
     return cudaGetLastError();
 }
@@ -497,9 +510,15 @@ int ensure_hsde(cdsdp* h, cudaStream_t st) {
     put(h->image, L.zhy, hp.zhat_y);
     put(h->image, L.atb, hp.atb);
     put(h->image, L.azhx, hp.a_zhat_x);
-    const size_t sections[5][2] = {{L.kinv, hp.kinv.size() * 8}, {L.zhx, hp.zhat_x.size() * 8},
+    put(h->image, L.zhx_c, hp.zhat_x_c);
+    put(h->image, L.zhy_c, hp.zhat_y_c);
+    put(h->image, L.azhx_c, hp.a_zhat_x_c);
+    put(h->image, L.hs_zdz, hp.zdz_c);
+    const size_t sections[9][2] = {{L.kinv, hp.kinv.size() * 8}, {L.zhx, hp.zhat_x.size() * 8},
                                    {L.zhy, hp.zhat_y.size() * 8}, {L.atb, hp.atb.size() * 8},
-                                   {L.azhx, hp.a_zhat_x.size() * 8}};
+                                   {L.azhx, hp.a_zhat_x.size() * 8}, {L.zhx_c, hp.zhat_x_c.size() * 8},
+                                   {L.zhy_c, hp.zhat_y_c.size() * 8}, {L.azhx_c, hp.a_zhat_x_c.size() * 8},
+                                   {L.hs_zdz, hp.zdz_c.size() * 8}};
     for (const auto& sec : sections)
         if (sec[1]) CK(cudaMemcpyAsync(h->ws + sec[0], h->image.data() + sec[0], sec[1], cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
@@ -542,9 +561,11 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
     double* tmpE = d.t;  // scratch after the solve
     double* tmpM = d.g;
     const double* tau = d.scal + SC_TAU;
+    const bool hs_comp = form == 2 && h->last_comp_mode;  // tau per component
     if (X) {
         if (form == 0) k_scale_out<<<64, 256, 0, st>>>(NE, d.x, 1.0, nullptr, tmpE);
         else if (form == 1) k_scale_rho<<<64, 256, 0, st>>>(d, NE, d.x, -1.0, 0, tmpE);
+        else if (hs_comp) k_scale_hs_tau<<<64, 256, 0, st>>>(d, NE, d.x, 0, tmpE);
         else k_scale_out<<<64, 256, 0, st>>>(NE, d.x, 1.0, tau, tmpE);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(X, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -553,6 +574,7 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
     if (y) {
         if (form == 0) k_scale_rho<<<8, 256, 0, st>>>(d, m, d.y, -1.0, 1, tmpM);
         else if (form == 1) k_scale_out<<<8, 256, 0, st>>>(m, d.y, 1.0, nullptr, tmpM);
+        else if (hs_comp) k_scale_hs_tau<<<8, 256, 0, st>>>(d, m, d.y, 1, tmpM);
         else k_scale_out<<<8, 256, 0, st>>>(m, d.y, 1.0, tau, tmpM);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(y, tmpM, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -562,7 +584,8 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
         const void* src = form == 0 ? d.ck1 : (form == 1 ? d.ck0 : d.ck1);  // lambda, z, v_z
         if (fp64) k_scatter<double><<<h->GE, ETHREADS, 0, st>>>(d, (const double*)src, nullptr, 0.0, 1.0, 0.0, 0, 0, nullptr, tmpE, 0, h->Gs);
         else k_scatter<float><<<h->GE, ETHREADS, 0, st>>>(d, (const float*)src, nullptr, 0.0, 1.0, 0.0, 0, 0, nullptr, tmpE, 0, h->Gs);
-        if (form == 2) k_scale_out<<<64, 256, 0, st>>>(NE, tmpE, 1.0, tau, tmpE);
+        if (form == 2 && hs_comp) k_scale_hs_tau<<<64, 256, 0, st>>>(d, NE, tmpE, 0, tmpE);
+        else if (form == 2) k_scale_out<<<64, 256, 0, st>>>(NE, tmpE, 1.0, tau, tmpE);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(Z, tmpE, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -572,7 +595,7 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
         CK(cudaMemcpyAsync(hist, d.hist, (size_t)h->last_iters * HIST_COLS * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
-    if (cert && form == 2) {
+    if (cert && form == 2 && !hs_comp) {
         if (h->last_status == CDSDP_PRIMAL_INFEASIBLE) {  // u_y / (b^T u_y)
             double* dots = d.scal + 8;
             k_dot<<<1, 256, 0, st>>>(m, d.y, d.b, nullptr, dots);
@@ -993,7 +1016,12 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     if (form == 2 && (rc = ensure_hsde(h, st)) != CDSDP_SOLVED) return rc;
     Dev& d = h->dev;
     d.max_iter = o.max_iter;
-    d.comp_mode = (h->hp.ncomp > 1 && form != 2 && o.component_stop && o.linear_solver == 0) ? 1 : 0;
+    d.comp_mode = (h->hp.ncomp > 1 && o.component_stop && o.linear_solver == 0) ? 1 : 0;
+    // Algorithm 3: one embedding per component in component mode, else one over the whole problem
+    const bool hs_comp = form == 2 && d.comp_mode;
+    d.zhx = (const double*)(h->ws + (hs_comp ? h->L.zhx_c : h->L.zhx));
+    d.zhy = (const double*)(h->ws + (hs_comp ? h->L.zhy_c : h->L.zhy));
+    d.azhx = (const double*)(h->ws + (hs_comp ? h->L.azhx_c : h->L.azhx));
     d.cg_tol = o.cg_tol;
     d.cg_max = o.cg_max_steps;
     h->x_split = h->ns.nb > 0 || (o.x_update == 0 ? h->x_split_auto : o.x_update == 2);

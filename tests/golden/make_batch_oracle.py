@@ -14,6 +14,7 @@ and a median one (index 254: l=91, d=18, h=15, m=348).
 
     python tests/golden/make_batch_oracle.py [--jobs N]
     python tests/golden/make_batch_oracle.py --banded   (banded_oracle.json)
+    python tests/golden/make_batch_oracle.py --hsde     (batch_hsde_oracle.json: Algorithm 3)
 """
 from __future__ import annotations
 
@@ -31,13 +32,17 @@ FORMS = ["primal", "dual"]
 
 def _solve(args):
     j, form = args
+    os.environ["OMP_NUM_THREADS"] = "1"
     sys.path.insert(0, ROOT)
     from oracle import admm
     from paper_1707_05058_gb300 import workloads as W
     prob = W.workload_batch_member(2, j)
     dp = admm.decompose(prob)
-    fn = admm.primal_admm if form == "primal" else admm.dual_admm
-    r = fn(dp, eps=1e-4, max_iter=20000, adapt_every=1)
+    if form == "hsde":
+        r = admm.hsde_admm(dp, eps=1e-4, max_iter=20000)
+    else:
+        fn = admm.primal_admm if form == "primal" else admm.dual_admm
+        r = fn(dp, eps=1e-4, max_iter=20000, adapt_every=1)
     return {"summand": j, "form": form, "n": int(prob.n), "m": int(prob.m), "iters": int(r.iters),
             "status": int(r.status), "objective": [float(v) for v in r.hist[:, 4]],
             "rho": [float(v) for v in r.hist[:, 2]]}
@@ -66,7 +71,17 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=len(SUMMANDS) * len(FORMS))
     ap.add_argument("--banded", action="store_true", help="write banded_oracle.json instead")
+    ap.add_argument("--hsde", action="store_true", help="write batch_hsde_oracle.json (Algorithm 3) instead")
     a = ap.parse_args()
+    if a.hsde:
+        with mp.get_context("spawn").Pool(len(SUMMANDS)) as pool:
+            res = pool.map(_solve, [(j, "hsde") for j in SUMMANDS])
+        doc = {"what": "oracle solves (FP64, eps 1e-4) of summands of the 256-SDP block-arrow batch, each alone, by "
+                       "Algorithm 3 of arXiv 1707.05058 (history column 4: c^T x of each iteration)",
+               "generator": "paper_1707_05058_gb300.workloads.workload_batch_member(2, index)", "results": res}
+        with open(os.path.join(os.path.dirname(OUT), "batch_hsde_oracle.json"), "w") as f:
+            json.dump(doc, f)
+        return
     if a.banded:
         with open(os.path.join(os.path.dirname(OUT), "banded_oracle.json"), "w") as f:
             json.dump(_banded(), f)

@@ -133,9 +133,41 @@ def test_direct_sum_hsde_trajectory(lib, torch_cuda):
     dp = admm.decompose(prob)
     ref = admm.hsde_admm(dp, eps=0.0, max_iter=40)
     P = lib.Problem(prob).bind(max_iter=40)
-    out = P.solve("hsde", eps=0.0, max_iter=40, precision="fp64")
+    out = P.solve("hsde", eps=0.0, max_iter=40, precision="fp64", component_stop=0)
     assert out["iters"] == 40
     np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-7, atol=1e-10)
+
+
+def _normalised(q):
+    w = np.where(q.C_row == q.C_col, 1.0, 2.0)
+    return dataclasses.replace(q, C_val=q.C_val / np.sqrt(np.sum(w * q.C_val ** 2)), b=q.b / np.linalg.norm(q.b),
+                               name=q.name + "_normalised")
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_direct_sum_hsde_per_component(lib, torch_cuda, use_graph):
+    """Algorithm 3 with one embedding per summand (component mode, the
+    default for a direct sum): each summand stops on its own test, and its
+    status, iteration count (within one) and X, y, Z equal the oracle's
+    Algorithm 3 on that summand alone (FP64; data normalised as in the
+    trajectory test above)."""
+    parts = [_normalised(q) for q in _parts()]
+    P = lib.Problem(W.direct_sum(parts)).bind(max_iter=5000)
+    out = P.solve("hsde", eps=1e-4, max_iter=5000, precision="fp64", use_graph=use_graph, check_every=11)
+    it, st, res = P.component_results()
+    r, c = P.pattern()
+    vo = mo = 0
+    for j, q in enumerate(parts):
+        dp, ref = admm.solve(q, "hsde", eps=1e-4, max_iter=5000)
+        assert st[j] == ref.status == 0, (j, st[j], ref.status)
+        assert abs(int(it[j]) - ref.iters) <= 1, (j, it[j], ref.iters)
+        mask = (c >= vo) & (c < vo + q.n)
+        _close(out["X"][mask], dp.lower_values(ref.X), 1e-6, f"X[{j}]")
+        _close(out["Z"][mask], dp.lower_values(ref.Z), 1e-6, f"Z[{j}]")
+        _close(out["y"][mo:mo + q.m], ref.y, 1e-6, f"y[{j}]")
+        vo += q.n
+        mo += q.m
+    assert out["status"] == 0 and out["iters"] == int(it.max())
 
 
 @pytest.mark.parametrize("form", ["primal", "dual"])
