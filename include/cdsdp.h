@@ -78,8 +78,9 @@ typedef struct {
                               (see cdsdp_components): 1 = each component runs its own
                               stopping test and is frozen once it holds, so its result
                               is that of a solve of the component alone; 0 = one test
-                              over the whole problem.  HSDE always uses one test (tau
-                              and kappa are shared).                                   */
+                              over the whole problem.  HSDE: 1 = one embedding (tau,
+                              kappa) and one test per component; 0 = one embedding
+                              over the whole problem.                                  */
     int adaptive_rho;      /* Algorithms 1-2: 0 = fixed rho; N > 0 = after every N-th
                               iteration whose stopping test failed, apply the adaptive
                               penalty rule of Section 7.1.2 to (eps_c, eps_lambda):
@@ -103,6 +104,13 @@ typedef struct {
                               CDSDP_ERR_UNSUPPORTED.                                  */
     double cg_tol;         /* relative residual tolerance of the CG solve (>= 0)       */
     int cg_max_steps;      /* CG steps per ADMM iteration (0..1024)                    */
+    int proj_streams;      /* with component_stop on a problem with independent
+                              components: the projection launches of the size classes
+                              (and the step of the cliques above order 128) run on this
+                              many streams forked from `stream` and joined before the
+                              stopping tests, largest work first, so that one class's
+                              tail overlaps the next class (1..4; 1 = one after the
+                              other on `stream`).  No effect otherwise.  Default 4.   */
 } cdsdp_opts;
 
 typedef struct {
@@ -386,8 +394,9 @@ int cdsdp_fma_peak(int precision, int iters, void* stream, double* tflops);
  *   x_update        1 or 2 (Algorithm 1 only)
  *   proj_warps_div  1, 2 or 4
  *   warm_start      16 or 64 (only when opts->warm_start > 0)
+ *   proj_streams    4 or 1
  * ms_per_iter[] receives each candidate's device time per iteration in
- * candidate order (at most 12 entries; may be NULL), *n_cand their number (may
+ * candidate order (at most 24 entries; may be NULL), *n_cand their number (may
  * be NULL).  Overwrites the last solve's state.  Errors as cdsdp_solve. */
 int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* stream, cdsdp_opts* tuned,
                    double* ms_per_iter, int* n_cand);

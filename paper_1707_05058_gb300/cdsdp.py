@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
                 ("jacobi_max_sweeps", ctypes.c_int), ("warm_start", ctypes.c_int), ("profile", ctypes.c_int),
                 ("component_stop", ctypes.c_int), ("adaptive_rho", ctypes.c_int), ("rho_mu", ctypes.c_double),
                 ("rho_nu", ctypes.c_double), ("x_update", ctypes.c_int), ("proj_warps_div", ctypes.c_int),
-                ("linear_solver", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_max_steps", ctypes.c_int)]
+                ("linear_solver", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_max_steps", ctypes.c_int),
+                ("proj_streams", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -398,13 +399,14 @@ class Problem:
         if self.workspace is None or self.max_iter < iters:
             self.bind(max(iters, self.max_iter or 0))
         tuned = Opts()
-        ms = np.zeros(12)
+        ms = np.zeros(24)
         n = ctypes.c_int(0)
         st = _lib.cdsdp_autotune(self._h, FORMS.get(form, form), ctypes.byref(o), int(iters), _stream_ptr(stream),
                                  ctypes.byref(tuned), _ptr(ms, ctypes.c_double), ctypes.byref(n))
         if st < 0:
             raise CdsdpError(st, "cdsdp_autotune")
-        return ({"x_update": tuned.x_update, "proj_warps_div": tuned.proj_warps_div, "warm_start": tuned.warm_start},
+        return ({"x_update": tuned.x_update, "proj_warps_div": tuned.proj_warps_div, "warm_start": tuned.warm_start,
+                 "proj_streams": tuned.proj_streams},
                 ms[:n.value].tolist())
 
     def profile(self):

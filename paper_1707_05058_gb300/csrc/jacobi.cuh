@@ -72,18 +72,20 @@ __device__ __forceinline__ int packed_ab(int f, int s) {
     return (a << 8) | b;
 }
 
-template <typename T, int S>
+template <typename T, int S, int LW = 32>
 struct BLJacobi {
+    static_assert(LW == 32 || LW == 16 || LW == 8, "lanes per clique");
+    static_assert(LW == 32 || S <= LW, "row `lane` of V needs a lane per row");
     using RR = RoundRobin<S>;
     static constexpr int K = S / 2;
     static constexpr int R = S - 1;
     static constexpr int LDA = S + 1;
     static constexpr int BUF = S * LDA;
     static constexpr int NB = K * (K + 1) / 2;      // lower pair-blocks
-    static constexpr int NS = (NB + 31) / 32;       // blocks per lane
+    static constexpr int NS = (NB + LW - 1) / LW;   // blocks per lane
     static constexpr int NPK = S * (S + 1) / 2;
-    static constexpr int MAXE = (NPK + 31) / 32;    // packed elements per lane
-    static constexpr size_t bytes = (2 * BUF * sizeof(T) + 15) & ~size_t(15);  // per warp
+    static constexpr int MAXE = (NPK + LW - 1) / LW;  // packed elements per lane
+    static constexpr size_t bytes = (2 * BUF * sizeof(T) + 15) & ~size_t(15);  // per clique
 
     T* X;  // current buffer
     T* Y;  // next buffer
@@ -96,7 +98,7 @@ struct BLJacobi {
         Y = X + BUF;
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
-            const int b = lane + 32 * t;
+            const int b = lane + LW * t;
             int I = 0, J = 0;
             if (b < K) {
                 I = J = b;
@@ -125,7 +127,7 @@ struct BLJacobi {
 
     // Zero the working buffer (padding rows must read as exact zeros).
     __device__ __forceinline__ void clear(int lane) {
-        for (int i = lane; i < BUF; i += 32) X[i] = T(0);
+        for (int i = lane; i < BUF; i += LW) X[i] = T(0);
         __syncwarp();
     }
     __device__ __forceinline__ void put(int a, int b, T w) {
@@ -147,7 +149,7 @@ struct BLJacobi {
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        for (int o = LW / 2; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));  // within the group
         return m;
     }
 
@@ -156,7 +158,7 @@ struct BLJacobi {
     // sweeps continue from the basis V (the final eigenvectors are V J_1 J_2 ...).
     // Both products are spread element-wise over the 32 lanes; Y is scratch.
     __device__ void rotate_into_basis(int lane) {
-        constexpr int NE1 = (S * S + 31) / 32;
+        constexpr int NE1 = (S * S + LW - 1) / LW;
         if (lane < S) {
 #pragma unroll
             for (int j = 0; j < S; ++j) Y[lane * LDA + j] = v[j];
@@ -165,7 +167,7 @@ struct BLJacobi {
         T acc[NE1];
 #pragma unroll
         for (int e = 0; e < NE1; ++e) {  // (W V)_{rj}
-            const int idx = lane + 32 * e;
+            const int idx = lane + LW * e;
             T a = T(0);
             if (idx < S * S) {
                 const int r = idx / S, j = idx - r * S;
@@ -178,7 +180,7 @@ struct BLJacobi {
         __syncwarp();
 #pragma unroll
         for (int e = 0; e < NE1; ++e) {
-            const int idx = lane + 32 * e;
+            const int idx = lane + LW * e;
             if (idx < S * S) {
                 const int r = idx / S, j = idx - r * S;
                 X[r * LDA + j] = acc[e];
@@ -187,7 +189,7 @@ struct BLJacobi {
         __syncwarp();
 #pragma unroll
         for (int e = 0; e < NE1; ++e) {  // (V^T (W V))_{ij}
-            const int idx = lane + 32 * e;
+            const int idx = lane + LW * e;
             T a = T(0);
             if (idx < S * S) {
                 const int i = idx / S, j = idx - i * S;
@@ -199,7 +201,7 @@ struct BLJacobi {
         __syncwarp();
 #pragma unroll
         for (int e = 0; e < NE1; ++e) {
-            const int idx = lane + 32 * e;
+            const int idx = lane + LW * e;
             if (idx < S * S) {
                 const int i = idx / S, j = idx - i * S;
                 X[i * LDA + j] = acc[e];
@@ -210,7 +212,7 @@ struct BLJacobi {
 
     // X <- V X V^T (inverse of rotate_into_basis; X symmetric, both triangles).
     __device__ void rotate_out_of_basis(int lane) {
-        constexpr int NE1 = (S * S + 31) / 32;
+        constexpr int NE1 = (S * S + LW - 1) / LW;
         if (lane < S) {
 #pragma unroll
             for (int j = 0; j < S; ++j) Y[lane * LDA + j] = v[j];
@@ -219,7 +221,7 @@ struct BLJacobi {
         T acc[NE1];
 #pragma unroll
         for (int e = 0; e < NE1; ++e) {  // (X V^T)_{ib} = sum_j X_ij V_bj
-            const int idx = lane + 32 * e;
+            const int idx = lane + LW * e;
             T a = T(0);
             if (idx < S * S) {
                 const int i = idx / S, b = idx - i * S;
@@ -231,13 +233,13 @@ struct BLJacobi {
         __syncwarp();
 #pragma unroll
         for (int e = 0; e < NE1; ++e) {
-            const int idx = lane + 32 * e;
+            const int idx = lane + LW * e;
             if (idx < S * S) X[(idx / S) * LDA + idx % S] = acc[e];
         }
         __syncwarp();
 #pragma unroll
         for (int e = 0; e < NE1; ++e) {  // (V (X V^T))_{ab} = sum_i V_ai (X V^T)_ib
-            const int idx = lane + 32 * e;
+            const int idx = lane + LW * e;
             T a = T(0);
             if (idx < S * S) {
                 const int ar = idx / S, b = idx - ar * S;
@@ -249,7 +251,7 @@ struct BLJacobi {
         __syncwarp();
 #pragma unroll
         for (int e = 0; e < NE1; ++e) {
-            const int idx = lane + 32 * e;
+            const int idx = lane + LW * e;
             if (idx < S * S) X[(idx / S) * LDA + idx % S] = acc[e];
         }
         __syncwarp();
@@ -305,8 +307,8 @@ struct BLJacobi {
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
             const int I = bI[t] >= 0 ? bI[t] : 0, J = bJ[t];
-            const T sI = __shfl_sync(0xffffffffu, sn, I), uI = __shfl_sync(0xffffffffu, tau, I);
-            const T sJ = __shfl_sync(0xffffffffu, sn, J), uJ = __shfl_sync(0xffffffffu, tau, J);
+            const T sI = __shfl_sync(0xffffffffu, sn, I, LW), uI = __shfl_sync(0xffffffffu, tau, I, LW);
+            const T sJ = __shfl_sync(0xffffffffu, sn, J, LW), uJ = __shfl_sync(0xffffffffu, tau, J, LW);
             if (bI[t] < 0) continue;
             if (t == 0 && lane < K) {  // diagonal block: the 2x2 Schur result
                 Y[dst[t][0]] = bv[t][0] - ta;
@@ -326,7 +328,7 @@ struct BLJacobi {
         // V <- V J on this lane's row, then re-index its columns by sigma like A
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const T sk = __shfl_sync(0xffffffffu, sn, k), uk = __shfl_sync(0xffffffffu, tau, k);
+            const T sk = __shfl_sync(0xffffffffu, sn, k, LW), uk = __shfl_sync(0xffffffffu, tau, k, LW);
             const T vp = vin[2 * k], vq = vin[2 * k + 1];
             vout[RR::sigma(2 * k)] = vp - sk * (vq + uk * vp);
             vout[RR::sigma(2 * k + 1)] = vq + sk * (vp - uk * vq);
@@ -340,7 +342,14 @@ struct BLJacobi {
     // v_preset the sweeps start from the basis already in v (see
     // rotate_into_basis); otherwise from the identity.  A sweep runs only while
     // some off-diagonal entry exceeds tol.
-    __device__ int run(T tol, int max_sweeps, int lane, bool v_preset = false) {
+    //
+    // With LW < 32 the warp serves 32 / LW cliques, one per group of LW lanes;
+    // the sweep loop runs while any group still sweeps, and a group that has
+    // stopped (or is inactive) goes through the remaining rounds with every
+    // rotation skipped (threshold +inf): its storage order returns to the
+    // identity after each sweep and its matrix and V stay as they were, so each
+    // clique's result is the one it gets alone.
+    __device__ int run(T tol, int max_sweeps, int lane, bool v_preset = false, bool active = true) {
         const T noise = tol * T(2 * S);  // 4 S u ||W||_F when tol = 2 u ||W||_F
         if (!v_preset) {
 #pragma unroll
@@ -350,19 +359,22 @@ struct BLJacobi {
         int sw = 0;
         T w[S];
         T prev = T(3.0e38);
-        while (sw < max_sweeps) {
+        bool go = active;
+        while (true) {
             const T off = off_max(lane);
-            if (off <= tol) break;
-            if (off <= noise && off > T(0.5) * prev) break;  // stagnated at the rounding-noise level
+            if (go && (sw >= max_sweeps || off <= tol || (off <= noise && off > T(0.5) * prev)))
+                go = false;  // converged, or stagnated at the rounding-noise level
+            if (!__any_sync(0xffffffffu, go)) break;
             prev = off;
-            ++sw;
+            if (go) ++sw;
+            const T t_eff = go ? tol : T(INFINITY);
             // rounds in pairs, V ping-ponging between v and w (R = S - 1 is odd)
 #pragma unroll 1
             for (int r = 0; r + 1 < R; r += 2) {
-                round(tol, lane, v, w);
-                round(tol, lane, w, v);
+                round(t_eff, lane, v, w);
+                round(t_eff, lane, w, v);
             }
-            round(tol, lane, v, w);
+            round(t_eff, lane, v, w);
 #pragma unroll
             for (int j = 0; j < S; ++j) v[j] = w[j];
         }
@@ -414,30 +426,35 @@ struct BLJacobi {
 template <typename T, int S>
 __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_project_primal(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
                                                          FinishArgs fa) {
-    using J = BLJacobi<T, S>;
+    constexpr int LW = proj_lanes(S), G = 32 / LW;  // lanes per clique, cliques per warp
+    using J = BLJacobi<T, S, LW>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int lane = (threadIdx.x & 31) % LW, grp = (threadIdx.x & 31) / LW;  // lane within its group
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     J jac;
-    jac.bind(smem + warp * J::bytes, lane);
+    jac.bind(smem + (warp * G + grp) * J::bytes, lane);
     T* xk = reinterpret_cast<T*>(d.ck0);
     T* lam = reinterpret_cast<T*>(d.ck1);
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
-        const int k = list[li];
-        if (frozen_clique(d, k)) continue;  // warp-uniform
+    for (int li0 = (blockIdx.x * wpb + warp) * G; li0 < nlist; li0 += gridDim.x * wpb * G) {
+        // group grp takes clique li0 + grp; a group past the list or on a
+        // frozen clique is inactive: it touches no state and skips every rotation
+        const int li = li0 + grp;
+        const int k = list[li < nlist ? li : li0];
+        const bool active = li < nlist && !frozen_clique(d, k);
         const double rho = rho_clique(d, k);
         const T rho_t = T(rho), irho = T(1.0 / rho);
-        const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
+        const int s = active ? d.csize[k] : 0, off = d.pk_off[k], npk = s * (s + 1) / 2;
         jac.clear(lane);
         T nrm = T(0);
         T hx[J::MAXE];
         double cx = 0.0;
 #pragma unroll
         for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
+            const int f = lane + LW * e;
             hx[e] = T(0);
             if (f < npk) {
                 const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
@@ -466,14 +483,14 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
                 nrm += (a == b ? T(1) : T(2)) * w * w;
             }
         }
-        nrm = warp_sum(nrm);
-        const double cxk = warp_sum(cx);
+        nrm = group_sum(nrm, LW);
+        const double cxk = group_sum(cx, LW);
         __syncwarp();
         if (warm) {
             jac.load_basis(vc + d.vv_off[k], s, lane);
             jac.rotate_into_basis(lane);
         }
-        jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm);
+        jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm, active);
         if (pa.warm_start) jac.store_basis(vc + d.vv_off[k], s, lane);
         jac.prepare_rebuild(lane);
         // per-clique sums of the stopping test in the clique state's precision
@@ -481,7 +498,7 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
         T p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0;
 #pragma unroll
         for (int e = 0; e < J::MAXE; ++e) {
-            const int f = lane + 32 * e;
+            const int f = lane + LW * e;
             if (f < npk) {
                 const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
                 const T lm = lam[off + f];
@@ -499,10 +516,10 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
                 p4 += w * ln * ln;
             }
         }
-        const double q[6] = {double(warp_sum(p0)), double(warp_sum(p1)), double(warp_sum(p2)),
-                             double(warp_sum(p3)), double(warp_sum(p4)), cxk};
+        const double q[6] = {double(group_sum(p0, LW)), double(group_sum(p1, LW)), double(group_sum(p2, LW)),
+                             double(group_sum(p3, LW)), double(group_sum(p4, LW)), cxk};
         if (d.comp_mode) {  // per-clique row, reduced per component
-            if (lane == 0)
+            if (lane == 0 && active)
 #pragma unroll
                 for (int c = 0; c < 6; ++c) d.part[(size_t)k * PART_COLS + c] = q[c];
         } else {
@@ -512,6 +529,9 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
         __syncwarp();
     }
     if (d.comp_mode) return;
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+        for (int o = LW; o < 32; o <<= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);  // over the groups
     const int cols[6] = {0, 1, 2, 3, 4, 5};
     block_partial_row<6>(acc, d.part, pa.row_off + blockIdx.x, cols);
     if (fa.enabled && last_block_single_writer(d)) finish_primal_block(d, fa);
@@ -521,57 +541,63 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
 // part[k][5] = |z_k - z_k_old|^2 (for eps_lambda).
 template <typename T, int S>
 __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_project_dual(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa) {
-    using J = BLJacobi<T, S>;
+    constexpr int LW = proj_lanes(S), G = 32 / LW;  // lanes per clique, cliques per warp
+    using J = BLJacobi<T, S, LW>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int lane = (threadIdx.x & 31) % LW, grp = (threadIdx.x & 31) / LW;  // lane within its group
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     J jac;
-    jac.bind(smem + warp * J::bytes, lane);
+    jac.bind(smem + (warp * G + grp) * J::bytes, lane);
     T* z = reinterpret_cast<T*>(d.ck0);
     const T* v = reinterpret_cast<const T*>(d.ck1);
     const T* lam = reinterpret_cast<const T*>(d.ck2);
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     double acc[1] = {0};
-    for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
-        const int k = list[li];
-        if (frozen_clique(d, k)) continue;  // warp-uniform
+    for (int li0 = (blockIdx.x * wpb + warp) * G; li0 < nlist; li0 += gridDim.x * wpb * G) {
+        // group grp takes clique li0 + grp; a group past the list or on a
+        // frozen clique is inactive: it touches no state and skips every rotation
+        const int li = li0 + grp;
+        const int k = list[li < nlist ? li : li0];
+        const bool active = li < nlist && !frozen_clique(d, k);
         const T irho = T(1.0 / rho_clique(d, k));
-        const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
+        const int s = active ? d.csize[k] : 0, off = d.pk_off[k], npk = s * (s + 1) / 2;
         jac.clear(lane);
         T nrm = T(0);
-        for (int f = lane; f < npk; f += 32) {
+        for (int f = lane; f < npk; f += LW) {
             const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
             const T w = v[off + f] - lam[off + f] * irho;
             jac.put(a, b, w);
             nrm += (a == b ? T(1) : T(2)) * w * w;
         }
-        nrm = warp_sum(nrm);
+        nrm = group_sum(nrm, LW);
         __syncwarp();
         if (warm) {
             jac.load_basis(vc + d.vv_off[k], s, lane);
             jac.rotate_into_basis(lane);
         }
-        jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm);
+        jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm, active);
         if (pa.warm_start) jac.store_basis(vc + d.vv_off[k], s, lane);
         jac.prepare_rebuild(lane);
         T p0 = 0;  // in the clique state's precision; float64 across cliques
-        for (int f = lane; f < npk; f += 32) {
+        for (int f = lane; f < npk; f += LW) {
             const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
             const T zn = jac.rebuild(a, b, s);
             const T dz = zn - z[off + f];
             z[off + f] = zn;
             p0 += (a == b ? T(1) : T(2)) * dz * dz;
         }
-        const double q0 = double(warp_sum(p0));
+        const double q0 = double(group_sum(p0, LW));
         if (d.comp_mode) {
-            if (lane == 0) d.part[(size_t)k * PART_COLS + 5] = q0;
+            if (lane == 0 && active) d.part[(size_t)k * PART_COLS + 5] = q0;
         } else {
             acc[0] += q0;
         }
         __syncwarp();
     }
     if (d.comp_mode) return;
+    for (int o = LW; o < 32; o <<= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);  // over the groups
     const int cols[1] = {5};
     block_partial_row<1>(acc, d.part, pa.row_off + blockIdx.x, cols);
 }
@@ -588,26 +614,31 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
 // |v_z|^2, |u_t|^2, where u_x = sigma_11 - gamma zeta_hat_x.
 template <typename T, int S>
 __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_project_hsde(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa) {
-    using J = BLJacobi<T, S>;
+    constexpr int LW = proj_lanes(S), G = 32 / LW;  // lanes per clique, cliques per warp
+    using J = BLJacobi<T, S, LW>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (stopped(d)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int lane = (threadIdx.x & 31) % LW, grp = (threadIdx.x & 31) / LW;  // lane within its group
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     J jac;
-    jac.bind(smem + warp * J::bytes, lane);
+    jac.bind(smem + (warp * G + grp) * J::bytes, lane);
     T* us = reinterpret_cast<T*>(d.ck0);
     T* vz = reinterpret_cast<T*>(d.ck1);
     T* ut = reinterpret_cast<T*>(d.ck2);
     T* vc = reinterpret_cast<T*>(d.vcache);
     const bool warm = pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int li = blockIdx.x * wpb + warp; li < nlist; li += gridDim.x * wpb) {
-        const int k = list[li];
-        if (frozen_clique(d, k)) continue;  // warp-uniform
+    for (int li0 = (blockIdx.x * wpb + warp) * G; li0 < nlist; li0 += gridDim.x * wpb * G) {
+        // group grp takes clique li0 + grp; a group past the list or on a
+        // frozen clique is inactive: it touches no state and skips every rotation
+        const int li = li0 + grp;
+        const int k = list[li < nlist ? li : li0];
+        const bool active = li < nlist && !frozen_clique(d, k);
         const double gamma = hs_gamma_c(d, comp_k(d, k));
-        const int s = d.csize[k], off = d.pk_off[k], npk = s * (s + 1) / 2;
+        const int s = active ? d.csize[k] : 0, off = d.pk_off[k], npk = s * (s + 1) / 2;
         jac.clear(lane);
         T nrm = T(0);
-        for (int f = lane; f < npk; f += 32) {
+        for (int f = lane; f < npk; f += LW) {
             const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
             const int ent = d.gmap[off + f];
             const double hs = d.s11[ent];
@@ -619,17 +650,17 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
             jac.put(a, b, w);
             nrm += (a == b ? T(1) : T(2)) * w * w;
         }
-        nrm = warp_sum(nrm);
+        nrm = group_sum(nrm, LW);
         __syncwarp();
         if (warm) {
             jac.load_basis(vc + d.vv_off[k], s, lane);
             jac.rotate_into_basis(lane);
         }
-        jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm);
+        jac.run(T(pa.tolrel) * sqrt(nrm), pa.max_sweeps, lane, warm, active);
         if (pa.warm_start) jac.store_basis(vc + d.vv_off[k], s, lane);
         jac.prepare_rebuild(lane);
         double p[6] = {0, 0, 0, 0, 0, 0};
-        for (int f = lane; f < npk; f += 32) {
+        for (int f = lane; f < npk; f += LW) {
             const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
             const int ent = d.gmap[off + f];
             const double hs = d.s11[ent];
@@ -657,9 +688,9 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
         }
         double q[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) q[c] = warp_sum(p[c]);
+        for (int c = 0; c < 6; ++c) q[c] = group_sum(p[c], LW);
         if (d.comp_mode) {  // per-clique row, reduced per component
-            if (lane == 0)
+            if (lane == 0 && active)
 #pragma unroll
                 for (int c = 0; c < 6; ++c) d.part[(size_t)k * PART_COLS + c] = q[c];
         } else {
@@ -669,6 +700,9 @@ __global__ void __launch_bounds__(32 * proj_max_warps(S, sizeof(T) == 4)) k_proj
         __syncwarp();
     }
     if (d.comp_mode) return;
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+        for (int o = LW; o < 32; o <<= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);  // over the groups
     const int cols[6] = {0, 1, 2, 3, 4, 5};
     block_partial_row<6>(acc, d.part, pa.row_off + blockIdx.x, cols);
 }

@@ -13,9 +13,11 @@ cudaError_t launch_form(int form, const Dev& d, const int* list, int nlist, cons
                         const FinishArgs& fa, cudaStream_t st) {
     if (nlist <= 0) return cudaSuccess;
     constexpr int MW = proj_max_warps(S, sizeof(T) == 4);
-    const ProjShape sh = proj_shape(nlist, std::max(1, MW / std::max(1, pa_in.warps_div)));
-    const size_t smem = (size_t)sh.wpb * BLJacobi<T, S>::bytes;
-    const size_t smem_max = (size_t)MW * BLJacobi<T, S>::bytes;
+    constexpr int LW = proj_lanes(S), G = 32 / LW;  // G cliques per warp
+    using J = BLJacobi<T, S, LW>;
+    const ProjShape sh = proj_shape((nlist + G - 1) / G, std::max(1, MW / std::max(1, pa_in.warps_div)));
+    const size_t smem = (size_t)sh.wpb * G * J::bytes;
+    const size_t smem_max = (size_t)MW * G * J::bytes;
     ProjArgs pa = pa_in;
     pa.tolrel = jacobi_tolrel(S, sizeof(T) == 4);
     static bool attr_done[3] = {false, false, false};  // per instantiation; setting twice is harmless

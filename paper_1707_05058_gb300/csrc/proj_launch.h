@@ -17,6 +17,10 @@ constexpr int kNumProjClasses = 22;
 constexpr int kMaxWarpOrder = 32;
 constexpr int kMaxOrderF32 = 128;
 constexpr int kMaxOrderF64 = 64;
+// Lanes per clique of the warp projections: orders up to 8 share a warp four
+// ways, up to 16 two ways (every lane then owns pair-blocks and a row of V),
+// larger orders take the whole warp.
+__host__ __device__ constexpr int proj_lanes(int S) { return S <= 8 ? 8 : (S <= 16 ? 16 : 32); }
 // Warps per block allowed for a projection kernel of padded order S
 // (registers: 16 warps only while a thread needs <= 128 registers).
 __host__ __device__ constexpr int proj_max_warps(int S, bool fp32) { return S <= 16 ? 16 : (fp32 ? 8 : 4); }
@@ -110,7 +114,8 @@ inline cudaError_t launch_proj_f64(int form, int cls, const Dev& d, const int* l
 inline int proj_launch_grid(int cls, int nlist, bool fp32, int warps_div = 1) {
     const int S = kProjClasses[cls];
     if (S > kMaxWarpOrder) return proj_cta_grid(nlist);
-    return proj_shape(nlist, std::max(1, proj_max_warps(S, fp32) / std::max(1, warps_div))).grid;
+    const int G = 32 / proj_lanes(S);
+    return proj_shape((nlist + G - 1) / G, std::max(1, proj_max_warps(S, fp32) / std::max(1, warps_div))).grid;
 }
 inline cudaError_t launch_proj_standalone_f32(int cls, int p, const int* off, const int* size, const void* W, void* X,
                                               void* eig, const int* voff, void* V, const int* vvoff, double tolrel,

@@ -13,6 +13,10 @@ __device__ __forceinline__ double group_sum(double v, int G) {
     for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ float group_sum(float v, int G) {
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // Reduction over a row group of TPR threads (TPR a multiple of 32, the group
 // is TPR/32 consecutive warps of the block); result valid in the group's

@@ -91,6 +91,12 @@ struct cdsdp {
     cdsdp_large::NsLayout ns;
     double prof_large_ms = 0.0;
     int prof_large_n = 0;
+    // concurrent size classes (opts.proj_streams): side streams forked from
+    // the solve's stream, classes in decreasing order of work (sum of s^3)
+    cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int cls_order[kNumClasses] = {0};
 };
 
 namespace {
@@ -311,22 +317,55 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
     pa.row_off = 0;
     pa.warps_div = o.proj_warps_div;
     pa.x_ready = (form == 0 && h->x_split) ? 1 : 0;
-    for (int c = 0; c < kNumClasses && e == cudaSuccess; ++c) {
+    // first partial-table row of each class (class order), then the launches
+    int row0[kNumClasses + 1];
+    for (int c = 0; c < kNumClasses; ++c) {
+        const int nl = h->cls_off[c + 1] - h->cls_off[c];
+        row0[c] = pa.row_off;
+        if (nl > 0) pa.row_off += proj_launch_grid(c, nl, sizeof(T) == 4, pa.warps_div);
+    }
+    row0[kNumClasses] = pa.row_off;
+    // Concurrent classes need stopping tests that run after all of them (the
+    // component mode's own kernel): fork side streams, join them at the end.
+    int ns = 1;
+    if (h->dev.comp_mode && o.proj_streams > 1 && h->side[0]) {
+        int work = large ? 1 : 0;
+        for (int c = 0; c < kNumClasses; ++c) work += h->cls_off[c + 1] > h->cls_off[c] ? 1 : 0;
+        ns = std::min(std::min(o.proj_streams, 4), work);
+    }
+    if (ns > 1) {
+        if ((e = cudaEventRecord(h->fork_ev, st)) != cudaSuccess) return e;
+        for (int i = 0; i < ns; ++i)
+            if ((e = cudaStreamWaitEvent(h->side[i], h->fork_ev, 0)) != cudaSuccess) return e;
+    }
+    int q = 0;
+    for (int i = 0; i < kNumClasses && e == cudaSuccess; ++i) {
+        const int c = ns > 1 ? h->cls_order[i] : i;
         const int* list = bl + h->cls_off[c];
         const int nl = h->cls_off[c + 1] - h->cls_off[c];
         if (nl <= 0) continue;
+        cudaStream_t sc = ns > 1 ? h->side[q++ % ns] : st;
         FinishArgs f = fa;
         f.enabled = (c == last) ? fa.enabled : 0;  // the last launch finishes the iteration
-        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * c], st);
-        e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, pa, f, st)
-                           : launch_proj_f64(form, c, h->dev, list, nl, pa, f, st);
-        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * c + 1], st);
-        pa.row_off += proj_launch_grid(c, nl, sizeof(T) == 4, pa.warps_div);  // rows of this launch
+        ProjArgs pc = pa;
+        pc.row_off = row0[c];
+        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * c], sc);
+        e = sizeof(T) == 4 ? launch_proj_f32(form, c, h->dev, list, nl, pc, f, sc)
+                           : launch_proj_f64(form, c, h->dev, list, nl, pc, f, sc);
+        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * c + 1], sc);
     }
     if (large && e == cudaSuccess) {  // float clique state only (FP64 refuses these orders)
-        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * kNumClasses], st);
-        e = cdsdp_large::large_step(form, h->dev, h->ns, h->ws + h->L.ns_off, pa.row_off, fa, st);
-        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * kNumClasses + 1], st);
+        cudaStream_t sc = ns > 1 ? h->side[q++ % ns] : st;
+        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * kNumClasses], sc);
+        e = cdsdp_large::large_step(form, h->dev, h->ns, h->ws + h->L.ns_off, row0[kNumClasses], fa, sc);
+        if (h->cls_ev) cudaEventRecord(h->cls_ev[2 * kNumClasses + 1], sc);
+    }
+    if (ns > 1) {
+        for (int i = 0; i < ns; ++i) {
+            const cudaError_t e2 = cudaEventRecord(h->join_ev[i], h->side[i]);
+            const cudaError_t e3 = cudaStreamWaitEvent(st, h->join_ev[i], 0);
+            if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+        }
     }
     return e;
 }
@@ -433,7 +472,8 @@ bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
            a.jacobi_max_sweeps == b.jacobi_max_sweeps && a.warm_start == b.warm_start &&
            a.component_stop == b.component_stop && a.adaptive_rho == b.adaptive_rho && a.rho_mu == b.rho_mu &&
            a.rho_nu == b.rho_nu && a.x_update == b.x_update && a.proj_warps_div == b.proj_warps_div &&
-           a.linear_solver == b.linear_solver && a.cg_tol == b.cg_tol && a.cg_max_steps == b.cg_max_steps;
+           a.linear_solver == b.linear_solver && a.cg_tol == b.cg_tol && a.cg_max_steps == b.cg_max_steps &&
+           a.proj_streams == b.proj_streams;
 }
 
 void drop_graph(cdsdp* h) {
@@ -488,6 +528,7 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     if (o.linear_solver != 0 && o.linear_solver != 1) return CDSDP_ERR_ARG;
     if (!(o.cg_tol >= 0.0) || !std::isfinite(o.cg_tol) || o.cg_max_steps < 0 || o.cg_max_steps > 1024)
         return CDSDP_ERR_ARG;
+    if (o.proj_streams < 1 || o.proj_streams > 4) return CDSDP_ERR_ARG;
     if (o.precision == CDSDP_FP64 && h->hp.max_clique > kMaxOrderF64) return CDSDP_ERR_UNSUPPORTED;
     return CDSDP_SOLVED;
 }
@@ -699,6 +740,7 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->linear_solver = 0;
     o->cg_tol = 1e-10;
     o->cg_max_steps = 5;
+    o->proj_streams = 4;
 }
 
 namespace {
@@ -984,6 +1026,23 @@ int cdsdp_bind(cdsdp* h, void* d_workspace, size_t bytes, int max_iter, void* st
             list.push_back((int)k);
             poff.push_back(h->hp.pk_off[k]);
         }
+    {
+        double work[kNumClasses] = {0};
+        for (size_t k = 0; k + 1 < h->hp.cl_off.size(); ++k) {
+            const double sk = h->hp.cl_off[k + 1] - h->hp.cl_off[k];
+            const int c = class_of((int)sk);
+            if (c >= 0) work[c] += sk * sk * sk;
+        }
+        for (int c = 0; c < kNumClasses; ++c) h->cls_order[c] = c;
+        std::stable_sort(h->cls_order, h->cls_order + kNumClasses, [&](int a, int b) { return work[a] > work[b]; });
+        if (!h->side[0] && h->hp.ncomp > 1) {
+            for (int i = 0; i < 4; ++i) {
+                CK(cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming));
+            }
+            CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+        }
+    }
     h->ns = cdsdp_large::ns_layout(large_sizes(h->hp));
     if (h->ns.nb > 0) {
         std::vector<unsigned char> img;
@@ -1159,16 +1218,18 @@ int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* 
     // candidate schedules: x-update placement (Algorithm 1), warps per block of
     // the warp-per-clique projections, cold-restart interval of the eigensolver
     std::vector<cdsdp_opts> cand;
-    const int xs[2] = {2, 1}, wd[3] = {1, 2, 4}, rs[2] = {16, 64};
+    const int xs[2] = {2, 1}, wd[3] = {1, 2, 4}, rs[2] = {16, 64}, ps[2] = {4, 1};
     for (int xi = 0; xi < (form == 0 ? 2 : 1); ++xi)
         for (int wi = 0; wi < 3; ++wi)
-            for (int ri = 0; ri < (base.warm_start > 0 ? 2 : 1); ++ri) {
-                cdsdp_opts o = base;
-                o.x_update = xs[xi];
-                o.proj_warps_div = wd[wi];
-                if (base.warm_start > 0) o.warm_start = rs[ri];
-                cand.push_back(o);
-            }
+            for (int ri = 0; ri < (base.warm_start > 0 ? 2 : 1); ++ri)
+                for (int pi = 0; pi < 2; ++pi) {
+                    cdsdp_opts o = base;
+                    o.x_update = xs[xi];
+                    o.proj_warps_div = wd[wi];
+                    if (base.warm_start > 0) o.warm_start = rs[ri];
+                    o.proj_streams = ps[pi];
+                    cand.push_back(o);
+                }
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -1197,6 +1258,7 @@ int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* 
     tuned->x_update = cand[ibest].x_update;
     tuned->proj_warps_div = cand[ibest].proj_warps_div;
     tuned->warm_start = cand[ibest].warm_start;
+    tuned->proj_streams = cand[ibest].proj_streams;
     if (n_cand) *n_cand = (int)cand.size();
     return CDSDP_SOLVED;
 }
@@ -1256,6 +1318,11 @@ int cdsdp_free(cdsdp* h) {
     cdsdp_impl::completion_release(h->cmp_graph);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : h->cls_evs) cudaEventDestroy(e);
+    for (int i = 0; i < 4; ++i) {
+        if (h->side[i]) cudaStreamDestroy(h->side[i]);
+        if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     delete h;
     return CDSDP_SOLVED;
 }

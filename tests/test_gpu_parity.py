@@ -436,7 +436,8 @@ def test_autotune_picks_a_candidate_and_keeps_parity(lib, torch_cuda, form):
     dp, ref = _oracle(prob, form, 1e-4, 2000)
     P = lib.Problem(prob).bind(max_iter=2000)
     tuned, ms = P.autotune(form, iters=20, precision="fp64")
-    assert len(ms) == (12 if form == "primal" else 6) and all(m > 0 for m in ms)
+    assert len(ms) == (24 if form == "primal" else 12) and all(m > 0 for m in ms)
     assert tuned["x_update"] in (1, 2) and tuned["proj_warps_div"] in (1, 2, 4) and tuned["warm_start"] in (16, 64)
+    assert tuned["proj_streams"] in (1, 4)
     out = P.solve(form, eps=1e-4, max_iter=2000, precision="fp64", **tuned)
     _assert_trajectory(dp, ref, out)
