@@ -27,9 +27,11 @@ reductions).
   parity    objective gap of the timed solve's SDPs against stored oracle
             solves of three summands (tests/golden/batch_oracle.json)
   roofline  the projection size class with the largest device time (FP32 ALU
-            bound): nominal 10 s^3 flops per clique / its launch duration from
-            CUDA events in a profiled solve, against the FMA peak measured by
-            cdsdp_fma_peak on this GPU
+            bound): nominal 10 s^3 flops per clique / its mean launch duration
+            from CUDA events over a profiled 200-iteration solve from the cold
+            start (every SDP active, size classes launched one after the other
+            so that each launch is timed alone), against the FMA peak measured
+            by cdsdp_fma_peak on this GPU
   banded    the banded workload (n=2000, w=10, m=500; 1990 cliques of order
             11): time to 1e-4 in the FP32 graph and plain FP64 forms
   maxcut    the MaxCut workload (n = 10^4, G(n, 6/(n-1)), merged cliques up to
@@ -60,6 +62,8 @@ WORKLOAD = "batch256_block_arrow_l10-100_d10-40_h10-20_m50-400_density0.05"
 BANDED = "banded_n2000_w10_m500"
 # SDPs of the batch in the CPU-baseline sample (every 32nd) and oracle iterations per SDP
 CPU_SAMPLE = list(range(0, 256, 32))
+# iterations of the profiled solve behind the per-class launch times
+PROFILE_ITERS = 200
 CPU_ITERS = 4
 # DRAM bytes of one launch of the roofline's kernel from the ncu capture
 # summarised under profiles/ (None until a capture of the current kernel exists)
@@ -480,9 +484,11 @@ def main():
     pit["ratio_fp64_plain_cold_vs_fp32_graph"] = pit["fp64_plain_cold_jacobi"] / pit["fp32_graph"]
     pit["ratio_fp64_graph_warm_vs_fp32_graph"] = pit["fp64_graph_warm_jacobi"] / pit["fp32_graph"]
 
-    # ---- profiled FP32 solve: per size class, launch durations from CUDA events
-    P.solve("primal", outputs=False, eps=0.0, max_iter=20, precision="fp32", profile=1, check_every=20, **ADAPT,
-            **TUNED)
+    # ---- profiled FP32 solve: per size class, launch durations from CUDA events,
+    # classes one after the other on the solve's stream (proj_streams = 1) so that
+    # each launch is timed alone; 200 iterations from the cold start
+    P.solve("primal", outputs=False, eps=0.0, max_iter=PROFILE_ITERS, precision="fp32", profile=1,
+            check_every=PROFILE_ITERS, **ADAPT, **{**TUNED, "proj_streams": 1})
     proj_ms, proj_launches, iter_ms = P.profile()
     cls = P.profile_orders()
     top = max(cls, key=lambda c: c["ms"])

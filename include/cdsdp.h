@@ -111,6 +111,11 @@ typedef struct {
                               stopping tests, largest work first, so that one class's
                               tail overlaps the next class (1..4; 1 = one after the
                               other on `stream`).  No effect otherwise.  Default 4.   */
+    int proj_cta_kernel;   /* float32 projections of padded orders 36..64 (one thread
+                              block per clique): 0 = eigenvectors in shared memory,
+                              two barriers per Jacobi round; 1 = eigenvectors in
+                              registers, one barrier per round (default).  Same
+                              rotations and results up to rounding order.            */
 } cdsdp_opts;
 
 typedef struct {
@@ -225,9 +230,13 @@ int cdsdp_setup_flags(int n, int m,
  * triangle); b is the concatenation of the b vectors.  The sum numbers the
  * vertices and constraints of problem j after those of problems 0..j-1, so X
  * and Z (pattern order), y and cliques of problem j are contiguous in the
- * results.  scale_passes and flags as cdsdp_setup_flags (scaling factors of the
- * sum as a whole).  Errors: as cdsdp_setup_flags; CDSDP_ERR_ARG for a local
- * index out of its problem's range. */
+ * results.  scale_passes and flags as cdsdp_setup_flags; with scale_passes >= 0
+ * every SDP is scaled as if alone (Section 7.1.3): d and e from the
+ * equilibration passes (which act within each SDP), tau_j = 1 / ||E b_j|| and
+ * sigma_j = 1 / ||D C_j D||_F of SDP j, so that each SDP's scaled problem,
+ * iterates and stopping test are those of a scaled solve of that SDP alone
+ * (cdsdp_scaling_batch reports tau_j, sigma_j).  Errors: as cdsdp_setup_flags;
+ * CDSDP_ERR_ARG for a local index out of its problem's range. */
 int cdsdp_setup_batch(int count, const int* n, const int* m,
                       const long long* nnzA, const int* A_con, const int* A_row, const int* A_col,
                       const double* A_val, const double* b,
@@ -236,9 +245,17 @@ int cdsdp_setup_batch(int count, const int* n, const int* m,
                       int scale_passes, unsigned flags, cdsdp** out);
 
 /* Scaling factors of a handle (Section 7.1.3): d [n], e [m] (host buffers the
- * caller owns; any may be NULL), tau and sigma.  A handle made by cdsdp_setup
- * reports d = e = 1, tau = sigma = 1.  Errors: CDSDP_ERR_ARG (NULL handle). */
+ * caller owns; any may be NULL), tau and sigma (for a scaled batch, those of
+ * SDP 0).  A handle made by cdsdp_setup reports d = e = 1, tau = sigma = 1.
+ * Errors: CDSDP_ERR_ARG (NULL handle). */
 int cdsdp_scaling(const cdsdp* h, double* d, double* e, double* tau, double* sigma);
+
+/* tau and sigma of every SDP of a scaled batch (cdsdp_setup_batch with
+ * scale_passes >= 0, Section 7.1.3): *count (may be NULL) receives the number
+ * of SDPs (1 for any other handle), tau [count] and sigma [count] (host
+ * buffers the caller owns, large enough for the batch; may be NULL) the
+ * factors; ones for an unscaled handle.  Errors: CDSDP_ERR_ARG (NULL handle). */
+int cdsdp_scaling_batch(const cdsdp* h, int* count, double* tau, double* sigma);
 
 /* Maximum-determinant positive definite completion (Section 7.1.1) of a
  * partial matrix X on the handle's extended pattern E* (the X that
@@ -395,8 +412,10 @@ int cdsdp_fma_peak(int precision, int iters, void* stream, double* tflops);
  *   proj_warps_div  1, 2 or 4
  *   warm_start      16 or 64 (only when opts->warm_start > 0)
  *   proj_streams    4 or 1
+ *   proj_cta_kernel 0 or 1 (one more candidate: the fastest of the above with
+ *                   the other value)
  * ms_per_iter[] receives each candidate's device time per iteration in
- * candidate order (at most 24 entries; may be NULL), *n_cand their number (may
+ * candidate order (at most 25 entries; may be NULL), *n_cand their number (may
  * be NULL).  Overwrites the last solve's state.  Errors as cdsdp_solve. */
 int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* stream, cdsdp_opts* tuned,
                    double* ms_per_iter, int* n_cand);

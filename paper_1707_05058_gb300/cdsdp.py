@@ -39,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("component_stop", ctypes.c_int), ("adaptive_rho", ctypes.c_int), ("rho_mu", ctypes.c_double),
                 ("rho_nu", ctypes.c_double), ("x_update", ctypes.c_int), ("proj_warps_div", ctypes.c_int),
                 ("linear_solver", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_max_steps", ctypes.c_int),
-                ("proj_streams", ctypes.c_int)]
+                ("proj_streams", ctypes.c_int), ("proj_cta_kernel", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -56,6 +56,7 @@ _lib.cdsdp_setup.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32
 _lib.cdsdp_setup_scaled.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32p, _f64p, _f64p,
                                     _ll, _i32p, _i32p, _f64p, _ll, _i32p, _i32p, ctypes.c_int, ctypes.POINTER(_vp)]
 _lib.cdsdp_scaling.argtypes = [_vp, _f64p, _f64p, _f64p, _f64p]
+_lib.cdsdp_scaling_batch.argtypes = [_vp, _i32p, _f64p, _f64p]
 _lib.cdsdp_setup_flags.argtypes = [ctypes.c_int, ctypes.c_int, _ll, _i32p, _i32p, _i32p, _f64p, _f64p,
                                    _ll, _i32p, _i32p, _f64p, _ll, _i32p, _i32p, ctypes.c_int, ctypes.c_uint,
                                    ctypes.POINTER(_vp)]
@@ -108,7 +109,7 @@ EXPORTED = ["cdsdp_default_opts", "cdsdp_setup", "cdsdp_info", "cdsdp_cliques", 
             "cdsdp_strerror", "cdsdp_psd_project", "cdsdp_profile", "cdsdp_psd_violation_scratch_bytes",
             "cdsdp_psd_violation", "cdsdp_psd_violation_noalloc", "cdsdp_grad_workspace_bytes",
             "cdsdp_unrolled_forward", "cdsdp_unrolled_backward", "cdsdp_components",
-            "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling",
+            "cdsdp_component_results", "cdsdp_autotune", "cdsdp_setup_scaled", "cdsdp_scaling", "cdsdp_scaling_batch",
             "cdsdp_completion_sizes", "cdsdp_complete", "cdsdp_setup_flags", "cdsdp_setup_batch",
             "cdsdp_fma_peak", "cdsdp_profile_orders", "cdsdp_psd_project_large_bytes",
             "cdsdp_psd_project_large", "cdsdp_profile_large"]
@@ -290,6 +291,19 @@ class Problem:
             raise CdsdpError(st, "cdsdp_scaling")
         return d, e, tau.value, sigma.value
 
+    def scaling_batch(self):
+        """(tau [count], sigma [count]) of every SDP of a scaled batch
+        (cdsdp_scaling_batch); one entry for any other handle."""
+        n = ctypes.c_int(0)
+        st = _lib.cdsdp_scaling_batch(self._h, ctypes.byref(n), None, None)
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_scaling_batch")
+        tau, sigma = np.zeros(n.value), np.zeros(n.value)
+        st = _lib.cdsdp_scaling_batch(self._h, None, _ptr(tau, ctypes.c_double), _ptr(sigma, ctypes.c_double))
+        if st != 0:
+            raise CdsdpError(st, "cdsdp_scaling_batch")
+        return tau, sigma
+
     def completion_sizes(self):
         """(device scratch bytes, doubles of the dense blocks, block offsets [ncomp + 1])."""
         sb = ctypes.c_size_t()
@@ -399,14 +413,14 @@ class Problem:
         if self.workspace is None or self.max_iter < iters:
             self.bind(max(iters, self.max_iter or 0))
         tuned = Opts()
-        ms = np.zeros(24)
+        ms = np.zeros(25)
         n = ctypes.c_int(0)
         st = _lib.cdsdp_autotune(self._h, FORMS.get(form, form), ctypes.byref(o), int(iters), _stream_ptr(stream),
                                  ctypes.byref(tuned), _ptr(ms, ctypes.c_double), ctypes.byref(n))
         if st < 0:
             raise CdsdpError(st, "cdsdp_autotune")
         return ({"x_update": tuned.x_update, "proj_warps_div": tuned.proj_warps_div, "warm_start": tuned.warm_start,
-                 "proj_streams": tuned.proj_streams},
+                 "proj_streams": tuned.proj_streams, "proj_cta_kernel": tuned.proj_cta_kernel},
                 ms[:n.value].tolist())
 
     def profile(self):

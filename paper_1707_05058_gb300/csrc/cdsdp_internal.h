@@ -106,6 +106,11 @@ struct HostProblem {
     bool scaled = false;
     std::vector<double> sc_d, sc_e;   // [n], [m]
     double sc_tau = 1.0, sc_sigma = 1.0;
+    // tau and sigma seen by each vertex and each constraint: the scalars above,
+    // or, for a batch of SDPs (cdsdp_setup_batch), those of the vertex's or the
+    // constraint's own SDP; sc_tau_b / sc_sigma_b per SDP (one entry otherwise)
+    std::vector<double> sc_tau_v, sc_sigma_v, sc_tau_r, sc_sigma_r;
+    std::vector<double> sc_tau_b, sc_sigma_b;
 };
 
 // Build everything above.  Returns a cdsdp_status.

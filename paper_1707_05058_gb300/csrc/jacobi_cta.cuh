@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "jacobi.cuh"
+#include "jacobi_reg.cuh"
 
 namespace cdsdp_dev {
 
@@ -573,31 +574,54 @@ struct CTAJacobiMid {
 template <typename T, int S>
 using CTASolver = typename std::conditional<(S <= 64), CTAJacobiMid<T, S>, CTAJacobi<T, S>>::type;
 
+// Solver of k_project_cta: VARIANT 0 keeps V in shared memory (CTAJacobiMid,
+// CTAJacobi); VARIANT 1 (float32, padded orders 36..64) keeps V in registers
+// (CTAJacobiReg).
+template <typename T, int S, int VARIANT>
+struct CTAPick {
+    using type = CTASolver<T, S>;
+    static constexpr int threads = cta_threads<T, S>();
+    static constexpr int min_blocks = cta_min_blocks<T, S>();
+};
+template <int S>
+struct CTAPick<float, S, 1> {
+    using type = CTAJacobiReg<S>;
+    static constexpr int threads = CTAJacobiReg<S>::NT;
+    // about 64 registers a thread
+    static constexpr int min_blocks = 65536 / (CTAJacobiReg<S>::NT * 80);
+};
+
 template <int NV>
 __device__ __forceinline__ void cta_sum(double (&v)[NV], double* sh) {
     block_sum<NV>(v, sh);  // valid in thread 0
 }
 
 // One kernel for every form: FORM 0/1/2 = Algorithm 1/2/3 step (as the warp
-// kernels of jacobi.cuh), FORM 3 = standalone projection.
-template <typename T, int S, int FORM>
-__global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k_project_cta(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
+// kernels of jacobi.cuh), FORM 3 = standalone projection; VARIANT selects the
+// solver (CTAPick).
+template <typename T, int S, int FORM, int VARIANT>
+__global__ void __launch_bounds__(CTAPick<T, S, VARIANT>::threads, CTAPick<T, S, VARIANT>::min_blocks) k_project_cta(Dev d, const int* __restrict__ list, int nlist, ProjArgs pa,
                                                               FinishArgs fa, const int* __restrict__ off_arr,
                                                               const int* __restrict__ size_arr,
                                                               const T* __restrict__ Win, T* Xout) {
-    using J = CTASolver<T, S>;
+    using J = typename CTAPick<T, S, VARIANT>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double shr[32 * 6];
     if (FORM != 3 && stopped(d)) return;
     J jac;
     jac.bind(smem);
     const int tid = threadIdx.x;
-    T* c0 = reinterpret_cast<T*>(d.ck0);
-    T* c1 = reinterpret_cast<T*>(d.ck1);
-    T* c2 = reinterpret_cast<T*>(d.ck2);
-    T* vc = reinterpret_cast<T*>(d.vcache);
+    // clique state and eigenvector cache (taken from the parameters where used)
+#define c0 (reinterpret_cast<T*>(d.ck0))
+#define c1 (reinterpret_cast<T*>(d.ck1))
+#define c2 (reinterpret_cast<T*>(d.ck2))
+#define vc (reinterpret_cast<T*>(d.vcache))
     const bool warm = FORM != 3 && pa.warm_start && (d.ctl[CTL_ITER] % pa.restart) != 0;
     __shared__ double acc[6];  // block partial sums, kept by thread 0
+    // the clique's scalars, read back after the eigensolve so that they hold
+    // no registers during it: k, s, offset; rho, gamma, <c, x> (thread 0's sum)
+    __shared__ int ck_i[3];
+    __shared__ double ck_d[3];
     if (tid < 6) acc[tid] = 0.0;
     for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
         const int k = FORM == 3 ? li : list[li];
@@ -608,6 +632,10 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
         const double rho = (FORM == 0 || FORM == 1) ? rho_clique(d, k) : 1.0, irho = 1.0 / rho;
         const double gamma = FORM == 2 ? hs_gamma_c(d, comp_k(d, k)) : 0.0;
         const int npk = s * (s + 1) / 2;
+        if (tid == 0) {
+            ck_i[0] = k; ck_i[1] = s; ck_i[2] = off;
+            ck_d[0] = rho; ck_d[1] = gamma;
+        }
         jac.clear();
         double nrm = 0.0, cx = 0.0;
         for (int f = tid; f < npk; f += blockDim.x) {
@@ -646,16 +674,30 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
         }
         double tmp[2] = {nrm, cx};
         cta_sum<2>(tmp, shr);
-        double cxk = 0.0;
-        if (tid == 0) { shr[0] = tmp[0]; cxk = tmp[1]; }
+        if (tid == 0) { shr[0] = tmp[0]; ck_d[2] = tmp[1]; }
         __syncthreads();
         nrm = shr[0];
         __syncthreads();
-        if (warm) {
-            jac.load_basis(vc + d.vv_off[k], s);
-            jac.rotate_into_basis();
+        if constexpr (VARIANT == 1) {  // V's registers assigned on both paths
+            if (warm) {
+                jac.load_basis(vc + d.vv_off[k], s);
+                jac.rotate_into_basis();
+            } else {
+                jac.identity_basis();
+            }
+            jac.run(T(pa.tolrel) * T(sqrt(nrm)), pa.max_sweeps, true);
+        } else {
+            if (warm) {
+                jac.load_basis(vc + d.vv_off[k], s);
+                jac.rotate_into_basis();
+            }
+            jac.run(T(pa.tolrel) * T(sqrt(nrm)), pa.max_sweeps, warm);
         }
-        jac.run(T(pa.tolrel) * T(sqrt(nrm)), pa.max_sweeps, warm);
+        {  // epilogue: the clique's scalars from shared memory
+        const int k = ck_i[0], s = ck_i[1], off = ck_i[2];
+        const double rho = ck_d[0], gamma = ck_d[1];
+        const double cxk = tid == 0 ? ck_d[2] : 0.0;
+        const int npk = s * (s + 1) / 2;
         if (FORM != 3 && pa.warm_start) jac.store_basis(vc + d.vv_off[k], s);
         jac.prepare_rebuild();
         double p[6] = {0, 0, 0, 0, 0, 0};
@@ -724,6 +766,7 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
             }
         }
         __syncthreads();
+        }
     }
     if (FORM == 3) return;
     if (d.comp_mode) return;
@@ -734,6 +777,10 @@ __global__ void __launch_bounds__(cta_threads<T, S>(), cta_min_blocks<T, S>()) k
         else { for (int c = 0; c < 6; ++c) pr[c] = acc[c]; }
     }
     if (FORM == 0 && fa.enabled && last_block_single_writer(d)) finish_primal_block(d, fa);
+#undef c0
+#undef c1
+#undef c2
+#undef vc
 }
 
 }  // namespace cdsdp_dev

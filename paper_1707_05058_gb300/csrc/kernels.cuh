@@ -139,6 +139,8 @@ struct ProjArgs {
     int warps_div;       // warp-per-clique launches: warps per block = the maximum / warps_div
     int x_ready;         // Algorithm 1: x was computed by a separate kernel this
                          // iteration (read it) instead of inside the gather
+    int cta_variant;     // thread-block projections, float32 orders 36..64: 0 = V in
+                         // shared memory (CTAJacobiMid), 1 = V in registers (CTAJacobiReg)
 };
 
 __device__ __forceinline__ bool stopped(const Dev& d) {

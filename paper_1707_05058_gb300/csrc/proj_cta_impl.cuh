@@ -10,24 +10,36 @@
 namespace cdsdp_dev {
 namespace {
 
-template <typename T, int S, int FORM>
-cudaError_t launch_cta(const Dev& d, const int* list, int nlist, const ProjArgs& pa_in, const FinishArgs& fa,
-                       const int* off, const int* size, const void* W, void* X, int max_sweeps, cudaStream_t st) {
-    if (nlist <= 0) return cudaSuccess;
-    const size_t smem = CTASolver<T, S>::bytes;
+template <typename T, int S, int FORM, int VARIANT>
+cudaError_t launch_cta_v(const Dev& d, const int* list, int nlist, const ProjArgs& pa_in, const FinishArgs& fa,
+                         const int* off, const int* size, const void* W, void* X, int max_sweeps, cudaStream_t st) {
+    using Pick = CTAPick<T, S, VARIANT>;
+    const size_t smem = Pick::type::bytes;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_project_cta<T, S, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_project_cta<T, S, FORM, VARIANT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     ProjArgs pa = pa_in;
     pa.tolrel = jacobi_tolrel(S, sizeof(T) == 4);
     if (FORM == 3) pa.max_sweeps = max_sweeps;
-    k_project_cta<T, S, FORM><<<proj_cta_grid(nlist), cta_threads<T, S>(), smem, st>>>(d, list, nlist, pa, fa, off, size,
-                                                                               (const T*)W, (T*)X);
+    k_project_cta<T, S, FORM, VARIANT><<<proj_cta_grid(nlist), Pick::threads, smem, st>>>(d, list, nlist, pa, fa, off,
+                                                                                         size, (const T*)W, (T*)X);
     return cudaGetLastError();
+}
+
+// pa.cta_variant = 1 selects variant 1 (V in registers) for float32 orders 36..64.
+template <typename T, int S, int FORM>
+cudaError_t launch_cta(const Dev& d, const int* list, int nlist, const ProjArgs& pa, const FinishArgs& fa,
+                       const int* off, const int* size, const void* W, void* X, int max_sweeps, cudaStream_t st) {
+    if (nlist <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4 && S >= 36 && S <= 64) {
+        if (pa.cta_variant == 1)
+            return launch_cta_v<T, S, FORM, 1>(d, list, nlist, pa, fa, off, size, W, X, max_sweeps, st);
+    }
+    return launch_cta_v<T, S, FORM, 0>(d, list, nlist, pa, fa, off, size, W, X, max_sweeps, st);
 }
 
 template <typename T, int S>
@@ -54,11 +66,12 @@ cudaError_t CTA_SUFFIX(launch_proj_cta)(int S, int form, const Dev& d, const int
 }
 
 cudaError_t CTA_SUFFIX(launch_proj_cta_standalone)(int S, int p, const int* off, const int* size, const void* W,
-                                                   void* X, int max_sweeps, cudaStream_t st) {
+                                                   void* X, int max_sweeps, int variant, cudaStream_t st) {
     Dev d{};
     ProjArgs pa{};
     FinishArgs fa{};
     pa.restart = 1;
+    pa.cta_variant = variant;
     switch (S) {
 #define CTA_CASE(N) \
     case N: return launch_cta<CTA_T, N, 3>(d, nullptr, p, pa, fa, off, size, W, X, max_sweeps, st);

@@ -69,7 +69,7 @@ CDSDP_DECLARE_PROJ(f64_large)
     cudaError_t launch_proj_cta_##SUF(int S, int form, const Dev& d, const int* list, int nlist,               \
                                       const ProjArgs& pa, const FinishArgs& fa, cudaStream_t st);                \
     cudaError_t launch_proj_cta_standalone_##SUF(int S, int p, const int* off, const int* size, const void* W, \
-                                                 void* X, int max_sweeps, cudaStream_t st);
+                                                 void* X, int max_sweeps, int variant, cudaStream_t st);
 CDSDP_DECLARE_CTA(f32a)
 CDSDP_DECLARE_CTA(f32b)
 CDSDP_DECLARE_CTA(f32c)
@@ -91,11 +91,11 @@ inline cudaError_t launch_proj_cta_standalone(bool fp32, int cls, int p, const i
                                               const void* W, void* X, int max_sweeps, cudaStream_t st) {
     const int S = kProjClasses[cls];
     if (fp32)
-        return S <= 48 ? launch_proj_cta_standalone_f32a(S, p, off, size, W, X, max_sweeps, st)
-                       : (S <= 64 ? launch_proj_cta_standalone_f32b(S, p, off, size, W, X, max_sweeps, st)
-                                  : launch_proj_cta_standalone_f32c(S, p, off, size, W, X, max_sweeps, st));
-    return S <= 48 ? launch_proj_cta_standalone_f64a(S, p, off, size, W, X, max_sweeps, st)
-                   : launch_proj_cta_standalone_f64b(S, p, off, size, W, X, max_sweeps, st);
+        return S <= 48 ? launch_proj_cta_standalone_f32a(S, p, off, size, W, X, max_sweeps, 0, st)
+                       : (S <= 64 ? launch_proj_cta_standalone_f32b(S, p, off, size, W, X, max_sweeps, 0, st)
+                                  : launch_proj_cta_standalone_f32c(S, p, off, size, W, X, max_sweeps, 0, st));
+    return S <= 48 ? launch_proj_cta_standalone_f64a(S, p, off, size, W, X, max_sweeps, 0, st)
+                   : launch_proj_cta_standalone_f64b(S, p, off, size, W, X, max_sweeps, 0, st);
 }
 
 inline cudaError_t launch_proj_f32(int form, int cls, const Dev& d, const int* list, int nlist, const ProjArgs& pa,

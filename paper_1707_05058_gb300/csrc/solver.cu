@@ -317,6 +317,7 @@ cudaError_t launch_projection(cdsdp* h, int form, const cdsdp_opts& o, const Fin
     pa.row_off = 0;
     pa.warps_div = o.proj_warps_div;
     pa.x_ready = (form == 0 && h->x_split) ? 1 : 0;
+    pa.cta_variant = o.proj_cta_kernel;
     // first partial-table row of each class (class order), then the launches
     int row0[kNumClasses + 1];
     for (int c = 0; c < kNumClasses; ++c) {
@@ -473,7 +474,7 @@ bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
            a.component_stop == b.component_stop && a.adaptive_rho == b.adaptive_rho && a.rho_mu == b.rho_mu &&
            a.rho_nu == b.rho_nu && a.x_update == b.x_update && a.proj_warps_div == b.proj_warps_div &&
            a.linear_solver == b.linear_solver && a.cg_tol == b.cg_tol && a.cg_max_steps == b.cg_max_steps &&
-           a.proj_streams == b.proj_streams;
+           a.proj_streams == b.proj_streams && a.proj_cta_kernel == b.proj_cta_kernel;
 }
 
 void drop_graph(cdsdp* h) {
@@ -529,6 +530,7 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
     if (!(o.cg_tol >= 0.0) || !std::isfinite(o.cg_tol) || o.cg_max_steps < 0 || o.cg_max_steps > 1024)
         return CDSDP_ERR_ARG;
     if (o.proj_streams < 1 || o.proj_streams > 4) return CDSDP_ERR_ARG;
+    if (o.proj_cta_kernel != 0 && o.proj_cta_kernel != 1) return CDSDP_ERR_ARG;
     if (o.precision == CDSDP_FP64 && h->hp.max_clique > kMaxOrderF64) return CDSDP_ERR_UNSUPPORTED;
     return CDSDP_SOLVED;
 }
@@ -574,11 +576,11 @@ void unscale_results(const HostProblem& hp, double* X, double* y, double* Z) {
     const size_t NE = hp.prow.size();
     for (size_t k = 0; k < NE; ++k) {
         const double dd = hp.sc_d[hp.prow[k]] * hp.sc_d[hp.pcol[k]];
-        if (X) X[k] *= dd / hp.sc_tau;
-        if (Z) Z[k] /= dd * hp.sc_sigma;
+        if (X) X[k] *= dd / hp.sc_tau_v[hp.prow[k]];
+        if (Z) Z[k] /= dd * hp.sc_sigma_v[hp.prow[k]];
     }
     if (y)
-        for (int i = 0; i < hp.m; ++i) y[i] *= hp.sc_e[i] / hp.sc_sigma;
+        for (int i = 0; i < hp.m; ++i) y[i] *= hp.sc_e[i] / hp.sc_sigma_r[i];
 }
 
 // Certificates of the scaled problem mapped back.  A primal infeasibility
@@ -587,10 +589,11 @@ void unscale_results(const HostProblem& hp, double* X, double* y, double* Z) {
 // with C . X = -1, the normalisations of an unscaled solve.
 void unscale_cert(const HostProblem& hp, int status, double* cert) {
     if (status == CDSDP_PRIMAL_INFEASIBLE) {
-        for (int i = 0; i < hp.m; ++i) cert[i] *= hp.sc_tau * hp.sc_e[i];
+        for (int i = 0; i < hp.m; ++i) cert[i] *= hp.sc_tau_r[i] * hp.sc_e[i];
     } else if (status == CDSDP_DUAL_INFEASIBLE) {
         const size_t NE = hp.prow.size();
-        for (size_t k = 0; k < NE; ++k) cert[k] *= hp.sc_sigma * hp.sc_d[hp.prow[k]] * hp.sc_d[hp.pcol[k]];
+        for (size_t k = 0; k < NE; ++k)
+            cert[k] *= hp.sc_sigma_v[hp.prow[k]] * hp.sc_d[hp.prow[k]] * hp.sc_d[hp.pcol[k]];
     }
 }
 
@@ -741,6 +744,7 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->cg_tol = 1e-10;
     o->cg_max_steps = 5;
     o->proj_streams = 4;
+    o->proj_cta_kernel = 1;
 }
 
 namespace {
@@ -750,7 +754,8 @@ namespace {
 int setup_common(int n, int m, long long nnzA, const int* A_con, const int* A_row, const int* A_col,
                  const double* A_val, const double* b, long long nnzC, const int* C_row, const int* C_col,
                  const double* C_val, long long nnzP, const int* P_row, const int* P_col, int scale_passes,
-                 unsigned flags, cdsdp** out) {
+                 unsigned flags, cdsdp** out, int count = 0, const int* sdp_n = nullptr,
+                 const int* sdp_m = nullptr) {
     if (!out) return CDSDP_ERR_ARG;
     *out = nullptr;
     if (flags & ~(unsigned)(CDSDP_SETUP_NO_FACTOR | CDSDP_SETUP_MERGE_CLIQUES)) return CDSDP_ERR_ARG;
@@ -779,18 +784,49 @@ int setup_common(int n, int m, long long nnzA, const int* A_con, const int* A_ro
             double tau = 1.0, sigma = 1.0;
             cdsdp_impl::scaling_factors(n, m, nnzA, A_con, A_row, A_col, A_val, b, nnzC, C_row, C_col, C_val,
                                         scale_passes, d, e, tau, sigma);
+            // tau and sigma per vertex and per constraint: the problem's, or in a
+            // batch those of each SDP alone, 1 / ||E b_j|| and 1 / ||D C_j D||_F
+            // (the equilibration passes act within each SDP already)
+            const int nb = count > 0 ? count : 1;
+            std::vector<double> tb(nb, tau), sb(nb, sigma), tv(n), sv(n), tr(m), sr(m);
+            std::vector<int> sdp_of_v(n, 0), sdp_of_r(m, 0);
+            if (count > 0) {
+                for (int j = 0, vo = 0, mo = 0; j < count; vo += sdp_n[j], mo += sdp_m[j], ++j) {
+                    for (int v = vo; v < vo + sdp_n[j]; ++v) sdp_of_v[v] = j;
+                    for (int i = mo; i < mo + sdp_m[j]; ++i) sdp_of_r[i] = j;
+                }
+                std::vector<double> nbj(count, 0.0), ncj(count, 0.0);
+                for (int i = 0; i < m; ++i) nbj[sdp_of_r[i]] += (e[i] * b[i]) * (e[i] * b[i]);
+                for (long long k = 0; k < nnzC; ++k) {
+                    const double v = d[C_row[k]] * d[C_col[k]] * C_val[k];
+                    ncj[sdp_of_v[C_row[k]]] += (C_row[k] == C_col[k] ? 1.0 : 2.0) * v * v;
+                }
+                for (int j = 0; j < count; ++j) {
+                    const double a = std::sqrt(nbj[j]), c = std::sqrt(ncj[j]);
+                    tb[j] = a > 0.0 ? 1.0 / a : 1.0;
+                    sb[j] = c > 0.0 ? 1.0 / c : 1.0;
+                }
+            }
+            for (int v = 0; v < n; ++v) { tv[v] = tb[sdp_of_v[v]]; sv[v] = sb[sdp_of_v[v]]; }
+            for (int i = 0; i < m; ++i) { tr[i] = tb[sdp_of_r[i]]; sr[i] = sb[sdp_of_r[i]]; }
             std::vector<double> av(nnzA), bv(m), cv(nnzC);
             for (long long k = 0; k < nnzA; ++k) av[k] = e[A_con[k]] * d[A_row[k]] * d[A_col[k]] * A_val[k];
-            for (int i = 0; i < m; ++i) bv[i] = tau * e[i] * b[i];
-            for (long long k = 0; k < nnzC; ++k) cv[k] = sigma * d[C_row[k]] * d[C_col[k]] * C_val[k];
+            for (int i = 0; i < m; ++i) bv[i] = tr[i] * e[i] * b[i];
+            for (long long k = 0; k < nnzC; ++k) cv[k] = sv[C_row[k]] * d[C_row[k]] * d[C_col[k]] * C_val[k];
             st = cdsdp_impl::build_host_problem(n, m, nnzA, A_con, A_row, A_col, av.data(), bv.data(), nnzC, C_row,
                                                 C_col, cv.data(), nnzP, P_row, P_col, h->hp, cache_factor, merge);
             if (st == CDSDP_SOLVED) {
                 h->hp.scaled = true;
                 h->hp.sc_d = std::move(d);
                 h->hp.sc_e = std::move(e);
-                h->hp.sc_tau = tau;
-                h->hp.sc_sigma = sigma;
+                h->hp.sc_tau = tb[0];
+                h->hp.sc_sigma = sb[0];
+                h->hp.sc_tau_v = std::move(tv);
+                h->hp.sc_sigma_v = std::move(sv);
+                h->hp.sc_tau_r = std::move(tr);
+                h->hp.sc_sigma_r = std::move(sr);
+                h->hp.sc_tau_b = std::move(tb);
+                h->hp.sc_sigma_b = std::move(sb);
             }
         }
     } catch (const std::exception&) {  // allocation or thread creation failed
@@ -878,7 +914,7 @@ int cdsdp_setup_batch(int count, const int* n, const int* m, const long long* nn
             mo += m[j];
         }
         return setup_common((int)N, (int)M, tA, ac.data(), ar.data(), acl.data(), A_val, b, tC, cr.data(), cc.data(),
-                            C_val, tP, pr.data(), pc.data(), scale_passes, flags, out);
+                            C_val, tP, pr.data(), pc.data(), scale_passes, flags, out, count, n, m);
     } catch (const std::exception&) {  // allocation failed
         return CDSDP_ERR_NOMEM;
     }
@@ -897,6 +933,18 @@ int cdsdp_scaling(const cdsdp* h, double* d, double* e, double* tau, double* sig
     }
     if (tau) *tau = hp.sc_tau;
     if (sigma) *sigma = hp.sc_sigma;
+    return CDSDP_SOLVED;
+}
+
+int cdsdp_scaling_batch(const cdsdp* h, int* count, double* tau, double* sigma) {
+    if (!h) return CDSDP_ERR_ARG;
+    const HostProblem& hp = h->hp;
+    const int nb = hp.scaled ? (int)hp.sc_tau_b.size() : 1;
+    if (count) *count = nb;
+    for (int j = 0; j < nb; ++j) {
+        if (tau) tau[j] = hp.scaled ? hp.sc_tau_b[j] : 1.0;
+        if (sigma) sigma[j] = hp.scaled ? hp.sc_sigma_b[j] : 1.0;
+    }
     return CDSDP_SOLVED;
 }
 
@@ -1236,7 +1284,13 @@ int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* 
     CK(cudaEventCreate(&e1));
     double best = 1e300;
     int ibest = 0, rc = CDSDP_SOLVED;
-    for (size_t i = 0; i < cand.size() && rc >= 0; ++i) {
+    const size_t n_grid = cand.size();
+    for (size_t i = 0; i <= n_grid && rc >= 0; ++i) {
+        if (i == n_grid) {  // the fastest so far with the other thread-block projection kernel
+            cdsdp_opts o = cand[ibest];
+            o.proj_cta_kernel = 1 - o.proj_cta_kernel;
+            cand.push_back(o);
+        }
         rc = cdsdp_solve(h, form, &cand[i], stream, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);  // warm-up
         if (rc < 0) break;
         cudaEventRecord(e0, st);
@@ -1259,6 +1313,7 @@ int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* 
     tuned->proj_warps_div = cand[ibest].proj_warps_div;
     tuned->warm_start = cand[ibest].warm_start;
     tuned->proj_streams = cand[ibest].proj_streams;
+    tuned->proj_cta_kernel = cand[ibest].proj_cta_kernel;
     if (n_cand) *n_cand = (int)cand.size();
     return CDSDP_SOLVED;
 }

@@ -35,6 +35,8 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--x-update", type=int, default=0, choices=[0, 1, 2],
                     help="Algorithm 1: 0 automatic, 1 inside the projection gather, 2 separate kernel")
+    ap.add_argument("--cta-kernel", type=int, default=1, choices=[0, 1],
+                    help="float32 orders 36..64: 0 eigenvectors in shared memory, 1 in registers")
     args = ap.parse_args(argv)
 
     import torch
@@ -53,7 +55,7 @@ def main(argv=None):
         prob = workloads.workload(1 if args.workload == "banded" else 0)
     P = cdsdp.Problem(prob, merge_cliques=merge).bind(max_iter=args.iters)
     out = P.solve(args.form, eps=0.0, max_iter=args.iters, precision=args.precision, use_graph=0,
-                  check_every=args.iters, outputs=False, x_update=args.x_update)
+                  check_every=args.iters, outputs=False, x_update=args.x_update, proj_cta_kernel=args.cta_kernel)
     torch.cuda.synchronize()
     print(f"{args.workload} {args.form} {args.precision}: {out['iters']} iterations, status {out['status']}")
 

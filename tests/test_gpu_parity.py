@@ -249,6 +249,41 @@ def test_block_arrow_fp32_matches_oracle(lib, torch_cuda, form):
     assert max(rp, rd) <= 5e-4
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("form", ["primal", "dual"])
+def test_cta_kernels_fp32_warm_start_match_oracle(lib, torch_cuda, form, kernel):
+    """Both thread-block projection kernels of the FP32 form (proj_cta_kernel 0:
+    eigenvectors in shared memory; 1: in registers), warm-started from the
+    previous iteration's eigenvectors (cold every 16th iteration), on a direct
+    sum of block-arrows with
+    cliques of orders 36, 53 and 64: each summand solved at eps = 1e-4 in the
+    oracle's iteration count (+-3) with objective within 1e-4 of the oracle's
+    solve of that summand alone (its eigendecomposition step from LAPACK)."""
+    parts = [W.block_arrow(2, 30, 6, 10, seed=77), W.block_arrow(3, 45, 8, 15, seed=78),
+             W.block_arrow(2, 56, 8, 12, seed=79)]
+    P = lib.Problem(W.direct_sum(parts)).bind(max_iter=3000)
+    out = P.solve(form, eps=1e-4, max_iter=3000, precision="fp32", proj_cta_kernel=kernel)
+    assert out["status"] == 0
+    it, st, res = P.component_results()
+    assert np.all(st == 0)
+    r, c = P.pattern()
+    vo = np.concatenate([[0], np.cumsum([q.n for q in parts])])
+    for j, q in enumerate(parts):
+        dp = admm.decompose(q, eig="lapack")
+        ref = (admm.primal_admm if form == "primal" else admm.dual_admm)(dp, eps=1e-4, max_iter=3000)
+        assert ref.status == 0 and abs(int(it[j]) - ref.iters) <= 3, (j, it[j], ref.iters)
+        assert max(res[j, 0], res[j, 1]) <= 1e-4
+        mask = (c >= vo[j]) & (c < vo[j + 1])
+        cv = np.zeros(int(mask.sum()))
+        idx = {(int(a) - vo[j], int(b) - vo[j]): e for e, (a, b) in enumerate(zip(r[mask], c[mask]))}
+        for a, b, v in zip(q.C_row, q.C_col, q.C_val):
+            cv[idx[(int(a), int(b))]] += v
+        w = np.where(r[mask] == c[mask], 1.0, 2.0)
+        obj = float(np.sum(w * cv * out["X"][mask]))
+        want = float(dp.c @ ref.X)
+        assert abs(obj - want) <= 1e-4 * abs(want), (j, obj, want)
+
+
 def _full(dp, lower_vals):
     x = np.zeros(dp.N)
     for (i, j), v in zip(dp.lower, lower_vals):
@@ -436,8 +471,8 @@ def test_autotune_picks_a_candidate_and_keeps_parity(lib, torch_cuda, form):
     dp, ref = _oracle(prob, form, 1e-4, 2000)
     P = lib.Problem(prob).bind(max_iter=2000)
     tuned, ms = P.autotune(form, iters=20, precision="fp64")
-    assert len(ms) == (24 if form == "primal" else 12) and all(m > 0 for m in ms)
+    assert len(ms) == (25 if form == "primal" else 13) and all(m > 0 for m in ms)
     assert tuned["x_update"] in (1, 2) and tuned["proj_warps_div"] in (1, 2, 4) and tuned["warm_start"] in (16, 64)
-    assert tuned["proj_streams"] in (1, 4)
+    assert tuned["proj_streams"] in (1, 4) and tuned["proj_cta_kernel"] in (0, 1)
     out = P.solve(form, eps=1e-4, max_iter=2000, precision="fp64", **tuned)
     _assert_trajectory(dp, ref, out)

@@ -25,6 +25,31 @@ def test_scaling_factors_match_oracle(lib, prob, passes):
     assert abs(sigma - rsigma) <= 1e-13 * rsigma
 
 
+@pytest.mark.parametrize("passes", [0, 4])
+def test_batch_scaling_factors_per_sdp(lib, passes):
+    """A scaled batch (cdsdp_setup_batch) scales every SDP as if alone: d and e
+    of the sum and tau_j, sigma_j of each SDP equal the oracle's factors of that
+    SDP scaled on its own."""
+    parts = [W.block_arrow(2, 3, 2, 4, seed=1), W.maxcut_cycle(5), W.block_arrow(3, 4, 2, 6, seed=5),
+             W.lambda_max_tridiagonal(8, 1.0, 0.5)]
+    P = lib.Problem.batch(parts, scale_passes=passes)
+    d, e, tau0, sigma0 = P.scaling()
+    tau, sigma = P.scaling_batch()
+    assert len(tau) == len(sigma) == len(parts)
+    assert tau0 == tau[0] and sigma0 == sigma[0]
+    vo = np.concatenate([[0], np.cumsum([q.n for q in parts])])
+    mo = np.concatenate([[0], np.cumsum([q.m for q in parts])])
+    for j, q in enumerate(parts):
+        rd, re, rtau, rsigma = scaling.scaling_factors(q, passes)
+        np.testing.assert_allclose(d[vo[j]:vo[j + 1]], rd, rtol=1e-14)
+        np.testing.assert_allclose(e[mo[j]:mo[j + 1]], re, rtol=1e-14)
+        assert abs(tau[j] - rtau) <= 1e-13 * rtau and abs(sigma[j] - rsigma) <= 1e-13 * rsigma
+    t1, s1 = lib.Problem(parts[0], scale_passes=passes).scaling_batch()
+    assert len(t1) == 1
+    tu, su = lib.Problem.batch(parts).scaling_batch()
+    assert len(tu) == 1 and tu[0] == 1.0 and su[0] == 1.0
+
+
 def test_unscaled_handle_reports_unit_factors(lib):
     prob = W.workload(0)
     d, e, tau, sigma = lib.Problem(prob).scaling()
