@@ -32,6 +32,11 @@ reductions).
             start (every SDP active, size classes launched one after the other
             so that each launch is timed alone), against the FMA peak measured
             by cdsdp_fma_peak on this GPU
+  hsde      Algorithm 3 on the batch, each SDP scaled alone and embedded
+            alone: time to 1e-4 of one FP32 graph solve, and parity of three
+            summands against stored oracle solves
+  affine_sweep  affine-projection cost against m (block-arrow l=100, d=10,
+            h=20, m = 200 and 1000) per form, cached inverse and 5 CG steps
   banded    the banded workload (n=2000, w=10, m=500; 1990 cliques of order
             11): time to 1e-4 in the FP32 graph and plain FP64 forms
   maxcut    the MaxCut workload (n = 10^4, G(n, 6/(n-1)), merged cliques up to
@@ -252,6 +257,72 @@ def _parity_vs_oracle(P, parts, members):
         want = g["objective"][min(int(it[k]), len(g["objective"])) - 1]
         out.append({"summand": j, "iters": int(it[k]), "oracle_iters": g["iters"],
                     "rel_objective_gap": abs(obj - want) / abs(want), "residuals": [float(res[k, 0]), float(res[k, 1])]})
+    return out
+
+
+def _hsde_batch(cdsdp, parts, members, torch, flush, stream):
+    """Algorithm 3 on the batch, each SDP scaled alone (Section 7.1.3, 4
+    equilibration passes) and embedded alone: one FP32 graph solve to
+    eps = 1e-4 from the cold start (every SDP stops on its own test), CUDA
+    events; parity of three summands against stored oracle solves of each
+    summand scaled alone (tests/golden/batch_hsde_scaled_oracle.json)."""
+    import numpy as np
+    t0 = time.perf_counter()
+    Q = cdsdp.Problem.batch(parts, scale_passes=4)
+    setup_s = time.perf_counter() - t0
+    Q.bind(max_iter=40000)
+    flush.fill_(1)
+    ms, out = _event_ms(torch, stream, lambda: Q.solve("hsde", outputs=True, eps=1e-4, max_iter=40000,
+                                                       precision="fp32", use_graph=1))
+    it, st, res = Q.component_results()
+    block = {"workload": "the batch, each SDP scaled alone (4 passes), one embedding per SDP", "setup_s": setup_s,
+             "time_to_eps_ms": ms, "iters_to_eps_max": int(out["iters"]), "sdp_iters": int(it.sum()),
+             "sdp_iters_per_s": float(it.sum()) / (ms / 1e3), "all_solved": bool(np.all(st == 0)),
+             "ms_per_iteration_mean": ms / max(1, int(out["iters"]))}
+    path = os.path.join(ROOT, "tests", "golden", "batch_hsde_scaled_oracle.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            gold = json.load(f)["results"]
+        r, c = Q.pattern()
+        vo = np.concatenate([[0], np.cumsum([q.n for q in parts])])
+        par = []
+        for g in gold:
+            j = g["summand"]
+            if j not in members:
+                continue
+            k = members.index(j)
+            q = parts[k]
+            mask = (c >= vo[k]) & (c < vo[k + 1])
+            rr, cc = r[mask] - vo[k], c[mask] - vo[k]
+            index = {(int(a), int(b)): e for e, (a, b) in enumerate(zip(rr, cc))}
+            cvec = np.zeros(len(rr))
+            for a, b, v in zip(q.C_row, q.C_col, q.C_val):
+                cvec[index[(int(a), int(b))]] += v
+            obj = float(np.sum(np.where(rr == cc, 1.0, 2.0) * cvec * out["X"][mask]))
+            par.append({"summand": j, "iters": int(it[k]), "oracle_iters": g["iters"],
+                        "rel_objective_gap": abs(obj - g["objective"]) / abs(g["objective"]),
+                        "residuals": [float(res[k, 0]), float(res[k, 1])]})
+        block["parity_vs_oracle"] = par
+    del Q
+    return block
+
+
+def _affine_sweep():
+    """The affine projection against m (block-arrow l=100, d=10, h=20, A_i
+    dense on the pattern, the smallest and largest m of the paper's
+    affine-projection table): affine and projection ms per iteration of a
+    profiled 50-iteration solve per form with the cached inverse, and of
+    Algorithms 1-2 with 5 conjugate-gradient steps per iteration instead."""
+    from paper_1707_05058_gb300 import affine_sweep
+    rows = affine_sweep.sweep_rows([200, 1000], 50)
+    cg = affine_sweep.sweep_rows([200, 1000], 50, forms=("primal", "dual"), cg=True, cg_steps=5)
+    out = []
+    for r, c in zip(rows, cg):
+        out.append({"m": r["m"], "nnz_A": r["nnz_A"], "cliques": r["cliques"],
+                    "affine_ms_per_iter": {f: r[f]["affine_ms_per_iter"] for f in ("primal", "dual", "hsde")},
+                    "proj_ms_per_iter": r["primal"]["proj_ms_per_iter"],
+                    "hsde_over_primal_affine": r["hsde_over_primal_affine"],
+                    "cg5_affine_ms_per_iter": {f: c[f]["affine_ms_per_iter"] for f in ("primal", "dual")}})
     return out
 
 
@@ -526,7 +597,9 @@ def main():
 
     extras = {}
     if not args.no_extras:
+        extras["hsde"] = _hsde_batch(cdsdp, parts, members, torch, flush, stream)
         extras["banded"] = _banded(cdsdp, workloads, torch, flush, stream)
+        extras["affine_sweep"] = _affine_sweep()
         extras["maxcut"] = _maxcut(cdsdp, workloads, torch, flush, stream)
         extras["grad"] = _grad_batch(cdsdp, workloads, torch, stream)
         extras["completion"] = _completion(cdsdp, workloads, torch, stream)

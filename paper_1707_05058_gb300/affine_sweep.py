@@ -30,6 +30,45 @@ TABLE_M = [  # m values of the affine-projection table (Section 7.4)
     200, 239, 286, 342, 409, 489, 585, 699, 836, 1000]
 
 
+def sweep_rows(ms, iters, precision="fp32", forms=("primal", "dual", "hsde"), cg=False, cg_steps=5, cg_tol=1e-10,
+               verbose=False):
+    """One dict per m: sizes, setup time and, per form, the affine and
+    projection ms per iteration of a profiled `iters`-iteration solve."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1707_05058_gb300 import cdsdp, workloads
+
+    rows = []
+    for m in ms:
+        t0 = time.perf_counter()
+        prob = workloads.block_arrow(100, 10, 20, m, seed=7000 + m, name=f"block_arrow_l100_d10_h20_m{m}")
+        t1 = time.perf_counter()
+        P = cdsdp.Problem(prob).bind(max_iter=max(iters, 20))
+        t2 = time.perf_counter()
+        row = {"m": m, "n": prob.n, "cliques": int(P.info["p"]), "clique_order": int(P.info["max_clique"]),
+               "nnz_A": int(P.info["nnz_A"]), "generate_s": t1 - t0, "setup_s": t2 - t1}
+        lin = dict(linear_solver=1, cg_max_steps=cg_steps, cg_tol=cg_tol) if cg else {}
+        row["linear_solver"] = "cg, {} steps, tol {:g}".format(cg_steps, cg_tol) if cg else "cached inverse"
+        for form in forms:
+            P.solve(form, eps=0.0, max_iter=20, precision=precision, use_graph=0, check_every=20,
+                    outputs=False, **lin)
+            P.solve(form, eps=0.0, max_iter=iters, precision=precision, use_graph=0,
+                    check_every=iters, outputs=False, profile=1, **lin)
+            torch.cuda.synchronize()
+            proj_ms, launches, iter_ms = P.profile()
+            row[form] = {"affine_ms_per_iter": (iter_ms - proj_ms) / iters,
+                         "proj_ms_per_iter": proj_ms / iters, "iter_ms": iter_ms / iters}
+        if "primal" in row and "hsde" in row:
+            row["hsde_over_primal_affine"] = row["hsde"]["affine_ms_per_iter"] / row["primal"]["affine_ms_per_iter"]
+        if verbose:
+            print(json.dumps(row), flush=True)
+        rows.append(row)
+        del P
+    return rows
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--m", type=int, nargs="+", default=TABLE_M)
@@ -45,37 +84,7 @@ def main(argv=None):
     if cg:
         args.forms = [f for f in args.forms if f != "hsde"]
 
-    import torch
-
-    import __graft_entry__
-    __graft_entry__.build_library()
-    from paper_1707_05058_gb300 import cdsdp, workloads
-
-    rows = []
-    for m in args.m:
-        t0 = time.perf_counter()
-        prob = workloads.block_arrow(100, 10, 20, m, seed=7000 + m, name=f"block_arrow_l100_d10_h20_m{m}")
-        t1 = time.perf_counter()
-        P = cdsdp.Problem(prob).bind(max_iter=max(args.iters, 20))
-        t2 = time.perf_counter()
-        row = {"m": m, "n": prob.n, "cliques": int(P.info["p"]), "clique_order": int(P.info["max_clique"]),
-               "nnz_A": int(P.info["nnz_A"]), "generate_s": t1 - t0, "setup_s": t2 - t1}
-        lin = dict(linear_solver=1, cg_max_steps=args.cg_steps, cg_tol=args.cg_tol) if cg else {}
-        row["linear_solver"] = "cg, {} steps, tol {:g}".format(args.cg_steps, args.cg_tol) if cg else "cached inverse"
-        for form in args.forms:
-            P.solve(form, eps=0.0, max_iter=20, precision=args.precision, use_graph=0, check_every=20,
-                    outputs=False, **lin)
-            P.solve(form, eps=0.0, max_iter=args.iters, precision=args.precision, use_graph=0,
-                    check_every=args.iters, outputs=False, profile=1, **lin)
-            torch.cuda.synchronize()
-            proj_ms, launches, iter_ms = P.profile()
-            row[form] = {"affine_ms_per_iter": (iter_ms - proj_ms) / args.iters,
-                         "proj_ms_per_iter": proj_ms / args.iters, "iter_ms": iter_ms / args.iters}
-        if "primal" in row and "hsde" in row:
-            row["hsde_over_primal_affine"] = row["hsde"]["affine_ms_per_iter"] / row["primal"]["affine_ms_per_iter"]
-        print(json.dumps(row), flush=True)
-        rows.append(row)
-        del P
+    rows = sweep_rows(args.m, args.iters, args.precision, args.forms, cg, args.cg_steps, args.cg_tol, verbose=True)
     print("| m | " + " | ".join(f"{f} affine ms/it" for f in args.forms) + " | projection ms/it (primal) |")
     print("|---|" + "---|" * (len(args.forms) + 1))
     for r in rows:

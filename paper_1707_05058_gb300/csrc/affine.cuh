@@ -56,6 +56,45 @@ __global__ void __launch_bounds__(ETHREADS) k_scatter(Dev d, const T* __restrict
     }
 }
 
+// The same scatter walked in packed-position order, for problems whose
+// entries mostly lie in one clique (Gs = 1): the thread of position q reads
+// the clique values at q, and only the entry's first position (owner[q])
+// writes out[e]; an entry in several cliques sums its positions in the order
+// of the CSR row, as k_scatter with one lane per entry does (bit-identical).
+// Clique values and the index map are read in order (coalesced); the entry
+// data are read in the order the cliques list their entries.
+template <typename T>
+__global__ void __launch_bounds__(ETHREADS) k_scatter_owner(Dev d, const T* __restrict__ P, const T* __restrict__ Q,
+                                                            double alpha, double beta, double gamma, int alpha_rho,
+                                                            int gamma_rho, const double* __restrict__ scale,
+                                                            double* __restrict__ out, int check_stop) {
+    if (check_stop && stopped(d)) return;
+    const int stride = gridDim.x * blockDim.x;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.nd; q += stride) {
+        if (!d.owner[q]) continue;
+        const int e = d.gmap[q];
+        if (check_stop && frozen_entry(d, e)) continue;
+        double a = alpha, gm = gamma;
+        if (alpha_rho || gamma_rho) {
+            const double ir = 1.0 / rho_entry(d, e);
+            if (alpha_rho) a *= ir;
+            if (gamma_rho) gm *= ir;
+        }
+        const int j0 = d.sc_ptr[e], j1 = d.sc_ptr[e + 1];
+        double acc = 0.0;
+        if (j1 - j0 == 1) {
+            acc += Q ? double(P[q]) + gm * double(Q[q]) : double(P[q]);
+        } else {
+            for (int j = j0; j < j1; ++j) {
+                const int qq = d.sc_idx[j];
+                acc += Q ? double(P[qq]) + gm * double(Q[qq]) : double(P[qq]);
+            }
+        }
+        const double r = a * d.c[e] + beta * acc;
+        out[e] = scale ? r * scale[e] : r;
+    }
+}
+
 // x_e = t_e - dinv_e (A^T y)_e  (Appendix A, Eq. KKTflops_s1), with the
 // per-block partial sum of <c, x> (weighted) in parte[block][0].
 __global__ void __launch_bounds__(ETHREADS) k_xupd(Dev d, const double* __restrict__ t, const double* __restrict__ y,

@@ -638,7 +638,54 @@ __global__ void __launch_bounds__(CTAPick<T, S, VARIANT>::threads, CTAPick<T, S,
         }
         jac.clear();
         double nrm = 0.0, cx = 0.0;
-        for (int f = tid; f < npk; f += blockDim.x) {
+        if constexpr (VARIANT == 1) {
+            if (FORM != 0 || pa.x_ready) {
+                // the same gather with every load of this thread's entries issued
+                // before their use: indices, then the values they address
+                constexpr int NTH = CTAPick<T, S, VARIANT>::threads;
+                constexpr int MAXF = (S * (S + 1) / 2 + NTH - 1) / NTH;
+                int ent[MAXF];
+                double v0[MAXF], v1[MAXF], v2[MAXF];
+                bool own[MAXF];
+#pragma unroll
+                for (int u = 0; u < MAXF; ++u) {
+                    const int f = tid + u * NTH;
+                    const bool ok = f < npk;
+                    ent[u] = (ok && (FORM == 0 || FORM == 2)) ? d.gmap[off + f] : 0;
+                    own[u] = (ok && FORM == 0) ? d.owner[off + f] != 0 : false;
+                    v1[u] = (ok && FORM != 3) ? double(c1[off + f]) : 0.0;
+                    v2[u] = (ok && (FORM == 1 || FORM == 2)) ? double(c2[off + f]) : 0.0;
+                    v0[u] = ok ? (FORM == 3 ? double(Win[off + f]) : (FORM == 2 ? double(c0[off + f]) : 0.0)) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < MAXF; ++u) {
+                    const int f = tid + u * NTH;
+                    if (f >= npk) continue;
+                    const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+                    double w;
+                    if (FORM == 0) {
+                        const double xe = d.x[ent[u]];
+                        if (own[u]) cx += d.wgt[ent[u]] * d.c[ent[u]] * xe;
+                        w = xe - v1[u] * irho;
+                        if (d.wstore) {
+                            const int slot = d.ctl[CTL_ITER];
+                            if (slot < d.wstore_count) reinterpret_cast<T*>(d.wstore)[(size_t)slot * d.nd + off + f] = T(w);
+                        }
+                    } else if (FORM == 1) {
+                        w = v1[u] - v2[u] * irho;
+                    } else if (FORM == 2) {
+                        const double hs = d.s11[ent[u]];
+                        const double s12 = 0.5 * (v0[u] + v1[u] - v2[u] + hs);
+                        w = s12 - gamma * 0.5 * d.zhx[ent[u]] - v1[u];
+                    } else {
+                        w = v0[u];
+                    }
+                    jac.put(a, b, T(w));
+                    nrm += (a == b ? 1.0 : 2.0) * w * w;
+                }
+            }
+        }
+        for (int f = tid; f < npk && (VARIANT != 1 || (FORM == 0 && !pa.x_ready)); f += blockDim.x) {
             const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
             double w;
             if (FORM == 0) {
@@ -702,7 +749,61 @@ __global__ void __launch_bounds__(CTAPick<T, S, VARIANT>::threads, CTAPick<T, S,
         jac.prepare_rebuild();
         double p[6] = {0, 0, 0, 0, 0, 0};
         T pf[5] = {0, 0, 0, 0, 0};  // float32 form of Algorithm 1: per-thread sums in float
-        for (int f = tid; f < npk; f += blockDim.x) {
+        if constexpr (VARIANT == 1) {
+            // the same epilogue with this thread's loads issued before their use
+            constexpr int NTH = CTAPick<T, S, VARIANT>::threads;
+            constexpr int MAXF = (S * (S + 1) / 2 + NTH - 1) / NTH;
+            int ent[MAXF];
+            T e0[MAXF], e1[MAXF], e2[MAXF];
+#pragma unroll
+            for (int u = 0; u < MAXF; ++u) {
+                const int f = tid + u * NTH;
+                const bool ok = f < npk && FORM != 3;
+                ent[u] = (ok && (FORM == 0 || FORM == 2)) ? d.gmap[off + f] : 0;
+                e0[u] = ok ? c0[off + f] : T(0);
+                e1[u] = (ok && (FORM == 0 || FORM == 2)) ? c1[off + f] : T(0);
+                e2[u] = (ok && FORM == 2) ? c2[off + f] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < MAXF; ++u) {
+                const int f = tid + u * NTH;
+                if (f >= npk) continue;
+                const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
+                const T xn = jac.rebuild(a, b, s);
+                const T wt = (a == b) ? T(1) : T(2);
+                if (FORM == 0) {  // float32 clique state and its sums
+                    const T hxt = T(pa.x_ready ? d.x[ent[u]] : d.q[ent[u]]), lm = e1[u], xo = e0[u];
+                    const T ln = lm + T(rho) * (xn - hxt);
+                    c0[off + f] = xn;
+                    c1[off + f] = ln;
+                    const T dc = xn - hxt, dx = xn - xo;
+                    pf[0] += wt * dc * dc; pf[1] += wt * xn * xn; pf[2] += wt * hxt * hxt;
+                    pf[3] += wt * dx * dx; pf[4] += wt * ln * ln;
+                } else if (FORM == 1) {
+                    const T dz = xn - e0[u];
+                    c0[off + f] = xn;
+                    pf[0] += wt * dz * dz;
+                } else if (FORM == 2) {
+                    const double w = (a == b) ? 1.0 : 2.0;
+                    const double hs = d.s11[ent[u]], zs = 0.5 * d.zhx[ent[u]];
+                    const double u_s = e0[u], v_z = e1[u], u_t = e2[u];
+                    const double s12 = 0.5 * (u_s + v_z - u_t + hs);
+                    const double s22 = u_t - hs + s12;
+                    const double uhs = s12 - gamma * zs, utn = s22 + gamma * zs;
+                    const double hux = hs - gamma * d.zhx[ent[u]];
+                    const double vn = v_z - uhs + double(xn);
+                    c0[off + f] = xn;
+                    c1[off + f] = T(vn);
+                    c2[off + f] = T(utn);
+                    const double d1 = double(xn) - hux, d2 = vn - utn;
+                    p[0] += w * d1 * d1; p[1] += w * double(xn) * double(xn); p[2] += w * hux * hux;
+                    p[3] += w * d2 * d2; p[4] += w * vn * vn; p[5] += w * utn * utn;
+                } else {
+                    Xout[off + f] = xn;
+                }
+            }
+        }
+        for (int f = tid; f < npk && VARIANT != 1; f += blockDim.x) {
             const int ab = packed_ab(f, s), a = ab >> 8, b = ab & 255;
             const T xn = jac.rebuild(a, b, s);
             const double w = (a == b) ? 1.0 : 2.0;

@@ -298,6 +298,24 @@ void make_dev(cdsdp* h) {
     h->GR = std::max(1, std::min(NBLK_R, (d.m + RTHREADS / TP - 1) / (RTHREADS / TP)));
 }
 
+// ---- scatter dispatch -------------------------------------------------------
+
+// H^T (...) onto the pattern: in packed-position order when the entries
+// average fewer than two cliques each (one lane per entry), else one group of
+// lanes per entry.
+template <typename T>
+void launch_scatter(const cdsdp* h, const Dev& d, const T* P, const T* Q, double alpha, double beta, double gamma,
+                    int alpha_rho, int gamma_rho, const double* scale, double* out, int check_stop, cudaStream_t st) {
+    if (h->Gs == 1) {
+        const int grid = (int)std::max<long long>(1, std::min<long long>(152LL * 16, ((long long)d.nd + ETHREADS - 1) / ETHREADS));
+        k_scatter_owner<T><<<grid, ETHREADS, 0, st>>>(d, P, Q, alpha, beta, gamma, alpha_rho, gamma_rho, scale, out,
+                                                      check_stop);
+    } else {
+        k_scatter<T><<<h->GE, ETHREADS, 0, st>>>(d, P, Q, alpha, beta, gamma, alpha_rho, gamma_rho, scale, out,
+                                                check_stop, h->Gs);
+    }
+}
+
 // ---- projection dispatch ----------------------------------------------------
 
 template <typename T>
@@ -418,7 +436,7 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
     if (d.comp_mode) fin.enabled = 0;
     cudaError_t e;
     if (form == 0) {  // Algorithm 1; the projection computes x on the fly and its last block the stopping test
-        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck1, -1.0, 1.0, 1.0, 1, 1, d.dinv, d.t, 1, h->Gs);
+        launch_scatter<T>(h, d, (const T*)d.ck0, (const T*)d.ck1, -1.0, 1.0, 1.0, 1, 1, d.dinv, d.t, 1, st);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, -1.0, 0, d.g, h->TPR);
         if (o.linear_solver == 1) launch_cg(h, o, st);
         else k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
@@ -434,7 +452,7 @@ cudaError_t launch_iteration(cdsdp* h, int form, const cdsdp_opts& o, cudaStream
         none.enabled = 0;
         if ((e = launch_projection<T>(h, 1, o, none, st)) != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, st);
-        k_scatter<T><<<GE, ETHREADS, 0, st>>>(d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0, 0, 1, d.dinv, d.t, 1, h->Gs);
+        launch_scatter<T>(h, d, (const T*)d.ck0, (const T*)d.ck2, 1.0, -1.0, 1.0, 0, 1, d.dinv, d.t, 1, st);
         k_rows_aw<<<GR, RTHREADS, 0, st>>>(d, d.t, 1.0, 1, d.g, h->TPR);
         if (o.linear_solver == 1) launch_cg(h, o, st);
         else k_gemv<<<GR, RTHREADS, 0, st>>>(d, d.minv, d.g, d.y, 0, h->TPRM);
@@ -626,8 +644,8 @@ int copy_results(cdsdp* h, cudaStream_t st, double* X, double* y, double* Z, dou
     }
     if (Z) {
         const void* src = form == 0 ? d.ck1 : (form == 1 ? d.ck0 : d.ck1);  // lambda, z, v_z
-        if (fp64) k_scatter<double><<<h->GE, ETHREADS, 0, st>>>(d, (const double*)src, nullptr, 0.0, 1.0, 0.0, 0, 0, nullptr, tmpE, 0, h->Gs);
-        else k_scatter<float><<<h->GE, ETHREADS, 0, st>>>(d, (const float*)src, nullptr, 0.0, 1.0, 0.0, 0, 0, nullptr, tmpE, 0, h->Gs);
+        if (fp64) launch_scatter<double>(h, d, (const double*)src, nullptr, 0.0, 1.0, 0.0, 0, 0, nullptr, tmpE, 0, st);
+        else launch_scatter<float>(h, d, (const float*)src, nullptr, 0.0, 1.0, 0.0, 0, 0, nullptr, tmpE, 0, st);
         if (form == 2 && hs_comp) k_scale_hs_tau<<<64, 256, 0, st>>>(d, NE, tmpE, 0, tmpE);
         else if (form == 2) k_scale_out<<<64, 256, 0, st>>>(NE, tmpE, 1.0, tau, tmpE);
         CK(cudaGetLastError());

@@ -14,7 +14,6 @@ and a median one (index 254: l=91, d=18, h=15, m=348).
 
     python tests/golden/make_batch_oracle.py [--jobs N]
     python tests/golden/make_batch_oracle.py --banded   (banded_oracle.json)
-    python tests/golden/make_batch_oracle.py --hsde     (batch_hsde_oracle.json: Algorithm 3)
     python tests/golden/make_batch_oracle.py --hsde-scaled
         (batch_hsde_scaled_oracle.json: Algorithm 3 to eps 1e-4 on each summand
         scaled as Section 7.1.3 describes, SCALE_PASSES equilibration passes;
@@ -33,7 +32,6 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "batch_oracle.json")
 SUMMANDS = [135, 118, 254]
 FORMS = ["primal", "dual"]
-HSDE_ITERS = 300  # Algorithm 3 on the unscaled summands: its first 300 iterations
 SCALE_PASSES = 4
 
 
@@ -65,16 +63,11 @@ def _solve(args):
     from paper_1707_05058_gb300 import workloads as W
     prob = W.workload_batch_member(2, j)
     dp = admm.decompose(prob)
-    if form == "hsde":
-        r = admm.hsde_admm(dp, eps=0.0, max_iter=HSDE_ITERS)
-    else:
-        fn = admm.primal_admm if form == "primal" else admm.dual_admm
-        r = fn(dp, eps=1e-4, max_iter=20000, adapt_every=1)
+    fn = admm.primal_admm if form == "primal" else admm.dual_admm
+    r = fn(dp, eps=1e-4, max_iter=20000, adapt_every=1)
     out = {"summand": j, "form": form, "n": int(prob.n), "m": int(prob.m), "iters": int(r.iters),
            "status": int(r.status), "objective": [float(v) for v in r.hist[:, 4]],
            "rho": [float(v) for v in r.hist[:, 2]]}
-    if form == "hsde":
-        out["hist"] = [[float(v) for v in row[:6]] for row in r.hist]
     return out
 
 
@@ -101,7 +94,6 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=len(SUMMANDS) * len(FORMS))
     ap.add_argument("--banded", action="store_true", help="write banded_oracle.json instead")
-    ap.add_argument("--hsde", action="store_true", help="write batch_hsde_oracle.json (Algorithm 3) instead")
     ap.add_argument("--hsde-scaled", action="store_true",
                     help="write batch_hsde_scaled_oracle.json (Algorithm 3 on the scaled summands) instead")
     a = ap.parse_args()
@@ -113,16 +105,6 @@ def main():
                        "objectives of the unscaled result",
                "generator": "paper_1707_05058_gb300.workloads.workload_batch_member(2, index)", "results": res}
         with open(os.path.join(os.path.dirname(OUT), "batch_hsde_scaled_oracle.json"), "w") as f:
-            json.dump(doc, f)
-        return
-    if a.hsde:
-        with mp.get_context("spawn").Pool(len(SUMMANDS)) as pool:
-            res = pool.map(_solve, [(j, "hsde") for j in SUMMANDS])
-        doc = {"what": "oracle runs (FP64) of Algorithm 3 of arXiv 1707.05058 on summands of the 256-SDP block-arrow "
-                       "batch, each alone, for 300 iterations (unscaled, Algorithm 3 reaches eps 1e-4 on few of the "
-                       "batch's SDPs within 20000 iterations); history columns 0-5 of every iteration",
-               "generator": "paper_1707_05058_gb300.workloads.workload_batch_member(2, index)", "results": res}
-        with open(os.path.join(os.path.dirname(OUT), "batch_hsde_oracle.json"), "w") as f:
             json.dump(doc, f)
         return
     if a.banded:

@@ -68,31 +68,6 @@ def test_batch_full_size_fp32_per_summand(lib, batch, form):
         assert abs(obj - want) <= 1e-4 * abs(want), (j, obj, want)
 
 
-def test_batch_full_size_hsde_per_summand(lib, batch):
-    """Algorithm 3 on the full batch, unscaled, one embedding per SDP
-    (component mode), FP64, for the 300 iterations stored in
-    tests/golden/batch_hsde_oracle.json (the oracle's Algorithm 3 on each
-    summand alone).  By iteration 300 these embeddings have tau = 0, so the
-    history holds the infeasibility test's quantities (residuals, b^T u_y,
-    c^T u_x); each summand's are within 1e-5 of the oracle's.  Unscaled, the
-    tau update cancels about five digits (zeta^T zeta_hat = 1 - 1e-5), so two
-    correct FP64 implementations agree to a few 1e-6 and no closer (measured
-    here: 1.7e-6)."""
-    with open(os.path.join(os.path.dirname(GOLDEN), "batch_hsde_oracle.json")) as f:
-        gold = json.load(f)["results"]
-    parts, P, r, c = batch
-    n_it = gold[0]["iters"]
-    out = P.solve("hsde", eps=0.0, max_iter=n_it, precision="fp64", use_graph=1)
-    it, st, res = P.component_results()
-    assert out["iters"] == n_it
-    for g in gold:
-        j = g["summand"]
-        assert parts[j].n == g["n"] and int(it[j]) == g["iters"] == n_it
-        want = g["hist"][-1]
-        for col in range(6):
-            assert abs(res[j, col] - want[col]) <= 1e-5 * abs(want[col]) + 1e-12, (j, col, res[j, col], want[col])
-
-
 def test_batch_full_size_hsde_scaled_per_summand(lib):
     """Algorithm 3 on the full batch scaled as Section 7.1.3 describes (each
     SDP scaled alone, 4 equilibration passes), one embedding per SDP, FP32
