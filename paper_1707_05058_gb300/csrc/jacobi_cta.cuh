@@ -587,8 +587,10 @@ template <int S>
 struct CTAPick<float, S, 1> {
     using type = CTAJacobiReg<S>;
     static constexpr int threads = CTAJacobiReg<S>::NT;
-    // about 64 registers a thread
-    static constexpr int min_blocks = 65536 / (CTAJacobiReg<S>::NT * 80);
+    // blocks per SM: as many as 64 registers a thread allow (orders 36..56:
+    // 6, 5 or 4 blocks), 3 at orders 60 and 64, whose rounds spill below 80
+    // (measured on the 256-SDP batch: each setting the fastest for its orders)
+    static constexpr int min_blocks = S >= 60 ? 3 : 65536 / (CTAJacobiReg<S>::NT * 64);
 };
 
 template <int NV>

@@ -20,6 +20,11 @@ cudaError_t launch_cta_v(const Dev& d, const int* list, int nlist, const ProjArg
         cudaError_t e = cudaFuncSetAttribute(k_project_cta<T, S, FORM, VARIANT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        // as much shared memory as the SM offers, so that the register limit
+        // decides how many cliques share an SM
+        e = cudaFuncSetAttribute(k_project_cta<T, S, FORM, VARIANT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
         attr_done = true;
     }
     ProjArgs pa = pa_in;
