@@ -70,9 +70,12 @@ CPU_SAMPLE = list(range(0, 256, 32))
 # iterations of the profiled solve behind the per-class launch times
 PROFILE_ITERS = 200
 CPU_ITERS = 4
-# DRAM bytes of one launch of the roofline's kernel from the ncu capture
-# summarised under profiles/ (None until a capture of the current kernel exists)
-KERNEL_TRAFFIC_BYTES = None
+# DRAM bytes of one launch of the roofline's kernel (padded order 52, 1667
+# cliques): the ncu capture summarised in profiles/k_project_cta52_batched128_fp32.md
+# read 44.18 MB for 812 cliques of the class (the clique state, the gathered x
+# and the eigenvector cache; no re-reads), scaled by the clique count.  Set to
+# None when the kernel changes until it is captured again.
+KERNEL_TRAFFIC_BYTES = 44.18e6 * 1667 / 812
 
 
 def _clock_sampler(dev_index):
