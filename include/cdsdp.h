@@ -116,6 +116,9 @@ typedef struct {
                               two barriers per Jacobi round; 1 = eigenvectors in
                               registers, one barrier per round (default).  Same
                               rotations and results up to rounding order.            */
+    int row_threads;       /* threads per constraint row of the sparse A-row products
+                              (A W v): 0 = from the average row length (default), or
+                              32, 64, 128, 256.                                       */
 } cdsdp_opts;
 
 typedef struct {
@@ -414,8 +417,10 @@ int cdsdp_fma_peak(int precision, int iters, void* stream, double* tflops);
  *   proj_streams    4 or 1
  *   proj_cta_kernel 0 or 1 (one more candidate: the fastest of the above with
  *                   the other value)
+ *   row_threads     64, 128, 256 (three more candidates: the fastest of the
+ *                   above with each value)
  * ms_per_iter[] receives each candidate's device time per iteration in
- * candidate order (at most 25 entries; may be NULL), *n_cand their number (may
+ * candidate order (at most 28 entries; may be NULL), *n_cand their number (may
  * be NULL).  Overwrites the last solve's state.  Errors as cdsdp_solve. */
 int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* stream, cdsdp_opts* tuned,
                    double* ms_per_iter, int* n_cand);

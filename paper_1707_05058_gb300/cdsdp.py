@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("component_stop", ctypes.c_int), ("adaptive_rho", ctypes.c_int), ("rho_mu", ctypes.c_double),
                 ("rho_nu", ctypes.c_double), ("x_update", ctypes.c_int), ("proj_warps_div", ctypes.c_int),
                 ("linear_solver", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_max_steps", ctypes.c_int),
-                ("proj_streams", ctypes.c_int), ("proj_cta_kernel", ctypes.c_int)]
+                ("proj_streams", ctypes.c_int), ("proj_cta_kernel", ctypes.c_int),
+                ("row_threads", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -413,14 +414,15 @@ class Problem:
         if self.workspace is None or self.max_iter < iters:
             self.bind(max(iters, self.max_iter or 0))
         tuned = Opts()
-        ms = np.zeros(25)
+        ms = np.zeros(28)
         n = ctypes.c_int(0)
         st = _lib.cdsdp_autotune(self._h, FORMS.get(form, form), ctypes.byref(o), int(iters), _stream_ptr(stream),
                                  ctypes.byref(tuned), _ptr(ms, ctypes.c_double), ctypes.byref(n))
         if st < 0:
             raise CdsdpError(st, "cdsdp_autotune")
         return ({"x_update": tuned.x_update, "proj_warps_div": tuned.proj_warps_div, "warm_start": tuned.warm_start,
-                 "proj_streams": tuned.proj_streams, "proj_cta_kernel": tuned.proj_cta_kernel},
+                 "proj_streams": tuned.proj_streams, "proj_cta_kernel": tuned.proj_cta_kernel,
+                 "row_threads": tuned.row_threads},
                 ms[:n.value].tolist())
 
     def profile(self):

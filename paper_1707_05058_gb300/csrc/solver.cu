@@ -63,6 +63,7 @@ struct cdsdp {
     // per entry for scatters (Gs) and A^T rows (Ga), threads per A row (TPR)
     // and per row of the cached inverse (TPRM)
     int GE = 1, GR = 1, Gs = 1, Ga = 1, Gx = 1, TPR = 32, TPRM = 32;
+    int TPR_auto = 32;  // TPR from the row lengths (opts.row_threads = 0)
     // Algorithm 1: compute x = t - D^-1 A^T y in its own kernel (coalesced
     // A^T rows) rather than inside the projection's gather (the default)
     bool x_split_auto = false;
@@ -284,14 +285,16 @@ void make_dev(cdsdp* h) {
     h->Gs = pow2_clamp(avg_sc / 2.0, 1, 32);
     h->Ga = pow2_clamp(std::max(avg_at, avg_sc) / 3.0, 1, 32);
     h->Gx = pow2_clamp(avg_at / 6.0, 1, 32);  // lanes per A^T row in the separate x-update
-    h->TPR = pow2_clamp(avg_a / 4.0, 32, RTHREADS);
+    h->TPR = h->TPR_auto = pow2_clamp(avg_a / 4.0, 32, RTHREADS);
     // The separate kernel forms each x_e once (in float64, whose throughput is
     // low on this GPU); inside the gather it is formed once per clique holding e.
     h->x_split_auto = true;
     h->x_split = h->x_split_auto;
     int max_mc = 0;
     for (int c = 0; c < hp.ncomp; ++c) max_mc = std::max(max_mc, hp.crow_ptr[c + 1] - hp.crow_ptr[c]);
-    h->TPRM = hp.diag_factor ? 32 : pow2_clamp(max_mc / 4.0, 32, RTHREADS);
+    // threads per row of the cached inverse: about 16 entries a thread (rows of
+    // a few hundred entries take one warp, reduced without a barrier)
+    h->TPRM = hp.diag_factor ? 32 : pow2_clamp(max_mc / 16.0, 32, RTHREADS);
     const int G = std::max(h->Gs, h->Ga);
     h->GE = std::max(1, std::min(NBLK_E, (int)(((long long)d.NE * G + ETHREADS - 1) / ETHREADS)));
     const int TP = std::max(h->TPR, h->TPRM);
@@ -492,7 +495,8 @@ bool same_opts(const cdsdp_opts& a, const cdsdp_opts& b) {
            a.component_stop == b.component_stop && a.adaptive_rho == b.adaptive_rho && a.rho_mu == b.rho_mu &&
            a.rho_nu == b.rho_nu && a.x_update == b.x_update && a.proj_warps_div == b.proj_warps_div &&
            a.linear_solver == b.linear_solver && a.cg_tol == b.cg_tol && a.cg_max_steps == b.cg_max_steps &&
-           a.proj_streams == b.proj_streams && a.proj_cta_kernel == b.proj_cta_kernel;
+           a.proj_streams == b.proj_streams && a.proj_cta_kernel == b.proj_cta_kernel &&
+           a.row_threads == b.row_threads;
 }
 
 void drop_graph(cdsdp* h) {
@@ -549,6 +553,9 @@ int check_opts(const cdsdp* h, const cdsdp_opts& o) {
         return CDSDP_ERR_ARG;
     if (o.proj_streams < 1 || o.proj_streams > 4) return CDSDP_ERR_ARG;
     if (o.proj_cta_kernel != 0 && o.proj_cta_kernel != 1) return CDSDP_ERR_ARG;
+    if (o.row_threads != 0 && o.row_threads != 32 && o.row_threads != 64 && o.row_threads != 128 &&
+        o.row_threads != 256)
+        return CDSDP_ERR_ARG;
     if (o.precision == CDSDP_FP64 && h->hp.max_clique > kMaxOrderF64) return CDSDP_ERR_UNSUPPORTED;
     return CDSDP_SOLVED;
 }
@@ -763,6 +770,7 @@ void cdsdp_default_opts(cdsdp_opts* o) {
     o->cg_max_steps = 5;
     o->proj_streams = 4;
     o->proj_cta_kernel = 1;
+    o->row_threads = 0;
 }
 
 namespace {
@@ -1141,6 +1149,12 @@ int cdsdp_solve(cdsdp* h, int form, const cdsdp_opts* opts, void* stream, double
     if (form == 2 && (rc = ensure_hsde(h, st)) != CDSDP_SOLVED) return rc;
     Dev& d = h->dev;
     d.max_iter = o.max_iter;
+    // threads per constraint row of the A-row kernels, and the row grid
+    h->TPR = o.row_threads ? o.row_threads : h->TPR_auto;
+    {
+        const int TP = std::max(h->TPR, h->TPRM);
+        h->GR = std::max(1, std::min(NBLK_R, (d.m + RTHREADS / TP - 1) / (RTHREADS / TP)));
+    }
     d.comp_mode = (h->hp.ncomp > 1 && o.component_stop && o.linear_solver == 0) ? 1 : 0;
     // Algorithm 3: one embedding per component in component mode, else one over the whole problem
     const bool hs_comp = form == 2 && d.comp_mode;
@@ -1302,11 +1316,18 @@ int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* 
     CK(cudaEventCreate(&e1));
     double best = 1e300;
     int ibest = 0, rc = CDSDP_SOLVED;
+    // then, from the fastest so far: the other thread-block projection kernel,
+    // and 64, 128 and 256 threads per constraint row
     const size_t n_grid = cand.size();
-    for (size_t i = 0; i <= n_grid && rc >= 0; ++i) {
-        if (i == n_grid) {  // the fastest so far with the other thread-block projection kernel
+    const int rt[3] = {64, 128, 256};
+    for (size_t i = 0; i < n_grid + 4 && rc >= 0; ++i) {
+        if (i == n_grid) {
             cdsdp_opts o = cand[ibest];
             o.proj_cta_kernel = 1 - o.proj_cta_kernel;
+            cand.push_back(o);
+        } else if (i > n_grid) {
+            cdsdp_opts o = cand[ibest];
+            o.row_threads = rt[i - n_grid - 1];
             cand.push_back(o);
         }
         rc = cdsdp_solve(h, form, &cand[i], stream, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);  // warm-up
@@ -1332,6 +1353,7 @@ int cdsdp_autotune(cdsdp* h, int form, const cdsdp_opts* opts, int iters, void* 
     tuned->warm_start = cand[ibest].warm_start;
     tuned->proj_streams = cand[ibest].proj_streams;
     tuned->proj_cta_kernel = cand[ibest].proj_cta_kernel;
+    tuned->row_threads = cand[ibest].row_threads;
     if (n_cand) *n_cand = (int)cand.size();
     return CDSDP_SOLVED;
 }

@@ -463,6 +463,23 @@ def test_projection_warps_per_block_fp64(lib, torch_cuda, div):
     np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-8, atol=1e-10)
 
 
+@pytest.mark.parametrize("row_threads", [32, 64, 256])
+@pytest.mark.parametrize("form", ["primal", "dual", "hsde"])
+def test_row_threads_fp64(lib, torch_cuda, form, row_threads):
+    """Threads per constraint row of the A-row kernels (opts.row_threads): the
+    first 30 FP64 iterates equal the oracle's whatever the split (HSDE on the
+    normalised instance, see test_hsde_fp64_block_arrow_unscaled)."""
+    prob = W.workload(0)
+    if form == "hsde":
+        prob = _normalised(prob)
+    dp = admm.decompose(prob)
+    fn = {"primal": admm.primal_admm, "dual": admm.dual_admm, "hsde": admm.hsde_admm}[form]
+    ref = fn(dp, eps=0.0, max_iter=30)
+    P = lib.Problem(prob).bind(max_iter=30)
+    out = P.solve(form, eps=0.0, max_iter=30, precision="fp64", row_threads=row_threads)
+    np.testing.assert_allclose(out["hist"][:, :6], ref.hist[:, :6], rtol=1e-8, atol=1e-10)
+
+
 @pytest.mark.parametrize("form", ["primal", "dual"])
 def test_autotune_picks_a_candidate_and_keeps_parity(lib, torch_cuda, form):
     """The schedule autotuner times its candidates and returns one of them;
@@ -471,8 +488,9 @@ def test_autotune_picks_a_candidate_and_keeps_parity(lib, torch_cuda, form):
     dp, ref = _oracle(prob, form, 1e-4, 2000)
     P = lib.Problem(prob).bind(max_iter=2000)
     tuned, ms = P.autotune(form, iters=20, precision="fp64")
-    assert len(ms) == (25 if form == "primal" else 13) and all(m > 0 for m in ms)
+    assert len(ms) == (28 if form == "primal" else 16) and all(m > 0 for m in ms)
     assert tuned["x_update"] in (1, 2) and tuned["proj_warps_div"] in (1, 2, 4) and tuned["warm_start"] in (16, 64)
     assert tuned["proj_streams"] in (1, 4) and tuned["proj_cta_kernel"] in (0, 1)
+    assert tuned["row_threads"] in (0, 64, 128, 256)
     out = P.solve(form, eps=1e-4, max_iter=2000, precision="fp64", **tuned)
     _assert_trajectory(dp, ref, out)
