@@ -18,6 +18,8 @@
 // Orders 65..128 (CTAJacobi): A double-buffered as above, V single-buffered
 // and rotated in place at the round's logical column pair (L[2k], L[2k+1]),
 // L following sigma.
+// Float32 orders 36..64 can also run CTAJacobiReg (jacobi_reg.cuh: V in
+// registers, one barrier per round); k_project_cta's VARIANT selects it.
 #pragma once
 
 #include <type_traits>
@@ -587,9 +589,9 @@ template <int S>
 struct CTAPick<float, S, 1> {
     using type = CTAJacobiReg<S>;
     static constexpr int threads = CTAJacobiReg<S>::NT;
-    // blocks per SM: as many as 64 registers a thread allow (orders 36..56:
-    // 6, 5 or 4 blocks), 3 at orders 60 and 64, whose rounds spill below 80
-    // (measured on the 256-SDP batch: each setting the fastest for its orders)
+    // blocks per SM: as many as 64 registers a thread allow at orders 36..56
+    // (6, 5 or 4 blocks); 3 at orders 60 and 64, which spill at 64 registers
+    // and ran slower with 4 (measured on the 256-SDP batch)
     static constexpr int min_blocks = S >= 60 ? 3 : 65536 / (CTAJacobiReg<S>::NT * 64);
 };
 
