@@ -46,7 +46,7 @@ reductions).
             SDPs, 4 iterations each, on 1 host thread and on one process per
             SDP
 
---impl reference runs the FP64 oracle (the CPU reference of this build) on
+--impl reference runs the FP64 oracle (the CPU reference implementation) on
 the same workload and metric (bounded samples; see run_reference).
 """
 from __future__ import annotations

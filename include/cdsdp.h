@@ -51,7 +51,7 @@ typedef enum {
     CDSDP_ERR_TIMEOUT = -5,      /* a bounded device wait gave up                 */
     CDSDP_ERR_NUMERIC = -6,      /* NaN or Inf met in the iteration               */
     CDSDP_ERR_STATE = -7,        /* call out of order (e.g. solve before bind)    */
-    CDSDP_ERR_UNSUPPORTED = -8   /* size beyond what this build handles           */
+    CDSDP_ERR_UNSUPPORTED = -8   /* size or option the library does not handle    */
 } cdsdp_status;
 
 typedef enum {

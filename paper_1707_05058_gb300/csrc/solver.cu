@@ -1436,7 +1436,7 @@ const char* cdsdp_strerror(int s) {
         case CDSDP_ERR_TIMEOUT: return "bounded device wait timed out";
         case CDSDP_ERR_NUMERIC: return "NaN or Inf in the iteration";
         case CDSDP_ERR_STATE: return "call out of order";
-        case CDSDP_ERR_UNSUPPORTED: return "size not supported by this build";
+        case CDSDP_ERR_UNSUPPORTED: return "size or option not supported by the library";
         default: return "unknown status";
     }
 }

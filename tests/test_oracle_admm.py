@@ -90,7 +90,7 @@ CLOSED = [
 @pytest.mark.parametrize("prob", CLOSED, ids=lambda p: p.name)
 def test_closed_form_optimum(prob, form):
     """lambda_max(S) of a tridiagonal Toeplitz S, theta(C_5) = sqrt(5) and the
-    MaxCut relaxation of cycles (Section 8 pins of the build)."""
+    MaxCut relaxation of cycles."""
     dp, r = admm.solve(prob, form, eps=1e-8, max_iter=20000)
     assert r.status == admm.SOLVED
     obj = float(dp.c @ r.X)
