@@ -59,7 +59,6 @@ struct CTAJacobiReg {
     static constexpr size_t bytes = ((3 * (size_t)BUF + 4 * K + 2 * K + 32 + S) * sizeof(T) + 15) & ~size_t(15);
 
     __host__ __device__ static constexpr int phys(int i) { return (i & 1) ? K + (i >> 1) : (i >> 1); }
-    __host__ __device__ static constexpr int logical(int q) { return q < K ? 2 * q : 2 * (q - K) + 1; }
     __device__ __forceinline__ static int at(int r, int c) { return phys(r) * LDA + phys(c); }
     __device__ __forceinline__ static int lower(int r, int c) { return r >= c ? at(r, c) : at(c, r); }
 
