@@ -37,6 +37,9 @@ reductions).
             summands against stored oracle solves
   affine_sweep  affine-projection cost against m (block-arrow l=100, d=10,
             h=20, m = 200 and 1000) per form, cached inverse and 5 CG steps
+  dense_sample  eight SDPs of the batch with A_i dense on the pattern (1.1e8
+            nonzeros): ms per iteration, the non-projection part's GB/s
+            against the measured HBM peak, time to 1e-4
   banded    the banded workload (n=2000, w=10, m=500; 1990 cliques of order
             11): time to 1e-4 in the FP32 graph and plain FP64 forms
   maxcut    the MaxCut workload (n = 10^4, G(n, 6/(n-1)), merged cliques up to
@@ -329,6 +332,55 @@ def _affine_sweep():
     return out
 
 
+def _dense_sample(cdsdp, workloads, torch, flush, stream):
+    """Eight SDPs of the batch (every 32nd) with every A_i dense on the
+    block-arrow pattern (the batch's shapes at full density; the whole batch
+    at that density would hold 2.2e9 nonzeros).  FP32 graph ms per
+    iteration with every SDP active; a profiled 50-iteration solve splits it
+    into the projection and the rest (scatter, A W t, cached inverse, x
+    update, stopping tests), whose algorithmic bytes (A W and A^T streamed
+    once each, 12 B a nonzero, and the cached inverse blocks once, 8 B an
+    entry) give its GB/s; one solve to eps = 1e-4 from the cold start."""
+    members = list(range(0, 256, 32))
+    t0 = time.perf_counter()
+    parts = [workloads.block_arrow_batch_member(256, 3707, j, density=None) for j in members]
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Q = cdsdp.Problem.batch(parts)
+    setup_s = time.perf_counter() - t0
+    Q.bind(max_iter=10000)
+    info = Q.info
+    KWD = dict(precision="fp32", adaptive_rho=1)
+    tuned, _ = Q.autotune("primal", iters=20, **KWD)
+    flush.fill_(1)
+    ms, out = _event_ms(torch, stream, lambda: Q.solve("primal", outputs=False, eps=0.0, max_iter=50, use_graph=1,
+                                                       **KWD, **tuned))
+    Q.solve("primal", outputs=False, eps=0.0, max_iter=50, profile=1, check_every=50, **KWD,
+            **{**tuned, "proj_streams": 1})
+    proj_ms, launches, iter_ms = Q.profile()
+    affine_ms = (iter_ms - proj_ms) / launches
+    nnz, m = int(info["nnz_A"]), int(info["m"])
+    inv_doubles = sum(int(q.m) ** 2 for q in parts)
+    bytes_affine = 2 * nnz * 12 + inv_doubles * 8
+    flush.fill_(1)
+    tms, tout = _event_ms(torch, stream, lambda: Q.solve("primal", outputs=False, eps=1e-4, max_iter=10000,
+                                                         use_graph=1, **KWD, **tuned))
+    it, st, _ = Q.component_results()
+    hbm = _peaks().get("hbm_gbs")
+    block = {"workload": "SDPs 0, 32, ..., 224 of the batch with A_i dense on the pattern", "sdps": len(parts),
+             "n": int(info["n"]), "m": m, "nnz_A": nnz, "generate_s": gen_s, "setup_s": setup_s,
+             "upload_bytes": int(info["upload_bytes"]), "schedule": tuned,
+             "fp32_graph_ms_per_iter": ms / out["iters"],
+             "profiled": {"proj_ms_per_iter": proj_ms / launches, "rest_ms_per_iter": affine_ms,
+                          "rest_algorithmic_bytes": bytes_affine,
+                          "rest_gbs": bytes_affine / (affine_ms / 1e3) / 1e9,
+                          "rest_frac_of_hbm": (bytes_affine / (affine_ms / 1e3) / 1e9) / hbm if hbm else None},
+             "time_to_eps_ms": tms, "iters_to_eps_max": int(tout["iters"]), "sdp_iters": int(it.sum()),
+             "all_solved": bool((st == 0).all())}
+    del Q
+    return block
+
+
 def _banded(cdsdp, workloads, torch, flush, stream):
     """Banded n=2000, w=10, m=500: time to eps = 1e-4 (adaptive penalty every
     iteration) in the FP32 graph form (autotuned schedule) and the plain FP64
@@ -603,6 +655,7 @@ def main():
         extras["hsde"] = _hsde_batch(cdsdp, parts, members, torch, flush, stream)
         extras["banded"] = _banded(cdsdp, workloads, torch, flush, stream)
         extras["affine_sweep"] = _affine_sweep()
+        extras["dense_sample"] = _dense_sample(cdsdp, workloads, torch, flush, stream)
         extras["maxcut"] = _maxcut(cdsdp, workloads, torch, flush, stream)
         extras["grad"] = _grad_batch(cdsdp, workloads, torch, stream)
         extras["completion"] = _completion(cdsdp, workloads, torch, stream)
